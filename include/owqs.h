@@ -1,0 +1,242 @@
+/*
+ * owqs.h -- C ABI of the GB300 one-way quantum computer simulator.
+ *
+ * Simulates one-way quantum computation (1WQC) measurement patterns with the
+ * array method of Nikahd, Houshmand, Saheb Zamani and Sedighi, "One-Way
+ * Quantum Computer Simulation" (arXiv:1604.05659): qubit elimination
+ * (Section 4.2), pattern reordering (Section 4.3), implicit simulation of
+ * actions (Section 4.4) and the probability-free EOWQS mode for patterns with
+ * generalised flow (Section 4.5).
+ *
+ * Conventions shared by every entry point
+ *   - Qubits are the labels 0 .. nqubits-1 (the set V of Section 2.2).
+ *   - Commands are listed in EXECUTION order: cmds[0] acts first.  (The paper
+ *     writes patterns right to left.)
+ *   - A vector over an ordered qubit list q[0..n-1] has 2^n complex entries and
+ *     bit k of the index is qubit q[k]; input vectors use the input list I,
+ *     output vectors the output list O.
+ *   - |+-a> = (|0> +- e^{+ia}|1>)/sqrt2.  Eq. 1 prints e^{-ia}; Eqs. 9-12 and
+ *     the derivation of Section 4.2 need e^{+ia}, which is what is used.
+ *   - Complex numbers are interleaved (re, im): float pairs for OWQS_C64,
+ *     double pairs for OWQS_C128.
+ *   - The caller owns every buffer it passes.  The library owns the pattern
+ *     handle, its compiled schedule, its device workspace and its CUDA graphs;
+ *     all of them are released by owqs_free_pattern.
+ *   - Every function returns an owqs_status; no exception crosses the ABI.
+ *     On any error other than OWQS_ERR_IMPOSSIBLE_BRANCH and
+ *     OWQS_ERR_NOT_DETERMINISTIC the caller's output buffers are left untouched.
+ *     owqs_last_error() gives a message for the calling thread.
+ *   - A handle may be used by one thread at a time.
+ */
+#ifndef OWQS_H
+#define OWQS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OWQS_ABI_VERSION 1
+
+typedef enum {
+  OWQS_OK = 0,
+  OWQS_ERR_ARG = 1,                /* bad argument (null pointer, size, enum)        */
+  OWQS_ERR_PATTERN = 2,            /* pattern breaks D0-D3 (Section 2.2)            */
+  OWQS_ERR_NOT_STANDARD = 3,       /* reordering needs the standard form CME         */
+  OWQS_ERR_IMPOSSIBLE_BRANCH = 4,  /* a forced outcome has probability below 1e-24
+                                      (C128) or 1e-12 (C64); the output is zero     */
+  OWQS_ERR_NOT_DETERMINISTIC = 5,  /* EOWQS run whose output norm is not 1          */
+  OWQS_ERR_OOM = 6,                /* live width too large for device memory        */
+  OWQS_ERR_CUDA = 7,               /* a CUDA call failed (see owqs_last_error)      */
+  OWQS_ERR_TIMEOUT = 8,            /* a device-side wait gave up                    */
+  OWQS_ERR_UNSUPPORTED = 9         /* feature not available in this build           */
+} owqs_status;
+
+/* command kinds (Section 2.2) */
+enum { OWQS_CMD_N = 0, OWQS_CMD_E = 1, OWQS_CMD_M = 2, OWQS_CMD_X = 3, OWQS_CMD_Z = 4 };
+
+/* One command.
+ *   N  q0        prepare q0 in |+>.  Non-input qubits with no N are prepared
+ *                before the first command (N commutes with commands on other
+ *                qubits, so the simulator prepares them just in time).
+ *   E  q0 q1     CZ on q0 and q1 (q0 != q1).
+ *   M  q0 angle  measure q0 at angle (-1)^s angle + t pi (Eq. 2), where s and t
+ *                are the parities of the outcomes of the qubits listed in
+ *                domain[s_off .. s_off+s_len) and domain[t_off .. t_off+t_len).
+ *   X, Z q0      Pauli on q0 when the parity of the outcomes in
+ *                domain[s_off .. s_off+s_len) is 1 (t_* ignored).            */
+typedef struct {
+  uint32_t kind;
+  uint32_t q0;
+  uint32_t q1;
+  uint32_t pad_;
+  double angle;
+  uint32_t s_off, s_len;
+  uint32_t t_off, t_len;
+} owqs_cmd;
+
+typedef struct owqs_pattern owqs_pattern;
+
+/* Load and validate a pattern P = (V, I, O, A) (Section 2.2).
+ *   nqubits        |V|; labels are 0 .. nqubits-1 (at most 1<<24)
+ *   inputs/nin     the input list I (distinct labels; bit k of psi_in is inputs[k])
+ *   outputs/nout   the output list O (distinct; bit k of psi_out is outputs[k])
+ *   cmds/ncmd      commands in execution order
+ *   domain/ndomain qubit labels referenced by the commands' signal domains
+ *   out            receives the new handle (owned by the library)
+ * Returns OWQS_ERR_PATTERN if the commands break D0 (depend on an outcome not
+ * yet measured), D1 (act on a measured qubit), D2 (act on a qubit before its
+ * N, unless it is an input) or D3 (a qubit is measured iff it is not an
+ * output), or if an E joins a qubit to itself.  Host-only; needs no GPU.   */
+owqs_status owqs_load_pattern(uint32_t nqubits, const uint32_t* inputs, uint32_t nin,
+                              const uint32_t* outputs, uint32_t nout, const owqs_cmd* cmds,
+                              size_t ncmd, const uint32_t* domain, size_t ndomain,
+                              owqs_pattern** out);
+
+void owqs_free_pattern(owqs_pattern* p);
+
+typedef struct {
+  uint32_t nqubits, nin, nout;
+  uint32_t nmeas;        /* K = |V| - |O| (Section 4.3)                     */
+  uint32_t standard;     /* 1 if the loaded order is the standard form CME  */
+  uint32_t peak_live;    /* widest live array of the ACTIVE command order   */
+  uint64_t amp_updates;  /* sum over commands of 2^(live width), active order */
+} owqs_pattern_info;
+
+/* Facts about the pattern under its active order.  Host-only. */
+owqs_status owqs_get_info(const owqs_pattern* p, owqs_pattern_info* info);
+
+/* modes (Section 4.5) */
+enum { OWQS_MODE_OWQS = 0, OWQS_MODE_EOWQS = 1 };
+
+typedef struct {
+  uint32_t mode;           /* OWQS: dependent measurements wait for their domains;
+                              EOWQS: outcomes preselected, every qubit ready   */
+  uint32_t product_input;  /* 1: every input qubit starts as its own sub-state  */
+  uint32_t sweep;          /* 1: Section 5 sweep a = |O| .. 1 with b = d = |O|,
+                              g = 0.5; 0: one run with the weights below        */
+  uint32_t use_learned;    /* 1: ask the learned proposal first; greedy judges  */
+  double alpha, beta, gamma, delta;  /* Eq. 18 weights when sweep == 0 (> 0)   */
+} owqs_reorder_opts;
+
+typedef struct {
+  uint32_t peak_m;         /* largest measurement state-space MS (Table I/III m) */
+  uint32_t peak_live;      /* widest single live array under the new order      */
+  uint64_t amp_updates;    /* amplitude updates under the new order             */
+  double alpha_used;       /* Eq. 18 a of the chosen run                        */
+  uint32_t learned_accepted; /* 1 if the learned proposal was kept              */
+  uint32_t pad_;
+} owqs_reorder_info;
+
+/* PROA (Section 4.3): greedy measurement order with the Eq. 18 cost
+ *   Cost(v) = a MS(v) + b OS(v) - g SS(v)            (v next to a selected qubit)
+ *           = a (MS(v)+1) d + b OS(v) - g SS(v)      (otherwise)
+ * MS: size of the sub-state measuring v creates (v's sub-state joined with
+ * those of its neighbours over E commands not yet applied); OS: output
+ * neighbours; SS: qubits whose domains contain v (0 in EOWQS); ties go to the
+ * lowest label.  The pattern must be in standard form.  On success the new
+ * order becomes the active order: for each chosen v, its pending E commands
+ * then M_v (Eq. 17); then the remaining E commands and the corrections.
+ *   order   optional, K entries: the measurement order (qubit labels)
+ *   info    optional
+ * Host-only; needs no GPU.                                                  */
+owqs_status owqs_reorder(owqs_pattern* p, const owqs_reorder_opts* opts,
+                         owqs_reorder_info* info, uint32_t* order);
+
+/* Make `order` (K measured qubits, each once, dependencies first) the active
+ * measurement order, built as in owqs_reorder.  Standard form required.    */
+owqs_status owqs_set_order(owqs_pattern* p, const uint32_t* order, uint32_t k);
+
+/* Restore the command order given to owqs_load_pattern. */
+owqs_status owqs_reset_order(owqs_pattern* p);
+
+/* Active measurement order (K labels). */
+owqs_status owqs_get_order(const owqs_pattern* p, uint32_t* order);
+
+enum { OWQS_C64 = 0, OWQS_C128 = 1 };
+enum { OWQS_OUTCOME_FORCED = 0, OWQS_OUTCOME_SAMPLED = 1, OWQS_OUTCOME_ZERO = 2 };
+enum { OWQS_IO_DEVICE = 0, OWQS_IO_HOST = 1 };
+
+typedef struct {
+  uint32_t dtype;     /* OWQS_C64 (complex64 amplitudes, FP64 reductions) or OWQS_C128 */
+  uint32_t mode;      /* OWQS_MODE_OWQS or OWQS_MODE_EOWQS                            */
+  uint32_t policy;    /* forced outcomes, sampled (outcome 0 iff u <= prob_0, u from
+                         splitmix64(seed) in [0,1)), or all zero                      */
+  uint32_t io;        /* OWQS_IO_DEVICE: psi_in/psi_out are device pointers;
+                         OWQS_IO_HOST: host pointers, copies done inside the call    */
+  uint64_t seed;      /* sampled policy only                                          */
+  void* stream;       /* cudaStream_t to run on; NULL = the legacy default stream    */
+  uint32_t use_graph; /* 1: replay the pass sequence as a CUDA graph (forced/zero)   */
+  uint32_t pad_;
+} owqs_run_opts;
+
+/* Simulate the pattern under its active order and return the output state.
+ *   psi_in    2^|I| amplitudes (bit k = inputs[k]); NULL = |+> on every input
+ *             (generated on the device, nothing is read).  OWQS mode divides
+ *             by the input norm; EOWQS uses the vector as given.
+ *   psi_out   2^|O| amplitudes (bit k = outputs[k]), the normalised branch
+ *             state M_s ... E N psi_in / sqrt(prob) followed by the corrections
+ *             (OWQS); in EOWQS every prob is taken as 1/2 (Section 4.5).
+ *   outcomes  host, K bytes in the order of the M commands as loaded; read for
+ *             the forced policy, written otherwise.  May be NULL for the zero
+ *             policy.
+ *   probs     host, K doubles or NULL: the probability of each recorded
+ *             outcome given the earlier ones (Eq. 13); 0.5 in EOWQS.
+ * Returns after the device work has finished.  In EOWQS mode the output
+ * norm is checked against 1 (tolerance 1e-10 C128, 1e-4 C64):
+ * OWQS_ERR_NOT_DETERMINISTIC otherwise (a necessary check, not a gflow proof). */
+owqs_status owqs_run(owqs_pattern* p, const owqs_run_opts* opts, const void* psi_in,
+                     void* psi_out, uint8_t* outcomes, double* probs);
+
+/* Per-kernel timing of one run (instrumentation).  Runs the same schedule
+ * without a graph, with a CUDA event pair around every launch on opts->stream,
+ * and fills ms[i] (i < *nlaunch, at most cap) with each launch's duration,
+ * bytes[i] with its algorithmic bytes (amplitudes read + written) and kind[i]
+ * with 0 = fast pass kernel, 1 = generic pass kernel, 2 = final kernel,
+ * 3 = norm kernel.  Device IO only; the forced or zero policy.             */
+owqs_status owqs_profile_run(owqs_pattern* p, const owqs_run_opts* opts, const void* psi_in,
+                             void* psi_out, const uint8_t* outcomes, float* ms, double* bytes,
+                             uint32_t* kind, uint32_t cap, uint32_t* nlaunch);
+
+/* Bit position of every qubit in the live array after pass `pass` of the
+ * active order (-1 if the qubit is not live), for pass = 0 .. K (pass K is
+ * the state before the final corrections).  The array grows by appending a
+ * new qubit as the top bit; eliminating a qubit shifts the higher bits down.
+ * Host-only. bit_of_qubit has nqubits entries.                             */
+owqs_status owqs_get_index_map(const owqs_pattern* p, uint32_t pass, int32_t* bit_of_qubit);
+
+/* Description of one compiled device pass (for host-logic tests). */
+typedef struct {
+  int32_t kind;        /* 0 measure pass, 1 final pass                          */
+  int32_t n_in, r, b;  /* live width in, new qubits, measured bit (extended)     */
+  int32_t n_out;
+  int32_t outcome;     /* measure pass: chosen outcome                         */
+  uint64_t xmask;      /* X on the input bits                                  */
+  uint64_t zmask;      /* linear sign terms                                    */
+  uint32_t c0;         /* constant sign                                        */
+  uint32_t nedges;
+  uint32_t edges[64][2]; /* quadratic sign terms (extended bit pairs)          */
+  double w1re, w1im;   /* weight of the bit-b = 1 amplitude: (-1)^s e^{-i theta} */
+  double scale;        /* constant factor (2^{-r/2} / sqrt2, EOWQS 2^{-r/2})   */
+  int32_t perm[64];    /* final pass: extended bit of outputs[k]               */
+} owqs_pass_desc;
+
+/* Compile the active order with the given outcome bits (K, load order) and
+ * copy up to cap pass descriptors to out; *npass receives the pass count.
+ * Host-only.                                                                */
+owqs_status owqs_describe_passes(const owqs_pattern* p, uint32_t mode, const uint8_t* outcomes,
+                                 owqs_pass_desc* out, uint32_t cap, uint32_t* npass);
+
+/* Message for the last error on the calling thread ("" if none). */
+const char* owqs_last_error(void);
+
+/* OWQS_ABI_VERSION of the loaded library. */
+uint32_t owqs_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OWQS_H */

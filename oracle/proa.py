@@ -202,9 +202,12 @@ def single_array_peak(pattern) -> int:
     live = set(pattern.inputs)
     peak = len(live)
     for c in pattern.cmds:
+        if c.kind == "N":
+            continue
         qs = [c.q0] + ([c.q1] if c.kind == "E" else [])
         live.update(qs)
         peak = max(peak, len(live))
         if c.kind == "M":
             live.discard(c.q0)
-    return peak
+    live.update(pattern.outputs)
+    return max(peak, len(live))

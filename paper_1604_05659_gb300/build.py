@@ -1,0 +1,89 @@
+"""Build libowqs.so in-tree for sm_103a (GB300).
+
+Host C++ goes through g++, the kernels through nvcc with
+-gencode arch=compute_103a,code=sm_103a; the objects are linked into one
+shared library with the CUDA runtime linked statically, so the library has
+no dependency beyond the driver.  Objects go to _build/ next to this file.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libowqs.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def cuda_home() -> str:
+    for c in (os.environ.get("CUDA_HOME"), "/usr/local/cuda"):
+        if c and os.path.exists(os.path.join(c, "bin", "nvcc")):
+            return c
+    nvcc = shutil.which("nvcc")
+    if nvcc:
+        return os.path.dirname(os.path.dirname(nvcc))
+    raise RuntimeError("nvcc not found; set CUDA_HOME")
+
+
+def sources():
+    cpp = sorted(f for f in os.listdir(CSRC) if f.endswith(".cpp"))
+    cu = sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
+    return cpp, cu
+
+
+def _run(cmd):
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"build step failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+    return r.stdout + r.stderr
+
+
+def build(verbose: bool = False, ptxas_info: bool = False) -> str:
+    cuda = cuda_home()
+    nvcc = os.path.join(cuda, "bin", "nvcc")
+    os.makedirs(BUILD, exist_ok=True)
+    cpp, cu = sources()
+    inc = ["-I", INCLUDE, "-I", CSRC, "-I", os.path.join(cuda, "include")]
+    jobs = []
+    for f in cpp:
+        obj = os.path.join(BUILD, f[:-4] + ".o")
+        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function", *inc, "-c",
+                     os.path.join(CSRC, f), "-o", obj])
+    for f in cu:
+        obj = os.path.join(BUILD, f[:-3] + ".o")
+        extra = ["-Xptxas", "-v"] if ptxas_info else []
+        jobs.append([nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+                     "--expt-relaxed-constexpr", *extra, *inc, "-c", os.path.join(CSRC, f), "-o", obj])
+    logs = []
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+        for out in ex.map(_run, jobs):
+            logs.append(out)
+    objs = [os.path.join(BUILD, f[:-4] + ".o") for f in cpp] + [os.path.join(BUILD, f[:-3] + ".o") for f in cu]
+    tmp = LIB + ".tmp"
+    logs.append(_run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread", "-ldl", "-lrt"]))
+    os.replace(tmp, LIB)
+    text = "\n".join(x for x in logs if x.strip())
+    if verbose and text:
+        print(text)
+    return text
+
+
+def ensure_built() -> str:
+    """Build if the library is missing or older than a source file."""
+    cpp, cu = sources()
+    srcs = [os.path.join(CSRC, f) for f in cpp + cu + os.listdir(CSRC) if f.endswith(".h")]
+    srcs.append(os.path.join(INCLUDE, "owqs.h"))
+    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(s) for s in srcs):
+        build()
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(verbose=True, ptxas_info="-v" in sys.argv))

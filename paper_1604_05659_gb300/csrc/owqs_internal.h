@@ -1,0 +1,161 @@
+// Internal declarations of the GB300 one-way quantum computer simulator.
+// Host side: pattern model, reordering, schedule compiler, run driver.
+// Device side: the pass kernels (owqs_kernels.cu) and their parameter block.
+#pragma once
+
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "owqs.h"
+
+namespace owqs {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+owqs_status set_error(owqs_status st, const std::string& msg);
+void clear_error();
+
+// ---------------------------------------------------------------------------
+// pattern model (Section 2.2)
+// ---------------------------------------------------------------------------
+struct Cmd {
+  uint32_t kind = 0;
+  uint32_t q0 = 0, q1 = 0;
+  double angle = 0.0;
+  std::vector<uint32_t> sdom, tdom;
+};
+
+struct RunCache;  // device workspace and graphs (owqs_run.cpp)
+
+struct Pattern {
+  uint32_t n = 0;
+  std::vector<uint32_t> inputs, outputs;
+  std::vector<Cmd> cmds;              // as loaded (execution order)
+  std::vector<int32_t> k_of_qubit;    // K-index (order of M commands as loaded), -1 if not measured
+  std::vector<uint32_t> meas_qubit;   // qubit of K-index k
+  std::vector<uint32_t> active;       // active execution order: indices into cmds
+  std::vector<uint32_t> active_meas;  // measurement order of the active order
+  bool standard = false;
+  bool deps_ok = true;                // active order measures every domain first (D0)
+  std::shared_ptr<RunCache> cache;
+  ~Pattern();
+};
+
+// peak live width and amplitude updates of the active order (host)
+void order_stats(const Pattern& p, uint32_t* peak_live, uint64_t* amp_updates);
+
+// ---------------------------------------------------------------------------
+// compiled pass: the contract between the schedule compiler and the kernels
+//
+// Extended index k of a pass: bits [0, n_in) are the live qubits read from the
+// input array, bits [n_in, n_in + r) the r qubits prepared in |+> during this
+// segment.  The segment's X, Z and E commands are normalised to
+//     x(k) = (-1)^{q(k)} in[(k ^ xmask) & (2^n_in - 1)],
+//     q(k) = c0 ^ parity(k & zmask) ^ XOR over edges (u,v) of k_u k_v,
+// (N commutes to the front, an X is pushed through the E and Z commands
+// before it, and X on a |+> qubit is dropped).  A measure pass writes
+//     out[j] = s_c (x(ins(j, b, 0)) + w1 x(ins(j, b, 1))),  j < 2^(n_in+r-1),
+// where ins inserts a bit at position b; a final pass writes
+//     out[u] = s_c x(sum_k u_k 2^perm[k]).
+// s_c = scale / sqrt(norm of the previous array) in OWQS mode, scale in EOWQS.
+// ---------------------------------------------------------------------------
+struct PassDesc {
+  int kind = 0;  // 0 measure, 1 final
+  int n_in = 0, r = 0, b = -1, n_out = 0;
+  int outcome = 0;
+  uint32_t meas_k = 0;  // K-index (load order) of the measured qubit
+  uint64_t xmask = 0, zmask = 0;
+  uint32_t c0 = 0;
+  std::vector<std::pair<int, int>> edges;  // u < v
+  double w1re = 0, w1im = 0;               // (-1)^outcome e^{-i theta}
+  double ere = 0, eim = 0;                 // e^{-i theta}
+  double scale = 1.0;
+  std::vector<int> perm;                   // final pass
+};
+
+constexpr int kMaxLive = 62;   // widest extended index the compiler accepts
+constexpr int kQMax = 64;      // quadratic lower endpoints (a vertex cover of any graph on 62 bits fits)
+
+// Kernel parameter block, passed by value.
+struct PassParams {
+  const void* in;        // input array, nullptr => virtual |+> input of value vconst
+  void* out;             // output array
+  double* norms;         // device norm slots
+  double* partials;      // per-block partial sums (2 * grid)
+  unsigned int* counter; // finished-block counter, left at 0
+  int n_in, r, b, n_out;
+  int norm_in;           // slot whose value N gives s_c = scale / sqrt(N); -1: s_c = scale
+  int norm_out;          // slot written with sum |out|^2 (prob pass: norm_out, norm_out+1); -1: none
+  double thresh;         // N below thresh => s_c = 0 (impossible branch)
+  uint64_t xmask, zmask;
+  uint32_t c0;
+  int nq;                // quadratic terms: k_{qu[e]} * parity(k & qa[e])
+  int qu[kQMax];
+  uint64_t qa[kQMax];
+  double scale, w1re, w1im, ere, eim, vconst;
+  // fast pass (star form at b, no X): uniform sign tables
+  uint64_t amask;        // neighbours of b
+  uint32_t zb;           // z bit at b
+  uint32_t tzl, tal;     // bit l: parity(delta_l & zmask), parity(delta_l & amask)
+  uint32_t tzt, tat;     // bit t: same for the in-thread broadcast offsets
+  int rt;                // in-thread broadcast bits
+  int nlo;               // live (non-broadcast) output bits
+  // final pass
+  int identity_perm;
+  int perm[64];
+};
+
+enum KernelKind { KK_FAST = 0, KK_GENERIC = 1, KK_FINAL = 2, KK_NORM = 3, KK_PROB = 4 };
+
+struct LaunchPlan {
+  int kind = KK_GENERIC;
+  int variant = 0;       // fast: measured-bit case
+  int grid = 1, block = 256;
+  double bytes = 0;      // algorithmic bytes (amplitudes read + written)
+};
+
+constexpr int kFastL = 2;     // log2 of consecutive outputs per thread tile
+constexpr int kFastRMax = 2;  // broadcast bits handled inside a thread
+constexpr int kBlock = 256;
+int max_grid();               // grid cap for grid-stride kernels
+
+// plan + fill the parameter block of one pass (host)
+void plan_pass(const PassDesc& d, int dtype, bool virt_in, PassParams& P, LaunchPlan& L);
+
+// device launches (owqs_kernels.cu)
+cudaError_t launch_pass(const PassParams& P, const LaunchPlan& L, int dtype, cudaStream_t s);
+cudaError_t launch_norm(const void* in, uint64_t n, int dtype, double* norms, int slot,
+                        double* partials, unsigned int* counter, int grid, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// schedule compiler
+// ---------------------------------------------------------------------------
+struct OutcomeSource {
+  virtual ~OutcomeSource() = default;
+  // forced and preselected outcomes are known before the run: fill
+  // outcome_by_qubit and return true.  Signals are then taken from the full
+  // outcome vector, which is exact for any order that applies every E on v
+  // before M_v, because measurements on different qubits commute (Eq. 14).
+  virtual bool known_upfront(std::vector<int8_t>& /*outcome_by_qubit*/) { return false; }
+  // decide the outcome of the measurement described by d (outcome field not
+  // yet set); return -1 on failure (error already recorded)
+  virtual int decide(const PassDesc& d) = 0;
+};
+
+// Walk the active order; emits K measure passes then the final pass.  Returns
+// OWQS_OK or an error.  maps (optional) receives bit_of_qubit after each pass.
+owqs_status compile_schedule(const Pattern& p, int mode, OutcomeSource& src,
+                             std::vector<PassDesc>& passes,
+                             std::vector<std::vector<int32_t>>* maps = nullptr);
+
+}  // namespace owqs
+
+// the opaque handle of the C ABI
+struct owqs_pattern {
+  owqs::Pattern p;
+};

@@ -1,0 +1,356 @@
+// Device passes of the GB300 one-way quantum computer simulator (sm_103a).
+//
+// One launch per measurement: it reads the live amplitude array once and
+// writes the halved (after elimination) array once, with the segment's N, E,
+// X and Z commands applied on the fly (Sections 4.2 and 4.4; Figs. 5 and 6 do
+// the same work as separate sweeps on the CPU).  The pass is a bandwidth-bound
+// pairwise update, so there are no tensor cores: the kernels move aligned
+// 16-byte vectors, keep every thread's reads and writes contiguous, and fold
+// the probability reduction of Eq. 13 into the same sweep (FP32 partial sums
+// per thread tile promoted to FP64, FP64 across threads and blocks).
+//
+// Contract with the schedule compiler: see PassDesc in owqs_internal.h.
+#include <cstdint>
+
+#include "owqs_internal.h"
+
+namespace owqs {
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using V = float2; };
+template <> struct Cplx<double> { using V = double2; };
+
+__device__ __forceinline__ uint32_t par64(uint64_t v) { return (uint32_t)__popcll(v) & 1u; }
+
+__device__ __forceinline__ uint64_t ins0(uint64_t j, int b) {
+  return ((j >> b) << (b + 1)) | (j & ((1ull << b) - 1));
+}
+
+// sign bit of x(k): c0 ^ parity(k & zmask) ^ XOR_e k_{qu[e]} parity(k & qa[e])
+__device__ __forceinline__ uint32_t qsign(const PassParams& P, uint64_t k) {
+  uint32_t s = P.c0 ^ par64(k & P.zmask);
+  for (int e = 0; e < P.nq; ++e) s ^= (uint32_t)((k >> P.qu[e]) & 1ull) & par64(k & P.qa[e]);
+  return s & 1u;
+}
+
+// 1/sqrt(N) of the previous array, 0 for an impossible branch
+__device__ __forceinline__ double prev_scale(const PassParams& P) {
+  if (P.norm_in < 0) return 1.0;
+  const double nv = P.norms[P.norm_in];
+  return (nv >= P.thresh && nv > 0.0) ? 1.0 / sqrt(nv) : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Block reduction of NV FP64 values into norms[slot .. slot+NV).  Each block
+// stores its partial; the last block to finish (counted with one atomic)
+// adds the partials in block order with Neumaier compensation, so the result
+// does not depend on block scheduling.  The counter is reset for the next
+// launch.  No thread ever waits on another block.
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void reduce_to_slots(const double (&acc)[NV], double* partials,
+                                                unsigned int* counter, double* norms, int slot) {
+  __shared__ double sh[NV][32];
+  __shared__ int am_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double v = acc[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[i][warp] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double v = lane < nwarp ? sh[i][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) partials[(size_t)i * gridDim.x + blockIdx.x] = v;
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(counter, 1u);
+    am_last = (prev == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double s = 0.0, c = 0.0;
+    for (unsigned blk = threadIdx.x; blk < gridDim.x; blk += blockDim.x) {
+      const double x = __ldcg(&partials[(size_t)i * gridDim.x + blk]);
+      const double t = s + x;
+      c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+      s = t;
+    }
+    s += c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if (lane == 0) sh[i][warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < nwarp; ++w) tot += sh[i][w];
+      norms[slot + i] = tot;
+    }
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// generic pass: one output amplitude per thread iteration; any sign function,
+// any X mask, any measured bit, virtual |+> input.  MODE 0 measure, 1 the
+// two outcome probabilities only, 2 final pass (corrections + output order).
+// ---------------------------------------------------------------------------
+template <typename T, int MODE, bool VIRT>
+__global__ void __launch_bounds__(kBlock) k_generic(const PassParams P) {
+  using V = typename Cplx<T>::V;
+  const V* __restrict__ in = reinterpret_cast<const V*>(P.in);
+  V* __restrict__ out = reinterpret_cast<V*>(P.out);
+  const double c = prev_scale(P);
+  const T sc = (T)(P.scale * c);
+  const T wr = (T)(P.scale * c * P.w1re), wi = (T)(P.scale * c * P.w1im);
+  const T er = (T)P.ere, ei = (T)P.eim;
+  const uint64_t nout = 1ull << P.n_out;
+  const uint64_t inmask = (1ull << P.n_in) - 1ull;
+  const uint64_t bb = MODE == 2 ? 0ull : (1ull << P.b);
+  const T vc = (T)P.vconst;
+  auto load = [&](uint64_t k) -> V {
+    V x;
+    if (VIRT) {
+      x.x = vc;
+      x.y = (T)0;
+    } else {
+      x = in[(k ^ P.xmask) & inmask];
+    }
+    if (qsign(P, k)) x.x = -x.x, x.y = -x.y;
+    return x;
+  };
+  double acc[2] = {0.0, 0.0};
+  T part[2] = {(T)0, (T)0};
+  int cnt = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nout; j += stride) {
+    if (MODE == 2) {
+      uint64_t k = j;
+      if (!P.identity_perm) {
+        k = 0;
+        for (int i = 0; i < P.n_out; ++i) k |= ((j >> i) & 1ull) << P.perm[i];
+      }
+      const V x = load(k);
+      V y;
+      y.x = sc * x.x;
+      y.y = sc * x.y;
+      out[j] = y;
+      part[0] += y.x * y.x + y.y * y.y;
+    } else {
+      const uint64_t k0 = ins0(j, P.b), k1 = k0 | bb;
+      const V x0 = load(k0), x1 = load(k1);
+      if (MODE == 0) {
+        V y;
+        y.x = sc * x0.x + wr * x1.x - wi * x1.y;
+        y.y = sc * x0.y + wr * x1.y + wi * x1.x;
+        out[j] = y;
+        part[0] += y.x * y.x + y.y * y.y;
+      } else {
+        const T ex = er * x1.x - ei * x1.y, ey = er * x1.y + ei * x1.x;
+        const T a0 = x0.x + ex, b0 = x0.y + ey, a1 = x0.x - ex, b1 = x0.y - ey;
+        part[0] += sc * sc * (a0 * a0 + b0 * b0);
+        part[1] += sc * sc * (a1 * a1 + b1 * b1);
+      }
+    }
+    if (++cnt == 8) {  // FP32 partials over short runs, promoted to FP64
+      acc[0] += (double)part[0];
+      acc[1] += (double)part[1];
+      part[0] = part[1] = (T)0;
+      cnt = 0;
+    }
+  }
+  acc[0] += (double)part[0];
+  acc[1] += (double)part[1];
+  if (P.norm_out >= 0) {
+    if (MODE == 1) {
+      reduce_to_slots<2>(acc, P.partials, P.counter, P.norms, P.norm_out);
+    } else {
+      const double a1[1] = {acc[0]};
+      reduce_to_slots<1>(a1, P.partials, P.counter, P.norms, P.norm_out);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fast measure pass: sign function in star form at the measured bit b (every
+// E of the segment touches the measured qubit, which is what reordering by
+// the Proposition of Section 4.3 produces), no X mask.  A thread tile is 2^L
+// consecutive outputs of the live part times 2^rt values of the lowest
+// broadcast (newly prepared) bits; it reads its input amplitudes once with
+// 16-byte loads and writes 2^(L+rt) outputs with 16-byte stores.
+//   BM < L   : b = BM, the pair partners sit in one aligned run of 2^(L+1)
+//   BM == L  : L <= b < n_in, two aligned runs of 2^L, 2^b apart
+//   BM == L+1: b is a new qubit, both partners read the same amplitude
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void ld_run(float2 (&v)[N], const float2* p) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) {
+    const float4 t = q[i];
+    v[2 * i] = make_float2(t.x, t.y);
+    v[2 * i + 1] = make_float2(t.z, t.w);
+  }
+}
+template <int N>
+__device__ __forceinline__ void ld_run(double2 (&v)[N], const double2* p) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = p[i];
+}
+template <int N>
+__device__ __forceinline__ void st_run(float2* p, const float2 (&v)[N]) {
+  float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) q[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+}
+template <int N>
+__device__ __forceinline__ void st_run(double2* p, const double2 (&v)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) p[i] = v[i];
+}
+
+__host__ __device__ constexpr int ins0c(int l, int b) { return ((l >> b) << (b + 1)) | (l & ((1 << b) - 1)); }
+
+template <typename T, int L, int BM>
+__global__ void __launch_bounds__(kBlock) k_fast(const PassParams P) {
+  using V = typename Cplx<T>::V;
+  constexpr int NL = 1 << L;
+  const V* __restrict__ in = reinterpret_cast<const V*>(P.in);
+  V* __restrict__ out = reinterpret_cast<V*>(P.out);
+  const double c = prev_scale(P);
+  const T sc = (T)(P.scale * c);
+  const T wr = (T)(P.scale * c * P.w1re), wi = (T)(P.scale * c * P.w1im);
+  const int b = P.b, nlo = P.nlo, rt = P.rt;
+  const uint64_t tiles = 1ull << (P.n_out - L - rt);
+  const uint64_t lomask = (1ull << (nlo - L)) - 1ull;
+  const int hishift = nlo + rt;
+  const uint64_t inmask = (1ull << P.n_in) - 1ull;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (uint64_t tile = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; tile < tiles; tile += stride) {
+    const uint64_t J = ((tile & lomask) << L) | ((tile >> (nlo - L)) << hishift);
+    const uint64_t K0 = ins0(J, b);
+    const uint32_t pz = P.c0 ^ par64(K0 & P.zmask);
+    const uint32_t pa = P.zb ^ par64(K0 & P.amask);
+    const uint64_t ib = K0 & inmask;
+    V v0[NL], v1[NL];
+    if constexpr (BM < L) {
+      V run[2 * NL];
+      ld_run(run, in + ib);
+#pragma unroll
+      for (int l = 0; l < NL; ++l) {
+        v0[l] = run[ins0c(l, BM)];
+        v1[l] = run[ins0c(l, BM) | (1 << BM)];
+      }
+    } else if constexpr (BM == L) {
+      ld_run(v0, in + ib);
+      ld_run(v1, in + ib + (1ull << b));
+    } else {
+      ld_run(v0, in + ib);
+#pragma unroll
+      for (int l = 0; l < NL; ++l) v1[l] = v0[l];
+    }
+    T tacc = (T)0;
+#pragma unroll
+    for (int t = 0; t < (1 << kFastRMax); ++t) {
+      if (t >= (1 << rt)) break;
+      const uint32_t st0 = pz ^ ((P.tzt >> t) & 1u);
+      const uint32_t st1 = st0 ^ pa ^ ((P.tat >> t) & 1u);
+      V y[NL];
+#pragma unroll
+      for (int l = 0; l < NL; ++l) {
+        const uint32_t s0 = (st0 ^ (P.tzl >> l)) & 1u;
+        const uint32_t s1 = (st1 ^ (P.tzl >> l) ^ (P.tal >> l)) & 1u;
+        const T a = s0 ? -sc : sc;
+        const T br = s1 ? -wr : wr, bi = s1 ? -wi : wi;
+        y[l].x = a * v0[l].x + br * v1[l].x - bi * v1[l].y;
+        y[l].y = a * v0[l].y + br * v1[l].y + bi * v1[l].x;
+        tacc += y[l].x * y[l].x + y[l].y * y[l].y;
+      }
+      st_run(out + J + ((uint64_t)t << nlo), y);
+    }
+    acc += (double)tacc;
+  }
+  if (P.norm_out >= 0) {
+    const double a1[1] = {acc};
+    reduce_to_slots<1>(a1, P.partials, P.counter, P.norms, P.norm_out);
+  }
+}
+
+// squared norm of an input vector (OWQS divides by it)
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_norm(const void* vin, uint64_t n, double* norms, int slot,
+                                                 double* partials, unsigned int* counter) {
+  using V = typename Cplx<T>::V;
+  const V* __restrict__ in = reinterpret_cast<const V*>(vin);
+  double acc = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const V x = in[i];
+    acc += (double)x.x * (double)x.x + (double)x.y * (double)x.y;
+  }
+  const double a1[1] = {acc};
+  reduce_to_slots<1>(a1, partials, counter, norms, slot);
+}
+
+// ---------------------------------------------------------------------------
+// launch wrappers
+// ---------------------------------------------------------------------------
+template <typename T>
+static cudaError_t launch_t(const PassParams& P, const LaunchPlan& L, cudaStream_t s) {
+  const dim3 g(L.grid), blk(L.block);
+  const bool virt = P.in == nullptr;
+  switch (L.kind) {
+    case KK_FAST:
+      switch (L.variant) {
+        case 0: k_fast<T, kFastL, 0><<<g, blk, 0, s>>>(P); break;
+        case 1: k_fast<T, kFastL, 1><<<g, blk, 0, s>>>(P); break;
+        case kFastL: k_fast<T, kFastL, kFastL><<<g, blk, 0, s>>>(P); break;
+        case kFastL + 1: k_fast<T, kFastL, kFastL + 1><<<g, blk, 0, s>>>(P); break;
+        default: return cudaErrorInvalidValue;
+      }
+      break;
+    case KK_GENERIC:
+      if (virt) k_generic<T, 0, true><<<g, blk, 0, s>>>(P);
+      else k_generic<T, 0, false><<<g, blk, 0, s>>>(P);
+      break;
+    case KK_PROB:
+      if (virt) k_generic<T, 1, true><<<g, blk, 0, s>>>(P);
+      else k_generic<T, 1, false><<<g, blk, 0, s>>>(P);
+      break;
+    case KK_FINAL:
+      if (virt) k_generic<T, 2, true><<<g, blk, 0, s>>>(P);
+      else k_generic<T, 2, false><<<g, blk, 0, s>>>(P);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+static_assert(kFastL == 2, "launch_t instantiates the low-bit variants for L = 2");
+
+cudaError_t launch_pass(const PassParams& P, const LaunchPlan& L, int dtype, cudaStream_t s) {
+  return dtype == OWQS_C64 ? launch_t<float>(P, L, s) : launch_t<double>(P, L, s);
+}
+
+cudaError_t launch_norm(const void* in, uint64_t n, int dtype, double* norms, int slot, double* partials,
+                        unsigned int* counter, int grid, cudaStream_t s) {
+  if (dtype == OWQS_C64) k_norm<float><<<grid, kBlock, 0, s>>>(in, n, norms, slot, partials, counter);
+  else k_norm<double><<<grid, kBlock, 0, s>>>(in, n, norms, slot, partials, counter);
+  return cudaGetLastError();
+}
+
+}  // namespace owqs

@@ -1,0 +1,599 @@
+// Run driver: device workspace, launch list, CUDA-graph capture and replay,
+// sampled outcomes, per-launch profiling, index maps and pass descriptions.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "owqs_internal.h"
+
+namespace owqs {
+
+struct RunCache {
+  int device = -1;
+  void* buf[2] = {nullptr, nullptr};
+  size_t buf_bytes = 0;
+  void* in_stage = nullptr;
+  size_t in_bytes = 0;
+  void* out_stage = nullptr;
+  size_t out_bytes = 0;
+  double* norms = nullptr;
+  size_t nnorms = 0;
+  double* partials = nullptr;
+  size_t npartials = 0;
+  unsigned int* counter = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::string gkey;
+  std::vector<double> h_norms;
+  uint32_t last_launches = 0;
+
+  ~RunCache() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (device >= 0 && cur != device) cudaSetDevice(device);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (cap) cudaStreamDestroy(cap);
+    for (void* p : {buf[0], buf[1], in_stage, out_stage, (void*)norms, (void*)partials, (void*)counter})
+      if (p) cudaFree(p);
+    if (device >= 0 && cur >= 0 && cur != device) cudaSetDevice(cur);
+  }
+};
+
+static owqs_status cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a non-sticky error
+  return set_error(e == cudaErrorMemoryAllocation ? OWQS_ERR_OOM : OWQS_ERR_CUDA,
+                   std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static owqs_status ensure_buf(void*& p, size_t& have, size_t need, const char* what) {
+  if (need <= have && p) return OWQS_OK;
+  if (p) {
+    cudaFree(p);
+    p = nullptr;
+    have = 0;
+  }
+  size_t freeb = 0, total = 0;
+  if (cudaMemGetInfo(&freeb, &total) == cudaSuccess && need > freeb)
+    return set_error(OWQS_ERR_OOM, std::string(what) + ": needs " + std::to_string(need) +
+                                       " bytes, device has " + std::to_string(freeb) + " free");
+  cudaError_t e = cudaMalloc(&p, need);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    return cuda_fail(e, what);
+  }
+  have = need;
+  return OWQS_OK;
+}
+
+static owqs_status get_cache(Pattern& p, RunCache*& rc) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (!p.cache) {
+    p.cache = std::make_shared<RunCache>();
+    p.cache->device = dev;
+  }
+  if (p.cache->device != dev) return set_error(OWQS_ERR_ARG, "pattern handle used on another device");
+  rc = p.cache.get();
+  return OWQS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// outcome sources
+// ---------------------------------------------------------------------------
+struct FixedSource : OutcomeSource {
+  const Pattern& p;
+  const uint8_t* bits;  // nullptr => all zero
+  FixedSource(const Pattern& pp, const uint8_t* b) : p(pp), bits(b) {}
+  bool known_upfront(std::vector<int8_t>& o) override {
+    for (size_t k = 0; k < p.meas_qubit.size(); ++k) o[p.meas_qubit[k]] = bits ? (int8_t)(bits[k] & 1u) : 0;
+    return true;
+  }
+  int decide(const PassDesc& d) override { return bits ? (bits[d.meas_k] & 1u) : 0; }
+};
+
+// ---------------------------------------------------------------------------
+// launch list
+// ---------------------------------------------------------------------------
+struct Item {
+  int type = 0;  // 0 pass, 1 norm
+  PassParams P;
+  LaunchPlan L;
+  const void* norm_in = nullptr;
+  uint64_t norm_n = 0;
+  int norm_slot = 0;
+};
+
+class Runner {
+ public:
+  Runner(Pattern& p, RunCache& rc, int dtype, int mode, cudaStream_t s)
+      : p_(p), rc_(rc), dtype_(dtype), mode_(mode), stream_(s) {
+    K_ = (int)p.meas_qubit.size();
+    thresh_ = dtype == OWQS_C128 ? 1e-24 : 1e-12;
+  }
+
+  bool immediate = false;
+  std::vector<Item> items;
+  owqs_status err = OWQS_OK;
+
+  void begin(const void* in0, uint64_t in_elems, void* out_final) {
+    cur_in_ = in0;
+    out_final_ = out_final;
+    pass_i_ = 0;
+    prev_slot_ = -1;
+    if (in0) {  // input norm: OWQS divides by it, EOWQS checks against it
+      Item it;
+      it.type = 1;
+      it.norm_in = in0;
+      it.norm_n = in_elems;
+      it.norm_slot = 0;
+      it.L.grid = (int)std::min<uint64_t>((in_elems + kBlock - 1) / kBlock, (uint64_t)max_grid());
+      it.L.kind = KK_NORM;
+      it.L.bytes = (double)in_elems * (dtype_ == OWQS_C64 ? 8.0 : 16.0);
+      issue(it);
+      if (mode_ == OWQS_MODE_OWQS) prev_slot_ = 0;
+    }
+  }
+
+  void measure(const PassDesc& d) {
+    Item it;
+    plan_pass(d, dtype_, cur_in_ == nullptr, it.P, it.L);
+    fill_common(it.P);
+    it.P.in = cur_in_;
+    it.P.out = rc_.buf[pass_i_ & 1];
+    it.P.norm_in = prev_slot_;
+    it.P.norm_out = mode_ == OWQS_MODE_OWQS ? pass_i_ + 1 : -1;
+    issue(it);
+    cur_in_ = it.P.out;
+    prev_slot_ = it.P.norm_out;
+    ++pass_i_;
+  }
+
+  // both outcome probabilities of the next measurement into slots
+  // prob_slot(i), prob_slot(i)+1 (sampled outcomes)
+  int prob(const PassDesc& d) {
+    Item it;
+    plan_pass(d, dtype_, cur_in_ == nullptr, it.P, it.L);
+    fill_common(it.P);
+    it.L.kind = KK_PROB;
+    it.L.grid = (int)std::min<uint64_t>(((1ull << d.n_out) + kBlock - 1) / kBlock, (uint64_t)max_grid());
+    it.L.bytes = (cur_in_ ? std::ldexp(1.0, d.n_in) : 0.0) * (dtype_ == OWQS_C64 ? 8.0 : 16.0);
+    it.P.in = cur_in_;
+    it.P.out = nullptr;
+    it.P.norm_in = prev_slot_;
+    it.P.norm_out = K_ + 2 + 2 * pass_i_;
+    issue(it);
+    return it.P.norm_out;
+  }
+
+  void final_pass(const PassDesc& d) {
+    Item it;
+    plan_pass(d, dtype_, cur_in_ == nullptr, it.P, it.L);
+    fill_common(it.P);
+    it.P.in = cur_in_;
+    it.P.out = out_final_;
+    it.P.norm_in = mode_ == OWQS_MODE_OWQS ? prev_slot_ : -1;
+    it.P.norm_out = K_ + 1;
+    issue(it);
+  }
+
+  owqs_status launch(const Item& it, cudaStream_t s) {
+    cudaError_t e;
+    if (it.type == 1)
+      e = launch_norm(it.norm_in, it.norm_n, dtype_, rc_.norms, it.norm_slot, rc_.partials, rc_.counter,
+                      it.L.grid, s);
+    else
+      e = launch_pass(it.P, it.L, dtype_, s);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return OWQS_OK;
+  }
+
+ private:
+  void fill_common(PassParams& P) {
+    P.norms = rc_.norms;
+    P.partials = rc_.partials;
+    P.counter = rc_.counter;
+    P.thresh = thresh_;
+  }
+  void issue(const Item& it) {
+    if (immediate) {
+      if (err == OWQS_OK) err = launch(it, stream_);
+    } else {
+      items.push_back(it);
+    }
+  }
+
+  Pattern& p_;
+  RunCache& rc_;
+  int dtype_, mode_;
+  cudaStream_t stream_;
+  int K_ = 0;
+  double thresh_;
+  const void* cur_in_ = nullptr;
+  void* out_final_ = nullptr;
+  int pass_i_ = 0;
+  int prev_slot_ = -1;
+};
+
+// sampled outcomes: the previous measure pass is launched, then the two
+// probabilities of this measurement are reduced and read back, and the
+// outcome is 0 iff u <= prob_0 with u the next splitmix64 uniform
+struct SampledSource : OutcomeSource {
+  Runner& R;
+  RunCache& rc;
+  cudaStream_t s;
+  uint64_t state;
+  bool have_pending = false;
+  PassDesc pending;
+  SampledSource(Runner& r, RunCache& c, cudaStream_t st, uint64_t seed) : R(r), rc(c), s(st), state(seed) {}
+  double uniform() {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  }
+  void flush() {
+    if (have_pending) {
+      R.measure(pending);
+      have_pending = false;
+    }
+  }
+  int decide(const PassDesc& d) override {
+    flush();
+    const int slot = R.prob(d);
+    if (R.err != OWQS_OK) return -1;
+    double pp[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(pp, rc.norms + slot, sizeof(pp), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      cuda_fail(e, "reading outcome probabilities");
+      return -1;
+    }
+    const int o = uniform() <= pp[0] ? 0 : 1;
+    pending = d;
+    pending.outcome = o;
+    pending.w1re = o ? -d.ere : d.ere;
+    pending.w1im = o ? -d.eim : d.eim;
+    have_pending = true;
+    return o;
+  }
+};
+
+static std::string graph_key(const Pattern& p, const owqs_run_opts* o, const void* in, const void* out,
+                             const uint8_t* outcomes) {
+  std::string k;
+  k.reserve(64 + p.meas_qubit.size());
+  auto add = [&](const void* v, size_t n) { k.append(reinterpret_cast<const char*>(v), n); };
+  add(&o->dtype, 4);
+  add(&o->mode, 4);
+  add(&o->policy, 4);
+  add(&in, sizeof(in));
+  add(&out, sizeof(out));
+  const void* pp = &p;
+  add(&pp, sizeof(pp));
+  uint64_t h = 1469598103934665603ull;  // active order fingerprint (FNV-1a)
+  for (uint32_t i : p.active) h = (h ^ i) * 1099511628211ull;
+  add(&h, 8);
+  if (o->policy == OWQS_OUTCOME_FORCED && outcomes) add(outcomes, p.meas_qubit.size());
+  return k;
+}
+
+struct Prepared {
+  std::vector<PassDesc> passes;
+  const void* in_dev = nullptr;
+  void* out_dev = nullptr;
+  size_t amp = 8;
+  uint64_t in_elems = 0, out_elems = 0;
+};
+
+static owqs_status prepare(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
+                           const uint8_t* outcomes, RunCache*& rc, Prepared& pr, bool sampled) {
+  if (!o || !psi_out) return set_error(OWQS_ERR_ARG, "NULL argument");
+  if (o->dtype > OWQS_C128 || o->mode > OWQS_MODE_EOWQS || o->policy > OWQS_OUTCOME_ZERO || o->io > OWQS_IO_HOST)
+    return set_error(OWQS_ERR_ARG, "bad option value");
+  if (o->policy == OWQS_OUTCOME_FORCED && !outcomes && !p.meas_qubit.empty())
+    return set_error(OWQS_ERR_ARG, "forced outcomes need the outcomes array");
+  pr.amp = o->dtype == OWQS_C64 ? 8 : 16;
+  if (o->io == OWQS_IO_DEVICE) {
+    if (((uintptr_t)psi_in % 16) || ((uintptr_t)psi_out % 16))
+      return set_error(OWQS_ERR_ARG, "device vectors must be 16-byte aligned");
+  }
+  owqs_status st = get_cache(p, rc);
+  if (st != OWQS_OK) return st;
+  if (!sampled) {  // sampled runs compile while they execute
+    FixedSource src(p, o->policy == OWQS_OUTCOME_ZERO ? nullptr : outcomes);
+    st = compile_schedule(p, o->mode, src, pr.passes);
+    if (st != OWQS_OK) return st;
+  }
+  const int K = (int)p.meas_qubit.size();
+  pr.in_elems = 1ull << p.inputs.size();
+  pr.out_elems = 1ull << p.outputs.size();
+  st = ensure_buf((void*&)rc->norms, rc->nnorms, sizeof(double) * (3 * (size_t)K + 8), "norm slots");
+  if (st == OWQS_OK)
+    st = ensure_buf((void*&)rc->partials, rc->npartials, sizeof(double) * 2 * (size_t)max_grid(), "partials");
+  if (st == OWQS_OK && !rc->counter) {
+    cudaError_t e = cudaMalloc(&rc->counter, sizeof(unsigned int));
+    if (e != cudaSuccess) return cuda_fail(e, "counter");
+    e = cudaMemset(rc->counter, 0, sizeof(unsigned int));
+    if (e != cudaSuccess) return cuda_fail(e, "counter");
+  }
+  if (st != OWQS_OK) return st;
+  if (o->io == OWQS_IO_HOST) {
+    if (psi_in) {
+      st = ensure_buf(rc->in_stage, rc->in_bytes, pr.in_elems * pr.amp, "input staging");
+      if (st != OWQS_OK) return st;
+      pr.in_dev = rc->in_stage;
+    }
+    st = ensure_buf(rc->out_stage, rc->out_bytes, pr.out_elems * pr.amp, "output staging");
+    if (st != OWQS_OK) return st;
+    pr.out_dev = rc->out_stage;
+  } else {
+    pr.in_dev = psi_in;
+    pr.out_dev = psi_out;
+    if (psi_in && psi_in == psi_out) return set_error(OWQS_ERR_ARG, "psi_in and psi_out must not overlap");
+  }
+  return OWQS_OK;
+}
+
+static owqs_status ensure_pingpong(RunCache* rc, size_t elems, size_t amp) {
+  const size_t need = std::max<size_t>(elems, 1) * amp;
+  if (rc->buf_bytes >= need && rc->buf[0] && rc->buf[1]) return OWQS_OK;
+  size_t have0 = rc->buf_bytes, have1 = rc->buf_bytes;
+  if (rc->gexec) {  // graphs hold the old buffer addresses
+    cudaGraphExecDestroy(rc->gexec);
+    rc->gexec = nullptr;
+    rc->gkey.clear();
+  }
+  owqs_status st = ensure_buf(rc->buf[0], have0, need, "state buffer");
+  if (st == OWQS_OK) st = ensure_buf(rc->buf[1], have1, need, "state buffer");
+  if (st != OWQS_OK) return st;
+  rc->buf_bytes = need;
+  return OWQS_OK;
+}
+
+static owqs_status finish(Pattern& p, const owqs_run_opts* o, RunCache* rc, const Prepared& pr,
+                          cudaStream_t s, uint8_t* outcomes, double* probs, const std::vector<int>& outcome_of_pass,
+                          bool has_input) {
+  const int K = (int)p.meas_qubit.size();
+  rc->h_norms.assign((size_t)K + 2, 0.0);
+  cudaError_t e = cudaMemcpyAsync(rc->h_norms.data(), rc->norms, sizeof(double) * (K + 2), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "run");
+  const double thresh = o->dtype == OWQS_C128 ? 1e-24 : 1e-12;
+  owqs_status st = OWQS_OK;
+  int mi = 0;
+  for (const PassDesc& d : pr.passes) {
+    if (d.kind != 0) continue;
+    const double pv = o->mode == OWQS_MODE_OWQS ? rc->h_norms[mi + 1] : 0.5;
+    if (probs) probs[d.meas_k] = pv;
+    if (outcomes && o->policy != OWQS_OUTCOME_FORCED) outcomes[d.meas_k] = (uint8_t)outcome_of_pass[mi];
+    if (o->mode == OWQS_MODE_OWQS && !(pv >= thresh) && st == OWQS_OK)
+      st = set_error(OWQS_ERR_IMPOSSIBLE_BRANCH, "outcome of measurement " + std::to_string(d.meas_k) +
+                                                      " has probability " + std::to_string(pv));
+    ++mi;
+  }
+  if (o->mode == OWQS_MODE_EOWQS) {
+    const double nin = has_input ? rc->h_norms[0] : 1.0;
+    const double nout = rc->h_norms[K + 1];
+    const double tol = o->dtype == OWQS_C128 ? 1e-10 : 1e-4;
+    if (!(std::fabs(nout - nin) <= tol * std::max(nin, 1e-300)))
+      st = set_error(OWQS_ERR_NOT_DETERMINISTIC,
+                     "EOWQS output norm " + std::to_string(nout) + " differs from the input norm " + std::to_string(nin));
+  }
+  return st;
+}
+
+static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
+                            uint8_t* outcomes, double* probs, float* prof_ms, double* prof_bytes,
+                            uint32_t* prof_kind, uint32_t prof_cap, uint32_t* prof_n) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(o ? o->stream : nullptr);
+  RunCache* rc = nullptr;
+  Prepared pr;
+  const bool sampled = o && o->policy == OWQS_OUTCOME_SAMPLED;
+  owqs_status st = prepare(p, o, psi_in, psi_out, outcomes, rc, pr, sampled);
+  if (st != OWQS_OK) return st;
+  const int K = (int)p.meas_qubit.size();
+  std::vector<int> outcome_of_pass;
+
+  if (sampled) {
+    if (prof_ms) return set_error(OWQS_ERR_ARG, "profiling needs forced or zero outcomes");
+    // structure pass (outcome-independent widths) to size the buffers
+    {
+      FixedSource zero(p, nullptr);
+      std::vector<PassDesc> tmp;
+      if (!p.deps_ok)
+        return set_error(OWQS_ERR_ARG, "sampled outcomes need an order that measures every domain first");
+      st = compile_schedule(p, o->mode, zero, tmp);
+      if (st != OWQS_OK) return st;
+      size_t wmax = 1;
+      for (const PassDesc& d : tmp)
+        if (d.kind == 0) wmax = std::max<size_t>(wmax, (size_t)1 << d.n_out);
+      st = ensure_pingpong(rc, wmax, pr.amp);
+      if (st != OWQS_OK) return st;
+    }
+    if (o->io == OWQS_IO_HOST && psi_in) {
+      cudaError_t e = cudaMemcpyAsync(rc->in_stage, psi_in, pr.in_elems * pr.amp, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return cuda_fail(e, "input copy");
+    }
+    Runner R(p, *rc, o->dtype, o->mode, s);
+    R.immediate = true;
+    R.begin(pr.in_dev, pr.in_elems, pr.out_dev);
+    SampledSource src(R, *rc, s, o->seed);
+    st = compile_schedule(p, o->mode, src, pr.passes);
+    if (st != OWQS_OK) return st;
+    src.flush();
+    R.final_pass(pr.passes.back());
+    if (R.err != OWQS_OK) return R.err;
+    for (const PassDesc& d : pr.passes)
+      if (d.kind == 0) outcome_of_pass.push_back(d.outcome);
+  } else {
+    size_t wmax = 1;
+    for (const PassDesc& d : pr.passes)
+      if (d.kind == 0) wmax = std::max<size_t>(wmax, (size_t)1 << d.n_out);
+    st = ensure_pingpong(rc, wmax, pr.amp);
+    if (st != OWQS_OK) return st;
+    for (const PassDesc& d : pr.passes)
+      if (d.kind == 0) outcome_of_pass.push_back(d.outcome);
+    Runner R(p, *rc, o->dtype, o->mode, s);
+    R.begin(pr.in_dev, pr.in_elems, pr.out_dev);
+    for (const PassDesc& d : pr.passes) {
+      if (d.kind == 0) R.measure(d);
+      else R.final_pass(d);
+    }
+    if (o->io == OWQS_IO_HOST && psi_in) {
+      cudaError_t e = cudaMemcpyAsync(rc->in_stage, psi_in, pr.in_elems * pr.amp, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return cuda_fail(e, "input copy");
+    }
+    rc->last_launches = (uint32_t)R.items.size();
+    if (prof_ms) {
+      std::vector<cudaEvent_t> ev(2 * R.items.size());
+      for (auto& x : ev)
+        if (cudaEventCreate(&x) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+      for (size_t i = 0; i < R.items.size(); ++i) {
+        cudaEventRecord(ev[2 * i], s);
+        st = R.launch(R.items[i], s);
+        cudaEventRecord(ev[2 * i + 1], s);
+        if (st != OWQS_OK) break;
+      }
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (st == OWQS_OK && e != cudaSuccess) st = cuda_fail(e, "profiled run");
+      const uint32_t n = (uint32_t)std::min<size_t>(R.items.size(), prof_cap);
+      for (uint32_t i = 0; i < n && st == OWQS_OK; ++i) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+        prof_ms[i] = ms;
+        if (prof_bytes) prof_bytes[i] = R.items[i].L.bytes;
+        if (prof_kind) prof_kind[i] = (uint32_t)R.items[i].L.kind;
+      }
+      if (prof_n) *prof_n = (uint32_t)R.items.size();
+      for (auto& x : ev) cudaEventDestroy(x);
+      if (st != OWQS_OK) return st;
+    } else if (o->use_graph) {
+      const std::string key = graph_key(p, o, pr.in_dev, pr.out_dev, outcomes);
+      if (!rc->gexec || key != rc->gkey) {
+        if (rc->gexec) {
+          cudaGraphExecDestroy(rc->gexec);
+          rc->gexec = nullptr;
+        }
+        if (!rc->cap) {
+          cudaError_t e = cudaStreamCreateWithFlags(&rc->cap, cudaStreamNonBlocking);
+          if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+        }
+        cudaError_t e = cudaStreamBeginCapture(rc->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+        for (const Item& it : R.items) {
+          st = R.launch(it, rc->cap);
+          if (st != OWQS_OK) break;
+        }
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(rc->cap, &g);
+        if (st != OWQS_OK) {
+          if (g) cudaGraphDestroy(g);
+          return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "end capture");
+        e = cudaGraphInstantiate(&rc->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          rc->gexec = nullptr;
+          return cuda_fail(e, "graph instantiate");
+        }
+        rc->gkey = key;
+      }
+      cudaError_t e = cudaGraphLaunch(rc->gexec, s);
+      if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    } else {
+      for (const Item& it : R.items) {
+        st = R.launch(it, s);
+        if (st != OWQS_OK) return st;
+      }
+    }
+  }
+  if (o->io == OWQS_IO_HOST) {
+    cudaError_t e = cudaMemcpyAsync(psi_out, rc->out_stage, pr.out_elems * pr.amp, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "output copy");
+  }
+  (void)K;
+  return finish(p, o, rc, pr, s, outcomes, probs, outcome_of_pass, pr.in_dev != nullptr);
+}
+
+}  // namespace owqs
+
+using namespace owqs;
+
+extern "C" {
+
+owqs_status owqs_run(owqs_pattern* h, const owqs_run_opts* o, const void* psi_in, void* psi_out,
+                     uint8_t* outcomes, double* probs) {
+  clear_error();
+  if (!h) return set_error(OWQS_ERR_ARG, "NULL pattern");
+  return run_impl(h->p, o, psi_in, psi_out, outcomes, probs, nullptr, nullptr, nullptr, 0, nullptr);
+}
+
+owqs_status owqs_profile_run(owqs_pattern* h, const owqs_run_opts* o, const void* psi_in, void* psi_out,
+                             const uint8_t* outcomes, float* ms, double* bytes, uint32_t* kind, uint32_t cap,
+                             uint32_t* nlaunch) {
+  clear_error();
+  if (!h || !o || !ms || !nlaunch) return set_error(OWQS_ERR_ARG, "NULL argument");
+  if (o->io != OWQS_IO_DEVICE) return set_error(OWQS_ERR_ARG, "profiling takes device vectors");
+  std::vector<uint8_t> oc;
+  if (outcomes) oc.assign(outcomes, outcomes + h->p.meas_qubit.size());
+  return run_impl(h->p, o, psi_in, psi_out, oc.empty() ? nullptr : oc.data(), nullptr, ms, bytes, kind, cap,
+                  nlaunch);
+}
+
+owqs_status owqs_get_index_map(const owqs_pattern* h, uint32_t pass, int32_t* bit_of_qubit) {
+  clear_error();
+  if (!h || !bit_of_qubit) return set_error(OWQS_ERR_ARG, "NULL argument");
+  FixedSource zero(h->p, nullptr);
+  std::vector<PassDesc> passes;
+  std::vector<std::vector<int32_t>> maps;
+  owqs_status st = compile_schedule(h->p, OWQS_MODE_EOWQS, zero, passes, &maps);
+  if (st != OWQS_OK) return st;
+  if (pass >= maps.size()) return set_error(OWQS_ERR_ARG, "pass index out of range");
+  std::copy(maps[pass].begin(), maps[pass].end(), bit_of_qubit);
+  return OWQS_OK;
+}
+
+owqs_status owqs_describe_passes(const owqs_pattern* h, uint32_t mode, const uint8_t* outcomes,
+                                 owqs_pass_desc* out, uint32_t cap, uint32_t* npass) {
+  clear_error();
+  if (!h || !npass || (cap && !out)) return set_error(OWQS_ERR_ARG, "NULL argument");
+  if (mode > OWQS_MODE_EOWQS) return set_error(OWQS_ERR_ARG, "bad mode");
+  FixedSource src(h->p, outcomes);
+  std::vector<PassDesc> passes;
+  owqs_status st = compile_schedule(h->p, (int)mode, src, passes);
+  if (st != OWQS_OK) return st;
+  *npass = (uint32_t)passes.size();
+  for (uint32_t i = 0; i < passes.size() && i < cap; ++i) {
+    const PassDesc& d = passes[i];
+    owqs_pass_desc& o = out[i];
+    std::memset(&o, 0, sizeof(o));
+    o.kind = d.kind;
+    o.n_in = d.n_in;
+    o.r = d.r;
+    o.b = d.b;
+    o.n_out = d.n_out;
+    o.outcome = d.outcome;
+    o.xmask = d.xmask;
+    o.zmask = d.zmask;
+    o.c0 = d.c0;
+    if (d.edges.size() > 64) return set_error(OWQS_ERR_UNSUPPORTED, "more than 64 sign terms in one pass");
+    o.nedges = (uint32_t)d.edges.size();
+    for (size_t e = 0; e < d.edges.size(); ++e) {
+      o.edges[e][0] = (uint32_t)d.edges[e].first;
+      o.edges[e][1] = (uint32_t)d.edges[e].second;
+    }
+    o.w1re = d.w1re;
+    o.w1im = d.w1im;
+    o.scale = d.scale;
+    for (size_t k = 0; k < d.perm.size() && k < 64; ++k) o.perm[k] = d.perm[k];
+  }
+  return OWQS_OK;
+}
+
+}  // extern "C"

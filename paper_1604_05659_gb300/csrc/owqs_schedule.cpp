@@ -1,0 +1,296 @@
+// Schedule compiler: turns the active command order into device passes.
+//
+// Each measurement closes a segment.  The segment's N commands are virtual
+// (Section 4.1: a new qubit is a tensor factor |+>; here it becomes a new top
+// bit that the pass broadcasts, never materialised), its E, X and Z commands
+// are folded into one sign function and one index XOR (Section 4.4.1: CZ
+// negates the amplitudes whose two bits are 1, Z negates the bit-1 half, X
+// exchanges the halves), and the measurement with elimination (Section 4.2,
+// Eqs. 11-13, Fig. 6) combines each amplitude pair that differs in the
+// measured bit into one output amplitude.  The surviving qubits keep their
+// relative order; bits above the measured one shift down.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "owqs_internal.h"
+
+namespace owqs {
+
+static inline int parity_of(const std::vector<int8_t>& outcome, const std::vector<uint32_t>& dom) {
+  int s = 0;
+  for (uint32_t d : dom) s ^= outcome[d];
+  return s;
+}
+
+// 2^(-h/2) with h >= 0, exact up to the final 1/sqrt2 rounding
+static inline double pow2_half(int h) {
+  return std::ldexp((h & 1) ? M_SQRT1_2 : 1.0, -(h / 2));
+}
+
+owqs_status compile_schedule(const Pattern& p, int mode, OutcomeSource& src,
+                             std::vector<PassDesc>& passes,
+                             std::vector<std::vector<int32_t>>* maps) {
+  passes.clear();
+  const uint32_t n = p.n;
+  std::vector<int32_t> bit_of(n, -1);
+  std::vector<uint32_t> at_bit;
+  std::vector<int8_t> outcome(n, 0);
+  const bool upfront = src.known_upfront(outcome);
+  if (!upfront && !p.deps_ok)
+    return set_error(OWQS_ERR_ARG, "sampled outcomes need an order that measures every domain first");
+  for (uint32_t q : p.inputs) {
+    bit_of[q] = (int32_t)at_bit.size();
+    at_bit.push_back(q);
+  }
+  if ((int)at_bit.size() > kMaxLive) return set_error(OWQS_ERR_OOM, "more than 62 input qubits");
+  int n_in = (int)at_bit.size();
+  uint64_t adj[64];
+  std::memset(adj, 0, sizeof(adj));
+  uint64_t z = 0, x = 0;
+  uint32_t c0 = 0;
+  if (maps) maps->push_back(bit_of);
+
+  bool overflow = false;
+  auto touch = [&](uint32_t q) -> int {
+    if (bit_of[q] >= 0) return bit_of[q];
+    if ((int)at_bit.size() >= kMaxLive) {
+      overflow = true;
+      return 0;
+    }
+    bit_of[q] = (int32_t)at_bit.size();
+    at_bit.push_back(q);
+    return bit_of[q];
+  };
+  auto edges_of = [&](PassDesc& d, int next) {
+    for (int u = 0; u < next; ++u) {
+      uint64_t m = adj[u] & ~((2ull << u) - 1);  // partners above u
+      while (m) {
+        int v = __builtin_ctzll(m);
+        m &= m - 1;
+        d.edges.emplace_back(u, v);
+      }
+    }
+  };
+
+  for (uint32_t idx : p.active) {
+    const Cmd& c = p.cmds[idx];
+    switch (c.kind) {
+      case OWQS_CMD_N:
+        break;  // prepared at first touch
+      case OWQS_CMD_E: {
+        int u = touch(c.q0), v = touch(c.q1);
+        if (overflow) break;
+        adj[u] ^= 1ull << v;
+        adj[v] ^= 1ull << u;
+        break;
+      }
+      case OWQS_CMD_Z: {
+        int u = touch(c.q0);
+        if (overflow) break;
+        if (parity_of(outcome, c.sdom)) z ^= 1ull << u;
+        break;
+      }
+      case OWQS_CMD_X: {
+        int u = touch(c.q0);
+        if (overflow) break;
+        // X_u D_q X^m = D_{q(. ^ e_u)} X^{m ^ e_u}: substituting k_u -> k_u ^ 1
+        // turns each edge (u,w) into a linear term on w and z_u into a constant
+        if (parity_of(outcome, c.sdom)) {
+          c0 ^= (uint32_t)((z >> u) & 1u);
+          z ^= adj[u];
+          x ^= 1ull << u;
+        }
+        break;
+      }
+      case OWQS_CMD_M: {
+        int b = touch(c.q0);
+        if (overflow) break;
+        const int next = (int)at_bit.size();
+        PassDesc d;
+        d.kind = 0;
+        d.n_in = n_in;
+        d.r = next - n_in;
+        d.b = b;
+        d.n_out = next - 1;
+        d.meas_k = (uint32_t)p.k_of_qubit[c.q0];
+        d.xmask = n_in ? (x & ((1ull << n_in) - 1)) : 0;  // X on a |+> qubit is dropped
+        d.zmask = z;
+        d.c0 = c0;
+        edges_of(d, next);
+        const int s = parity_of(outcome, c.sdom), t = parity_of(outcome, c.tdom);
+        // e^{-i theta}, theta = (-1)^s alpha + t pi (Eq. 2), t pi as an exact sign
+        double er = std::cos(c.angle), ei = s ? std::sin(c.angle) : -std::sin(c.angle);
+        if (t) er = -er, ei = -ei;
+        d.ere = er;
+        d.eim = ei;
+        d.scale = mode == OWQS_MODE_OWQS ? pow2_half(d.r + 1) : pow2_half(d.r);
+        int o = src.decide(d);
+        if (o < 0) return OWQS_ERR_CUDA;  // error recorded by the source
+        d.outcome = o & 1;
+        d.w1re = d.outcome ? -er : er;
+        d.w1im = d.outcome ? -ei : ei;
+        outcome[c.q0] = (int8_t)d.outcome;
+        passes.push_back(std::move(d));
+        // eliminate bit b (Section 4.2)
+        bit_of[c.q0] = -1;
+        at_bit.erase(at_bit.begin() + b);
+        for (size_t i = (size_t)b; i < at_bit.size(); ++i) bit_of[at_bit[i]] = (int32_t)i;
+        n_in = (int)at_bit.size();
+        std::memset(adj, 0, sizeof(adj));
+        z = x = 0;
+        c0 = 0;
+        if (maps) maps->push_back(bit_of);
+        break;
+      }
+      default:
+        return set_error(OWQS_ERR_ARG, "unknown command kind");
+    }
+    if (overflow) return set_error(OWQS_ERR_OOM, "live width above 62 qubits; reorder the pattern");
+  }
+  for (uint32_t q : p.outputs) touch(q);
+  if (overflow) return set_error(OWQS_ERR_OOM, "live width above 62 qubits");
+  if (at_bit.size() != p.outputs.size())
+    return set_error(OWQS_ERR_PATTERN, "live qubits at the end are not the outputs");
+  PassDesc f;
+  f.kind = 1;
+  f.n_in = n_in;
+  f.r = (int)at_bit.size() - n_in;
+  f.b = -1;
+  f.n_out = (int)at_bit.size();
+  f.xmask = n_in ? (x & ((1ull << n_in) - 1)) : 0;
+  f.zmask = z;
+  f.c0 = c0;
+  edges_of(f, (int)at_bit.size());
+  f.scale = pow2_half(f.r);
+  f.perm.resize(p.outputs.size());
+  for (size_t k = 0; k < p.outputs.size(); ++k) f.perm[k] = bit_of[p.outputs[k]];
+  passes.push_back(std::move(f));
+  return OWQS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch planning
+// ---------------------------------------------------------------------------
+static int g_max_grid = 0;
+
+int max_grid() {
+  if (g_max_grid == 0) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+      g_max_grid = sms * 8;  // 8 blocks of 256 threads fill an SM
+    else
+      g_max_grid = 152 * 8;
+  }
+  return g_max_grid;
+}
+
+static inline uint64_t ins0(uint64_t j, int b) {  // insert a 0 bit at position b
+  return ((j >> b) << (b + 1)) | (j & ((1ull << b) - 1));
+}
+
+static inline uint32_t par64(uint64_t v) { return (uint32_t)__builtin_parityll(v); }
+
+void plan_pass(const PassDesc& d, int dtype, bool virt_in, PassParams& P, LaunchPlan& L) {
+  std::memset(&P, 0, sizeof(P));
+  P.n_in = d.n_in;
+  P.r = d.r;
+  P.b = d.b;
+  P.n_out = d.n_out;
+  P.norm_in = -1;
+  P.norm_out = -1;
+  P.xmask = d.xmask;
+  P.zmask = d.zmask;
+  P.c0 = d.c0;
+  P.scale = d.scale;
+  P.w1re = d.w1re;
+  P.w1im = d.w1im;
+  P.ere = d.ere;
+  P.eim = d.eim;
+  P.vconst = virt_in ? std::ldexp((d.n_in & 1) ? M_SQRT1_2 : 1.0, -(d.n_in / 2)) : 0.0;
+  const double amp = dtype == OWQS_C64 ? 8.0 : 16.0;
+  const double in_elems = virt_in ? 0.0 : std::ldexp(1.0, d.n_in);
+  L.bytes = (in_elems + std::ldexp(1.0, d.n_out)) * amp;
+  L.block = kBlock;
+
+  // star form: every quadratic term contains the measured bit
+  bool star = d.kind == 0;
+  uint64_t amask = 0;
+  for (auto& e : d.edges) {
+    if (d.kind == 0 && (e.first == d.b || e.second == d.b)) {
+      amask ^= 1ull << (e.first == d.b ? e.second : e.first);
+    } else {
+      star = false;
+    }
+  }
+  // generic quadratic cover: greedy, highest remaining degree first
+  {
+    std::vector<std::pair<int, int>> rest = d.edges;
+    int nq = 0;
+    while (!rest.empty() && nq < kQMax) {
+      int deg[64] = {0};
+      for (auto& e : rest) deg[e.first]++, deg[e.second]++;
+      int best = 0;
+      for (int u = 1; u < 64; ++u)
+        if (deg[u] > deg[best]) best = u;
+      uint64_t m = 0;
+      std::vector<std::pair<int, int>> keep;
+      for (auto& e : rest) {
+        if (e.first == best) m ^= 1ull << e.second;
+        else if (e.second == best) m ^= 1ull << e.first;
+        else keep.push_back(e);
+      }
+      P.qu[nq] = best;
+      P.qa[nq] = m;
+      ++nq;
+      rest.swap(keep);
+    }
+    P.nq = nq;  // a graph on at most 62 bits has a vertex cover below 64
+  }
+
+  const int Lg = kFastL;
+  if (d.kind == 1) {
+    L.kind = KK_FINAL;
+    bool ident = true;
+    for (size_t k = 0; k < d.perm.size(); ++k) {
+      P.perm[k] = d.perm[k];
+      if (d.perm[k] != (int)k) ident = false;
+    }
+    P.identity_perm = ident ? 1 : 0;
+    uint64_t elems = 1ull << d.n_out;
+    L.grid = (int)std::min<uint64_t>((elems + kBlock - 1) / kBlock, (uint64_t)max_grid());
+    return;
+  }
+  const bool b_new = d.b >= d.n_in;
+  const int nlo = b_new ? d.n_in : d.n_in - 1;
+  const bool fast = !virt_in && d.xmask == 0 && star && nlo >= Lg &&
+                    (b_new || d.b >= Lg || d.n_in >= Lg + 1);
+  if (!fast) {
+    L.kind = KK_GENERIC;
+    uint64_t elems = 1ull << d.n_out;
+    L.grid = (int)std::min<uint64_t>((elems + kBlock - 1) / kBlock, (uint64_t)max_grid());
+    return;
+  }
+  L.kind = KK_FAST;
+  L.variant = b_new ? Lg + 1 : (d.b >= Lg ? Lg : d.b);
+  P.nlo = nlo;
+  const int nbc = d.n_out - nlo;
+  P.rt = std::min(nbc, kFastRMax);
+  P.amask = amask;
+  P.zb = (uint32_t)((d.zmask >> d.b) & 1u);
+  for (int l = 0; l < (1 << Lg); ++l) {
+    uint64_t dl = ins0((uint64_t)l, d.b);
+    P.tzl |= par64(dl & d.zmask) << l;
+    P.tal |= par64(dl & amask) << l;
+  }
+  for (int t = 0; t < (1 << P.rt); ++t) {
+    uint64_t dt = ins0((uint64_t)t << nlo, d.b);
+    P.tzt |= par64(dt & d.zmask) << t;
+    P.tat |= par64(dt & amask) << t;
+  }
+  uint64_t tiles = 1ull << (d.n_out - Lg - P.rt);
+  L.grid = (int)std::min<uint64_t>((tiles + kBlock - 1) / kBlock, (uint64_t)max_grid());
+}
+
+}  // namespace owqs

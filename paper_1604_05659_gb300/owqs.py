@@ -1,0 +1,282 @@
+"""Python binding of libowqs.so (ctypes; argument marshalling only).
+
+Every step of a simulation runs in the library's CUDA kernels; this module
+only converts patterns, options and buffers into the C ABI of include/owqs.h.
+If the library has not been built, library() raises: there is no Python or
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libowqs.so")
+
+OK, ERR_ARG, ERR_PATTERN, ERR_NOT_STANDARD, ERR_IMPOSSIBLE_BRANCH, ERR_NOT_DETERMINISTIC, \
+    ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(10)
+STATUS_NAMES = ["OK", "ERR_ARG", "ERR_PATTERN", "ERR_NOT_STANDARD", "ERR_IMPOSSIBLE_BRANCH",
+                "ERR_NOT_DETERMINISTIC", "ERR_OOM", "ERR_CUDA", "ERR_TIMEOUT", "ERR_UNSUPPORTED"]
+CMD_KIND = {"N": 0, "E": 1, "M": 2, "X": 3, "Z": 4}
+MODE = {"owqs": 0, "eowqs": 1}
+DTYPE = {"c64": 0, "c128": 1}
+POLICY = {"forced": 0, "sampled": 1, "zero": 2}
+KERNEL_KIND = {0: "fast_pass", 1: "generic_pass", 2: "final", 3: "norm", 4: "prob"}
+
+
+class OwqsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class owqs_cmd(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("q0", C.c_uint32), ("q1", C.c_uint32), ("pad_", C.c_uint32),
+                ("angle", C.c_double), ("s_off", C.c_uint32), ("s_len", C.c_uint32),
+                ("t_off", C.c_uint32), ("t_len", C.c_uint32)]
+
+
+class owqs_pattern_info(C.Structure):
+    _fields_ = [("nqubits", C.c_uint32), ("nin", C.c_uint32), ("nout", C.c_uint32), ("nmeas", C.c_uint32),
+                ("standard", C.c_uint32), ("peak_live", C.c_uint32), ("amp_updates", C.c_uint64)]
+
+
+class owqs_reorder_opts(C.Structure):
+    _fields_ = [("mode", C.c_uint32), ("product_input", C.c_uint32), ("sweep", C.c_uint32),
+                ("use_learned", C.c_uint32), ("alpha", C.c_double), ("beta", C.c_double),
+                ("gamma", C.c_double), ("delta", C.c_double)]
+
+
+class owqs_reorder_info(C.Structure):
+    _fields_ = [("peak_m", C.c_uint32), ("peak_live", C.c_uint32), ("amp_updates", C.c_uint64),
+                ("alpha_used", C.c_double), ("learned_accepted", C.c_uint32), ("pad_", C.c_uint32)]
+
+
+class owqs_run_opts(C.Structure):
+    _fields_ = [("dtype", C.c_uint32), ("mode", C.c_uint32), ("policy", C.c_uint32), ("io", C.c_uint32),
+                ("seed", C.c_uint64), ("stream", C.c_void_p), ("use_graph", C.c_uint32), ("pad_", C.c_uint32)]
+
+
+class owqs_pass_desc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_in", C.c_int32), ("r", C.c_int32), ("b", C.c_int32),
+                ("n_out", C.c_int32), ("outcome", C.c_int32), ("xmask", C.c_uint64), ("zmask", C.c_uint64),
+                ("c0", C.c_uint32), ("nedges", C.c_uint32), ("edges", (C.c_uint32 * 2) * 64),
+                ("w1re", C.c_double), ("w1im", C.c_double), ("scale", C.c_double), ("perm", C.c_int32 * 64)]
+
+
+EXPORTS = {
+    "owqs_load_pattern": (C.c_int, [C.c_uint32, C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32),
+                                    C.c_uint32, C.POINTER(owqs_cmd), C.c_size_t, C.POINTER(C.c_uint32),
+                                    C.c_size_t, C.POINTER(C.c_void_p)]),
+    "owqs_free_pattern": (None, [C.c_void_p]),
+    "owqs_get_info": (C.c_int, [C.c_void_p, C.POINTER(owqs_pattern_info)]),
+    "owqs_reorder": (C.c_int, [C.c_void_p, C.POINTER(owqs_reorder_opts), C.POINTER(owqs_reorder_info),
+                               C.POINTER(C.c_uint32)]),
+    "owqs_set_order": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.c_uint32]),
+    "owqs_reset_order": (C.c_int, [C.c_void_p]),
+    "owqs_get_order": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32)]),
+    "owqs_run": (C.c_int, [C.c_void_p, C.POINTER(owqs_run_opts), C.c_void_p, C.c_void_p,
+                           C.POINTER(C.c_uint8), C.POINTER(C.c_double)]),
+    "owqs_profile_run": (C.c_int, [C.c_void_p, C.POINTER(owqs_run_opts), C.c_void_p, C.c_void_p,
+                                   C.POINTER(C.c_uint8), C.POINTER(C.c_float), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32)]),
+    "owqs_get_index_map": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_int32)]),
+    "owqs_describe_passes": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_uint8), C.POINTER(owqs_pass_desc),
+                                       C.c_uint32, C.POINTER(C.c_uint32)]),
+    "owqs_last_error": (C.c_char_p, []),
+    "owqs_abi_version": (C.c_uint32, []),
+}
+
+_lib = None
+
+
+def library(path: str = LIB_PATH):
+    """Load libowqs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != OK:
+        raise OwqsError(st, library().owqs_last_error().decode())
+
+
+def _u32(a: Sequence[int]):
+    arr = (C.c_uint32 * max(1, len(a)))(*a)
+    return arr
+
+
+class Handle:
+    """A loaded pattern (owned by the library)."""
+
+    def __init__(self, pattern):
+        lib = library()
+        self.pattern = pattern
+        cmds = (owqs_cmd * max(1, len(pattern.cmds)))()
+        domain = []
+        for i, c in enumerate(pattern.cmds):
+            x = cmds[i]
+            x.kind = CMD_KIND[c.kind]
+            x.q0 = c.q0
+            x.q1 = c.q1 if c.kind == "E" else 0
+            x.angle = c.angle
+            x.s_off, x.s_len = len(domain), len(c.sdom)
+            domain += list(c.sdom)
+            x.t_off, x.t_len = len(domain), len(c.tdom)
+            domain += list(c.tdom)
+        h = C.c_void_p()
+        _check(lib.owqs_load_pattern(pattern.nqubits, _u32(pattern.inputs), len(pattern.inputs),
+                                     _u32(pattern.outputs), len(pattern.outputs), cmds, len(pattern.cmds),
+                                     _u32(domain), len(domain), C.byref(h)))
+        self._h = h
+        self.K = sum(1 for c in pattern.cmds if c.kind == "M")
+        self.nin = len(pattern.inputs)
+        self.nout = len(pattern.outputs)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            library().owqs_free_pattern(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- host-only calls -------------------------------------------------
+    def info(self) -> dict:
+        i = owqs_pattern_info()
+        _check(library().owqs_get_info(self._h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in owqs_pattern_info._fields_}
+
+    def reorder(self, mode: str = "owqs", product_input: bool = False, sweep: bool = True,
+                weights=(1.0, 1.0, 0.5, 1.0)):
+        o = owqs_reorder_opts(MODE[mode], int(product_input), int(sweep), 0, *weights)
+        info = owqs_reorder_info()
+        order = (C.c_uint32 * max(1, self.K))()
+        _check(library().owqs_reorder(self._h, C.byref(o), C.byref(info), order))
+        return list(order)[: self.K], {f: getattr(info, f) for f, _ in owqs_reorder_info._fields_ if f != "pad_"}
+
+    def set_order(self, order: Sequence[int]):
+        _check(library().owqs_set_order(self._h, _u32(order), len(order)))
+
+    def reset_order(self):
+        _check(library().owqs_reset_order(self._h))
+
+    def order(self):
+        out = (C.c_uint32 * max(1, self.K))()
+        _check(library().owqs_get_order(self._h, out))
+        return list(out)[: self.K]
+
+    def index_map(self, pass_index: int):
+        out = (C.c_int32 * self.pattern.nqubits)()
+        _check(library().owqs_get_index_map(self._h, pass_index, out))
+        return list(out)
+
+    def describe_passes(self, outcomes=None, mode: str = "owqs"):
+        n = C.c_uint32()
+        oc = _outcome_buf(outcomes, self.K)
+        _check(library().owqs_describe_passes(self._h, MODE[mode], oc, None, 0, C.byref(n)))
+        buf = (owqs_pass_desc * max(1, n.value))()
+        _check(library().owqs_describe_passes(self._h, MODE[mode], oc, buf, n.value, C.byref(n)))
+        return [buf[i] for i in range(n.value)]
+
+    # -- device calls ----------------------------------------------------
+    def run(self, psi_in=None, *, dtype: str = "c128", mode: str = "owqs", policy: str = "forced",
+            outcomes=None, seed: int = 0, stream=None, use_graph: bool = True, out=None,
+            check: bool = True):
+        """Run on the GPU.  psi_in: torch tensor on the GPU (complex64 for
+        c64, complex128 for c128) or None for |+> inputs; returns
+        (psi_out tensor, outcomes array, probs array, status)."""
+        import torch
+        tdt = torch.complex64 if dtype == "c64" else torch.complex128
+        if psi_in is not None:
+            if not psi_in.is_cuda or psi_in.dtype != tdt or not psi_in.is_contiguous():
+                raise ValueError("psi_in must be a contiguous CUDA tensor of the run's dtype")
+        dev = psi_in.device if psi_in is not None else torch.device("cuda", torch.cuda.current_device())
+        if out is None:
+            out = torch.empty(1 << self.nout, dtype=tdt, device=dev)
+        oc = np.zeros(max(1, self.K), dtype=np.uint8)
+        if outcomes is not None:
+            oc[: self.K] = np.asarray(outcomes, dtype=np.uint8)[: self.K]
+        probs = np.zeros(max(1, self.K), dtype=np.float64)
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        opts = owqs_run_opts(DTYPE[dtype], MODE[mode], POLICY[policy], 0, seed, C.c_void_p(s.cuda_stream),
+                             int(use_graph), 0)
+        st = library().owqs_run(self._h, C.byref(opts), C.c_void_p(psi_in.data_ptr() if psi_in is not None else 0),
+                                C.c_void_p(out.data_ptr()), oc.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                probs.ctypes.data_as(C.POINTER(C.c_double)))
+        if check and st not in (OK,):
+            _check(st)
+        return out, oc[: self.K].copy(), probs[: self.K].copy(), st
+
+    def run_host(self, psi_in: Optional[np.ndarray], out: np.ndarray, *, dtype: str = "c64",
+                 mode: str = "owqs", policy: str = "forced", outcomes=None, stream=None,
+                 use_graph: bool = True):
+        """Run with host vectors; the library copies them in and out."""
+        import torch
+        oc = np.zeros(max(1, self.K), dtype=np.uint8)
+        if outcomes is not None:
+            oc[: self.K] = np.asarray(outcomes, dtype=np.uint8)[: self.K]
+        probs = np.zeros(max(1, self.K), dtype=np.float64)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        opts = owqs_run_opts(DTYPE[dtype], MODE[mode], POLICY[policy], 1, 0, C.c_void_p(s.cuda_stream),
+                             int(use_graph), 0)
+        pin = 0 if psi_in is None else _host_ptr(psi_in)
+        _check(library().owqs_run(self._h, C.byref(opts), C.c_void_p(pin), C.c_void_p(_host_ptr(out)),
+                                  oc.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                  probs.ctypes.data_as(C.POINTER(C.c_double))))
+        return oc[: self.K].copy(), probs[: self.K].copy()
+
+    def profile(self, psi_in=None, *, dtype: str = "c64", mode: str = "owqs", policy: str = "forced",
+                outcomes=None, stream=None, out=None):
+        """Per-launch CUDA-event durations of one run (no graph)."""
+        import torch
+        tdt = torch.complex64 if dtype == "c64" else torch.complex128
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if out is None:
+            out = torch.empty(1 << self.nout, dtype=tdt, device=dev)
+        cap = 4 * self.K + 16
+        ms = (C.c_float * cap)()
+        by = (C.c_double * cap)()
+        kd = (C.c_uint32 * cap)()
+        n = C.c_uint32()
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        opts = owqs_run_opts(DTYPE[dtype], MODE[mode], POLICY[policy], 0, 0, C.c_void_p(s.cuda_stream), 0, 0)
+        oc = _outcome_buf(outcomes, self.K)
+        _check(library().owqs_profile_run(self._h, C.byref(opts),
+                                          C.c_void_p(psi_in.data_ptr() if psi_in is not None else 0),
+                                          C.c_void_p(out.data_ptr()), oc, ms, by, kd, cap, C.byref(n)))
+        k = min(n.value, cap)
+        return np.array(ms[:k]), np.array(by[:k]), np.array(kd[:k]), out
+
+
+def _host_ptr(a) -> int:
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _outcome_buf(outcomes, K):
+    if outcomes is None:
+        return None
+    arr = (C.c_uint8 * max(1, K))(*[int(x) & 1 for x in list(outcomes)[:K]])
+    return arr
+
+
+def load(pattern) -> Handle:
+    return Handle(pattern)

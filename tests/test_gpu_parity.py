@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: complex128 amplitudes and probabilities within 1e-12 max-abs of
+the oracle, complex64 within 2e-5 max-abs after global-phase alignment
+(forced-outcome results carry no phase freedom, so the alignment is a no-op
+up to rounding).  Outcome bits and index maps are compared exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import proa, substate
+from owqs_inputs import workloads
+from owqs_inputs.patterns import E, M, N, Pattern, X, Z, circuit_to_pattern, random_jcz_circuit
+from owqs_inputs.rng import SplitMix64, random_state
+
+from helpers import outcomes_by_label, phase_aligned_maxabs
+from test_oracle_pins import _wild_patterns, cnot_eq22
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-12, "c64": 2e-5}
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1604_05659_gb300 import build, owqs
+    build.ensure_built()
+    owqs.library()
+    return torch, owqs
+
+
+def _dev(torch, psi, dtype):
+    if psi is None:
+        return None
+    t = torch.complex64 if dtype == "c64" else torch.complex128
+    return torch.from_numpy(np.asarray(psi, dtype=np.complex128)).to(t).cuda()
+
+
+def _oracle_for(h, p):
+    order = h.order()
+    return proa.reorder_commands(p, order) if p.is_standard() else p
+
+
+def _compare(env, p, psi, bits, dtype, mode, reorder=True, graph=True):
+    torch, owqs = env
+    h = owqs.load(p)
+    if reorder and p.is_standard():
+        h.reorder()
+    op = _oracle_for(h, p) if reorder and p.is_standard() else p
+    out, oc, probs, st = h.run(_dev(torch, psi, dtype), dtype=dtype, mode=mode, outcomes=bits, use_graph=graph)
+    torch.cuda.synchronize()
+    ref = substate.run(op, psi, outcomes=outcomes_by_label(p, bits), mode=mode)
+    got = out.cpu().numpy().astype(np.complex128)
+    err = phase_aligned_maxabs(ref.psi_out, got) if dtype == "c64" else float(np.max(np.abs(ref.psi_out - got)))
+    assert err <= TOL[dtype], (p.name, dtype, mode, err)
+    if mode == "owqs":
+        ref_p = np.array([ref.probs[q] for q in p.measured()])
+        assert np.max(np.abs(probs - ref_p)) <= (1e-12 if dtype == "c128" else 1e-5)
+    else:
+        assert np.all(probs == 0.5)
+    return h, got
+
+
+def _small_cases():
+    cases = [cnot_eq22(), workloads.small_random().pattern, workloads.brickwork(6, 10).pattern,
+             workloads.qft(5, with_input=False).pattern]
+    cases += [w.pattern for w in workloads.random_batch(count=8, wmin=3, wmax=9, dmin=3, dmax=10)]
+    return cases
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("mode", ["owqs", "eowqs"])
+def test_small_patterns(env, dtype, mode):
+    rng = SplitMix64(101)
+    for p in _small_cases():
+        psi = random_state(rng, len(p.inputs))
+        bits = rng.bits(p.K)
+        _compare(env, p, psi, bits, dtype, mode)
+        _compare(env, p, None, bits, dtype, mode)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_wild_patterns_pattern_order(env, dtype):
+    """X/Z between measurements and every E up front (generic kernel, X
+    masks, non-star sign functions)."""
+    rng = SplitMix64(102)
+    for p in _wild_patterns():
+        psi = random_state(rng, len(p.inputs))
+        for _ in range(2):
+            _compare(env, p, psi, rng.bits(p.K), dtype, "owqs", reorder=False)
+
+
+def _medium_cases():
+    """Several thread tiles and every fast-kernel case: measured bit 0 and 1,
+    a middle bit, a newly prepared bit; widths 10-17."""
+    cases = [workloads.brickwork(12, 16).pattern, workloads.qft(11, with_input=False).pattern]
+    for i in range(4):
+        rng = SplitMix64(900 + i)
+        n = 10 + rng.randint(5)
+        cases.append(circuit_to_pattern(n, random_jcz_circuit(n, 6, rng, cz_per_layer=3), f"rand{n}"))
+    return cases
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_medium_patterns_tiles(env, dtype):
+    torch, owqs = env
+    rng = SplitMix64(103)
+    kinds = set()
+    for p in _medium_cases():
+        psi = random_state(rng, len(p.inputs))
+        bits = rng.bits(p.K)
+        h, _ = _compare(env, p, psi, bits, dtype, "owqs")
+        ms, by, kd, _ = h.profile(_dev(torch, psi, dtype), dtype=dtype, outcomes=bits)
+        kinds |= set(int(k) for k in kd)
+    assert 0 in kinds and 2 in kinds   # fast passes and the final pass ran
+
+
+def test_fast_kernel_variants_covered(env):
+    """The medium cases hit the measured-bit cases 0, 1, middle and new."""
+    torch, owqs = env
+    seen = set()
+    for p in _medium_cases():
+        h = owqs.load(p)
+        h.reorder()
+        for d in h.describe_passes(np.zeros(p.K, np.uint8)):
+            if d.kind:
+                continue
+            if d.b >= d.n_in:
+                seen.add("new")
+            elif d.b >= 2:
+                seen.add("mid")
+            else:
+                seen.add(d.b)
+    assert {0, 1, "mid", "new"} <= seen, seen
+
+
+def test_graph_replay_matches_direct(env):
+    torch, owqs = env
+    wl = workloads.brickwork(10, 12)
+    h = owqs.load(wl.pattern)
+    h.reorder()
+    outs = []
+    for graph in (False, True, True):
+        out, _, probs, _ = h.run(None, dtype="c64", outcomes=wl.outcomes, use_graph=graph)
+        torch.cuda.synchronize()
+        outs.append((out.cpu().numpy(), probs))
+    for o, p in outs[1:]:
+        assert np.array_equal(o, outs[0][0]) and np.array_equal(p, outs[0][1])
+
+
+def test_sampled_outcomes_follow_the_oracle_stream(env):
+    torch, owqs = env
+    rng = SplitMix64(104)
+    for p in _small_cases()[:6]:
+        psi = random_state(rng, len(p.inputs))
+        h = owqs.load(p)
+        h.reorder()
+        op = _oracle_for(h, p)
+        for seed in (1, 2, 3):
+            out, oc, probs, _ = h.run(_dev(torch, psi, "c128"), dtype="c128", policy="sampled", seed=seed)
+            ref = substate.run(op, psi, policy="sampled", seed=seed)
+            assert [int(oc[k]) for k in range(p.K)] == [ref.outcomes[q] for q in p.measured()]
+            assert np.max(np.abs(out.cpu().numpy() - ref.psi_out)) <= 1e-12
+
+
+def test_host_io_matches_device_io(env):
+    torch, owqs = env
+    wl = workloads.qft(8)
+    h = owqs.load(wl.pattern)
+    h.reorder()
+    dev, _, pd, _ = h.run(_dev(torch, wl.psi_in, "c64"), dtype="c64", outcomes=wl.outcomes)
+    host_in = torch.from_numpy(wl.psi_in.astype(np.complex64)).pin_memory()
+    host_out = torch.empty(1 << 8, dtype=torch.complex64).pin_memory()
+    oc, ph = h.run_host(host_in, host_out, dtype="c64", outcomes=wl.outcomes)
+    assert np.array_equal(host_out.numpy(), dev.cpu().numpy()) and np.array_equal(ph, pd)
+
+
+def test_impossible_branch_and_eowqs_check(env):
+    torch, owqs = env
+    p = Pattern(2, [0], [1], [N(1), M(0, 0.0)])          # |+> measured at angle 0
+    plus = np.array([1, 1]) / math.sqrt(2)
+    h = owqs.load(p)
+    out, _, probs, st = h.run(_dev(torch, plus, "c128"), dtype="c128", outcomes=[1], check=False)
+    assert st == owqs.ERR_IMPOSSIBLE_BRANCH and probs[0] < 1e-24
+    assert np.all(out.cpu().numpy() == 0)
+    out, _, probs, st = h.run(_dev(torch, plus, "c128"), dtype="c128", outcomes=[0], check=False)
+    assert st == owqs.OK and abs(probs[0] - 1) < 1e-15
+    # EOWQS on a pattern without flow: the output norm is 2, flagged
+    out, _, _, st = h.run(_dev(torch, plus, "c128"), dtype="c128", mode="eowqs", outcomes=[0], check=False)
+    assert st == owqs.ERR_NOT_DETERMINISTIC
+    with pytest.raises(owqs.OwqsError):
+        h.run(_dev(torch, plus, "c64"), dtype="c128", outcomes=[0])   # dtype mismatch caught in binding
+
+
+def test_qft24_full_size_closed_form(env):
+    """QFT-shaped pattern on 24 logical qubits (2784 measurements, peak 25):
+    the output equals the discrete Fourier transform of the bit-reversed
+    input (the circuit has no final swaps) up to a global phase."""
+    torch, owqs = env
+    wl = workloads.qft(24)
+    h = owqs.load(wl.pattern)
+    _, info = h.reorder()
+    assert info["peak_m"] == 25
+    n = 24
+    idx = np.arange(1 << n, dtype=np.int64)
+    rev = np.zeros_like(idx)
+    for b in range(n):
+        rev |= ((idx >> b) & 1) << (n - 1 - b)
+    ref = np.fft.ifft(wl.psi_in[rev]) * math.sqrt(1 << n)     # sum_x e^{+2 pi i x y / N} / sqrt(N)
+    for dtype in ("c128", "c64"):
+        out, _, probs, _ = h.run(_dev(torch, wl.psi_in, dtype), dtype=dtype, outcomes=wl.outcomes)
+        got = out.cpu().numpy().astype(np.complex128)
+        err = phase_aligned_maxabs(ref, got)
+        assert err <= (1e-11 if dtype == "c128" else 2e-5), (dtype, err)
+        assert np.max(np.abs(probs - 0.5)) <= (1e-12 if dtype == "c128" else 1e-5)
+
+
+def test_brickwork_full_size_properties(env):
+    """Brickwork 28 x 40 (1092 measurements, 2^28 live amplitudes): every
+    branch probability is 1/2 (flow pattern, Section 4.5), the output is
+    normalised, complex64 agrees with complex128 and a second outcome branch
+    gives the same state up to a global phase."""
+    torch, owqs = env
+    wl = workloads.brickwork(28, 40)
+    h = owqs.load(wl.pattern)
+    _, info = h.reorder()
+    assert info["peak_m"] == 29 and info["peak_live"] == 29
+    o128, _, p128, _ = h.run(None, dtype="c128", outcomes=wl.outcomes)
+    assert np.max(np.abs(p128 - 0.5)) <= 1e-12
+    o64, _, p64, _ = h.run(None, dtype="c64", outcomes=wl.outcomes)
+    assert np.max(np.abs(p64 - 0.5)) <= 1e-5
+    d = (o64.to(torch.complex128) - o128)
+    ov = torch.vdot(o64.to(torch.complex128), o128)
+    assert abs(abs(ov.item()) - 1) < 1e-5
+    assert torch.max(torch.abs(o64.to(torch.complex128) * (ov / abs(ov)) - o128)).item() <= 2e-5
+    assert abs(torch.linalg.vector_norm(o128).item() - 1) < 1e-12
+    other = SplitMix64(55).bits(wl.pattern.K)
+    o2, _, _, _ = h.run(None, dtype="c64", outcomes=other)
+    ov2 = torch.vdot(o2, o64)
+    assert abs(abs(ov2.item()) - 1) < 1e-4
+    del d
