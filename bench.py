@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rows", type=int, default=ROWS)
     ap.add_argument("--cols", type=int, default=COLS)
+    ap.add_argument("--legs", default="c64,c128,e2e,cpu",
+                    help="comma list of c64 (always run), c128, e2e, cpu; fewer legs for profiler runs")
     return ap.parse_args()
 
 
@@ -256,36 +258,45 @@ def run_owqs(args):
                 "share_of_step": share, "bytes_per_launch": float(by[sel].mean()),
                 "avg_launch_ms": float(ms[sel].mean()), "peak_source": f"{peak_kind} hbm_gbs (copy, burst)"}, len(ms)
 
+    legs = set(args.legs.split(","))
     roof64, launches_per_step = roofline("c64")
 
-    # FP64 (complex128) path on the same workload
-    out128 = torch.empty(1 << nout, dtype=torch.complex128, device="cuda")
-    run128 = lambda: h.run(None, dtype="c128", outcomes=wl.outcomes, out=out128)
-    run128()
-    t128 = timed(run128, args.fp64_steps)
-    roof128, _ = roofline("c128")
-    _, _, p128, _ = h.run(None, dtype="c128", outcomes=wl.outcomes, out=out128)
-    _, _, p64, _ = run64()
-    a = out64.to(torch.complex128)
-    ov = torch.vdot(a, out128)
-    amp_err = torch.max(torch.abs(a * (ov / abs(ov)) - out128)).item()
-    prob_err = float(np.max(np.abs(p64 - p128)))
-    del a
+    fp64, accuracy = None, None
+    if "c128" in legs:
+        # FP64 (complex128) path on the same workload
+        out128 = torch.empty(1 << nout, dtype=torch.complex128, device="cuda")
+        run128 = lambda: h.run(None, dtype="c128", outcomes=wl.outcomes, out=out128)
+        run128()
+        t128 = timed(run128, args.fp64_steps)
+        roof128, _ = roofline("c128")
+        _, _, p128, _ = h.run(None, dtype="c128", outcomes=wl.outcomes, out=out128)
+        _, _, p64, _ = run64()
+        a = out64.to(torch.complex128)
+        ov = torch.vdot(a, out128)
+        amp_err = torch.max(torch.abs(a * (ov / abs(ov)) - out128)).item()
+        prob_err = float(np.max(np.abs(p64 - p128)))
+        del a, out128
+        fp64 = {"dtype": "c128", "value": upd * args.fp64_steps * world / t128,
+                "ms_per_step": 1e3 * t128 / args.fp64_steps, "roofline": roof128}
+        accuracy = {"c64_vs_c128_max_abs_amp_err": amp_err, "c64_vs_c128_max_prob_err": prob_err, "bound": 2e-5}
 
-    # end to end through the public call with host vectors: the |+>^28 input
-    # is copied in from pinned memory and the output copied back every step
-    nin = len(p.inputs)
-    host_in = torch.full((1 << nin,), complex(2.0 ** (-nin / 2.0), 0.0), dtype=torch.complex64).pin_memory()
-    host_out = torch.empty(1 << nout, dtype=torch.complex64).pin_memory()
-    run_e2e = lambda: h.run_host(host_in, host_out, dtype="c64", outcomes=wl.outcomes)
-    run_e2e()
-    te = timed(run_e2e, args.e2e_steps)
-    e2e = {"value": upd * args.e2e_steps * world / te, "unit": UNIT,
-           "h2d_bytes_per_step": (1 << nin) * 8, "d2h_bytes_per_step": (1 << nout) * 8 + 8 * (p.K + 2),
-           "ms_per_step": 1e3 * te / args.e2e_steps}
+    e2e = None
+    if "e2e" in legs:
+        # end to end through the public call with host vectors: the |+>^28
+        # input is copied in from pinned memory and the output copied back
+        # every step
+        nin = len(p.inputs)
+        host_in = torch.full((1 << nin,), complex(2.0 ** (-nin / 2.0), 0.0), dtype=torch.complex64).pin_memory()
+        host_out = torch.empty(1 << nout, dtype=torch.complex64).pin_memory()
+        run_e2e = lambda: h.run_host(host_in, host_out, dtype="c64", outcomes=wl.outcomes)
+        run_e2e()
+        te = timed(run_e2e, args.e2e_steps)
+        e2e = {"value": upd * args.e2e_steps * world / te, "unit": UNIT,
+               "h2d_bytes_per_step": (1 << nin) * 8, "d2h_bytes_per_step": (1 << nout) * 8 + 8 * (p.K + 2),
+               "ms_per_step": 1e3 * te / args.e2e_steps}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and "cpu" in legs:
         v, desc, dt = oracle_sample(22, args.cols, target_s=15.0)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "seconds": dt}
 
@@ -301,10 +312,8 @@ def run_owqs(args):
                        "outcomes": "forced seeded bits, same every step; schedule compiled every call, "
                                    "kernels replayed from a CUDA graph"},
             "roofline": roof64,
-            "fp64": {"dtype": "c128", "value": upd * args.fp64_steps * world / t128,
-                     "ms_per_step": 1e3 * t128 / args.fp64_steps, "roofline": roof128},
-            "accuracy": {"c64_vs_c128_max_abs_amp_err": amp_err, "c64_vs_c128_max_prob_err": prob_err,
-                         "bound": 2e-5},
+            "fp64": fp64,
+            "accuracy": accuracy,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks,

@@ -114,13 +114,18 @@ enum KernelKind { KK_FAST = 0, KK_GENERIC = 1, KK_FINAL = 2, KK_NORM = 3, KK_PRO
 
 struct LaunchPlan {
   int kind = KK_GENERIC;
-  int variant = 0;       // fast: measured-bit case
+  int variant = 0;       // fast: measured-bit case (b < lg: b; lg: middle bit; lg+1: new qubit)
+  int lg = 2;            // fast: log2 of consecutive outputs per thread tile
+  int hint = 0;          // fast: 1 = streaming (evict-first) loads and stores
   int grid = 1, block = 256;
   double bytes = 0;      // algorithmic bytes (amplitudes read + written)
 };
 
-constexpr int kFastL = 2;     // log2 of consecutive outputs per thread tile
 constexpr int kFastRMax = 2;  // broadcast bits handled inside a thread
+
+// Fast-pass configuration for a dtype: tile width (c64: 2 or 3, c128: 1 or 2)
+// and cache hint.  OWQS_FAST="lg,hint" overrides the default (tuning runs).
+void fast_config(int dtype, int* lg, int* hint);
 constexpr int kBlock = 256;
 int max_grid();               // grid cap for grid-stride kernels
 

@@ -11,6 +11,8 @@
 //
 // Contract with the schedule compiler: see PassDesc in owqs_internal.h.
 #include <cstdint>
+#include <map>
+#include <mutex>
 
 #include "owqs_internal.h"
 
@@ -194,36 +196,50 @@ __global__ void __launch_bounds__(kBlock) k_generic(const PassParams P) {
 //   BM == L  : L <= b < n_in, two aligned runs of 2^L, 2^b apart
 //   BM == L+1: b is a new qubit, both partners read the same amplitude
 // ---------------------------------------------------------------------------
-template <int N>
+// 16-byte vector loads and stores of aligned runs; HINT 1 marks them
+// evict-first (each amplitude is read and written once per pass)
+template <int HINT, typename V>
+__device__ __forceinline__ V ld16(const V* p) {
+  if constexpr (HINT) return __ldcs(p);
+  else return *p;
+}
+template <int HINT, typename V>
+__device__ __forceinline__ void st16(V* p, const V& v) {
+  if constexpr (HINT) __stcs(p, v);
+  else *p = v;
+}
+template <int HINT, int N>
 __device__ __forceinline__ void ld_run(float2 (&v)[N], const float2* p) {
+  static_assert(N % 2 == 0, "float2 runs move in pairs");
   const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
   for (int i = 0; i < N / 2; ++i) {
-    const float4 t = q[i];
+    const float4 t = ld16<HINT>(q + i);
     v[2 * i] = make_float2(t.x, t.y);
     v[2 * i + 1] = make_float2(t.z, t.w);
   }
 }
-template <int N>
+template <int HINT, int N>
 __device__ __forceinline__ void ld_run(double2 (&v)[N], const double2* p) {
 #pragma unroll
-  for (int i = 0; i < N; ++i) v[i] = p[i];
+  for (int i = 0; i < N; ++i) v[i] = ld16<HINT>(p + i);
 }
-template <int N>
+template <int HINT, int N>
 __device__ __forceinline__ void st_run(float2* p, const float2 (&v)[N]) {
   float4* q = reinterpret_cast<float4*>(p);
 #pragma unroll
-  for (int i = 0; i < N / 2; ++i) q[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+  for (int i = 0; i < N / 2; ++i)
+    st16<HINT>(q + i, make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y));
 }
-template <int N>
+template <int HINT, int N>
 __device__ __forceinline__ void st_run(double2* p, const double2 (&v)[N]) {
 #pragma unroll
-  for (int i = 0; i < N; ++i) p[i] = v[i];
+  for (int i = 0; i < N; ++i) st16<HINT>(p + i, v[i]);
 }
 
 __host__ __device__ constexpr int ins0c(int l, int b) { return ((l >> b) << (b + 1)) | (l & ((1 << b) - 1)); }
 
-template <typename T, int L, int BM>
+template <typename T, int L, int BM, int HINT>
 __global__ void __launch_bounds__(kBlock) k_fast(const PassParams P) {
   using V = typename Cplx<T>::V;
   constexpr int NL = 1 << L;
@@ -248,17 +264,17 @@ __global__ void __launch_bounds__(kBlock) k_fast(const PassParams P) {
     V v0[NL], v1[NL];
     if constexpr (BM < L) {
       V run[2 * NL];
-      ld_run(run, in + ib);
+      ld_run<HINT>(run, in + ib);
 #pragma unroll
       for (int l = 0; l < NL; ++l) {
         v0[l] = run[ins0c(l, BM)];
         v1[l] = run[ins0c(l, BM) | (1 << BM)];
       }
     } else if constexpr (BM == L) {
-      ld_run(v0, in + ib);
-      ld_run(v1, in + ib + (1ull << b));
+      ld_run<HINT>(v0, in + ib);
+      ld_run<HINT>(v1, in + ib + (1ull << b));
     } else {
-      ld_run(v0, in + ib);
+      ld_run<HINT>(v0, in + ib);
 #pragma unroll
       for (int l = 0; l < NL; ++l) v1[l] = v0[l];
     }
@@ -279,7 +295,7 @@ __global__ void __launch_bounds__(kBlock) k_fast(const PassParams P) {
         y[l].y = a * v0[l].y + br * v1[l].y + bi * v1[l].x;
         tacc += y[l].x * y[l].x + y[l].y * y[l].y;
       }
-      st_run(out + J + ((uint64_t)t << nlo), y);
+      st_run<HINT>(out + J + ((uint64_t)t << nlo), y);
     }
     acc += (double)tacc;
   }
@@ -306,41 +322,80 @@ __global__ void __launch_bounds__(kBlock) k_norm(const void* vin, uint64_t n, do
 }
 
 // ---------------------------------------------------------------------------
-// launch wrappers
+// launch wrappers.  Grid-stride kernels get at most as many blocks as can be
+// resident at once (occupancy x SMs), so every block runs in one wave.
 // ---------------------------------------------------------------------------
+template <typename K>
+static int resident_grid(K kernel, int want) {
+  static std::mutex mu;
+  static std::map<const void*, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find((const void*)kernel);
+  int cap;
+  if (it != cache.end()) {
+    cap = it->second;
+  } else {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess || per_sm <= 0)
+      per_sm = 1;
+    cap = std::min(per_sm * (max_grid() / 8), max_grid());
+    cache[(const void*)kernel] = cap;
+  }
+  return std::max(1, std::min(want, cap));
+}
+
+template <typename K>
+static void go(K kernel, const PassParams& P, int want, cudaStream_t s) {
+  kernel<<<resident_grid(kernel, want), kBlock, 0, s>>>(P);
+}
+
+template <typename T, int L, int HINT>
+static cudaError_t launch_fast(const PassParams& P, const LaunchPlan& Lp, cudaStream_t s) {
+  static_assert(L >= 1 && L <= 3, "tile width");
+  switch (Lp.variant) {
+    case 0: go(k_fast<T, L, 0, HINT>, P, Lp.grid, s); break;
+    case 1: go(k_fast<T, L, (L > 1 ? 1 : L), HINT>, P, Lp.grid, s); break;
+    case 2: go(k_fast<T, L, (L > 2 ? 2 : (L == 2 ? L : L + 1)), HINT>, P, Lp.grid, s); break;
+    case 3: go(k_fast<T, L, (L == 3 ? L : L + 1), HINT>, P, Lp.grid, s); break;
+    case 4: go(k_fast<T, L, L + 1, HINT>, P, Lp.grid, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
 template <typename T>
 static cudaError_t launch_t(const PassParams& P, const LaunchPlan& L, cudaStream_t s) {
-  const dim3 g(L.grid), blk(L.block);
   const bool virt = P.in == nullptr;
   switch (L.kind) {
-    case KK_FAST:
-      switch (L.variant) {
-        case 0: k_fast<T, kFastL, 0><<<g, blk, 0, s>>>(P); break;
-        case 1: k_fast<T, kFastL, 1><<<g, blk, 0, s>>>(P); break;
-        case kFastL: k_fast<T, kFastL, kFastL><<<g, blk, 0, s>>>(P); break;
-        case kFastL + 1: k_fast<T, kFastL, kFastL + 1><<<g, blk, 0, s>>>(P); break;
-        default: return cudaErrorInvalidValue;
+    case KK_FAST: {
+      cudaError_t e = cudaErrorInvalidValue;
+      if constexpr (sizeof(T) == 4) {
+        if (L.lg == 2) e = L.hint ? launch_fast<T, 2, 1>(P, L, s) : launch_fast<T, 2, 0>(P, L, s);
+        else if (L.lg == 3) e = L.hint ? launch_fast<T, 3, 1>(P, L, s) : launch_fast<T, 3, 0>(P, L, s);
+      } else {
+        if (L.lg == 1) e = L.hint ? launch_fast<T, 1, 1>(P, L, s) : launch_fast<T, 1, 0>(P, L, s);
+        else if (L.lg == 2) e = L.hint ? launch_fast<T, 2, 1>(P, L, s) : launch_fast<T, 2, 0>(P, L, s);
       }
+      if (e != cudaSuccess) return e;
       break;
+    }
     case KK_GENERIC:
-      if (virt) k_generic<T, 0, true><<<g, blk, 0, s>>>(P);
-      else k_generic<T, 0, false><<<g, blk, 0, s>>>(P);
+      if (virt) go(k_generic<T, 0, true>, P, L.grid, s);
+      else go(k_generic<T, 0, false>, P, L.grid, s);
       break;
     case KK_PROB:
-      if (virt) k_generic<T, 1, true><<<g, blk, 0, s>>>(P);
-      else k_generic<T, 1, false><<<g, blk, 0, s>>>(P);
+      if (virt) go(k_generic<T, 1, true>, P, L.grid, s);
+      else go(k_generic<T, 1, false>, P, L.grid, s);
       break;
     case KK_FINAL:
-      if (virt) k_generic<T, 2, true><<<g, blk, 0, s>>>(P);
-      else k_generic<T, 2, false><<<g, blk, 0, s>>>(P);
+      if (virt) go(k_generic<T, 2, true>, P, L.grid, s);
+      else go(k_generic<T, 2, false>, P, L.grid, s);
       break;
     default:
       return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
-
-static_assert(kFastL == 2, "launch_t instantiates the low-bit variants for L = 2");
 
 cudaError_t launch_pass(const PassParams& P, const LaunchPlan& L, int dtype, cudaStream_t s) {
   return dtype == OWQS_C64 ? launch_t<float>(P, L, s) : launch_t<double>(P, L, s);

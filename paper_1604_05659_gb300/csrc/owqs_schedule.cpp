@@ -11,6 +11,8 @@
 // relative order; bits above the measured one shift down.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "owqs_internal.h"
@@ -186,6 +188,27 @@ int max_grid() {
   return g_max_grid;
 }
 
+void fast_config(int dtype, int* lg, int* hint) {
+  static int cfg[2][2] = {{-1, -1}, {-1, -1}};
+  int d = dtype == OWQS_C64 ? 0 : 1;
+  if (cfg[d][0] < 0) {
+    // measured on GB300 (brickwork 28x40, 2^28 amplitudes per pass): c64 with
+    // 8 outputs (64 bytes) per run 0.730 ms/pass vs 0.769 ms with 4; c128 with
+    // 4 outputs 4.44 ms vs 4.65 ms with 2; evict-first hints made no difference
+    cfg[0][0] = 3, cfg[0][1] = 0;
+    cfg[1][0] = 2, cfg[1][1] = 0;
+    if (const char* e = std::getenv(d == 0 ? "OWQS_FAST_C64" : "OWQS_FAST_C128")) {
+      int a = -1, b = -1;
+      if (std::sscanf(e, "%d,%d", &a, &b) == 2) {
+        const bool ok = d == 0 ? (a == 2 || a == 3) : (a == 1 || a == 2);
+        if (ok && (b == 0 || b == 1)) cfg[d][0] = a, cfg[d][1] = b;
+      }
+    }
+  }
+  *lg = cfg[d][0];
+  *hint = cfg[d][1];
+}
+
 static inline uint64_t ins0(uint64_t j, int b) {  // insert a 0 bit at position b
   return ((j >> b) << (b + 1)) | (j & ((1ull << b) - 1));
 }
@@ -249,7 +272,8 @@ void plan_pass(const PassDesc& d, int dtype, bool virt_in, PassParams& P, Launch
     P.nq = nq;  // a graph on at most 62 bits has a vertex cover below 64
   }
 
-  const int Lg = kFastL;
+  int Lg = 2, hint = 0;
+  fast_config(dtype, &Lg, &hint);
   if (d.kind == 1) {
     L.kind = KK_FINAL;
     bool ident = true;
@@ -273,6 +297,8 @@ void plan_pass(const PassDesc& d, int dtype, bool virt_in, PassParams& P, Launch
     return;
   }
   L.kind = KK_FAST;
+  L.lg = Lg;
+  L.hint = hint;
   L.variant = b_new ? Lg + 1 : (d.b >= Lg ? Lg : d.b);
   P.nlo = nlo;
   const int nbc = d.n_out - nlo;
