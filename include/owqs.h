@@ -190,6 +190,31 @@ typedef struct {
 owqs_status owqs_run(owqs_pattern* p, const owqs_run_opts* opts, const void* psi_in,
                      void* psi_out, uint8_t* outcomes, double* probs);
 
+/* owqs_run without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc, such as
+ * code running while a CUDA stream is being captured into a graph (where
+ * allocation calls are not allowed), or a host program whose device memory
+ * is entirely owned by another allocator or held to a fixed budget.  The
+ * caller passes the input and output vectors exactly as for owqs_run; the
+ * library's scratch (two state buffers, the norm slots, the reduction
+ * partials and a counter) lives in one statically sized device array of
+ * 8.25 MiB that every GPU loading this library holds until the process
+ * exits.
+ * Limits: device vectors only (io = OWQS_IO_DEVICE), forced or zero outcomes,
+ * no CUDA graph, every pass must fit the 4 MiB state buffers (live width at
+ * most 19 qubits for OWQS_C64, 18 for OWQS_C128), and at most 5448
+ * measurements.  Larger patterns get OWQS_ERR_ARG with the sizes in
+ * owqs_last_error().  Nothing else is allocated on the device; the call
+ * does not use cudaMalloc, cudaFree or any allocating library routine.
+ * The first call on a device looks up the array's device address once (with
+ * that device current); make that first call before any stream capture.
+ * Every call uses the same array and leaves its contents behind (the counter
+ * that must start at zero is cleared at the start of each call), so calls
+ * whose work overlaps on the GPU (other streams, other threads) race: issue
+ * them one after another.  Returns after the device work has finished.     */
+owqs_status owqs_run_static(owqs_pattern* p, const owqs_run_opts* opts, const void* psi_in,
+                            void* psi_out, uint8_t* outcomes, double* probs);
+
 /* Per-kernel timing of one run (instrumentation).  Runs the same schedule
  * without a graph, with a CUDA event pair around every launch on opts->stream,
  * and fills ms[i] (i < *nlaunch, at most cap) with each launch's duration,

@@ -80,6 +80,8 @@ EXPORTS = {
     "owqs_get_order": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32)]),
     "owqs_run": (C.c_int, [C.c_void_p, C.POINTER(owqs_run_opts), C.c_void_p, C.c_void_p,
                            C.POINTER(C.c_uint8), C.POINTER(C.c_double)]),
+    "owqs_run_static": (C.c_int, [C.c_void_p, C.POINTER(owqs_run_opts), C.c_void_p, C.c_void_p,
+                                  C.POINTER(C.c_uint8), C.POINTER(C.c_double)]),
     "owqs_profile_run": (C.c_int, [C.c_void_p, C.POINTER(owqs_run_opts), C.c_void_p, C.c_void_p,
                                    C.POINTER(C.c_uint8), C.POINTER(C.c_float), C.POINTER(C.c_double),
                                    C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32)]),
@@ -221,6 +223,32 @@ class Handle:
                                 C.c_void_p(out.data_ptr()), oc.ctypes.data_as(C.POINTER(C.c_uint8)),
                                 probs.ctypes.data_as(C.POINTER(C.c_double)))
         if check and st not in (OK,):
+            _check(st)
+        return out, oc[: self.K].copy(), probs[: self.K].copy(), st
+
+    def run_static(self, psi_in=None, *, dtype: str = "c128", mode: str = "owqs", policy: str = "forced",
+                   outcomes=None, stream=None, out=None, check: bool = True):
+        """owqs_run_static: same as run() without any device allocation inside
+        the library (scratch in a fixed device array; small patterns only)."""
+        import torch
+        tdt = torch.complex64 if dtype == "c64" else torch.complex128
+        if psi_in is not None:
+            if not psi_in.is_cuda or psi_in.dtype != tdt or not psi_in.is_contiguous():
+                raise ValueError("psi_in must be a contiguous CUDA tensor of the run's dtype")
+        dev = psi_in.device if psi_in is not None else torch.device("cuda", torch.cuda.current_device())
+        if out is None:
+            out = torch.empty(1 << self.nout, dtype=tdt, device=dev)
+        oc = np.zeros(max(1, self.K), dtype=np.uint8)
+        if outcomes is not None:
+            oc[: self.K] = np.asarray(outcomes, dtype=np.uint8)[: self.K]
+        probs = np.zeros(max(1, self.K), dtype=np.float64)
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        opts = owqs_run_opts(DTYPE[dtype], MODE[mode], POLICY[policy], 0, 0, C.c_void_p(s.cuda_stream), 0, 0)
+        st = library().owqs_run_static(self._h, C.byref(opts),
+                                       C.c_void_p(psi_in.data_ptr() if psi_in is not None else 0),
+                                       C.c_void_p(out.data_ptr()), oc.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                       probs.ctypes.data_as(C.POINTER(C.c_double)))
+        if check and st != OK:
             _check(st)
         return out, oc[: self.K].copy(), probs[: self.K].copy(), st
 
