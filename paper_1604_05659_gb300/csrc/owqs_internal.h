@@ -88,6 +88,7 @@ struct PassParams {
   double* norms;         // device norm slots
   double* partials;      // per-block partial sums (2 * grid)
   unsigned int* counter; // finished-block counter, left at 0
+  unsigned int* errflag; // set to a nonzero code if a device-side wait gives up
   int n_in, r, b, n_out;
   int norm_in;           // slot whose value N gives s_c = scale / sqrt(N); -1: s_c = scale
   int norm_out;          // slot written with sum |out|^2 (prob pass: norm_out, norm_out+1); -1: none
@@ -110,7 +111,14 @@ struct PassParams {
   int perm[64];
 };
 
-enum KernelKind { KK_FAST = 0, KK_GENERIC = 1, KK_FINAL = 2, KK_NORM = 3, KK_PROB = 4 };
+enum KernelKind { KK_FAST = 0, KK_GENERIC = 1, KK_FINAL = 2, KK_NORM = 3, KK_PROB = 4, KK_TMA = 5 };
+
+// TMA-pipelined pass (complex64): log2 of the outputs per tile (16 KB of
+// outputs, 32 KB of inputs) and the number of shared-memory stages
+constexpr int kTmaLogTileC64 = 11;
+constexpr int kTmaStages = 3;
+// device-side wait limit (cycles) before a TMA pass gives up with an error
+constexpr long long kWaitLimitCycles = 4000000000ll;
 
 struct LaunchPlan {
   int kind = KK_GENERIC;
@@ -126,6 +134,8 @@ constexpr int kFastRMax = 2;  // broadcast bits handled inside a thread
 // Fast-pass configuration for a dtype: tile width (c64: 2 or 3, c128: 1 or 2)
 // and cache hint.  OWQS_FAST="lg,hint" overrides the default (tuning runs).
 void fast_config(int dtype, int* lg, int* hint);
+// 1 if eligible wide passes use the TMA-pipelined kernel (OWQS_TMA=0 turns it off)
+int tma_enabled();
 constexpr int kBlock = 256;
 int max_grid();               // grid cap for grid-stride kernels
 

@@ -10,6 +10,7 @@
 // per thread tile promoted to FP64, FP64 across threads and blocks).
 //
 // Contract with the schedule compiler: see PassDesc in owqs_internal.h.
+#include <algorithm>
 #include <cstdint>
 #include <map>
 #include <mutex>
@@ -305,6 +306,176 @@ __global__ void __launch_bounds__(kBlock) k_fast(const PassParams P) {
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// TMA-pipelined measure pass (same contract and eligibility as k_fast, for
+// passes whose live part spans at least one tile of TE outputs).
+//
+// A persistent CTA walks tiles of TE consecutive live outputs.  Thread 0
+// stages each tile's input amplitudes into shared memory with bulk async
+// copies (cp.async.bulk, completion counted in bytes on an mbarrier), up to
+// kTmaStages tiles ahead, so many bytes are in flight per SM while the
+// threads only hold a few registers.  The threads then combine the pairs
+// (x(k0), x(k1)) from shared memory for every value of the broadcast bits and
+// write the outputs with 16-byte coalesced stores.
+//   CASE 0: b < log2 TE    one run of 2 TE inputs, partners 2^b apart
+//   CASE 1: b >= log2 TE   two runs of TE inputs, 2^b apart in the input
+//   CASE 2: b >= n_in      b is a new qubit; one run of TE inputs
+// Every mbarrier wait is bounded (kWaitLimitCycles): on expiry the block
+// agrees to stop, records an error code and returns.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > kWaitLimitCycles) return false;
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <typename T>
+struct TmaShape {
+  static constexpr int LTE = kTmaLogTileC64;
+  static constexpr int TE = 1 << LTE;
+  static constexpr int STAGE_BYTES = 2 * TE * (int)sizeof(T) * 2;
+  static constexpr int SMEM = kTmaStages * STAGE_BYTES + kTmaStages * 8;
+};
+
+template <typename T, int CASE>
+__global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
+  using V = typename Cplx<T>::V;
+  using S = TmaShape<T>;
+  constexpr int LTE = S::LTE, TE = S::TE, NS = kTmaStages;
+  constexpr int VE = sizeof(T) == 4 ? 2 : 1;  // outputs per 16-byte vector
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * S::STAGE_BYTES);
+  const V* __restrict__ in = reinterpret_cast<const V*>(P.in);
+  V* __restrict__ out = reinterpret_cast<V*>(P.out);
+  const double c = prev_scale(P);
+  const T sc = (T)(P.scale * c);
+  const T wr = (T)(P.scale * c * P.w1re), wi = (T)(P.scale * c * P.w1im);
+  const int b = P.b, nlo = P.nlo, nbc = P.n_out - P.nlo;
+  const uint64_t inmask = (1ull << P.n_in) - 1ull;
+  const uint64_t tiles = 1ull << (nlo - LTE);
+  const uint64_t step = gridDim.x;
+  const uint64_t mine = blockIdx.x < tiles ? (tiles - blockIdx.x + step - 1) / step : 0;
+  const uint32_t zlo = (uint32_t)(P.zmask & ((2ull << LTE) - 1ull));
+  const uint32_t alo = (uint32_t)(P.amask & ((2ull << LTE) - 1ull));
+  constexpr unsigned IN_BYTES = (CASE == 2 ? 1u : 2u) * TE * sizeof(V);
+
+  auto issue = [&](uint64_t i) {  // thread 0: stage tile i of this block
+    const int st = (int)(i % NS);
+    V* buf = reinterpret_cast<V*>(smem + st * S::STAGE_BYTES);
+    const uint64_t tile = blockIdx.x + i * step;
+    const uint64_t ib = ins0(tile << LTE, b) & inmask;
+    mbar_expect_tx(&full[st], IN_BYTES);
+    if constexpr (CASE == 1) {
+      bulk_g2s(buf, in + ib, TE * sizeof(V), &full[st]);
+      bulk_g2s(buf + TE, in + ib + (1ull << b), TE * sizeof(V), &full[st]);
+    } else {
+      bulk_g2s(buf, in + ib, IN_BYTES, &full[st]);
+    }
+  };
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NS; ++i) mbar_init(&full[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (uint64_t i = 0; i < mine && i < (uint64_t)NS; ++i) issue(i);
+
+  double acc = 0.0;
+  uint64_t issued = mine < (uint64_t)NS ? mine : (uint64_t)NS;
+  uint64_t i = 0;
+  bool failed = false;
+  for (; i < mine; ++i) {
+    const int st = (int)(i % NS);
+    const bool ok = mbar_wait_bounded(&full[st], (unsigned)((i / NS) & 1u));
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    const V* buf = reinterpret_cast<const V*>(smem + st * S::STAGE_BYTES);
+    const uint64_t tile = blockIdx.x + i * step;
+    const uint64_t J = tile << LTE;
+    const uint64_t K0 = ins0(J, b);
+    const uint32_t pz = P.c0 ^ par64(K0 & P.zmask);
+    const uint32_t pa = P.zb ^ par64(K0 & P.amask);
+    T tacc = (T)0;
+    for (uint64_t t = 0; t < (1ull << nbc); ++t) {
+      const uint64_t dt = ins0(t << nlo, b);
+      const uint32_t s0t = pz ^ par64(dt & P.zmask);
+      const uint32_t s1t = s0t ^ pa ^ par64(dt & P.amask);
+      V* o = out + J + (t << nlo);
+#pragma unroll 2
+      for (int e = threadIdx.x * VE; e < TE; e += kBlock * VE) {
+        V x0[VE], x1[VE], y[VE];
+#pragma unroll
+        for (int v = 0; v < VE; ++v) {
+          const int jj = e + v;
+          const int d0 = CASE == 0 ? (int)ins0((uint64_t)jj, b) : jj;
+          x0[v] = buf[d0];
+          x1[v] = CASE == 0 ? buf[d0 | (1 << b)] : (CASE == 1 ? buf[TE + jj] : buf[jj]);
+          const uint32_t s0 = (s0t ^ __popc((uint32_t)d0 & zlo)) & 1u;
+          const uint32_t s1 = (s1t ^ __popc((uint32_t)d0 & zlo) ^ __popc((uint32_t)d0 & alo)) & 1u;
+          const T a = s0 ? -sc : sc;
+          const T br = s1 ? -wr : wr, bi = s1 ? -wi : wi;
+          y[v].x = a * x0[v].x + br * x1[v].x - bi * x1[v].y;
+          y[v].y = a * x0[v].y + br * x1[v].y + bi * x1[v].x;
+          tacc += y[v].x * y[v].x + y[v].y * y[v].y;
+        }
+        if constexpr (VE == 2) {
+          *reinterpret_cast<float4*>(o + e) = make_float4(y[0].x, y[0].y, y[1].x, y[1].y);
+        } else {
+          o[e] = y[0];
+        }
+      }
+    }
+    acc += (double)tacc;
+    __syncthreads();  // every thread is done with stage st
+    if (threadIdx.x == 0 && issued < mine) issue(issued++);
+  }
+  if (failed) {
+    if (threadIdx.x == 0) {
+      atomicExch(P.errflag, 1u);
+      // let copies already issued land before the block's memory goes away
+      for (uint64_t j = i; j < issued; ++j) mbar_wait_bounded(&full[j % NS], (unsigned)((j / NS) & 1u));
+    }
+    __syncthreads();
+    return;  // the block partial is skipped; the host reports the error
+  }
+  if (P.norm_out >= 0) {
+    const double a1[1] = {acc};
+    reduce_to_slots<1>(a1, P.partials, P.counter, P.norms, P.norm_out);
+  }
+}
+
 // squared norm of an input vector (OWQS divides by it)
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_norm(const void* vin, uint64_t n, double* norms, int slot,
@@ -363,10 +534,41 @@ static cudaError_t launch_fast(const PassParams& P, const LaunchPlan& Lp, cudaSt
   return cudaSuccess;
 }
 
+template <typename T, int CASE>
+static cudaError_t launch_tma_case(const PassParams& P, cudaStream_t s) {
+  using S = TmaShape<T>;
+  auto kernel = k_tma<T, CASE>;
+  static int grid_cap = 0;
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (grid_cap == 0) {
+      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+      if (e != cudaSuccess) return e;
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, S::SMEM);
+      if (e != cudaSuccess) return e;
+      grid_cap = std::max(1, per_sm) * (max_grid() / 8);
+    }
+  }
+  const uint64_t tiles = 1ull << (P.nlo - S::LTE);
+  const int grid = (int)std::min<uint64_t>(tiles, (uint64_t)grid_cap);
+  kernel<<<grid, kBlock, S::SMEM, s>>>(P);
+  return cudaSuccess;
+}
+
 template <typename T>
 static cudaError_t launch_t(const PassParams& P, const LaunchPlan& L, cudaStream_t s) {
   const bool virt = P.in == nullptr;
   switch (L.kind) {
+    case KK_TMA: {  // planned for complex64 only
+      cudaError_t e = cudaErrorInvalidValue;
+      if constexpr (sizeof(T) == 4)
+        e = L.variant == 0 ? launch_tma_case<T, 0>(P, s)
+                           : (L.variant == 1 ? launch_tma_case<T, 1>(P, s) : launch_tma_case<T, 2>(P, s));
+      if (e != cudaSuccess) return e;
+      break;
+    }
     case KK_FAST: {
       cudaError_t e = cudaErrorInvalidValue;
       if constexpr (sizeof(T) == 4) {

@@ -195,6 +195,7 @@ class Runner {
     P.norms = rc_.norms;
     P.partials = rc_.partials;
     P.counter = rc_.counter;
+    P.errflag = rc_.counter + 1;
     P.thresh = thresh_;
   }
   void issue(const Item& it) {
@@ -315,10 +316,10 @@ static owqs_status prepare(Pattern& p, const owqs_run_opts* o, const void* psi_i
   st = ensure_buf((void*&)rc->norms, rc->nnorms, sizeof(double) * (3 * (size_t)K + 8), "norm slots");
   if (st == OWQS_OK)
     st = ensure_buf((void*&)rc->partials, rc->npartials, sizeof(double) * 2 * (size_t)max_grid(), "partials");
-  if (st == OWQS_OK && !rc->counter) {
-    cudaError_t e = cudaMalloc(&rc->counter, sizeof(unsigned int));
+  if (st == OWQS_OK && !rc->counter) {  // [0] finished-block counter, [1] error flag
+    cudaError_t e = cudaMalloc(&rc->counter, 2 * sizeof(unsigned int));
     if (e != cudaSuccess) return cuda_fail(e, "counter");
-    e = cudaMemset(rc->counter, 0, sizeof(unsigned int));
+    e = cudaMemset(rc->counter, 0, 2 * sizeof(unsigned int));
     if (e != cudaSuccess) return cuda_fail(e, "counter");
   }
   if (st != OWQS_OK) return st;
@@ -360,9 +361,16 @@ static owqs_status finish(Pattern& p, const owqs_run_opts* o, RunCache* rc, cons
                           bool has_input) {
   const int K = (int)p.meas_qubit.size();
   rc->h_norms.assign((size_t)K + 2, 0.0);
+  unsigned int flag = 0;
   cudaError_t e = cudaMemcpyAsync(rc->h_norms.data(), rc->norms, sizeof(double) * (K + 2), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, rc->counter + 1, sizeof(flag), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "run");
+  if (flag) {  // a device-side wait gave up: blocks skipped the reduction
+    cudaMemsetAsync(rc->counter, 0, 2 * sizeof(unsigned int), s);
+    cudaStreamSynchronize(s);
+    return set_error(OWQS_ERR_TIMEOUT, "a device-side wait in a pass kernel gave up; results are invalid");
+  }
   const double thresh = o->dtype == OWQS_C128 ? 1e-24 : 1e-12;
   owqs_status st = OWQS_OK;
   int mi = 0;

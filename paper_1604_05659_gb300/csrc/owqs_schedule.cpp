@@ -209,6 +209,15 @@ void fast_config(int dtype, int* lg, int* hint) {
   *hint = cfg[d][1];
 }
 
+int tma_enabled() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = std::getenv("OWQS_TMA");
+    on = (e && e[0] == '0') ? 0 : 1;
+  }
+  return on;
+}
+
 static inline uint64_t ins0(uint64_t j, int b) {  // insert a 0 bit at position b
   return ((j >> b) << (b + 1)) | (j & ((1ull << b) - 1));
 }
@@ -296,11 +305,26 @@ void plan_pass(const PassDesc& d, int dtype, bool virt_in, PassParams& P, Launch
     L.grid = (int)std::min<uint64_t>((elems + kBlock - 1) / kBlock, (uint64_t)max_grid());
     return;
   }
+  P.nlo = nlo;
+  // complex64 only: the complex128 pass is bound by the FP64 rate, where the
+  // register-tiled kernel's larger thread count wins (GB300: 4.43 vs 5.15 ms
+  // per 2^28 pass; complex64 0.733 vs 0.751 ms in favour of TMA)
+  const int lte = kTmaLogTileC64;
+  if (tma_enabled() && dtype == OWQS_C64 && nlo >= lte) {
+    // whole tiles of 2^lte live outputs: the TMA-pipelined pass
+    L.kind = KK_TMA;
+    L.variant = b_new ? 2 : (d.b >= lte ? 1 : 0);
+    P.amask = amask;
+    P.zb = (uint32_t)((d.zmask >> d.b) & 1u);
+    P.rt = 0;
+    uint64_t tiles = 1ull << (nlo - lte);
+    L.grid = (int)std::min<uint64_t>(tiles, (uint64_t)max_grid());
+    return;
+  }
   L.kind = KK_FAST;
   L.lg = Lg;
   L.hint = hint;
   L.variant = b_new ? Lg + 1 : (d.b >= Lg ? Lg : d.b);
-  P.nlo = nlo;
   const int nbc = d.n_out - nlo;
   P.rt = std::min(nbc, kFastRMax);
   P.amask = amask;

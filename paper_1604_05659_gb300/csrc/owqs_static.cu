@@ -113,8 +113,9 @@ static owqs_status run_static(Pattern& p, const owqs_run_opts* o, const void* ps
   cudaStream_t s = reinterpret_cast<cudaStream_t>(o->stream);
   const double thresh = dtype == OWQS_C128 ? 1e-24 : 1e-12;
 
-  // the array keeps the previous call's contents: the counter must start at 0
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
+  // the array keeps the previous call's contents: the counter and the error
+  // flag after it must start at 0
+  cudaError_t e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned int), s);
   if (e != cudaSuccess) return cuda_err(e, "clearing the static counter");
 
   const uint64_t in_elems = 1ull << p.inputs.size();
@@ -134,6 +135,7 @@ static owqs_status run_static(Pattern& p, const owqs_run_opts* o, const void* ps
     P.norms = norms;
     P.partials = partials;
     P.counter = counter;
+    P.errflag = counter + 1;
     P.thresh = thresh;
     P.in = cur;
     if (d.kind == 0) {
@@ -152,9 +154,12 @@ static owqs_status run_static(Pattern& p, const owqs_run_opts* o, const void* ps
     cur = P.out;
   }
   std::vector<double> h((size_t)K + 2, 0.0);
+  unsigned int flag = 0;
   e = cudaMemcpyAsync(h.data(), norms, sizeof(double) * (K + 2), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, counter + 1, sizeof(flag), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_err(e, "static run");
+  if (flag) return set_error(OWQS_ERR_TIMEOUT, "a device-side wait in a pass kernel gave up; results are invalid");
 
   st = OWQS_OK;
   int mi = 0;

@@ -24,7 +24,7 @@ CMD_KIND = {"N": 0, "E": 1, "M": 2, "X": 3, "Z": 4}
 MODE = {"owqs": 0, "eowqs": 1}
 DTYPE = {"c64": 0, "c128": 1}
 POLICY = {"forced": 0, "sampled": 1, "zero": 2}
-KERNEL_KIND = {0: "fast_pass", 1: "generic_pass", 2: "final", 3: "norm", 4: "prob"}
+KERNEL_KIND = {0: "fast_pass", 1: "generic_pass", 2: "final", 3: "norm", 4: "prob", 5: "tma_pass"}
 
 
 class OwqsError(RuntimeError):

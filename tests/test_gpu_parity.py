@@ -126,6 +126,8 @@ def _medium_cases():
         n = 10 + rng.randint(5)
         cases.append(circuit_to_pattern(n, random_jcz_circuit(n, 6, rng, cz_per_layer=3), f"rand{n}"))
     cases.append(dangling_pattern(13, 12, 905))
+    cases.append(dangling_pattern(8, 10, 906))          # new-qubit case of the register-tiled pass
+    cases.append(workloads.brickwork(16, 5).pattern)   # 2^16 per pass: TMA tiles, measured bit below and above 11
     return cases
 
 
@@ -144,7 +146,9 @@ def test_medium_patterns_tiles(env, dtype):
 
 
 def test_fast_kernel_variants_covered(env):
-    """The medium cases hit the measured-bit cases 0, 1, middle and new."""
+    """The medium cases hit every case of the register-tiled pass (measured
+    bit 0, 1, middle, new qubit) and of the complex64 TMA pass (one run with
+    the partner 2^b apart inside a 2^11 tile, two runs, new qubit)."""
     torch, owqs = env
     seen = set()
     for p in _medium_cases():
@@ -154,13 +158,18 @@ def test_fast_kernel_variants_covered(env):
         for d in h.describe_passes(np.zeros(p.K, np.uint8)):
             if d.kind:
                 continue
-            if d.b >= d.n_in:
-                seen.add("new")
-            elif d.b >= 2:
-                seen.add("mid")
-            else:
-                seen.add(d.b)
-    assert {0, 1, "mid", "new"} <= seen, seen
+            star = all(d.b in (d.edges[e][0], d.edges[e][1]) for e in range(d.nedges)) and d.xmask == 0
+            if not star:
+                continue
+            new = d.b >= d.n_in
+            nlo = d.n_in if new else d.n_in - 1
+            if nlo >= 11:
+                seen.add(("c64", "tma", "new" if new else ("two_runs" if d.b >= 11 else "one_run")))
+            if nlo >= 3 and nlo < 11:
+                seen.add(("reg", "new" if new else ("mid" if d.b >= 3 else d.b)))
+    want = {("c64", "tma", c) for c in ("one_run", "two_runs", "new")}
+    want |= {("reg", 0), ("reg", 1), ("reg", "mid"), ("reg", "new")}
+    assert want <= seen, want - seen
 
 
 def test_graph_replay_matches_direct(env):
