@@ -37,9 +37,17 @@ ROWS, COLS = 28, 40
 WORKLOAD = ("brickwork cluster 28x40 (1120 qubits, 1092 measurements), angles k*pi/4, |+>^28 input, "
             "forced seeded outcomes, greedy reordering (peak 29 live qubits, 2^28 complex64 amplitudes)")
 FALLBACK_HBM_GBS = 6800.0
-# ncu DRAM bytes per launch of the dominant kernel, keyed by the sha256 of the
-# kernel source they were measured on; None until a capture exists
-NCU_TRAFFIC = {}
+# ncu DRAM bytes (read + write) per launch of the dominant kernel, keyed by the
+# sha256 prefix of the kernel source they were measured on (a changed kernel
+# reports null).  c64: k_tma<float,1> on a 2^26-amplitude pass (536.9 MB read +
+# 486.8 MB written) scaled by 4 to the 2^28-amplitude launch
+# (profiles/k_tma_c64_brickwork26x4.md).
+NCU_TRAFFIC = {("0eaf65b1124c3d4d", "c64"): 4 * (536.947200e6 + 486.829568e6)}
+# nominal GB300 FP64 rate (no measured FP64 peak exists for this machine)
+FP64_PEAK_TFLOPS = 1.25
+# FP64 flops per output amplitude of the complex128 pass: complex multiply-add
+# (2 DMUL + 4 DFMA = 10 flops) and the squared-norm sum (DMUL + DFMA + DADD = 4)
+FP64_FLOPS_PER_OUTPUT = 14
 
 
 def parse():
@@ -250,13 +258,22 @@ def run_owqs(args):
         tot = {k: float(ms[kd == k].sum()) for k in kinds}
         dom = max(tot, key=tot.get)
         sel = kd == dom
-        achieved = float(by[sel].sum()) / (float(ms[sel].sum()) / 1e3) / 1e9
+        secs = float(ms[sel].sum()) / 1e3
         share = tot[dom] / sum(tot.values())
+        common = {"kernel": owqs.KERNEL_KIND[dom], "launches": int(sel.sum()), "share_of_step": share,
+                  "bytes_per_launch": float(by[sel].mean()), "avg_launch_ms": float(ms[sel].mean())}
+        if dtype == "c128":
+            # FP64-bound on GB300: every pass here reads and writes 2^n amplitudes
+            outputs = float(by[sel].sum()) / 32.0
+            achieved = outputs * FP64_FLOPS_PER_OUTPUT / secs / 1e12
+            return dict({"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get((kernel_source_hash(), dtype)),
+                         "hbm_gbs": float(by[sel].sum()) / secs / 1e9,
+                         "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no measured FP64 peak)"}, **common), len(ms)
+        achieved = float(by[sel].sum()) / secs / 1e9
         traffic = NCU_TRAFFIC.get((kernel_source_hash(), dtype))
-        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": traffic, "kernel": owqs.KERNEL_KIND[dom], "launches": int(sel.sum()),
-                "share_of_step": share, "bytes_per_launch": float(by[sel].mean()),
-                "avg_launch_ms": float(ms[sel].mean()), "peak_source": f"{peak_kind} hbm_gbs (copy, burst)"}, len(ms)
+        return dict({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs (copy, burst)"}, **common), len(ms)
 
     legs = set(args.legs.split(","))
     roof64, launches_per_step = roofline("c64")

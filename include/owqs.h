@@ -190,6 +190,70 @@ typedef struct {
 owqs_status owqs_run(owqs_pattern* p, const owqs_run_opts* opts, const void* psi_in,
                      void* psi_out, uint8_t* outcomes, double* probs);
 
+/* Recognition (Section 1: which unitary a pattern implements).  Computes
+ * every basis column at once: the pattern runs with |I| extra reference
+ * qubits that no command touches, starting from the sum over c of |c>|c>, so
+ * the final array (output bits low, reference bits high) is the matrix.
+ * Every measurement of the forced branch is taken with probability 1/2 (the
+ * EOWQS scaling of Section 4.5): the result is the branch as a linear map,
+ * which for a pattern with flow is the implemented unitary (up to the
+ * branch's global phase).
+ *   opts      dtype, stream, use_graph; policy FORCED (outcomes, K bytes in
+ *             load order) or ZERO (outcomes may be NULL); io must be DEVICE
+ *   U         device, 2^|O| x 2^|I| complex, column-major: U[o + 2^|O| c] is
+ *             output amplitude o for basis input c (bit k of c is inputs[k])
+ *   frob2     optional host double: ||U||_F^2 / 2^|I| (1 for an isometry)
+ * The live array is |I| qubits wider than in owqs_run.                     */
+owqs_status owqs_unitary(owqs_pattern* p, const owqs_run_opts* opts, const uint8_t* outcomes, void* U,
+                         double* frob2);
+
+/* Batched recognition and determinism checks.  One item is one pattern and
+ * one forced branch, with either all basis columns (psi_in NULL: out is the
+ * matrix, as for owqs_unitary) or one input vector (out is the output
+ * state).  Every measurement is taken with probability 1/2 (EOWQS scaling,
+ * Section 4.5), so the outputs are the branches as linear maps; for a pattern
+ * with flow every branch gives the same state up to a global phase, which the
+ * overlaps below measure.  Items whose widest array fits a shared-memory
+ * column block (at most 16 live qubits) run in ONE persistent launch: each
+ * block of threads pulls (item, column block) tasks, keeps its states on chip
+ * for the whole pass list and writes only the final columns; wider items run
+ * through the owqs_run / owqs_unitary pass kernels.  The column block is
+ * chosen by timing the candidate shared-memory budgets on the first call for
+ * a given batch shape (kept for the process) unless opts->column_block fixes
+ * it.  All items must be loaded on the current device; the call returns after
+ * the device work has finished.                                           */
+typedef struct {
+  owqs_pattern* pattern;    /* loaded pattern; its active order is used            */
+  const uint8_t* outcomes;  /* K forced outcome bits (load order); NULL = all zero  */
+  const void* psi_in;       /* NULL: every basis column; else device vector 2^|I|    */
+  void* out;                /* device: 2^|O| x 2^|I| (column-major) or 2^|O|         */
+  int32_t ref;              /* index of an item to overlap with, -1 for none        */
+  uint32_t pad_;
+} owqs_batch_item;
+
+typedef struct {
+  uint32_t dtype;           /* OWQS_C64 or OWQS_C128                                 */
+  uint32_t column_block;    /* columns per task (power of two); 0 = tuned            */
+  void* stream;             /* cudaStream_t; NULL = legacy default stream            */
+  uint32_t use_graph;       /* for the items run through the pass kernels            */
+  uint32_t pad_;
+  double* overlaps;         /* optional host array of 4n doubles: for items with
+                               ref >= 0, Re and Im of <out_ref|out>, |out|^2 and
+                               |out_ref|^2 (outputs as flat vectors); 0 otherwise     */
+} owqs_batch_opts;
+
+typedef struct {
+  uint32_t smem_items;      /* items run by the persistent shared-memory launch     */
+  uint32_t hbm_items;       /* items run through the pass kernels                   */
+  uint32_t tasks;           /* (item, column block) tasks of the persistent launch  */
+  uint32_t smem_bytes_per_cta;
+  uint32_t launches;        /* kernel launches of this call                         */
+  uint32_t pad_;
+} owqs_batch_info;
+
+owqs_status owqs_run_batch(const owqs_batch_item* items, uint32_t n, const owqs_batch_opts* opts,
+                           owqs_batch_info* info);
+
 /* owqs_run without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc, such as
  * code running while a CUDA stream is being captured into a graph (where

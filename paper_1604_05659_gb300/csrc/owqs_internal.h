@@ -42,7 +42,12 @@ struct Pattern {
   std::vector<uint32_t> active_meas;  // measurement order of the active order
   bool standard = false;
   bool deps_ok = true;                // active order measures every domain first (D0)
+  uint64_t order_version = 0;         // bumped whenever the active order changes
   std::shared_ptr<RunCache> cache;
+  // recognition: the same pattern with |I| untouched reference qubits added as
+  // inputs and outputs (all basis columns at once); rebuilt on order changes
+  std::shared_ptr<Pattern> aug;
+  uint64_t aug_version = ~0ull;
   ~Pattern();
 };
 
@@ -99,6 +104,8 @@ struct PassParams {
   int qu[kQMax];
   uint64_t qa[kQMax];
   double scale, w1re, w1im, ere, eim, vconst;
+  int vdiag;             // virtual input: 0 = |+> of value vconst; h > 0 = amplitude 1 where the
+                         // low h input bits equal the next h (all basis columns, recognition)
   // fast pass (star form at b, no X): uniform sign tables
   uint64_t amask;        // neighbours of b
   uint32_t zb;           // z bit at b

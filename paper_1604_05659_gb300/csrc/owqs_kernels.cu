@@ -107,10 +107,12 @@ __device__ __forceinline__ void reduce_to_slots(const double (&acc)[NV], double*
 
 // ---------------------------------------------------------------------------
 // generic pass: one output amplitude per thread iteration; any sign function,
-// any X mask, any measured bit, virtual |+> input.  MODE 0 measure, 1 the
-// two outcome probabilities only, 2 final pass (corrections + output order).
+// any X mask, any measured bit, virtual input (VIRT 1: |+> on every input,
+// VIRT 2: the diagonal sum over c of |c>|c> that carries every basis column
+// of a unitary at once).  MODE 0 measure, 1 the two outcome probabilities
+// only, 2 final pass (corrections + output order).
 // ---------------------------------------------------------------------------
-template <typename T, int MODE, bool VIRT>
+template <typename T, int MODE, int VIRT>
 __global__ void __launch_bounds__(kBlock) k_generic(const PassParams P) {
   using V = typename Cplx<T>::V;
   const V* __restrict__ in = reinterpret_cast<const V*>(P.in);
@@ -123,10 +125,15 @@ __global__ void __launch_bounds__(kBlock) k_generic(const PassParams P) {
   const uint64_t inmask = (1ull << P.n_in) - 1ull;
   const uint64_t bb = MODE == 2 ? 0ull : (1ull << P.b);
   const T vc = (T)P.vconst;
+  const uint64_t dmask = (1ull << P.vdiag) - 1ull;
   auto load = [&](uint64_t k) -> V {
     V x;
-    if (VIRT) {
+    if (VIRT == 1) {
       x.x = vc;
+      x.y = (T)0;
+    } else if (VIRT == 2) {
+      const uint64_t i = (k ^ P.xmask) & inmask;
+      x.x = ((i & dmask) == (i >> P.vdiag)) ? (T)1 : (T)0;
       x.y = (T)0;
     } else {
       x = in[(k ^ P.xmask) & inmask];
@@ -582,16 +589,18 @@ static cudaError_t launch_t(const PassParams& P, const LaunchPlan& L, cudaStream
       break;
     }
     case KK_GENERIC:
-      if (virt) go(k_generic<T, 0, true>, P, L.grid, s);
-      else go(k_generic<T, 0, false>, P, L.grid, s);
+      if (!virt) go(k_generic<T, 0, 0>, P, L.grid, s);
+      else if (P.vdiag) go(k_generic<T, 0, 2>, P, L.grid, s);
+      else go(k_generic<T, 0, 1>, P, L.grid, s);
       break;
     case KK_PROB:
-      if (virt) go(k_generic<T, 1, true>, P, L.grid, s);
-      else go(k_generic<T, 1, false>, P, L.grid, s);
+      if (virt) go(k_generic<T, 1, 1>, P, L.grid, s);
+      else go(k_generic<T, 1, 0>, P, L.grid, s);
       break;
     case KK_FINAL:
-      if (virt) go(k_generic<T, 2, true>, P, L.grid, s);
-      else go(k_generic<T, 2, false>, P, L.grid, s);
+      if (!virt) go(k_generic<T, 2, 0>, P, L.grid, s);
+      else if (P.vdiag) go(k_generic<T, 2, 2>, P, L.grid, s);
+      else go(k_generic<T, 2, 1>, P, L.grid, s);
       break;
     default:
       return cudaErrorInvalidValue;

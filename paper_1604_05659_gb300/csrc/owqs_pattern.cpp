@@ -91,6 +91,7 @@ static bool is_standard(const Pattern& p) {
 }
 
 static void set_active_loaded(Pattern& p) {
+  ++p.order_version;
   p.active.resize(p.cmds.size());
   std::iota(p.active.begin(), p.active.end(), 0u);
   p.active_meas.clear();
@@ -176,6 +177,7 @@ static owqs_status build_active(Pattern& p, const std::vector<uint32_t>& order, 
   p.active.swap(act);
   p.active_meas = order;
   p.deps_ok = deps_ok;
+  ++p.order_version;
   return OWQS_OK;
 }
 

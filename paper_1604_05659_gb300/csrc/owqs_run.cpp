@@ -115,6 +115,7 @@ class Runner {
   }
 
   bool immediate = false;
+  int vdiag = 0;  // virtual diagonal input over 2 * vdiag bits (recognition)
   std::vector<Item> items;
   owqs_status err = OWQS_OK;
 
@@ -141,6 +142,7 @@ class Runner {
     Item it;
     plan_pass(d, dtype_, cur_in_ == nullptr, it.P, it.L);
     fill_common(it.P);
+    if (!cur_in_) it.P.vdiag = vdiag;
     it.P.in = cur_in_;
     it.P.out = rc_.buf[pass_i_ & 1];
     it.P.norm_in = prev_slot_;
@@ -172,6 +174,7 @@ class Runner {
     Item it;
     plan_pass(d, dtype_, cur_in_ == nullptr, it.P, it.L);
     fill_common(it.P);
+    if (!cur_in_) it.P.vdiag = vdiag;
     it.P.in = cur_in_;
     it.P.out = out_final_;
     it.P.norm_in = mode_ == OWQS_MODE_OWQS ? prev_slot_ : -1;
@@ -358,7 +361,7 @@ static owqs_status ensure_pingpong(RunCache* rc, size_t elems, size_t amp) {
 
 static owqs_status finish(Pattern& p, const owqs_run_opts* o, RunCache* rc, const Prepared& pr,
                           cudaStream_t s, uint8_t* outcomes, double* probs, const std::vector<int>& outcome_of_pass,
-                          bool has_input) {
+                          bool has_input, int vdiag, double* frob2) {
   const int K = (int)p.meas_qubit.size();
   rc->h_norms.assign((size_t)K + 2, 0.0);
   unsigned int flag = 0;
@@ -384,6 +387,10 @@ static owqs_status finish(Pattern& p, const owqs_run_opts* o, RunCache* rc, cons
                                                       " has probability " + std::to_string(pv));
     ++mi;
   }
+  if (vdiag > 0) {  // recognition: |U|_F^2 / 2^|I| is 1 for an isometry; reported, not judged
+    if (frob2) *frob2 = rc->h_norms[K + 1] / std::ldexp(1.0, vdiag);
+    return st;
+  }
   if (o->mode == OWQS_MODE_EOWQS) {
     const double nin = has_input ? rc->h_norms[0] : 1.0;
     const double nout = rc->h_norms[K + 1];
@@ -397,7 +404,8 @@ static owqs_status finish(Pattern& p, const owqs_run_opts* o, RunCache* rc, cons
 
 static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
                             uint8_t* outcomes, double* probs, float* prof_ms, double* prof_bytes,
-                            uint32_t* prof_kind, uint32_t prof_cap, uint32_t* prof_n) {
+                            uint32_t* prof_kind, uint32_t prof_cap, uint32_t* prof_n, int vdiag = 0,
+                            double* frob2 = nullptr) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(o ? o->stream : nullptr);
   RunCache* rc = nullptr;
   Prepared pr;
@@ -447,6 +455,7 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
     for (const PassDesc& d : pr.passes)
       if (d.kind == 0) outcome_of_pass.push_back(d.outcome);
     Runner R(p, *rc, o->dtype, o->mode, s);
+    R.vdiag = vdiag;
     R.begin(pr.in_dev, pr.in_elems, pr.out_dev);
     for (const PassDesc& d : pr.passes) {
       if (d.kind == 0) R.measure(d);
@@ -526,7 +535,7 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
     if (e != cudaSuccess) return cuda_fail(e, "output copy");
   }
   (void)K;
-  return finish(p, o, rc, pr, s, outcomes, probs, outcome_of_pass, pr.in_dev != nullptr);
+  return finish(p, o, rc, pr, s, outcomes, probs, outcome_of_pass, pr.in_dev != nullptr, vdiag, frob2);
 }
 
 }  // namespace owqs
@@ -540,6 +549,47 @@ owqs_status owqs_run(owqs_pattern* h, const owqs_run_opts* o, const void* psi_in
   clear_error();
   if (!h) return set_error(OWQS_ERR_ARG, "NULL pattern");
   return run_impl(h->p, o, psi_in, psi_out, outcomes, probs, nullptr, nullptr, nullptr, 0, nullptr);
+}
+
+// recognition (Section 1: which unitary a pattern implements): the pattern
+// with |I| reference qubits that no command touches, started from the sum over
+// c of |c>|c>; the output (O bits low, reference bits high) is U column-major
+static owqs::Pattern& augmented(owqs::Pattern& p) {
+  if (p.aug && p.aug_version == p.order_version) return *p.aug;
+  auto a = std::make_shared<owqs::Pattern>();
+  const uint32_t nI = (uint32_t)p.inputs.size();
+  a->n = p.n + nI;
+  a->inputs = p.inputs;
+  a->outputs = p.outputs;
+  for (uint32_t k = 0; k < nI; ++k) {
+    a->inputs.push_back(p.n + k);
+    a->outputs.push_back(p.n + k);
+  }
+  a->cmds = p.cmds;
+  a->k_of_qubit = p.k_of_qubit;
+  a->k_of_qubit.resize(a->n, -1);
+  a->meas_qubit = p.meas_qubit;
+  a->active = p.active;
+  a->active_meas = p.active_meas;
+  a->standard = p.standard;
+  a->deps_ok = p.deps_ok;
+  p.aug = a;
+  p.aug_version = p.order_version;
+  return *a;
+}
+
+owqs_status owqs_unitary(owqs_pattern* h, const owqs_run_opts* o, const uint8_t* outcomes, void* U,
+                         double* frob2) {
+  clear_error();
+  if (!h || !o || !U) return set_error(OWQS_ERR_ARG, "NULL argument");
+  if (o->io != OWQS_IO_DEVICE) return set_error(OWQS_ERR_ARG, "owqs_unitary writes a device matrix");
+  if (o->policy == OWQS_OUTCOME_SAMPLED) return set_error(OWQS_ERR_ARG, "the recognition branch must be forced or zero");
+  if (2 * h->p.inputs.size() + 1 > (size_t)kMaxLive) return set_error(OWQS_ERR_OOM, "too many inputs for a unitary");
+  owqs_run_opts oo = *o;
+  oo.mode = OWQS_MODE_EOWQS;  // fixed sqrt2 per measurement: the branch as a linear map
+  Pattern& a = augmented(h->p);
+  return run_impl(a, &oo, nullptr, U, const_cast<uint8_t*>(outcomes), nullptr, nullptr, nullptr, nullptr, 0,
+                  nullptr, (int)h->p.inputs.size(), frob2);
 }
 
 owqs_status owqs_profile_run(owqs_pattern* h, const owqs_run_opts* o, const void* psi_in, void* psi_out,

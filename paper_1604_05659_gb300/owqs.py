@@ -60,6 +60,21 @@ class owqs_run_opts(C.Structure):
                 ("seed", C.c_uint64), ("stream", C.c_void_p), ("use_graph", C.c_uint32), ("pad_", C.c_uint32)]
 
 
+class owqs_batch_item(C.Structure):
+    _fields_ = [("pattern", C.c_void_p), ("outcomes", C.POINTER(C.c_uint8)), ("psi_in", C.c_void_p),
+                ("out", C.c_void_p), ("ref", C.c_int32), ("pad_", C.c_uint32)]
+
+
+class owqs_batch_opts(C.Structure):
+    _fields_ = [("dtype", C.c_uint32), ("column_block", C.c_uint32), ("stream", C.c_void_p),
+                ("use_graph", C.c_uint32), ("pad_", C.c_uint32), ("overlaps", C.POINTER(C.c_double))]
+
+
+class owqs_batch_info(C.Structure):
+    _fields_ = [("smem_items", C.c_uint32), ("hbm_items", C.c_uint32), ("tasks", C.c_uint32),
+                ("smem_bytes_per_cta", C.c_uint32), ("launches", C.c_uint32), ("pad_", C.c_uint32)]
+
+
 class owqs_pass_desc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_in", C.c_int32), ("r", C.c_int32), ("b", C.c_int32),
                 ("n_out", C.c_int32), ("outcome", C.c_int32), ("xmask", C.c_uint64), ("zmask", C.c_uint64),
@@ -80,6 +95,10 @@ EXPORTS = {
     "owqs_get_order": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32)]),
     "owqs_run": (C.c_int, [C.c_void_p, C.POINTER(owqs_run_opts), C.c_void_p, C.c_void_p,
                            C.POINTER(C.c_uint8), C.POINTER(C.c_double)]),
+    "owqs_unitary": (C.c_int, [C.c_void_p, C.POINTER(owqs_run_opts), C.POINTER(C.c_uint8), C.c_void_p,
+                               C.POINTER(C.c_double)]),
+    "owqs_run_batch": (C.c_int, [C.POINTER(owqs_batch_item), C.c_uint32, C.POINTER(owqs_batch_opts),
+                                 C.POINTER(owqs_batch_info)]),
     "owqs_run_static": (C.c_int, [C.c_void_p, C.POINTER(owqs_run_opts), C.c_void_p, C.c_void_p,
                                   C.POINTER(C.c_uint8), C.POINTER(C.c_double)]),
     "owqs_profile_run": (C.c_int, [C.c_void_p, C.POINTER(owqs_run_opts), C.c_void_p, C.c_void_p,
@@ -226,6 +245,22 @@ class Handle:
             _check(st)
         return out, oc[: self.K].copy(), probs[: self.K].copy(), st
 
+    def unitary(self, *, dtype: str = "c128", outcomes=None, stream=None, use_graph: bool = True, out=None):
+        """All basis columns of the forced branch as a matrix (2^|O| x 2^|I|,
+        column-major as a flat tensor); returns (U, ||U||_F^2 / 2^|I|)."""
+        import torch
+        tdt = torch.complex64 if dtype == "c64" else torch.complex128
+        if out is None:
+            out = torch.empty(1 << (self.nout + self.nin), dtype=tdt, device="cuda")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        policy = "zero" if outcomes is None else "forced"
+        opts = owqs_run_opts(DTYPE[dtype], MODE["eowqs"], POLICY[policy], 0, 0, C.c_void_p(s.cuda_stream),
+                             int(use_graph), 0)
+        f2 = C.c_double()
+        _check(library().owqs_unitary(self._h, C.byref(opts), _outcome_buf(outcomes, self.K),
+                                      C.c_void_p(out.data_ptr()), C.byref(f2)))
+        return out, f2.value
+
     def run_static(self, psi_in=None, *, dtype: str = "c128", mode: str = "owqs", policy: str = "forced",
                    outcomes=None, stream=None, out=None, check: bool = True):
         """owqs_run_static: same as run() without any device allocation inside
@@ -291,6 +326,36 @@ class Handle:
                                           C.c_void_p(out.data_ptr()), oc, ms, by, kd, cap, C.byref(n)))
         k = min(n.value, cap)
         return np.array(ms[:k]), np.array(by[:k]), np.array(kd[:k]), out
+
+
+def run_batch(items, *, dtype: str = "c128", column_block: int = 0, stream=None, use_graph: bool = True,
+              overlaps: bool = False):
+    """owqs_run_batch.  items: list of dicts with keys handle, outcomes (array
+    or None), psi_in (CUDA tensor or None), out (CUDA tensor), ref (int, -1).
+    Returns (info dict, overlaps array of shape (n, 4) or None)."""
+    import torch
+    n = len(items)
+    arr = (owqs_batch_item * max(1, n))()
+    keep = []
+    for i, it in enumerate(items):
+        h = it["handle"]
+        oc = None
+        if it.get("outcomes") is not None:
+            oc = _outcome_buf(it["outcomes"], h.K)
+            keep.append(oc)
+        arr[i].pattern = h._h
+        arr[i].outcomes = C.cast(oc, C.POINTER(C.c_uint8)) if oc is not None else None
+        arr[i].psi_in = it["psi_in"].data_ptr() if it.get("psi_in") is not None else None
+        arr[i].out = it["out"].data_ptr()
+        arr[i].ref = int(it.get("ref", -1))
+    ov = np.zeros(4 * max(1, n), dtype=np.float64) if overlaps else None
+    s = stream if stream is not None else torch.cuda.current_stream()
+    opts = owqs_batch_opts(DTYPE[dtype], column_block, C.c_void_p(s.cuda_stream), int(use_graph), 0,
+                           ov.ctypes.data_as(C.POINTER(C.c_double)) if ov is not None else None)
+    info = owqs_batch_info()
+    _check(library().owqs_run_batch(arr, n, C.byref(opts), C.byref(info)))
+    return ({f: getattr(info, f) for f, _ in owqs_batch_info._fields_ if f != "pad_"},
+            ov[: 4 * n].reshape(n, 4) if ov is not None else None)
 
 
 def _host_ptr(a) -> int:
