@@ -39,10 +39,10 @@ WORKLOAD = ("brickwork cluster 28x40 (1120 qubits, 1092 measurements), angles k*
 FALLBACK_HBM_GBS = 6800.0
 # ncu DRAM bytes (read + write) per launch of the dominant kernel, keyed by the
 # sha256 prefix of the kernel source they were measured on (a changed kernel
-# reports null).  c64: k_tma<float,1> on a 2^26-amplitude pass (536.9 MB read +
-# 486.8 MB written) scaled by 4 to the 2^28-amplitude launch
-# (profiles/k_tma_c64_brickwork26x4.md).
-NCU_TRAFFIC = {("0eaf65b1124c3d4d", "c64"): 4 * (536.947200e6 + 486.829568e6)}
+# reports null).  c64: k_tma<float,1> on the full 2^28-amplitude brickwork
+# pass, mean of three launches (2147.6 MB read + 2101.2 MB written;
+# profiles/k_tma_c64_brickwork28x40_dram.md).
+NCU_TRAFFIC = {("0eaf65b1124c3d4d", "c64"): (2147666432 + 2147585792 + 2147547648 + 2103186944 + 2100009984 + 2100388864) / 3.0}
 # nominal GB300 FP64 rate (no measured FP64 peak exists for this machine)
 FP64_PEAK_TFLOPS = 1.25
 # FP64 flops per output amplitude of the complex128 pass: complex multiply-add
@@ -61,8 +61,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rows", type=int, default=ROWS)
     ap.add_argument("--cols", type=int, default=COLS)
-    ap.add_argument("--legs", default="c64,c128,e2e,cpu",
-                    help="comma list of c64 (always run), c128, e2e, cpu; fewer legs for profiler runs")
+    ap.add_argument("--legs", default="c64,c128,e2e,cpu,rec",
+                    help="comma list of c64 (always run), c128, e2e, cpu, rec; fewer legs for profiler runs")
+    ap.add_argument("--rec-count", type=int, default=256, help="patterns in the recognition leg")
     return ap.parse_args()
 
 
@@ -192,6 +193,80 @@ def run_reference(args):
     return 0
 
 
+def recognition_leg(args, owqs, torch):
+    """Batched recognition: the full unitary (all 2^n basis columns) of every
+    pattern of the uneven random J/CZ set (widths 6..14, depths 10..40) in
+    complex64.  Items whose arrays fit a shared-memory column block run in one
+    persistent launch; wider ones are streamed through the pass kernels with
+    one reused output buffer.  The plain complex128 path (owqs_unitary per
+    pattern) is timed on the widths up to 10 with the c64 batch's error."""
+    import numpy as np
+    from owqs_inputs import workloads
+    wls = workloads.random_batch(count=args.rec_count)
+    small = []
+    for wl in wls:
+        if len(wl.pattern.inputs) <= 12:
+            h = owqs.load(wl.pattern)
+            h.reorder()
+            small.append((h, wl))
+    wide = [wl for wl in wls if len(wl.pattern.inputs) > 12]
+    outs = [torch.empty(1 << (2 * len(wl.pattern.inputs)), dtype=torch.complex64, device="cuda") for _, wl in small]
+    items = [{"handle": h, "outcomes": wl.outcomes, "psi_in": None, "out": o, "ref": -1}
+             for (h, wl), o in zip(small, outs)]
+    owqs.run_batch(items, dtype="c64")  # first call tunes the column block
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    info, _ = owqs.run_batch(items, dtype="c64")
+    e1.record()
+    torch.cuda.synchronize()
+    t_small = e0.elapsed_time(e1) / 1e3
+    # wide items one at a time (each handle's workspace is released after use);
+    # the first unitary call of a handle captures its graph, the timed second
+    # call replays it
+    t_wide = 0.0
+    upd = sum(h.info()["amp_updates"] << len(wl.pattern.inputs) for h, wl in small)
+    if wide:
+        nmax = max(len(wl.pattern.inputs) for wl in wide)
+        buf = torch.empty(1 << (2 * nmax), dtype=torch.complex64, device="cuda")
+        for wl in wide:
+            n = len(wl.pattern.inputs)
+            h = owqs.load(wl.pattern)
+            h.reorder()
+            upd += h.info()["amp_updates"] << n
+            h.unitary(dtype="c64", outcomes=wl.outcomes, out=buf[: 1 << (2 * n)])
+            e0.record()
+            h.unitary(dtype="c64", outcomes=wl.outcomes, out=buf[: 1 << (2 * n)])
+            e1.record()
+            torch.cuda.synchronize()
+            t_wide += e0.elapsed_time(e1) / 1e3
+            h.close()
+        del buf
+    cols = sum(1 << len(wl.pattern.inputs) for wl in wls)
+    # plain complex128 path on the widths up to 10, and the c64 error there
+    sub = [(i, h, wl) for i, (h, wl) in enumerate(small) if len(wl.pattern.inputs) <= 10]
+    e0.record()
+    refs = [h.unitary(dtype="c128", outcomes=wl.outcomes, use_graph=False)[0] for _, h, wl in sub]
+    e1.record()
+    torch.cuda.synchronize()
+    t128 = e0.elapsed_time(e1) / 1e3
+    err = 0.0
+    for (i, h, wl), r in zip(sub, refs):
+        err = max(err, torch.max(torch.abs(outs[i].to(torch.complex128) - r)).item())
+    e0.record()
+    sub_items = [items[i] for i, _, _ in sub]
+    owqs.run_batch(sub_items, dtype="c64")
+    e1.record()
+    torch.cuda.synchronize()
+    t64_sub = e0.elapsed_time(e1) / 1e3
+    return {"patterns": len(wls), "widths": "6..14", "columns": cols, "amp_updates": upd,
+            "seconds": t_small + t_wide, "smem_batch_seconds": t_small, "wide_seconds": t_wide,
+            "amp_updates_per_s": upd / (t_small + t_wide), "batch_info": info,
+            "c128_plain_subset": {"patterns": len(sub), "seconds_c128_per_pattern_calls": t128,
+                                  "seconds_c64_batch": t64_sub, "speedup": t128 / t64_sub if t64_sub else None,
+                                  "c64_max_abs_err_vs_c128": err, "bound": 2e-5}}
+
+
 def run_owqs(args):
     import numpy as np
     import torch
@@ -312,6 +387,8 @@ def run_owqs(args):
                "h2d_bytes_per_step": (1 << nin) * 8, "d2h_bytes_per_step": (1 << nout) * 8 + 8 * (p.K + 2),
                "ms_per_step": 1e3 * te / args.e2e_steps}
 
+    rec = recognition_leg(args, owqs, torch) if "rec" in legs else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and "cpu" in legs:
         v, desc, dt = oracle_sample(22, args.cols, target_s=15.0)
@@ -332,6 +409,7 @@ def run_owqs(args):
             "fp64": fp64,
             "accuracy": accuracy,
             "e2e": e2e,
+            "recognition": rec,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": launches_per_step * args.steps,
