@@ -111,14 +111,29 @@ owqs_status owqs_get_info(const owqs_pattern* p, owqs_pattern_info* info);
 /* modes (Section 4.5) */
 enum { OWQS_MODE_OWQS = 0, OWQS_MODE_EOWQS = 1 };
 
+/* Learned reorder proposal (not in the paper; it proposes, the greedy PROA
+ * judges).  A 3-layer MLP, OWQS_MODEL_FEATURES -> 64 -> 64 -> 1 with ReLU,
+ * scores every candidate qubit at each reordering step; the lowest score is
+ * measured next.  Its matrix products take bfloat16 inputs (features,
+ * weights and activations rounded to nearest even) and accumulate in FP32;
+ * biases and the FP32 master weights are FP32.  Parameters, in order:
+ * W1[64][F], b1[64], W2[64][64], b2[64], w3[64], b3 (row-major).          */
+#define OWQS_MODEL_FEATURES 12
+#define OWQS_MODEL_PARAMS 5057
+typedef struct owqs_model owqs_model;
+
 typedef struct {
   uint32_t mode;           /* OWQS: dependent measurements wait for their domains;
                               EOWQS: outcomes preselected, every qubit ready   */
   uint32_t product_input;  /* 1: every input qubit starts as its own sub-state  */
   uint32_t sweep;          /* 1: Section 5 sweep a = |O| .. 1 with b = d = |O|,
                               g = 0.5; 0: one run with the weights below        */
-  uint32_t use_learned;    /* 1: ask the learned proposal first; greedy judges  */
+  uint32_t use_learned;    /* 1: also build the learned proposal with `model`;
+                              it is kept only if its (peak live width, amplitude
+                              updates) is no worse than the greedy order's     */
   double alpha, beta, gamma, delta;  /* Eq. 18 weights when sweep == 0 (> 0)   */
+  const owqs_model* model; /* use_learned: the scoring network (runs on the
+                              current device)                                   */
 } owqs_reorder_opts;
 
 typedef struct {
@@ -127,7 +142,11 @@ typedef struct {
   uint64_t amp_updates;    /* amplitude updates under the new order             */
   double alpha_used;       /* Eq. 18 a of the chosen run                        */
   uint32_t learned_accepted; /* 1 if the learned proposal was kept              */
+  uint32_t greedy_peak_live;   /* the greedy order's figures (use_learned)      */
+  uint64_t greedy_amp_updates;
+  uint32_t learned_peak_live;  /* the proposal's figures (use_learned)          */
   uint32_t pad_;
+  uint64_t learned_amp_updates;
 } owqs_reorder_info;
 
 /* PROA (Section 4.3): greedy measurement order with the Eq. 18 cost
@@ -144,6 +163,53 @@ typedef struct {
  * Host-only; needs no GPU.                                                  */
 owqs_status owqs_reorder(owqs_pattern* p, const owqs_reorder_opts* opts,
                          owqs_reorder_info* info, uint32_t* order);
+
+/* Candidate features along a measurement order (training data for the
+ * learned proposal).  At every step of `order` the candidates are the ready
+ * qubits (all unmeasured qubits in EOWQS mode); the row of the qubit `order`
+ * measures there is written with up to max_cands - 1 other candidates drawn
+ * without replacement by a splitmix64 stream seeded with `seed`.  Per row,
+ * OWQS_MODEL_FEATURES floats, with S = max(|O|, 1):
+ *   0 MS/S  1 OS/S  2 SS/S  3 flag  4 degree/4  5 pending E/4
+ *   6 live width/S  7 width at the measurement/S  8 its increase
+ *   9 candidate already live  10 selected neighbours/4  11 steps left/K
+ * (MS, OS, SS and flag as in Eq. 18; live width = qubits of the single
+ * amplitude array).  Rows are grouped by step: step s owns rows
+ * step_first[s] .. step_first[s+1]-1 and target_row[s] is the row of the
+ * measured qubit.  Sizes: feats cap_rows x F, step_first K+1, target_row K;
+ * *nrows receives the row count (if it exceeds cap_rows nothing is written
+ * and OWQS_ERR_ARG is returned).  Host-only.                              */
+owqs_status owqs_reorder_features(const owqs_pattern* p, uint32_t mode, uint32_t product_input,
+                                  const uint32_t* order, uint32_t max_cands, uint64_t seed,
+                                  float* feats, uint32_t* step_first, uint32_t* target_row,
+                                  uint64_t cap_rows, uint64_t* nrows);
+
+/* Model life cycle.  weights: OWQS_MODEL_PARAMS host floats, or NULL for a
+ * seeded initialisation (uniform +-1/sqrt(fan_in)).  The model lives on the
+ * device that is current at creation.                                      */
+owqs_status owqs_model_create(const float* weights, uint64_t seed, owqs_model** m);
+void owqs_model_free(owqs_model* m);
+owqs_status owqs_model_get_weights(const owqs_model* m, float* weights);
+
+/* Scores of nrows feature rows (device arrays) on `stream`. */
+owqs_status owqs_model_score(owqs_model* m, const float* feats, uint64_t nrows, float* scores,
+                             void* stream);
+
+/* Loss and gradient (no update).  The loss is the mean over steps of the
+ * softmax cross-entropy of -score over each step's rows, with target_row as
+ * the label.  feats, step_first, target_row: device arrays as produced by
+ * owqs_reorder_features.  grad: OWQS_MODEL_PARAMS host floats.             */
+owqs_status owqs_model_gradient(owqs_model* m, const float* feats, const uint32_t* step_first,
+                                const uint32_t* target_row, uint32_t nsteps, float* grad,
+                                float* loss, void* stream);
+
+/* Adam training on the GPU: `epochs` sweeps over the steps in minibatches of
+ * batch_steps consecutive steps (shuffled per epoch with `seed`); losses
+ * (optional, host) receives the mean loss of each epoch.                    */
+owqs_status owqs_model_train(owqs_model* m, const float* feats, const uint32_t* step_first,
+                             const uint32_t* target_row, uint32_t nsteps, uint32_t epochs,
+                             uint32_t batch_steps, float lr, uint64_t seed, float* losses,
+                             void* stream);
 
 /* Make `order` (K measured qubits, each once, dependencies first) the active
  * measurement order, built as in owqs_reorder.  Standard form required.    */

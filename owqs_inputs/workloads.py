@@ -62,18 +62,23 @@ def qft(n: int = 24, pattern_index: int = 0, with_input: bool = True) -> Workloa
     return Workload(p, psi, out, p.name)
 
 
+def random_pattern(i: int, wmin: int, wmax: int, dmin: int, dmax: int, config_index: int,
+                   with_input: bool = True) -> Workload:
+    """Pattern i of an uneven random J/CZ set (seeded from config seed XOR i):
+    width uniform in [wmin, wmax], depth uniform in [dmin, dmax], ceil(width/4)
+    CZ pairs per layer; the random input state is drawn only if asked for."""
+    rng = pattern_rng(config_index, i)
+    n = wmin + rng.randint(wmax - wmin + 1)
+    d = dmin + rng.randint(dmax - dmin + 1)
+    gates = random_jcz_circuit(n, d, rng, cz_per_layer=max(1, (n + 3) // 4))
+    p = circuit_to_pattern(n, gates, f"rand{n}x{d}#{i}")
+    psi = random_state(rng, n) if with_input else None
+    out = forced_outcomes(p, rng)
+    return Workload(p, psi, out, p.name)
+
+
 def random_batch(count: int = 256, wmin: int = 6, wmax: int = 14, dmin: int = 10, dmax: int = 40,
-                 config_index: int = 3) -> List[Workload]:
-    """Uneven random J/CZ patterns: width uniform in [wmin, wmax], depth
-    uniform in [dmin, dmax], ceil(width/4) CZ pairs per layer."""
-    res = []
-    for i in range(count):
-        rng = pattern_rng(config_index, i)
-        n = wmin + rng.randint(wmax - wmin + 1)
-        d = dmin + rng.randint(dmax - dmin + 1)
-        gates = random_jcz_circuit(n, d, rng, cz_per_layer=max(1, (n + 3) // 4))
-        p = circuit_to_pattern(n, gates, f"rand{n}x{d}#{i}")
-        psi = random_state(rng, n)
-        out = forced_outcomes(p, rng)
-        res.append(Workload(p, psi, out, p.name))
-    return res
+                 config_index: int = 3, start: int = 0, with_input: bool = True) -> List[Workload]:
+    """Patterns start .. start+count-1 of the uneven random J/CZ set."""
+    return [random_pattern(i, wmin, wmax, dmin, dmax, config_index, with_input)
+            for i in range(start, start + count)]

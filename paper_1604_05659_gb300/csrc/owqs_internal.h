@@ -54,6 +54,29 @@ struct Pattern {
 // peak live width and amplitude updates of the active order (host)
 void order_stats(const Pattern& p, uint32_t* peak_live, uint64_t* amp_updates);
 
+// Make a measurement order the active order (Eq. 17); need_deps rejects
+// orders that measure a qubit before its domains.
+owqs_status build_active_order(Pattern& p, const std::vector<uint32_t>& order, bool need_deps);
+
+// Entanglement graph and dependency data used by the reordering criteria of
+// Section 4.3 (shared by the greedy PROA and the learned proposal).
+struct ReorderGraph {
+  uint32_t n = 0;
+  std::vector<std::vector<uint32_t>> adj;       // all E partners (set)
+  std::vector<std::vector<uint32_t>> pending0;  // E partners with odd multiplicity
+  std::vector<uint32_t> os, ss;                 // OS(v), SS(v)
+  std::vector<std::vector<uint32_t>> deps;      // measurement domains (empty in EOWQS)
+  std::vector<std::vector<uint32_t>> rdeps;     // qubits whose M depends on q
+  std::vector<uint32_t> measured;               // measured qubits (load order)
+  std::vector<char> is_meas;
+};
+ReorderGraph build_reorder_graph(const Pattern& p, bool eowqs);
+
+// The learned proposal's measurement order (owqs_learn.cu): at every step the
+// model scores the candidates and the lowest score is measured next.
+owqs_status learned_order(const Pattern& p, const owqs_model* m, bool eowqs, bool product_input,
+                          std::vector<uint32_t>& order);
+
 // ---------------------------------------------------------------------------
 // compiled pass: the contract between the schedule compiler and the kernels
 //

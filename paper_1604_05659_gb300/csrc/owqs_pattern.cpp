@@ -137,7 +137,7 @@ void order_stats(const Pattern& p, uint32_t* peak_live, uint64_t* amp_updates) {
 // and the corrections in load order.  N commands are dropped: every qubit is
 // prepared just in time.
 // ---------------------------------------------------------------------------
-static owqs_status build_active(Pattern& p, const std::vector<uint32_t>& order, bool need_deps) {
+owqs_status build_active_order(Pattern& p, const std::vector<uint32_t>& order, bool need_deps) {
   const uint32_t n = p.n;
   std::vector<int32_t> m_idx(n, -1);
   std::vector<std::vector<uint32_t>> e_of(n);
@@ -184,21 +184,8 @@ static owqs_status build_active(Pattern& p, const std::vector<uint32_t>& order, 
 // ---------------------------------------------------------------------------
 // PROA (Section 4.3)
 // ---------------------------------------------------------------------------
-namespace {
-
-struct ProaGraph {
-  uint32_t n = 0;
-  std::vector<std::vector<uint32_t>> adj;      // all E partners (set)
-  std::vector<std::vector<uint32_t>> pending0; // E partners with odd multiplicity
-  std::vector<uint32_t> os, ss;
-  std::vector<std::vector<uint32_t>> deps;     // measurement domains
-  std::vector<std::vector<uint32_t>> rdeps;    // qubits whose M depends on q
-  std::vector<uint32_t> measured;              // measured qubits (load order)
-  std::vector<char> is_meas;
-};
-
-ProaGraph build_graph(const Pattern& p, bool eowqs) {
-  ProaGraph g;
+ReorderGraph build_reorder_graph(const Pattern& p, bool eowqs) {
+  ReorderGraph g;
   g.n = p.n;
   const uint32_t n = p.n;
   std::vector<std::set<uint32_t>> adj(n), pend(n), dependents(n);
@@ -246,11 +233,13 @@ ProaGraph build_graph(const Pattern& p, bool eowqs) {
   return g;
 }
 
+namespace {
+
 struct GreedyResult {
   std::vector<uint32_t> order, ms;
 };
 
-GreedyResult greedy(const ProaGraph& g, const std::vector<uint32_t>& inputs, bool product_input,
+GreedyResult greedy(const ReorderGraph& g, const std::vector<uint32_t>& inputs, bool product_input,
                     double a, double b, double gm, double d) {
   const uint32_t n = g.n;
   std::vector<uint32_t> parent(n), size(n, 1);
@@ -416,9 +405,9 @@ owqs_status owqs_reorder(owqs_pattern* h, const owqs_reorder_opts* o, owqs_reord
   Pattern& p = h->p;
   if (!p.standard) return set_error(OWQS_ERR_NOT_STANDARD, "reordering needs the standard form (E, then M, then X/Z)");
   if (o->mode > OWQS_MODE_EOWQS) return set_error(OWQS_ERR_ARG, "bad mode");
-  if (o->use_learned) return set_error(OWQS_ERR_UNSUPPORTED, "learned proposal not available in this call");
+  if (o->use_learned && !o->model) return set_error(OWQS_ERR_ARG, "use_learned needs a model");
   const bool eowqs = o->mode == OWQS_MODE_EOWQS;
-  ProaGraph g = build_graph(p, eowqs);
+  ReorderGraph g = build_reorder_graph(p, eowqs);
   std::vector<std::array<double, 4>> runs;
   const double k = std::max<double>(1.0, (double)p.outputs.size());
   if (o->sweep) {
@@ -452,14 +441,39 @@ owqs_status owqs_reorder(owqs_pattern* h, const owqs_reorder_opts* o, owqs_reord
       best_a = w[0];
     }
   }
-  owqs_status st = build_active(p, best.order, !eowqs);
+  owqs_status st = build_active_order(p, best.order, !eowqs);
   if (st != OWQS_OK) return st;
-  if (order_out) std::copy(best.order.begin(), best.order.end(), order_out);
+  uint32_t g_peak = 0, l_peak = 0;
+  uint64_t g_upd = 0, l_upd = 0;
+  order_stats(p, &g_peak, &g_upd);
+  bool accepted = false;
+  std::vector<uint32_t> lorder;
+  if (o->use_learned) {
+    // the proposal is judged by the greedy order: kept only if its peak live
+    // width and amplitude updates are no worse
+    st = learned_order(p, o->model, eowqs, o->product_input != 0, lorder);
+    if (st != OWQS_OK) return st;
+    st = build_active_order(p, lorder, !eowqs);
+    if (st != OWQS_OK) return st;
+    order_stats(p, &l_peak, &l_upd);
+    accepted = l_peak < g_peak || (l_peak == g_peak && l_upd <= g_upd);
+    if (!accepted) {
+      st = build_active_order(p, best.order, !eowqs);
+      if (st != OWQS_OK) return st;
+    }
+  }
+  const std::vector<uint32_t>& chosen = accepted ? lorder : best.order;
+  if (order_out) std::copy(chosen.begin(), chosen.end(), order_out);
   if (info) {
     std::memset(info, 0, sizeof(*info));
-    info->peak_m = best_peak;
+    info->peak_m = best_peak;  // Table I/III m of the greedy order
     order_stats(p, &info->peak_live, &info->amp_updates);
     info->alpha_used = best_a;
+    info->learned_accepted = accepted ? 1u : 0u;
+    info->greedy_peak_live = g_peak;
+    info->greedy_amp_updates = g_upd;
+    info->learned_peak_live = l_peak;
+    info->learned_amp_updates = l_upd;
   }
   return OWQS_OK;
 }
@@ -468,7 +482,7 @@ owqs_status owqs_set_order(owqs_pattern* h, const uint32_t* order, uint32_t k) {
   clear_error();
   if (!h || (k && !order)) return set_error(OWQS_ERR_ARG, "NULL argument");
   if (!h->p.standard) return set_error(OWQS_ERR_NOT_STANDARD, "setting an order needs the standard form");
-  return build_active(h->p, std::vector<uint32_t>(order, order + k), true);
+  return build_active_order(h->p, std::vector<uint32_t>(order, order + k), true);
 }
 
 owqs_status owqs_reset_order(owqs_pattern* h) {

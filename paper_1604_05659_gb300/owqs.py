@@ -47,12 +47,14 @@ class owqs_pattern_info(C.Structure):
 class owqs_reorder_opts(C.Structure):
     _fields_ = [("mode", C.c_uint32), ("product_input", C.c_uint32), ("sweep", C.c_uint32),
                 ("use_learned", C.c_uint32), ("alpha", C.c_double), ("beta", C.c_double),
-                ("gamma", C.c_double), ("delta", C.c_double)]
+                ("gamma", C.c_double), ("delta", C.c_double), ("model", C.c_void_p)]
 
 
 class owqs_reorder_info(C.Structure):
     _fields_ = [("peak_m", C.c_uint32), ("peak_live", C.c_uint32), ("amp_updates", C.c_uint64),
-                ("alpha_used", C.c_double), ("learned_accepted", C.c_uint32), ("pad_", C.c_uint32)]
+                ("alpha_used", C.c_double), ("learned_accepted", C.c_uint32), ("greedy_peak_live", C.c_uint32),
+                ("greedy_amp_updates", C.c_uint64), ("learned_peak_live", C.c_uint32), ("pad_", C.c_uint32),
+                ("learned_amp_updates", C.c_uint64)]
 
 
 class owqs_run_opts(C.Structure):
@@ -107,6 +109,17 @@ EXPORTS = {
     "owqs_get_index_map": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_int32)]),
     "owqs_describe_passes": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_uint8), C.POINTER(owqs_pass_desc),
                                        C.c_uint32, C.POINTER(C.c_uint32)]),
+    "owqs_reorder_features": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32), C.c_uint32,
+                                        C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64,
+                                        C.POINTER(C.c_uint64)]),
+    "owqs_model_create": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_void_p)]),
+    "owqs_model_free": (None, [C.c_void_p]),
+    "owqs_model_get_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "owqs_model_score": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]),
+    "owqs_model_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p,
+                                      C.POINTER(C.c_float), C.c_void_p]),
+    "owqs_model_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32,
+                                   C.c_uint32, C.c_float, C.c_uint64, C.c_void_p, C.c_void_p]),
     "owqs_last_error": (C.c_char_p, []),
     "owqs_abi_version": (C.c_uint32, []),
 }
@@ -185,8 +198,9 @@ class Handle:
         return {f: getattr(i, f) for f, _ in owqs_pattern_info._fields_}
 
     def reorder(self, mode: str = "owqs", product_input: bool = False, sweep: bool = True,
-                weights=(1.0, 1.0, 0.5, 1.0)):
-        o = owqs_reorder_opts(MODE[mode], int(product_input), int(sweep), 0, *weights)
+                weights=(1.0, 1.0, 0.5, 1.0), model=None):
+        o = owqs_reorder_opts(MODE[mode], int(product_input), int(sweep), int(model is not None), *weights,
+                              model._m if model is not None else None)
         info = owqs_reorder_info()
         order = (C.c_uint32 * max(1, self.K))()
         _check(library().owqs_reorder(self._h, C.byref(o), C.byref(info), order))
@@ -202,6 +216,24 @@ class Handle:
         out = (C.c_uint32 * max(1, self.K))()
         _check(library().owqs_get_order(self._h, out))
         return list(out)[: self.K]
+
+    def features(self, order, mode: str = "eowqs", product_input: bool = False, max_cands: int = 32,
+                 seed: int = 0):
+        """Training rows along `order`: (feats [rows, F] float32, step_first
+        [K+1] uint32, target_row [K] uint32)."""
+        ordr = _u32(order)
+        n = C.c_uint64()
+        st = library().owqs_reorder_features(self._h, MODE[mode], int(product_input), ordr, max_cands, seed,
+                                             None, None, None, 0, C.byref(n))
+        if st not in (OK, ERR_ARG):
+            _check(st)
+        feats = np.zeros((max(1, n.value), NFEAT), dtype=np.float32)
+        first = np.zeros(self.K + 1, dtype=np.uint32)
+        tgt = np.zeros(max(1, self.K), dtype=np.uint32)
+        _check(library().owqs_reorder_features(self._h, MODE[mode], int(product_input), ordr, max_cands, seed,
+                                               feats.ctypes.data, first.ctypes.data, tgt.ctypes.data, n.value,
+                                               C.byref(n)))
+        return feats[: n.value], first, tgt[: self.K]
 
     def index_map(self, pass_index: int):
         out = (C.c_int32 * self.pattern.nqubits)()
@@ -356,6 +388,70 @@ def run_batch(items, *, dtype: str = "c128", column_block: int = 0, stream=None,
     _check(library().owqs_run_batch(arr, n, C.byref(opts), C.byref(info)))
     return ({f: getattr(info, f) for f, _ in owqs_batch_info._fields_ if f != "pad_"},
             ov[: 4 * n].reshape(n, 4) if ov is not None else None)
+
+
+NFEAT = 12
+NPARAM = 5057
+
+
+class Model:
+    """The learned reorder proposal's network (device resident)."""
+
+    def __init__(self, weights: Optional[np.ndarray] = None, seed: int = 0):
+        lib = library()
+        m = C.c_void_p()
+        if weights is not None:
+            w = np.ascontiguousarray(weights, dtype=np.float32)
+            if w.size != NPARAM:
+                raise ValueError(f"expected {NPARAM} weights")
+            _check(lib.owqs_model_create(w.ctypes.data, seed, C.byref(m)))
+        else:
+            _check(lib.owqs_model_create(None, seed, C.byref(m)))
+        self._m = m
+
+    def close(self):
+        if getattr(self, "_m", None):
+            library().owqs_model_free(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def weights(self) -> np.ndarray:
+        w = np.zeros(NPARAM, dtype=np.float32)
+        _check(library().owqs_model_get_weights(self._m, w.ctypes.data))
+        return w
+
+    def score(self, feats_dev, stream=None):
+        import torch
+        out = torch.empty(feats_dev.shape[0], dtype=torch.float32, device=feats_dev.device)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(library().owqs_model_score(self._m, feats_dev.data_ptr(), feats_dev.shape[0], out.data_ptr(),
+                                          C.c_void_p(s.cuda_stream)))
+        return out
+
+    def gradient(self, feats_dev, first_dev, target_dev, stream=None):
+        import torch
+        g = np.zeros(NPARAM, dtype=np.float32)
+        loss = C.c_float()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(library().owqs_model_gradient(self._m, feats_dev.data_ptr(), first_dev.data_ptr(),
+                                             target_dev.data_ptr(), target_dev.shape[0], g.ctypes.data,
+                                             C.byref(loss), C.c_void_p(s.cuda_stream)))
+        return g, loss.value
+
+    def train(self, feats_dev, first_dev, target_dev, *, epochs: int = 10, batch_steps: int = 512,
+              lr: float = 1e-3, seed: int = 0, stream=None):
+        import torch
+        losses = np.zeros(max(1, epochs), dtype=np.float32)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(library().owqs_model_train(self._m, feats_dev.data_ptr(), first_dev.data_ptr(),
+                                          target_dev.data_ptr(), target_dev.shape[0], epochs, batch_steps, lr,
+                                          seed, losses.ctypes.data, C.c_void_p(s.cuda_stream)))
+        return losses[:epochs]
 
 
 def _host_ptr(a) -> int:

@@ -1,0 +1,137 @@
+"""Train the learned reorder proposal on the GPU and save its weights.
+
+  python -m paper_1604_05659_gb300.train_reorder [--train 2000] [--heldout 200]
+
+Training patterns are random J/CZ circuits of 16..30 logical qubits and depth
+20..60 (seeded).  For each one the target order is the cheaper of the two
+greedy orders the library builds, PROA with every qubit ready (EOWQS) and
+PROA with measurement dependencies (OWQS), ranked by (peak live width,
+amplitude updates) -- the quantities that set GPU memory and time.  The
+network learns to score the target's choice lowest among the ready
+candidates at every step (features from owqs_reorder_features, training by
+owqs_model_train: the library's own forward and backward kernels).  The
+held-out patterns are then reordered in EOWQS mode with the proposal, which
+the greedy order judges, and the comparison is stored next to the weights.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+DEFAULT_OUT = os.path.join(HERE, "reorder_mlp.json")
+
+
+def target_order(h):
+    """Cheaper of the EOWQS and OWQS greedy orders by (peak live, updates)."""
+    best = None
+    for mode in ("eowqs", "owqs"):
+        order, info = h.reorder(mode=mode, sweep=(mode == "owqs"),
+                                weights=(float(max(1, h.nout)), float(max(1, h.nout)), 0.5, float(max(1, h.nout))))
+        key = (info["peak_live"], info["amp_updates"])
+        if best is None or key < best[0]:
+            best = (key, order)
+    return best[1]
+
+
+def build_dataset(handles, cands, seed):
+    """handles: iterable of loaded patterns (consumed one at a time)."""
+    feats, firsts, targets = [], [0], []
+    row = 0
+    for i, h in enumerate(handles):
+        order = target_order(h)
+        f, first, tgt = h.features(order, mode="eowqs", max_cands=cands, seed=seed + i)
+        feats.append(f)
+        firsts.extend((first[1:] + row).tolist())
+        targets.extend((tgt + row).tolist())
+        row += f.shape[0]
+    return (np.concatenate(feats).astype(np.float32), np.array(firsts, dtype=np.uint32),
+            np.array(targets, dtype=np.uint32))
+
+
+def evaluate(handles, model, sweep):
+    """EOWQS reordering of each pattern, greedy alone and with the proposal
+    (without the sweep the Eq. 18 weights are Section 5's first run,
+    a = b = d = |O|, g = 0.5)."""
+    rows = []
+    for h in handles:
+        k = float(max(1, h.nout))
+        w = (k, k, 0.5, k)
+        _, g = h.reorder(mode="eowqs", sweep=sweep, weights=w)
+        _, l = h.reorder(mode="eowqs", sweep=sweep, weights=w, model=model)
+        rows.append({"n": h.nin, "K": h.K, "greedy_peak": l["greedy_peak_live"],
+                     "greedy_updates": l["greedy_amp_updates"], "learned_peak": l["learned_peak_live"],
+                     "learned_updates": l["learned_amp_updates"], "accepted": l["learned_accepted"]})
+    return rows
+
+
+def summary(rows):
+    acc = sum(r["accepted"] for r in rows)
+    gp = np.mean([r["greedy_peak"] for r in rows])
+    lp = np.mean([r["learned_peak"] for r in rows])
+    ratio = np.exp(np.mean([np.log(r["greedy_updates"] / r["learned_updates"]) for r in rows]))
+    return {"patterns": len(rows), "accepted": acc, "mean_greedy_peak_live": gp, "mean_learned_peak_live": lp,
+            "geomean_update_ratio_greedy_over_learned": float(ratio),
+            "learned_peak_equals_n_plus_1": sum(r["learned_peak"] == r["n"] + 1 for r in rows)}
+
+
+def main(argv=None):
+    import torch
+    from owqs_inputs import workloads
+    from paper_1604_05659_gb300 import owqs
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--heldout", type=int, default=200)
+    ap.add_argument("--wmin", type=int, default=16)
+    ap.add_argument("--wmax", type=int, default=30)
+    ap.add_argument("--dmin", type=int, default=20)
+    ap.add_argument("--dmax", type=int, default=60)
+    ap.add_argument("--cands", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--batch-steps", type=int, default=2048)
+    ap.add_argument("--eval-sweep", action="store_true", help="judge with the full Section 5 sweep")
+    ap.add_argument("--out", default=DEFAULT_OUT)
+    a = ap.parse_args(argv)
+
+    t0 = time.time()
+
+    def handles(count, start):
+        for i in range(start, start + count):  # one pattern in memory at a time
+            w = workloads.random_pattern(i, a.wmin, a.wmax, a.dmin, a.dmax, 4, with_input=False)
+            yield owqs.load(w.pattern)
+
+    X, first, target = build_dataset(handles(a.train, 0), a.cands, seed=4)
+    t_data = time.time() - t0
+    Xd = torch.from_numpy(X).cuda()
+    Fd = torch.from_numpy(first.astype(np.int32)).cuda()
+    Td = torch.from_numpy(target.astype(np.int32)).cuda()
+    model = owqs.Model(seed=1604)
+    t1 = time.time()
+    losses = model.train(Xd, Fd, Td, epochs=a.epochs, batch_steps=a.batch_steps, lr=a.lr, seed=7)
+    torch.cuda.synchronize()
+    t_train = time.time() - t1
+    t2 = time.time()
+    rows = evaluate(handles(a.heldout, 1_000_000), model, a.eval_sweep)
+    t_eval = time.time() - t2
+    res = {"params": [float(x) for x in model.weights()],
+           "trained_on": {"patterns": a.train, "widths": [a.wmin, a.wmax], "depths": [a.dmin, a.dmax],
+                          "candidates_per_step": a.cands, "rows": int(X.shape[0]), "steps": int(len(target)),
+                          "epochs": a.epochs, "lr": a.lr, "batch_steps": a.batch_steps,
+                          "epoch_losses": [float(x) for x in losses]},
+           "heldout": summary(rows),
+           "seconds": {"data": t_data, "train": t_train, "eval": t_eval}}
+    with open(a.out, "w") as f:
+        json.dump(res, f)
+    print(json.dumps({k: v for k, v in res.items() if k != "params"}))
+
+
+if __name__ == "__main__":
+    main()
