@@ -61,8 +61,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rows", type=int, default=ROWS)
     ap.add_argument("--cols", type=int, default=COLS)
-    ap.add_argument("--legs", default="c64,c128,e2e,cpu,rec",
-                    help="comma list of c64 (always run), c128, e2e, cpu, rec; fewer legs for profiler runs")
+    ap.add_argument("--legs", default="c64,c128,e2e,cpu,rec,learned",
+                    help="comma list of c64 (always run), c128, e2e, cpu, rec, learned; fewer legs for profiler runs")
+    ap.add_argument("--learned-count", type=int, default=24, help="held-out patterns in the learned leg")
     ap.add_argument("--rec-count", type=int, default=256, help="patterns in the recognition leg")
     return ap.parse_args()
 
@@ -267,6 +268,63 @@ def recognition_leg(args, owqs, torch):
                                   "c64_max_abs_err_vs_c128": err, "bound": 2e-5}}
 
 
+def learned_leg(args, owqs, torch, hbm_gbs):
+    """Held-out random J/CZ patterns (16..30 qubits, depth 20..60) reordered
+    in EOWQS mode by the greedy Eq. 18 order alone and with the committed
+    learned proposal (greedy judges).  Reports peak live widths, amplitude
+    updates, acceptance, whether the greedy order's widest array would fit
+    in device memory at all, the GPU time of simulating each kept order
+    (complex64, EOWQS, all-zero branch) up to 26 live qubits, and for the
+    greedy order the time its amplitude updates need at the measured HBM
+    bandwidth (about 2.3 bytes per update)."""
+    import numpy as np
+    from owqs_inputs import workloads
+    path = os.path.join(ROOT, "paper_1604_05659_gb300", "reorder_mlp.json")
+    if not os.path.exists(path):
+        return {"unavailable": "no trained weights committed"}
+    meta = json.load(open(path))
+    model = owqs.Model(weights=np.array(meta["params"], dtype=np.float32))
+    free = torch.cuda.mem_get_info()[0]
+    rows = []
+    for i in range(1_000_000, 1_000_000 + args.learned_count):
+        wl = workloads.random_pattern(i, 16, 30, 20, 60, 4, with_input=False)
+        h = owqs.load(wl.pattern)
+        k = float(max(1, h.nout))
+        w = (k, k, 0.5, k)
+        t0 = time.perf_counter()
+        _, info = h.reorder(mode="eowqs", sweep=False, weights=w, model=model)
+        t_reorder = time.perf_counter() - t0
+        row = {"n": h.nin, "K": h.K, "greedy_peak_live": info["greedy_peak_live"],
+               "learned_peak_live": info["learned_peak_live"], "accepted": info["learned_accepted"],
+               "greedy_amp_updates": info["greedy_amp_updates"], "learned_amp_updates": info["learned_amp_updates"],
+               "reorder_seconds": t_reorder}
+        # a pass moves about 16 bytes per amplitude update of width w (read + write, complex64)
+        row["greedy_hbm_seconds_estimate"] = (2.3 * info["greedy_amp_updates"] / (hbm_gbs * 1e9)
+                                              if info["greedy_amp_updates"] < (1 << 64) - 1 else None)
+        width = info["peak_live"]
+        row["greedy_fits_in_hbm"] = bool((1 << min(info["greedy_peak_live"], 62)) * 8 * 2.5 < free * 0.8)
+        if width <= 26 and (1 << width) * 8 * 2.5 < free * 0.8:
+            out = torch.empty(1 << h.nout, dtype=torch.complex64, device="cuda")
+            h.run(None, dtype="c64", mode="eowqs", policy="zero", out=out, check=False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.run(None, dtype="c64", mode="eowqs", policy="zero", out=out, check=False)
+            torch.cuda.synchronize()
+            row["kept_order_gpu_seconds"] = time.perf_counter() - t0
+            del out
+        h.close()
+        rows.append(row)
+    acc = sum(r["accepted"] for r in rows)
+    return {"patterns": len(rows), "accepted": acc,
+            "mean_greedy_peak_live": float(np.mean([r["greedy_peak_live"] for r in rows])),
+            "mean_learned_peak_live": float(np.mean([r["learned_peak_live"] for r in rows])),
+            "learned_peak_equals_n_plus_1": sum(r["learned_peak_live"] == r["n"] + 1 for r in rows),
+            "greedy_updates_saturated": sum(r["greedy_amp_updates"] == (1 << 64) - 1 for r in rows),
+            "greedy_orders_fitting_hbm": sum(r["greedy_fits_in_hbm"] for r in rows),
+            "kept_order_gpu_seconds_total": float(sum(r.get("kept_order_gpu_seconds", 0.0) for r in rows)),
+            "trained": {k: v for k, v in meta.items() if k != "params"}, "rows": rows}
+
+
 def run_owqs(args):
     import numpy as np
     import torch
@@ -388,6 +446,7 @@ def run_owqs(args):
                "ms_per_step": 1e3 * te / args.e2e_steps}
 
     rec = recognition_leg(args, owqs, torch) if "rec" in legs else None
+    learned = learned_leg(args, owqs, torch, hbm) if "learned" in legs else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and "cpu" in legs:
@@ -410,6 +469,7 @@ def run_owqs(args):
             "accuracy": accuracy,
             "e2e": e2e,
             "recognition": rec,
+            "learned_reorder": learned,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": launches_per_step * args.steps,

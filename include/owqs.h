@@ -102,7 +102,8 @@ typedef struct {
   uint32_t nmeas;        /* K = |V| - |O| (Section 4.3)                     */
   uint32_t standard;     /* 1 if the loaded order is the standard form CME  */
   uint32_t peak_live;    /* widest live array of the ACTIVE command order   */
-  uint64_t amp_updates;  /* sum over commands of 2^(live width), active order */
+  uint64_t amp_updates;  /* sum over commands of 2^(live width), active order;
+                            saturates at UINT64_MAX (orders of 64+ live qubits) */
 } owqs_pattern_info;
 
 /* Facts about the pattern under its active order.  Host-only. */
@@ -139,7 +140,8 @@ typedef struct {
 typedef struct {
   uint32_t peak_m;         /* largest measurement state-space MS (Table I/III m) */
   uint32_t peak_live;      /* widest single live array under the new order      */
-  uint64_t amp_updates;    /* amplitude updates under the new order             */
+  uint64_t amp_updates;    /* amplitude updates under the new order (saturating,
+                              as in owqs_pattern_info)                          */
   double alpha_used;       /* Eq. 18 a of the chosen run                        */
   uint32_t learned_accepted; /* 1 if the learned proposal was kept              */
   uint32_t greedy_peak_live;   /* the greedy order's figures (use_learned)      */
@@ -250,11 +252,47 @@ typedef struct {
  *             policy.
  *   probs     host, K doubles or NULL: the probability of each recorded
  *             outcome given the earlier ones (Eq. 13); 0.5 in EOWQS.
- * Returns after the device work has finished.  In EOWQS mode the output
- * norm is checked against 1 (tolerance 1e-10 C128, 1e-4 C64):
- * OWQS_ERR_NOT_DETERMINISTIC otherwise (a necessary check, not a gflow proof). */
+ * Returns after the device work has finished.  In EOWQS mode the pattern's
+ * open graph must have a gflow (Section 4.5: a pattern without one is
+ * reported as incorrect): the first EOWQS run of a loaded pattern searches
+ * for one (owqs_find_flow, result kept with the pattern) and returns
+ * OWQS_ERR_NOT_DETERMINISTIC, running nothing, if there is none.  The output
+ * norm is then checked against the input's (tolerance 1e-10 C128, 1e-4 C64),
+ * which catches correction domains that do not match the flow:
+ * OWQS_ERR_NOT_DETERMINISTIC as well. */
 owqs_status owqs_run(owqs_pattern* p, const owqs_run_opts* opts, const void* psi_in,
                      void* psi_out, uint8_t* outcomes, double* probs);
+
+/* Flows of the pattern's open graph (G, I, O), Section 4.5 with the
+ * definitions of ref. [13]; G has an edge u-v iff the pattern holds an odd
+ * number of E commands on {u, v}.
+ *   OWQS_FLOW_CAUSAL  f maps each measured qubit i to a non-input f(i)
+ *                     adjacent to i, with i before f(i) and i before every
+ *                     other neighbour of f(i) (returned as g(i) = {f(i)}).
+ *   OWQS_FLOW_GFLOW   every measurement in the XY plane: g maps each measured
+ *                     i to a set of non-inputs, all after i, with i not in
+ *                     g(i), i in Odd(g(i)) (the qubits with an odd number of
+ *                     neighbours in g(i)) and every other member of Odd(g(i))
+ *                     after i.  The causal flow is returned when one exists.
+ * "Before" is by layer: outputs are at layer 0, measured qubits at layers
+ * >= 1, and i is measured before j iff layer[i] > layer[j].  Layers are built
+ * from the outputs back, each qubit placed in the first layer where a
+ * corrector set exists (so the flow is the most delayed one); the gflow
+ * search solves a GF(2) system over the unplaced qubits per layer, O(L |V|^3
+ * / 64) word operations for L layers, run only when no causal flow exists.
+ *   found      out: 1 if a flow of that kind exists, else 0 (status OK)
+ *   layer      optional, nqubits entries: each label's layer; all -1 when
+ *              found = 0
+ *   g_first    optional, nqubits + 1 entries: g(i) is g_members[g_first[i]
+ *              .. g_first[i+1]); empty for outputs and when found = 0
+ *   g_members  optional, g_cap entries (sorted labels per qubit); if g_cap is
+ *              smaller than *g_total nothing is written and OWQS_ERR_ARG is
+ *              returned
+ *   g_total    optional out: the number of members g needs
+ * Host only: needs no GPU. */
+enum { OWQS_FLOW_CAUSAL = 0, OWQS_FLOW_GFLOW = 1 };
+owqs_status owqs_find_flow(const owqs_pattern* p, uint32_t kind, uint32_t* found, int32_t* layer,
+                           uint32_t* g_first, uint32_t* g_members, uint32_t g_cap, uint32_t* g_total);
 
 /* Recognition (Section 1: which unitary a pattern implements).  Computes
  * every basis column at once: the pattern runs with |I| extra reference

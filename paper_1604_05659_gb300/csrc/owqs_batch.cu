@@ -433,8 +433,8 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
     ro.use_graph = o->use_graph;
     owqs_status st;
     if (items[i].psi_in) {
-      st = owqs_run(items[i].pattern, &ro, items[i].psi_in, items[i].out, const_cast<uint8_t*>(items[i].outcomes),
-                    nullptr);
+      st = run_unchecked(items[i].pattern->p, &ro, items[i].psi_in, items[i].out,
+                         const_cast<uint8_t*>(items[i].outcomes), nullptr);
       if (st == OWQS_ERR_NOT_DETERMINISTIC) st = OWQS_OK;  // the caller judges the overlaps
     } else {
       st = owqs_unitary(items[i].pattern, &ro, items[i].outcomes, items[i].out, nullptr);

@@ -43,6 +43,7 @@ struct Pattern {
   bool standard = false;
   bool deps_ok = true;                // active order measures every domain first (D0)
   uint64_t order_version = 0;         // bumped whenever the active order changes
+  int gflow_state = -1;               // open graph has a gflow: -1 not searched yet, 0 no, 1 yes
   std::shared_ptr<RunCache> cache;
   // recognition: the same pattern with |I| untouched reference qubits added as
   // inputs and outputs (all basis columns at once); rebuilt on order changes
@@ -50,6 +51,15 @@ struct Pattern {
   uint64_t aug_version = ~0ull;
   ~Pattern();
 };
+
+// Section 4.5 pre-check: does the open graph have a gflow (searched once,
+// kept with the pattern; owqs_flow.cpp)
+bool has_gflow(Pattern& p);
+
+// owqs_run without the gflow pre-check (batched determinism checks judge
+// the branch overlaps themselves)
+owqs_status run_unchecked(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
+                          uint8_t* outcomes, double* probs);
 
 // peak live width and amplitude updates of the active order (host)
 void order_stats(const Pattern& p, uint32_t* peak_live, uint64_t* amp_updates);
@@ -141,7 +151,34 @@ struct PassParams {
   int perm[64];
 };
 
-enum KernelKind { KK_FAST = 0, KK_GENERIC = 1, KK_FINAL = 2, KK_NORM = 3, KK_PROB = 4, KK_TMA = 5 };
+enum KernelKind { KK_FAST = 0, KK_GENERIC = 1, KK_FINAL = 2, KK_NORM = 3, KK_PROB = 4, KK_TMA = 5, KK_FUSED = 6 };
+
+// Two consecutive measure passes run as one sweep (complex64, TMA).  The
+// contract is the composition of the two single passes: y1 = pass1(in) is
+// rebuilt on chip and never stored, out = pass2(y1).  Both passes must be in
+// star form with no X mask, prepare at most one qubit each, measure bits of
+// the input array at or above the tile width, and the second must not
+// measure the first one's new qubit.  norms[norm_out1] = |y1|^2 and
+// norms[norm_out2] = |out|^2 = |y1|^2 |pass2(y1 / |y1|)|^2 (the stored array
+// is not rescaled by 1/|y1| in between).
+struct FusedParams {
+  const void* in;
+  void* out;
+  double* norms;
+  double* partials;
+  unsigned int* counter;
+  unsigned int* errflag;
+  int n1, r1, b1, r2, b2;   // pass coordinates as in PassDesc
+  int B1, B2;               // the two measured bits in input coordinates
+  int nlo, n_out;           // live output bits, output bits
+  int norm_in, norm_out1, norm_out2;
+  double thresh;
+  uint64_t z1, A1, z2, A2;  // sign forms (star at b1 / b2), in each pass's coordinates
+  uint32_t c01, zb1, c02, zb2;
+  double scale1, w1re, w1im, scale2, w2re, w2im;
+};
+constexpr int kFusedLogTile = 10;  // 2^10 outputs per tile, 4 input runs of 8 KB
+
 
 // TMA-pipelined pass (complex64): log2 of the outputs per tile (16 KB of
 // outputs, 32 KB of inputs) and the number of shared-memory stages
@@ -168,6 +205,11 @@ void fast_config(int dtype, int* lg, int* hint);
 int tma_enabled();
 constexpr int kBlock = 256;
 int max_grid();               // grid cap for grid-stride kernels
+
+bool fusable(const PassDesc& d1, const PassDesc& d2, int dtype);
+void plan_fused(const PassDesc& d1, const PassDesc& d2, FusedParams& F, LaunchPlan& L);
+cudaError_t launch_fused(const FusedParams& F, cudaStream_t s);
+int fusion_enabled();  // OWQS_FUSE=0 turns pass fusion off
 
 // plan + fill the parameter block of one pass (host)
 void plan_pass(const PassDesc& d, int dtype, bool virt_in, PassParams& P, LaunchPlan& L);

@@ -99,6 +99,14 @@ static void set_active_loaded(Pattern& p) {
     if (c.kind == OWQS_CMD_M) p.active_meas.push_back(c.q0);
 }
 
+// total + 2^w, saturating at 2^64 - 1 (orders wider than 63 live qubits
+// cannot be simulated anyway; their count only has to compare as huge).
+static inline uint64_t add_pow2_sat(uint64_t total, uint32_t w) {
+  if (w >= 64) return UINT64_MAX;
+  uint64_t add = 1ull << w;
+  return total > UINT64_MAX - add ? UINT64_MAX : total + add;
+}
+
 // Live width and amplitude updates of the active order.  A qubit joins the
 // live array just before the first command that touches it (N commutes with
 // commands on other qubits); every command counts 2^(live width), N after the
@@ -113,7 +121,7 @@ void order_stats(const Pattern& p, uint32_t* peak_live, uint64_t* amp_updates) {
     if (!live[q]) {
       live[q] = 1;
       ++w;
-      total += 1ull << w;
+      total = add_pow2_sat(total, w);
     }
   };
   for (uint32_t idx : p.active) {
@@ -122,7 +130,7 @@ void order_stats(const Pattern& p, uint32_t* peak_live, uint64_t* amp_updates) {
     touch(c.q0);
     if (c.kind == OWQS_CMD_E) touch(c.q1);
     peak = std::max(peak, w);
-    total += 1ull << w;
+    total = add_pow2_sat(total, w);
     if (c.kind == OWQS_CMD_M) live[c.q0] = 0, --w;
   }
   for (uint32_t q : p.outputs) touch(q);

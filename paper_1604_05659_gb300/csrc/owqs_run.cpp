@@ -98,8 +98,9 @@ struct FixedSource : OutcomeSource {
 // launch list
 // ---------------------------------------------------------------------------
 struct Item {
-  int type = 0;  // 0 pass, 1 norm
+  int type = 0;  // 0 pass, 1 norm, 2 fused pair
   PassParams P;
+  FusedParams F;
   LaunchPlan L;
   const void* norm_in = nullptr;
   uint64_t norm_n = 0;
@@ -117,12 +118,14 @@ class Runner {
   bool immediate = false;
   int vdiag = 0;  // virtual diagonal input over 2 * vdiag bits (recognition)
   std::vector<Item> items;
+  std::vector<char> fused_second;  // per measurement: second of a fused pair
   owqs_status err = OWQS_OK;
 
   void begin(const void* in0, uint64_t in_elems, void* out_final) {
     cur_in_ = in0;
     out_final_ = out_final;
     pass_i_ = 0;
+    sel_ = 0;
     prev_slot_ = -1;
     if (in0) {  // input norm: OWQS divides by it, EOWQS checks against it
       Item it;
@@ -144,13 +147,47 @@ class Runner {
     fill_common(it.P);
     if (!cur_in_) it.P.vdiag = vdiag;
     it.P.in = cur_in_;
-    it.P.out = rc_.buf[pass_i_ & 1];
+    it.P.out = rc_.buf[sel_];
+    sel_ ^= 1;
     it.P.norm_in = prev_slot_;
     it.P.norm_out = mode_ == OWQS_MODE_OWQS ? pass_i_ + 1 : -1;
     issue(it);
     cur_in_ = it.P.out;
     prev_slot_ = it.P.norm_out;
+    fused_second.push_back(0);
     ++pass_i_;
+  }
+
+  // can the next two measure passes run as one sweep
+  bool can_fuse(const PassDesc& d1, const PassDesc& d2) const {
+    return cur_in_ != nullptr && fusion_enabled() && fusable(d1, d2, dtype_);
+  }
+
+  // two measure passes in one sweep: slot pass_i+1 gets |y1|^2 = p(first),
+  // slot pass_i+2 gets p(first) p(second)
+  void measure_pair(const PassDesc& d1, const PassDesc& d2) {
+    Item it;
+    it.type = 2;
+    plan_fused(d1, d2, it.F, it.L);
+    it.F.norms = rc_.norms;
+    it.F.partials = rc_.partials;
+    it.F.counter = rc_.counter;
+    it.F.errflag = rc_.counter + 1;
+    it.F.thresh = thresh_;
+    it.F.in = cur_in_;
+    it.F.out = rc_.buf[sel_];
+    sel_ ^= 1;
+    it.F.norm_in = prev_slot_;
+    if (mode_ == OWQS_MODE_OWQS) {
+      it.F.norm_out1 = pass_i_ + 1;
+      it.F.norm_out2 = pass_i_ + 2;
+    }
+    issue(it);
+    cur_in_ = it.F.out;
+    prev_slot_ = it.F.norm_out1 >= 0 ? it.F.norm_out2 : -1;
+    fused_second.push_back(0);
+    fused_second.push_back(1);
+    pass_i_ += 2;
   }
 
   // both outcome probabilities of the next measurement into slots
@@ -184,7 +221,9 @@ class Runner {
 
   owqs_status launch(const Item& it, cudaStream_t s) {
     cudaError_t e;
-    if (it.type == 1)
+    if (it.type == 2)
+      e = launch_fused(it.F, s);
+    else if (it.type == 1)
       e = launch_norm(it.norm_in, it.norm_n, dtype_, rc_.norms, it.norm_slot, rc_.partials, rc_.counter,
                       it.L.grid, s);
     else
@@ -218,6 +257,7 @@ class Runner {
   const void* cur_in_ = nullptr;
   void* out_final_ = nullptr;
   int pass_i_ = 0;
+  int sel_ = 0;  // ping-pong buffer the next launch writes
   int prev_slot_ = -1;
 };
 
@@ -361,7 +401,7 @@ static owqs_status ensure_pingpong(RunCache* rc, size_t elems, size_t amp) {
 
 static owqs_status finish(Pattern& p, const owqs_run_opts* o, RunCache* rc, const Prepared& pr,
                           cudaStream_t s, uint8_t* outcomes, double* probs, const std::vector<int>& outcome_of_pass,
-                          bool has_input, int vdiag, double* frob2) {
+                          bool has_input, int vdiag, double* frob2, const std::vector<char>& fused_second) {
   const int K = (int)p.meas_qubit.size();
   rc->h_norms.assign((size_t)K + 2, 0.0);
   unsigned int flag = 0;
@@ -379,7 +419,12 @@ static owqs_status finish(Pattern& p, const owqs_run_opts* o, RunCache* rc, cons
   int mi = 0;
   for (const PassDesc& d : pr.passes) {
     if (d.kind != 0) continue;
-    const double pv = o->mode == OWQS_MODE_OWQS ? rc->h_norms[mi + 1] : 0.5;
+    double pv = o->mode == OWQS_MODE_OWQS ? rc->h_norms[mi + 1] : 0.5;
+    if (o->mode == OWQS_MODE_OWQS && (size_t)mi < fused_second.size() && fused_second[mi]) {
+      // second measurement of a fused pair: its slot holds p(first) p(second)
+      const double first = rc->h_norms[mi];
+      pv = first > 0.0 ? pv / first : 0.0;
+    }
     if (probs) probs[d.meas_k] = pv;
     if (outcomes && o->policy != OWQS_OUTCOME_FORCED) outcomes[d.meas_k] = (uint8_t)outcome_of_pass[mi];
     if (o->mode == OWQS_MODE_OWQS && !(pv >= thresh) && st == OWQS_OK)
@@ -414,6 +459,7 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
   if (st != OWQS_OK) return st;
   const int K = (int)p.meas_qubit.size();
   std::vector<int> outcome_of_pass;
+  std::vector<char> fused_second;
 
   if (sampled) {
     if (prof_ms) return set_error(OWQS_ERR_ARG, "profiling needs forced or zero outcomes");
@@ -457,10 +503,18 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
     Runner R(p, *rc, o->dtype, o->mode, s);
     R.vdiag = vdiag;
     R.begin(pr.in_dev, pr.in_elems, pr.out_dev);
-    for (const PassDesc& d : pr.passes) {
-      if (d.kind == 0) R.measure(d);
-      else R.final_pass(d);
+    for (size_t i = 0; i < pr.passes.size(); ++i) {
+      const PassDesc& d = pr.passes[i];
+      if (d.kind != 0) {
+        R.final_pass(d);
+      } else if (i + 1 < pr.passes.size() && pr.passes[i + 1].kind == 0 && R.can_fuse(d, pr.passes[i + 1])) {
+        R.measure_pair(d, pr.passes[i + 1]);
+        ++i;
+      } else {
+        R.measure(d);
+      }
     }
+    fused_second = R.fused_second;
     if (o->io == OWQS_IO_HOST && psi_in) {
       cudaError_t e = cudaMemcpyAsync(rc->in_stage, psi_in, pr.in_elems * pr.amp, cudaMemcpyHostToDevice, s);
       if (e != cudaSuccess) return cuda_fail(e, "input copy");
@@ -535,12 +589,21 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
     if (e != cudaSuccess) return cuda_fail(e, "output copy");
   }
   (void)K;
-  return finish(p, o, rc, pr, s, outcomes, probs, outcome_of_pass, pr.in_dev != nullptr, vdiag, frob2);
+  return finish(p, o, rc, pr, s, outcomes, probs, outcome_of_pass, pr.in_dev != nullptr, vdiag, frob2,
+                fused_second);
 }
 
 }  // namespace owqs
 
 using namespace owqs;
+
+namespace owqs {
+owqs_status run_unchecked(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
+                          uint8_t* outcomes, double* probs) {
+  clear_error();
+  return run_impl(p, o, psi_in, psi_out, outcomes, probs, nullptr, nullptr, nullptr, 0, nullptr);
+}
+}  // namespace owqs
 
 extern "C" {
 
@@ -548,6 +611,8 @@ owqs_status owqs_run(owqs_pattern* h, const owqs_run_opts* o, const void* psi_in
                      uint8_t* outcomes, double* probs) {
   clear_error();
   if (!h) return set_error(OWQS_ERR_ARG, "NULL pattern");
+  if (o && o->mode == OWQS_MODE_EOWQS && !has_gflow(h->p))
+    return set_error(OWQS_ERR_NOT_DETERMINISTIC, "EOWQS: the open graph has no gflow (Section 4.5)");
   return run_impl(h->p, o, psi_in, psi_out, outcomes, probs, nullptr, nullptr, nullptr, 0, nullptr);
 }
 
@@ -598,6 +663,8 @@ owqs_status owqs_profile_run(owqs_pattern* h, const owqs_run_opts* o, const void
   clear_error();
   if (!h || !o || !ms || !nlaunch) return set_error(OWQS_ERR_ARG, "NULL argument");
   if (o->io != OWQS_IO_DEVICE) return set_error(OWQS_ERR_ARG, "profiling takes device vectors");
+  if (o->mode == OWQS_MODE_EOWQS && !has_gflow(h->p))
+    return set_error(OWQS_ERR_NOT_DETERMINISTIC, "EOWQS: the open graph has no gflow (Section 4.5)");
   std::vector<uint8_t> oc;
   if (outcomes) oc.assign(outcomes, outcomes + h->p.meas_qubit.size());
   return run_impl(h->p, o, psi_in, psi_out, oc.empty() ? nullptr : oc.data(), nullptr, ms, bytes, kind, cap,

@@ -22,9 +22,11 @@ STATUS_NAMES = ["OK", "ERR_ARG", "ERR_PATTERN", "ERR_NOT_STANDARD", "ERR_IMPOSSI
                 "ERR_NOT_DETERMINISTIC", "ERR_OOM", "ERR_CUDA", "ERR_TIMEOUT", "ERR_UNSUPPORTED"]
 CMD_KIND = {"N": 0, "E": 1, "M": 2, "X": 3, "Z": 4}
 MODE = {"owqs": 0, "eowqs": 1}
+FLOW_CAUSAL, FLOW_GFLOW = 0, 1
 DTYPE = {"c64": 0, "c128": 1}
 POLICY = {"forced": 0, "sampled": 1, "zero": 2}
-KERNEL_KIND = {0: "fast_pass", 1: "generic_pass", 2: "final", 3: "norm", 4: "prob", 5: "tma_pass"}
+KERNEL_KIND = {0: "fast_pass", 1: "generic_pass", 2: "final", 3: "norm", 4: "prob", 5: "tma_pass",
+               6: "fused_pass"}
 
 
 class OwqsError(RuntimeError):
@@ -120,6 +122,8 @@ EXPORTS = {
                                       C.POINTER(C.c_float), C.c_void_p]),
     "owqs_model_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32,
                                    C.c_uint32, C.c_float, C.c_uint64, C.c_void_p, C.c_void_p]),
+    "owqs_find_flow": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32)]),
     "owqs_last_error": (C.c_char_p, []),
     "owqs_abi_version": (C.c_uint32, []),
 }
@@ -234,6 +238,24 @@ class Handle:
                                                feats.ctypes.data, first.ctypes.data, tgt.ctypes.data, n.value,
                                                C.byref(n)))
         return feats[: n.value], first, tgt[: self.K]
+
+    def find_flow(self, kind: str = "gflow"):
+        """Flow of the open graph (kind "causal" or "gflow"): None if there is
+        none, else (layer per label, g per measured label as a sorted list)."""
+        k = {"causal": FLOW_CAUSAL, "gflow": FLOW_GFLOW}[kind]
+        n = self.pattern.nqubits
+        found, total = C.c_uint32(), C.c_uint32()
+        layer = (C.c_int32 * n)()
+        first = (C.c_uint32 * (n + 1))()
+        _check(library().owqs_find_flow(self._h, k, C.byref(found), layer, first, None, 0, C.byref(total)))
+        if not found.value:
+            return None
+        members = (C.c_uint32 * max(1, total.value))()
+        _check(library().owqs_find_flow(self._h, k, C.byref(found), layer, first, members, total.value,
+                                        C.byref(total)))
+        outs = set(self.pattern.outputs)
+        g = {v: list(members[first[v]:first[v + 1]]) for v in range(n) if v not in outs}
+        return list(layer), g
 
     def index_map(self, pass_index: int):
         out = (C.c_int32 * self.pattern.nqubits)()

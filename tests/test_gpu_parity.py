@@ -277,3 +277,19 @@ def test_brickwork_full_size_properties(env):
     ov2 = torch.vdot(o2, o64)
     assert abs(abs(ov2.item()) - 1) < 1e-4
     del d
+
+
+def test_fused_measurement_pairs(env):
+    """Consecutive measure passes fused into one sweep (complex64): the
+    output and every per-measurement probability still match the oracle; the
+    profile shows the fused kernel ran."""
+    torch, owqs = env
+    rng = SplitMix64(105)
+    for rows, cols in ((14, 8), (13, 10)):
+        wl = workloads.brickwork(rows, cols)
+        p = wl.pattern
+        bits = rng.bits(p.K)
+        h, _ = _compare(env, p, None, bits, "c64", "owqs")
+        ms, by, kd, _ = h.profile(None, dtype="c64", outcomes=bits)
+        assert (kd == 6).sum() >= 5, sorted(set(kd.tolist()))
+        _compare(env, p, None, bits, "c64", "eowqs")
