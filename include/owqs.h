@@ -236,9 +236,13 @@ typedef struct {
                          OWQS_IO_HOST: host pointers, copies done inside the call    */
   uint64_t seed;      /* sampled policy only                                          */
   void* stream;       /* cudaStream_t to run on; NULL = the legacy default stream    */
-  uint32_t use_graph; /* 1: replay the pass sequence as a CUDA graph (forced/zero)   */
-  uint32_t pad_;
+  uint32_t use_graph; /* 1: replay the pass sequence as a CUDA graph                */
+  uint32_t flags;     /* OWQS_RUN_HOST_SAMPLING: draw sampled outcomes on the host,
+                         one device-to-host read per measurement (otherwise they are
+                         drawn on the device whenever no X or Z with a signal comes
+                         before the last measurement, e.g. standard form)            */
 } owqs_run_opts;
+enum { OWQS_RUN_HOST_SAMPLING = 1 };
 
 /* Simulate the pattern under its active order and return the output state.
  *   psi_in    2^|I| amplitudes (bit k = inputs[k]); NULL = |+> on every input

@@ -137,6 +137,8 @@ struct PassParams {
   int qu[kQMax];
   uint64_t qa[kQMax];
   double scale, w1re, w1im, ere, eim, vconst;
+  const double* w1dev;   // device (-1)^s e^{-i theta} written by k_decide; nullptr: w1re, w1im
+  const double* edev;    // device e^{-i theta} (probability pass); nullptr: ere, eim
   int vdiag;             // virtual input: 0 = |+> of value vconst; h > 0 = amplitude 1 where the
                          // low h input bits equal the next h (all basis columns, recognition)
   // fast pass (star form at b, no X): uniform sign tables
@@ -151,7 +153,9 @@ struct PassParams {
   int perm[64];
 };
 
-enum KernelKind { KK_FAST = 0, KK_GENERIC = 1, KK_FINAL = 2, KK_NORM = 3, KK_PROB = 4, KK_TMA = 5, KK_FUSED = 6 };
+enum KernelKind {
+  KK_FAST = 0, KK_GENERIC = 1, KK_FINAL = 2, KK_NORM = 3, KK_PROB = 4, KK_TMA = 5, KK_FUSED = 6, KK_DECIDE = 7
+};
 
 // Two consecutive measure passes run as one sweep (complex64, TMA).  The
 // contract is the composition of the two single passes: y1 = pass1(in) is
@@ -216,6 +220,26 @@ void plan_pass(const PassDesc& d, int dtype, bool virt_in, PassParams& P, Launch
 
 // device launches (owqs_kernels.cu)
 cudaError_t launch_pass(const PassParams& P, const LaunchPlan& L, int dtype, cudaStream_t s);
+
+// Device-drawn outcome of one measurement (sampled policy, k_decide)
+struct DecideParams {
+  const double* norms;   // prob_0 = norms[pslot]
+  int pslot;
+  const uint64_t* seed;  // device: the seed of the splitmix64 stream
+  uint64_t draw;         // which output of the stream (measurements in execution order)
+  uint8_t* outcomes;     // device, K bytes in load order
+  uint32_t meas_k;
+  const double* e_this;  // device: e^{-i theta} of this measurement
+  double* w1;            // out: (-1)^outcome e^{-i theta}
+  // the next measurement in execution order (has_next = 0 for the last)
+  int has_next;
+  const uint32_t* dom;   // device: K-indices of its s-domain, then its t-domain
+  uint32_t sd_off, sd_len, td_off, td_len;
+  double ca, sa;         // cos and sin of its angle alpha
+  double* e_next;        // out: its e^{-i theta}
+};
+cudaError_t launch_decide(const DecideParams& D, cudaStream_t s);
+cudaError_t launch_put_u64(uint64_t* dst, uint64_t v, cudaStream_t s);
 cudaError_t launch_norm(const void* in, uint64_t n, int dtype, double* norms, int slot,
                         double* partials, unsigned int* counter, int grid, cudaStream_t s);
 

@@ -43,6 +43,40 @@ __device__ __forceinline__ double prev_scale(const PassParams& P) {
   return (nv >= P.thresh && nv > 0.0) ? 1.0 / sqrt(nv) : 0.0;
 }
 
+// Compensated (Kahan) FP32 running sum: per-thread sums of squared norms
+// stay in FP32 across tiles and are promoted to FP64 once per kernel (FP64
+// issues at a small fraction of the FP32 rate on GB300)
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
+  const float y = x - comp;
+  const float t = sum + y;
+  comp = (t - sum) - y;
+  sum = t;
+}
+
+// Per-thread running sum of squared norms: compensated FP32 for complex64
+// passes, plain FP64 for complex128
+template <typename T>
+struct NormAcc;
+template <>
+struct NormAcc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) { kahan_add(s, c, x); }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+template <>
+struct NormAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+// (-1)^s e^{-i theta} of the pass: a launch parameter, or, when the outcome
+// is drawn on the device, the value k_decide wrote before this launch
+__device__ __forceinline__ double2 pass_w1(const PassParams& P) {
+  if (P.w1dev) return make_double2(P.w1dev[0], P.w1dev[1]);
+  return make_double2(P.w1re, P.w1im);
+}
+
 // ---------------------------------------------------------------------------
 // Block reduction of NV FP64 values into norms[slot .. slot+NV).  Each block
 // stores its partial; the last block to finish (counted with one atomic)
@@ -119,8 +153,9 @@ __global__ void __launch_bounds__(kBlock) k_generic(const PassParams P) {
   V* __restrict__ out = reinterpret_cast<V*>(P.out);
   const double c = prev_scale(P);
   const T sc = (T)(P.scale * c);
-  const T wr = (T)(P.scale * c * P.w1re), wi = (T)(P.scale * c * P.w1im);
-  const T er = (T)P.ere, ei = (T)P.eim;
+  const double2 w1 = pass_w1(P);
+  const T wr = (T)(P.scale * c * w1.x), wi = (T)(P.scale * c * w1.y);
+  const T er = (T)(P.edev ? P.edev[0] : P.ere), ei = (T)(P.edev ? P.edev[1] : P.eim);
   const uint64_t nout = 1ull << P.n_out;
   const uint64_t inmask = (1ull << P.n_in) - 1ull;
   const uint64_t bb = MODE == 2 ? 0ull : (1ull << P.b);
@@ -255,14 +290,15 @@ __global__ void __launch_bounds__(kBlock) k_fast(const PassParams P) {
   V* __restrict__ out = reinterpret_cast<V*>(P.out);
   const double c = prev_scale(P);
   const T sc = (T)(P.scale * c);
-  const T wr = (T)(P.scale * c * P.w1re), wi = (T)(P.scale * c * P.w1im);
+  const double2 w1 = pass_w1(P);
+  const T wr = (T)(P.scale * c * w1.x), wi = (T)(P.scale * c * w1.y);
   const int b = P.b, nlo = P.nlo, rt = P.rt;
   const uint64_t tiles = 1ull << (P.n_out - L - rt);
   const uint64_t lomask = (1ull << (nlo - L)) - 1ull;
   const int hishift = nlo + rt;
   const uint64_t inmask = (1ull << P.n_in) - 1ull;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  double acc = 0.0;
+  NormAcc<T> acc;
   for (uint64_t tile = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; tile < tiles; tile += stride) {
     const uint64_t J = ((tile & lomask) << L) | ((tile >> (nlo - L)) << hishift);
     const uint64_t K0 = ins0(J, b);
@@ -305,10 +341,10 @@ __global__ void __launch_bounds__(kBlock) k_fast(const PassParams P) {
       }
       st_run<HINT>(out + J + ((uint64_t)t << nlo), y);
     }
-    acc += (double)tacc;
+    acc.add(tacc);
   }
   if (P.norm_out >= 0) {
-    const double a1[1] = {acc};
+    const double a1[1] = {acc.value()};
     reduce_to_slots<1>(a1, P.partials, P.counter, P.norms, P.norm_out);
   }
 }
@@ -385,7 +421,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
   V* __restrict__ out = reinterpret_cast<V*>(P.out);
   const double c = prev_scale(P);
   const T sc = (T)(P.scale * c);
-  const T wr = (T)(P.scale * c * P.w1re), wi = (T)(P.scale * c * P.w1im);
+  const double2 w1 = pass_w1(P);
+  const T wr = (T)(P.scale * c * w1.x), wi = (T)(P.scale * c * w1.y);
   const int b = P.b, nlo = P.nlo, nbc = P.n_out - P.nlo;
   const uint64_t inmask = (1ull << P.n_in) - 1ull;
   const uint64_t tiles = 1ull << (nlo - LTE);
@@ -417,7 +454,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
   if (threadIdx.x == 0)
     for (uint64_t i = 0; i < mine && i < (uint64_t)NS; ++i) issue(i);
 
-  double acc = 0.0;
+  NormAcc<T> acc;
   uint64_t issued = mine < (uint64_t)NS ? mine : (uint64_t)NS;
   uint64_t i = 0;
   bool failed = false;
@@ -464,7 +501,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
         }
       }
     }
-    acc += (double)tacc;
+    acc.add(tacc);
     __syncthreads();  // every thread is done with stage st
     if (threadIdx.x == 0 && issued < mine) issue(issued++);
   }
@@ -478,7 +515,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
     return;  // the block partial is skipped; the host reports the error
   }
   if (P.norm_out >= 0) {
-    const double a1[1] = {acc};
+    const double a1[1] = {acc.value()};
     reduce_to_slots<1>(a1, P.partials, P.counter, P.norms, P.norm_out);
   }
 }
@@ -494,16 +531,48 @@ __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
 // into the second pass's outputs for each value of its new qubit t2.  The
 // low 10 bits of an output index are the same bits in every coordinate
 // system involved (both measured bits lie above them), so per-element signs
-// are the tile's base signs XOR parities of those low bits.
+// are the tile's base signs XOR parities of those low bits.  The base signs
+// are uniform over the tile: the thread that issues a tile's copies computes
+// them once and leaves them in a shared word beside the stage.  Squared
+// norms are summed per thread in FP32 with compensation (GB300 issues FP64
+// at a small fraction of the FP32 rate) and promoted to FP64 once.
+// R1, R2: qubits the two passes prepare (0 or 1).
 // ---------------------------------------------------------------------------
 constexpr int kFusedTE = 1 << kFusedLogTile;
 constexpr int kFusedStageBytes = 4 * kFusedTE * 8;
-constexpr int kFusedSmem = kTmaStages * kFusedStageBytes + kTmaStages * 8;
+constexpr int kFusedSmem = kTmaStages * kFusedStageBytes + kTmaStages * 8 + kTmaStages * 4;
 
+// bit t1*8 + c2: pz1, t1*8 + 2 + c2: pa1, t1*8 + 4 + t2: pz2, t1*8 + 6 + t2: pa2
+template <int R1, int R2>
+__device__ __forceinline__ uint32_t fused_tile_signs(const FusedParams& F, uint64_t L0, int m2bits) {
+  const uint64_t m2 = (1ull << m2bits) - 1ull;
+  uint32_t w = 0;
+#pragma unroll
+  for (int t1 = 0; t1 < (1 << R1); ++t1) {
+    const uint64_t J1 = L0 | ((uint64_t)t1 << F.nlo);
+#pragma unroll
+    for (int c2 = 0; c2 < 2; ++c2) {
+      const uint64_t I1 = (ins0(J1, F.b2) | ((uint64_t)c2 << F.b2)) & m2;
+      const uint64_t K1 = ins0(I1, F.b1);
+      w |= ((F.c01 ^ par64(K1 & F.z1)) & 1u) << (t1 * 8 + c2);
+      w |= ((F.zb1 ^ par64(K1 & F.A1)) & 1u) << (t1 * 8 + 2 + c2);
+    }
+#pragma unroll
+    for (int t2 = 0; t2 < (1 << R2); ++t2) {
+      const uint64_t K2 = ins0(J1 | ((uint64_t)t2 << (F.nlo + R1)), F.b2);
+      w |= ((F.c02 ^ par64(K2 & F.z2)) & 1u) << (t1 * 8 + 4 + t2);
+      w |= ((F.zb2 ^ par64(K2 & F.A2)) & 1u) << (t1 * 8 + 6 + t2);
+    }
+  }
+  return w;
+}
+
+template <int R1, int R2>
 __global__ void __launch_bounds__(kBlock, 2) k_fused(const FusedParams F) {
   constexpr int LTE = kFusedLogTile, TE = kFusedTE, NS = kTmaStages;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * kFusedStageBytes);
+  uint32_t* signs = reinterpret_cast<uint32_t*>(smem + NS * kFusedStageBytes + NS * 8);
   const float2* __restrict__ in = reinterpret_cast<const float2*>(F.in);
   float2* __restrict__ out = reinterpret_cast<float2*>(F.out);
   double cprev = 1.0;
@@ -515,8 +584,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_fused(const FusedParams F) {
               w1i = (float)(F.scale1 * cprev * F.w1im);
   const float sc2 = (float)F.scale2, w2r = (float)(F.scale2 * F.w2re), w2i = (float)(F.scale2 * F.w2im);
   const int lo = F.B1 < F.B2 ? F.B1 : F.B2, hi = F.B1 < F.B2 ? F.B2 : F.B1;
-  const int n2 = F.n1 + F.r1 - 1;
-  const uint64_t m2 = (1ull << n2) - 1ull, inmask = (1ull << F.n1) - 1ull;
+  const int n2 = F.n1 + R1 - 1;
+  const uint64_t inmask = (1ull << F.n1) - 1ull;
   const uint64_t tiles = 1ull << (F.nlo - LTE);
   const uint64_t step = gridDim.x;
   const uint64_t mine = blockIdx.x < tiles ? (tiles - blockIdx.x + step - 1) / step : 0;
@@ -525,11 +594,12 @@ __global__ void __launch_bounds__(kBlock, 2) k_fused(const FusedParams F) {
   const uint32_t z2lo = (uint32_t)F.z2 & lomask, a2lo = (uint32_t)F.A2 & lomask;
   constexpr unsigned RUN = TE * sizeof(float2);
 
-  auto issue = [&](uint64_t i) {
+  auto issue = [&](uint64_t i) {  // thread 0 only
     const int st = (int)(i % NS);
     float2* buf = reinterpret_cast<float2*>(smem + st * kFusedStageBytes);
     const uint64_t L0 = (blockIdx.x + i * step) << LTE;
     const uint64_t ib = ins0(ins0(L0, lo), hi) & inmask;
+    signs[st] = fused_tile_signs<R1, R2>(F, L0, n2);
     mbar_expect_tx(&full[st], 4 * RUN);
     for (int c = 0; c < 4; ++c) {  // corner c = 2*c1 + c2
       const uint64_t off = ((uint64_t)(c >> 1) << F.B1) + ((uint64_t)(c & 1) << F.B2);
@@ -545,7 +615,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_fused(const FusedParams F) {
   if (threadIdx.x == 0)
     for (uint64_t q = 0; q < mine && q < (uint64_t)NS; ++q) issue(q);
 
-  double acc1 = 0.0, acc2 = 0.0;
+  float s1 = 0.f, k1 = 0.f, s2 = 0.f, k2 = 0.f;  // compensated per-thread sums
   uint64_t issued = mine < (uint64_t)NS ? mine : (uint64_t)NS;
   uint64_t i = 0;
   bool failed = false;
@@ -557,28 +627,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_fused(const FusedParams F) {
       break;
     }
     const float2* buf = reinterpret_cast<const float2*>(smem + st * kFusedStageBytes);
+    const uint32_t sg = signs[st];
     const uint64_t L0 = (blockIdx.x + i * step) << LTE;
     float t1acc = 0.f, t2acc = 0.f;
-    for (int t1 = 0; t1 < (1 << F.r1); ++t1) {
-      // first pass: y1 at (c2, t1) for the tile; base signs per c2
-      uint32_t pz1[2], pa1[2];
 #pragma unroll
-      for (int c2 = 0; c2 < 2; ++c2) {
-        const uint64_t J = L0 | ((uint64_t)t1 << F.nlo);
-        const uint64_t I1 = (ins0(J, F.b2) | ((uint64_t)c2 << F.b2)) & m2;
-        const uint64_t K1 = ins0(I1, F.b1);
-        pz1[c2] = F.c01 ^ par64(K1 & F.z1);
-        pa1[c2] = F.zb1 ^ par64(K1 & F.A1);
-      }
-      uint32_t pz2[2] = {0u, 0u}, pa2[2] = {0u, 0u};
+    for (int t1 = 0; t1 < (1 << R1); ++t1) {
+      const uint32_t w = sg >> (t1 * 8);
 #pragma unroll
-      for (int t2 = 0; t2 < 2; ++t2) {
-        if (t2 >= (1 << F.r2)) break;
-        const uint64_t J = L0 | ((uint64_t)t1 << F.nlo) | ((uint64_t)t2 << (F.nlo + F.r1));
-        const uint64_t K2 = ins0(J, F.b2);
-        pz2[t2] = F.c02 ^ par64(K2 & F.z2);
-        pa2[t2] = F.zb2 ^ par64(K2 & F.A2);
-      }
       for (int e = threadIdx.x * 2; e < TE; e += kBlock * 2) {
         float2 y1[2][2];  // [c2][element]
 #pragma unroll
@@ -590,8 +645,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_fused(const FusedParams F) {
 #pragma unroll
           for (int v = 0; v < 2; ++v) {
             const uint32_t jj = (uint32_t)(e + v);
-            const uint32_t s0 = (pz1[c2] ^ __popc(jj & z1lo)) & 1u;
-            const uint32_t s1 = (s0 ^ pa1[c2] ^ __popc(jj & a1lo)) & 1u;
+            const uint32_t s0 = ((w >> c2) ^ __popc(jj & z1lo)) & 1u;
+            const uint32_t s1 = (s0 ^ (w >> (2 + c2)) ^ __popc(jj & a1lo)) & 1u;
             const float a = s0 ? -sc1 : sc1;
             const float br = s1 ? -w1r : w1r, bi = s1 ? -w1i : w1i;
             y1[c2][v].x = a * x0[v].x + br * x1[v].x - bi * x1[v].y;
@@ -600,27 +655,26 @@ __global__ void __launch_bounds__(kBlock, 2) k_fused(const FusedParams F) {
           }
         }
 #pragma unroll
-        for (int t2 = 0; t2 < 2; ++t2) {
-          if (t2 >= (1 << F.r2)) break;
+        for (int t2 = 0; t2 < (1 << R2); ++t2) {
           float2 o[2];
 #pragma unroll
           for (int v = 0; v < 2; ++v) {
             const uint32_t jj = (uint32_t)(e + v);
-            const uint32_t s0 = (pz2[t2] ^ __popc(jj & z2lo)) & 1u;
-            const uint32_t s1 = (s0 ^ pa2[t2] ^ __popc(jj & a2lo)) & 1u;
+            const uint32_t s0 = ((w >> (4 + t2)) ^ __popc(jj & z2lo)) & 1u;
+            const uint32_t s1 = (s0 ^ (w >> (6 + t2)) ^ __popc(jj & a2lo)) & 1u;
             const float a = s0 ? -sc2 : sc2;
             const float br = s1 ? -w2r : w2r, bi = s1 ? -w2i : w2i;
             o[v].x = a * y1[0][v].x + br * y1[1][v].x - bi * y1[1][v].y;
             o[v].y = a * y1[0][v].y + br * y1[1][v].y + bi * y1[1][v].x;
             t2acc += o[v].x * o[v].x + o[v].y * o[v].y;
           }
-          const uint64_t J = L0 | ((uint64_t)t1 << F.nlo) | ((uint64_t)t2 << (F.nlo + F.r1));
+          const uint64_t J = L0 | ((uint64_t)t1 << F.nlo) | ((uint64_t)t2 << (F.nlo + R1));
           *reinterpret_cast<float4*>(out + J + e) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
         }
       }
     }
-    acc1 += (double)t1acc;
-    acc2 += (double)t2acc;
+    kahan_add(s1, k1, t1acc);
+    kahan_add(s2, k2, t2acc);
     __syncthreads();
     if (threadIdx.x == 0 && issued < mine) issue(issued++);
   }
@@ -633,7 +687,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_fused(const FusedParams F) {
     return;
   }
   if (F.norm_out1 >= 0) {
-    const double a2[2] = {acc1, acc2};
+    const double a2[2] = {(double)s1 - (double)k1, (double)s2 - (double)k2};
     reduce_to_slots<2>(a2, F.partials, F.counter, F.norms, F.norm_out1);
   }
 }
@@ -767,22 +821,79 @@ cudaError_t launch_pass(const PassParams& P, const LaunchPlan& L, int dtype, cud
   return dtype == OWQS_C64 ? launch_t<float>(P, L, s) : launch_t<double>(P, L, s);
 }
 
-cudaError_t launch_fused(const FusedParams& F, cudaStream_t s) {
+template <int R1, int R2>
+static cudaError_t launch_fused_t(const FusedParams& F, cudaStream_t s) {
   static int grid_cap = 0;
   static std::mutex mu;
   {
     std::lock_guard<std::mutex> lock(mu);
     if (grid_cap == 0) {
-      cudaError_t e = cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem);
+      cudaError_t e = cudaFuncSetAttribute(k_fused<R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem);
       if (e != cudaSuccess) return e;
       int per_sm = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused, kBlock, kFusedSmem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<R1, R2>, kBlock, kFusedSmem);
       if (e != cudaSuccess) return e;
       grid_cap = std::max(1, per_sm) * (max_grid() / 8);
     }
   }
   const uint64_t tiles = 1ull << (F.nlo - kFusedLogTile);
-  k_fused<<<(int)std::min<uint64_t>(tiles, (uint64_t)grid_cap), kBlock, kFusedSmem, s>>>(F);
+  k_fused<R1, R2><<<(int)std::min<uint64_t>(tiles, (uint64_t)grid_cap), kBlock, kFusedSmem, s>>>(F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused(const FusedParams& F, cudaStream_t s) {
+  switch (F.r1 * 2 + F.r2) {
+    case 0: return launch_fused_t<0, 0>(F, s);
+    case 1: return launch_fused_t<0, 1>(F, s);
+    case 2: return launch_fused_t<1, 0>(F, s);
+    case 3: return launch_fused_t<1, 1>(F, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Outcome of one measurement drawn on the device (sampled policy): u is
+// output number `draw` of the splitmix64 stream seeded with *seed (the
+// generator is counter based: output k mixes seed + (k+1) * 0x9E3779B97F4A7C15
+// with the published splitmix64 finaliser), taken as its top 53 bits over
+// 2^53; outcome 0 iff u <= prob_0 (Fig. 6).  The thread then writes
+// (-1)^outcome e^{-i theta} for the measure pass that follows, and, since
+// every signal of the next measurement is now known (its domains were
+// measured first), the next measurement's e^{-i theta}, theta = (-1)^s alpha
+// + t pi (Eq. 2), for that measurement's probability pass.  One thread.
+// ---------------------------------------------------------------------------
+__global__ void k_decide(const DecideParams D) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  uint64_t z = *D.seed + (D.draw + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  const int o = u <= D.norms[D.pslot] ? 0 : 1;
+  D.outcomes[D.meas_k] = (uint8_t)o;
+  D.w1[0] = o ? -D.e_this[0] : D.e_this[0];
+  D.w1[1] = o ? -D.e_this[1] : D.e_this[1];
+  if (!D.has_next) return;
+  uint32_t ss = 0, tt = 0;
+  for (uint32_t i = 0; i < D.sd_len; ++i) ss ^= D.outcomes[D.dom[D.sd_off + i]];
+  for (uint32_t i = 0; i < D.td_len; ++i) tt ^= D.outcomes[D.dom[D.td_off + i]];
+  double er = D.ca, ei = (ss & 1u) ? D.sa : -D.sa;
+  if (tt & 1u) er = -er, ei = -ei;
+  D.e_next[0] = er;
+  D.e_next[1] = ei;
+}
+
+__global__ void k_put_u64(uint64_t* dst, uint64_t v) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *dst = v;
+}
+
+cudaError_t launch_decide(const DecideParams& D, cudaStream_t s) {
+  k_decide<<<1, 32, 0, s>>>(D);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_put_u64(uint64_t* dst, uint64_t v, cudaStream_t s) {
+  k_put_u64<<<1, 32, 0, s>>>(dst, v);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,9 @@ struct RunCache {
   double* partials = nullptr;
   size_t npartials = 0;
   unsigned int* counter = nullptr;
+  // device-drawn outcomes: [seed u64][w1: 2K doubles][domains: u32][outcomes: K bytes]
+  void* samp = nullptr;
+  size_t samp_bytes = 0;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::string gkey;
@@ -35,7 +38,7 @@ struct RunCache {
     if (device >= 0 && cur != device) cudaSetDevice(device);
     if (gexec) cudaGraphExecDestroy(gexec);
     if (cap) cudaStreamDestroy(cap);
-    for (void* p : {buf[0], buf[1], in_stage, out_stage, (void*)norms, (void*)partials, (void*)counter})
+    for (void* p : {buf[0], buf[1], in_stage, out_stage, (void*)norms, (void*)partials, (void*)counter, samp})
       if (p) cudaFree(p);
     if (device >= 0 && cur >= 0 && cur != device) cudaSetDevice(cur);
   }
@@ -98,9 +101,10 @@ struct FixedSource : OutcomeSource {
 // launch list
 // ---------------------------------------------------------------------------
 struct Item {
-  int type = 0;  // 0 pass, 1 norm, 2 fused pair
+  int type = 0;  // 0 pass, 1 norm, 2 fused pair, 3 device-drawn outcome
   PassParams P;
   FusedParams F;
+  DecideParams D;
   LaunchPlan L;
   const void* norm_in = nullptr;
   uint64_t norm_n = 0;
@@ -151,11 +155,30 @@ class Runner {
     sel_ ^= 1;
     it.P.norm_in = prev_slot_;
     it.P.norm_out = mode_ == OWQS_MODE_OWQS ? pass_i_ + 1 : -1;
+    it.P.w1dev = w1dev_;
     issue(it);
     cur_in_ = it.P.out;
     prev_slot_ = it.P.norm_out;
     fused_second.push_back(0);
     ++pass_i_;
+  }
+
+  // measure pass whose (-1)^s e^{-i theta} is read from device memory
+  // (written by a decide item just before it)
+  void measure_dev(const PassDesc& d, const double* w1) {
+    w1dev_ = w1;
+    measure(d);
+    w1dev_ = nullptr;
+  }
+
+  // draw the outcome of the next measurement on the device
+  void decide(const DecideParams& D) {
+    Item it;
+    it.type = 3;
+    it.D = D;
+    it.L.kind = KK_DECIDE;
+    it.L.bytes = 0.0;
+    issue(it);
   }
 
   // can the next two measure passes run as one sweep
@@ -203,8 +226,17 @@ class Runner {
     it.P.out = nullptr;
     it.P.norm_in = prev_slot_;
     it.P.norm_out = K_ + 2 + 2 * pass_i_;
+    it.P.edev = edev_;
     issue(it);
     return it.P.norm_out;
+  }
+
+  // probability pass whose e^{-i theta} is read from device memory
+  int prob_dev(const PassDesc& d, const double* e) {
+    edev_ = e;
+    const int slot = prob(d);
+    edev_ = nullptr;
+    return slot;
   }
 
   void final_pass(const PassDesc& d) {
@@ -221,7 +253,9 @@ class Runner {
 
   owqs_status launch(const Item& it, cudaStream_t s) {
     cudaError_t e;
-    if (it.type == 2)
+    if (it.type == 3)
+      e = launch_decide(it.D, s);
+    else if (it.type == 2)
       e = launch_fused(it.F, s);
     else if (it.type == 1)
       e = launch_norm(it.norm_in, it.norm_n, dtype_, rc_.norms, it.norm_slot, rc_.partials, rc_.counter,
@@ -258,6 +292,8 @@ class Runner {
   void* out_final_ = nullptr;
   int pass_i_ = 0;
   int sel_ = 0;  // ping-pong buffer the next launch writes
+  const double* w1dev_ = nullptr;
+  const double* edev_ = nullptr;
   int prev_slot_ = -1;
 };
 
@@ -447,6 +483,173 @@ static owqs_status finish(Pattern& p, const owqs_run_opts* o, RunCache* rc, cons
   return st;
 }
 
+// Launch a runner's item list: from a CUDA graph cached under `key` (captured
+// on first use) or one launch at a time.
+static owqs_status replay(RunCache* rc, Runner& R, const std::string& key, bool use_graph, cudaStream_t s) {
+  if (!use_graph) {
+    for (const Item& it : R.items) {
+      owqs_status st = R.launch(it, s);
+      if (st != OWQS_OK) return st;
+    }
+    return OWQS_OK;
+  }
+  if (!rc->gexec || key != rc->gkey) {
+    if (rc->gexec) {
+      cudaGraphExecDestroy(rc->gexec);
+      rc->gexec = nullptr;
+    }
+    if (!rc->cap) {
+      cudaError_t e = cudaStreamCreateWithFlags(&rc->cap, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+    }
+    cudaError_t e = cudaStreamBeginCapture(rc->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    owqs_status st = OWQS_OK;
+    for (const Item& it : R.items) {
+      st = R.launch(it, rc->cap);
+      if (st != OWQS_OK) break;
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(rc->cap, &g);
+    if (st != OWQS_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&rc->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      rc->gexec = nullptr;
+      return cuda_fail(e, "graph instantiate");
+    }
+    rc->gkey = key;
+  }
+  cudaError_t e = cudaGraphLaunch(rc->gexec, s);
+  if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  return OWQS_OK;
+}
+
+// Sampled outcomes without a host round trip per measurement.  Possible when
+// no X or Z command with a signal comes before the last measurement (so the
+// measure passes' sign forms and X masks do not depend on outcomes; true of
+// every standard-form pattern): per measurement a probability pass, k_decide
+// (draws the outcome, writes (-1)^s e^{-i theta} and the next measurement's
+// e^{-i theta}) and the measure pass reading them, all in one graph.  The
+// outcomes are read back once, and the final pass, whose corrections depend
+// on them, is compiled and launched afterwards.
+static bool masks_outcome_free(const Pattern& p) {
+  size_t last_m = 0;
+  for (size_t i = 0; i < p.active.size(); ++i)
+    if (p.cmds[p.active[i]].kind == OWQS_CMD_M) last_m = i;
+  for (size_t i = 0; i < last_m; ++i) {
+    const Cmd& c = p.cmds[p.active[i]];
+    if ((c.kind == OWQS_CMD_X || c.kind == OWQS_CMD_Z) && !c.sdom.empty()) return false;
+  }
+  return true;
+}
+
+static owqs_status sample_on_device(Pattern& p, const owqs_run_opts* o, RunCache* rc, Prepared& pr,
+                                    const std::vector<PassDesc>& zero_passes, cudaStream_t s,
+                                    std::vector<int>& outcome_of_pass) {
+  const size_t K = p.meas_qubit.size();
+  std::vector<const Cmd*> mcmd(K, nullptr);
+  for (const Cmd& c : p.cmds)
+    if (c.kind == OWQS_CMD_M) mcmd[(size_t)p.k_of_qubit[c.q0]] = &c;
+  std::vector<const PassDesc*> meas;
+  for (const PassDesc& d : zero_passes)
+    if (d.kind == 0) meas.push_back(&d);
+  // domains of every measurement after the first, as K-indices
+  std::vector<uint32_t> dom;
+  std::vector<uint32_t> sd_off(meas.size()), td_off(meas.size());
+  for (size_t i = 0; i < meas.size(); ++i) {
+    const Cmd& c = *mcmd[meas[i]->meas_k];
+    sd_off[i] = (uint32_t)dom.size();
+    for (uint32_t q : c.sdom) dom.push_back((uint32_t)p.k_of_qubit[q]);
+    td_off[i] = (uint32_t)dom.size();
+    for (uint32_t q : c.tdom) dom.push_back((uint32_t)p.k_of_qubit[q]);
+  }
+  // workspace: [seed][e: 2K][w1: 2K][dom][outcomes]
+  const size_t off_e = 8, off_w1 = off_e + 16 * K, off_dom = off_w1 + 16 * K;
+  const size_t off_oc = off_dom + 4 * ((dom.size() + 1) & ~(size_t)1);
+  const size_t need = off_oc + ((K + 15) & ~(size_t)15) + 16;
+  if (need > rc->samp_bytes || !rc->samp) {
+    if (rc->gexec) {  // graphs hold the old addresses
+      cudaGraphExecDestroy(rc->gexec);
+      rc->gexec = nullptr;
+      rc->gkey.clear();
+    }
+    owqs_status st = ensure_buf(rc->samp, rc->samp_bytes, need, "sampling workspace");
+    if (st != OWQS_OK) return st;
+  }
+  char* base = static_cast<char*>(rc->samp);
+  uint64_t* seed = reinterpret_cast<uint64_t*>(base);
+  double* e = reinterpret_cast<double*>(base + off_e);
+  double* w1 = reinterpret_cast<double*>(base + off_w1);
+  uint32_t* ddom = reinterpret_cast<uint32_t*>(base + off_dom);
+  uint8_t* doc = reinterpret_cast<uint8_t*>(base + off_oc);
+  // the first measurement's e^{-i theta}: its domains are empty (measured first)
+  double e0[2] = {1.0, 0.0};
+  if (!meas.empty()) {
+    e0[0] = meas[0]->ere;
+    e0[1] = meas[0]->eim;
+  }
+  cudaError_t ce = cudaMemcpyAsync(e, e0, sizeof(e0), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess && !dom.empty())
+    ce = cudaMemcpyAsync(ddom, dom.data(), 4 * dom.size(), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);  // host vectors go out of scope
+  if (ce != cudaSuccess) return cuda_fail(ce, "sampling tables");
+
+  Runner R(p, *rc, o->dtype, o->mode, s);
+  R.begin(pr.in_dev, pr.in_elems, pr.out_dev);
+  for (size_t i = 0; i < meas.size(); ++i) {
+    const PassDesc& d = *meas[i];
+    DecideParams D;
+    std::memset(&D, 0, sizeof(D));
+    D.norms = rc->norms;
+    D.pslot = R.prob_dev(d, e + 2 * i);
+    D.seed = seed;
+    D.draw = i;
+    D.outcomes = doc;
+    D.meas_k = d.meas_k;
+    D.e_this = e + 2 * i;
+    D.w1 = w1 + 2 * i;
+    if (i + 1 < meas.size()) {
+      const Cmd& c = *mcmd[meas[i + 1]->meas_k];
+      D.has_next = 1;
+      D.dom = ddom;
+      D.sd_off = sd_off[i + 1];
+      D.sd_len = (uint32_t)c.sdom.size();
+      D.td_off = td_off[i + 1];
+      D.td_len = (uint32_t)c.tdom.size();
+      D.ca = std::cos(c.angle);
+      D.sa = std::sin(c.angle);
+      D.e_next = e + 2 * (i + 1);
+    }
+    R.decide(D);
+    R.measure_dev(d, w1 + 2 * i);
+  }
+  owqs_status st = launch_put_u64(seed, o->seed, s) == cudaSuccess ? OWQS_OK : cuda_fail(cudaGetLastError(), "seed");
+  if (st != OWQS_OK) return st;
+  st = replay(rc, R, graph_key(p, o, pr.in_dev, pr.out_dev, nullptr), o->use_graph != 0, s);
+  if (st != OWQS_OK) return st;
+  std::vector<uint8_t> oc(std::max<size_t>(K, 1), 0);
+  if (K) ce = cudaMemcpyAsync(oc.data(), doc, K, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return cuda_fail(ce, "reading sampled outcomes");
+  // the whole schedule under the drawn outcomes: the measure passes launched
+  // above are its measure passes (up to their phases, read from the device)
+  FixedSource src(p, oc.data());
+  pr.passes.clear();
+  st = compile_schedule(p, o->mode, src, pr.passes);
+  if (st != OWQS_OK) return st;
+  R.immediate = true;
+  R.final_pass(pr.passes.back());
+  if (R.err != OWQS_OK) return R.err;
+  for (const PassDesc& d : pr.passes)
+    if (d.kind == 0) outcome_of_pass.push_back(d.outcome);
+  return OWQS_OK;
+}
+
 static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
                             uint8_t* outcomes, double* probs, float* prof_ms, double* prof_bytes,
                             uint32_t* prof_kind, uint32_t prof_cap, uint32_t* prof_n, int vdiag = 0,
@@ -464,22 +667,30 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
   if (sampled) {
     if (prof_ms) return set_error(OWQS_ERR_ARG, "profiling needs forced or zero outcomes");
     // structure pass (outcome-independent widths) to size the buffers
-    {
-      FixedSource zero(p, nullptr);
-      std::vector<PassDesc> tmp;
-      if (!p.deps_ok)
-        return set_error(OWQS_ERR_ARG, "sampled outcomes need an order that measures every domain first");
-      st = compile_schedule(p, o->mode, zero, tmp);
-      if (st != OWQS_OK) return st;
-      size_t wmax = 1;
-      for (const PassDesc& d : tmp)
-        if (d.kind == 0) wmax = std::max<size_t>(wmax, (size_t)1 << d.n_out);
-      st = ensure_pingpong(rc, wmax, pr.amp);
-      if (st != OWQS_OK) return st;
-    }
+    FixedSource zero(p, nullptr);
+    std::vector<PassDesc> tmp;
+    if (!p.deps_ok)
+      return set_error(OWQS_ERR_ARG, "sampled outcomes need an order that measures every domain first");
+    st = compile_schedule(p, o->mode, zero, tmp);
+    if (st != OWQS_OK) return st;
+    size_t wmax = 1;
+    for (const PassDesc& d : tmp)
+      if (d.kind == 0) wmax = std::max<size_t>(wmax, (size_t)1 << d.n_out);
+    st = ensure_pingpong(rc, wmax, pr.amp);
+    if (st != OWQS_OK) return st;
     if (o->io == OWQS_IO_HOST && psi_in) {
       cudaError_t e = cudaMemcpyAsync(rc->in_stage, psi_in, pr.in_elems * pr.amp, cudaMemcpyHostToDevice, s);
       if (e != cudaSuccess) return cuda_fail(e, "input copy");
+    }
+    if (!(o->flags & OWQS_RUN_HOST_SAMPLING) && vdiag == 0 && masks_outcome_free(p)) {
+      st = sample_on_device(p, o, rc, pr, tmp, s, outcome_of_pass);
+      if (st != OWQS_OK) return st;
+      if (o->io == OWQS_IO_HOST) {
+        cudaError_t e = cudaMemcpyAsync(psi_out, rc->out_stage, pr.out_elems * pr.amp, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "output copy");
+      }
+      return finish(p, o, rc, pr, s, outcomes, probs, outcome_of_pass, pr.in_dev != nullptr, vdiag, frob2,
+                    fused_second);
     }
     Runner R(p, *rc, o->dtype, o->mode, s);
     R.immediate = true;
@@ -543,45 +754,9 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
       if (prof_n) *prof_n = (uint32_t)R.items.size();
       for (auto& x : ev) cudaEventDestroy(x);
       if (st != OWQS_OK) return st;
-    } else if (o->use_graph) {
-      const std::string key = graph_key(p, o, pr.in_dev, pr.out_dev, outcomes);
-      if (!rc->gexec || key != rc->gkey) {
-        if (rc->gexec) {
-          cudaGraphExecDestroy(rc->gexec);
-          rc->gexec = nullptr;
-        }
-        if (!rc->cap) {
-          cudaError_t e = cudaStreamCreateWithFlags(&rc->cap, cudaStreamNonBlocking);
-          if (e != cudaSuccess) return cuda_fail(e, "capture stream");
-        }
-        cudaError_t e = cudaStreamBeginCapture(rc->cap, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_fail(e, "begin capture");
-        for (const Item& it : R.items) {
-          st = R.launch(it, rc->cap);
-          if (st != OWQS_OK) break;
-        }
-        cudaGraph_t g = nullptr;
-        e = cudaStreamEndCapture(rc->cap, &g);
-        if (st != OWQS_OK) {
-          if (g) cudaGraphDestroy(g);
-          return st;
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "end capture");
-        e = cudaGraphInstantiate(&rc->gexec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-          rc->gexec = nullptr;
-          return cuda_fail(e, "graph instantiate");
-        }
-        rc->gkey = key;
-      }
-      cudaError_t e = cudaGraphLaunch(rc->gexec, s);
-      if (e != cudaSuccess) return cuda_fail(e, "graph launch");
     } else {
-      for (const Item& it : R.items) {
-        st = R.launch(it, s);
-        if (st != OWQS_OK) return st;
-      }
+      st = replay(rc, R, graph_key(p, o, pr.in_dev, pr.out_dev, outcomes), o->use_graph != 0, s);
+      if (st != OWQS_OK) return st;
     }
   }
   if (o->io == OWQS_IO_HOST) {

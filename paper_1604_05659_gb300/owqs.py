@@ -23,10 +23,11 @@ STATUS_NAMES = ["OK", "ERR_ARG", "ERR_PATTERN", "ERR_NOT_STANDARD", "ERR_IMPOSSI
 CMD_KIND = {"N": 0, "E": 1, "M": 2, "X": 3, "Z": 4}
 MODE = {"owqs": 0, "eowqs": 1}
 FLOW_CAUSAL, FLOW_GFLOW = 0, 1
+RUN_HOST_SAMPLING = 1
 DTYPE = {"c64": 0, "c128": 1}
 POLICY = {"forced": 0, "sampled": 1, "zero": 2}
 KERNEL_KIND = {0: "fast_pass", 1: "generic_pass", 2: "final", 3: "norm", 4: "prob", 5: "tma_pass",
-               6: "fused_pass"}
+               6: "fused_pass", 7: "decide"}
 
 
 class OwqsError(RuntimeError):
@@ -61,7 +62,7 @@ class owqs_reorder_info(C.Structure):
 
 class owqs_run_opts(C.Structure):
     _fields_ = [("dtype", C.c_uint32), ("mode", C.c_uint32), ("policy", C.c_uint32), ("io", C.c_uint32),
-                ("seed", C.c_uint64), ("stream", C.c_void_p), ("use_graph", C.c_uint32), ("pad_", C.c_uint32)]
+                ("seed", C.c_uint64), ("stream", C.c_void_p), ("use_graph", C.c_uint32), ("flags", C.c_uint32)]
 
 
 class owqs_batch_item(C.Structure):
@@ -273,10 +274,12 @@ class Handle:
     # -- device calls ----------------------------------------------------
     def run(self, psi_in=None, *, dtype: str = "c128", mode: str = "owqs", policy: str = "forced",
             outcomes=None, seed: int = 0, stream=None, use_graph: bool = True, out=None,
-            check: bool = True):
+            check: bool = True, host_sampling: bool = False):
         """Run on the GPU.  psi_in: torch tensor on the GPU (complex64 for
         c64, complex128 for c128) or None for |+> inputs; returns
-        (psi_out tensor, outcomes array, probs array, status)."""
+        (psi_out tensor, outcomes array, probs array, status).
+        host_sampling: draw sampled outcomes on the host (one device read per
+        measurement) instead of on the device."""
         import torch
         tdt = torch.complex64 if dtype == "c64" else torch.complex128
         if psi_in is not None:
@@ -291,7 +294,7 @@ class Handle:
         probs = np.zeros(max(1, self.K), dtype=np.float64)
         s = stream if stream is not None else torch.cuda.current_stream(dev)
         opts = owqs_run_opts(DTYPE[dtype], MODE[mode], POLICY[policy], 0, seed, C.c_void_p(s.cuda_stream),
-                             int(use_graph), 0)
+                             int(use_graph), RUN_HOST_SAMPLING if host_sampling else 0)
         st = library().owqs_run(self._h, C.byref(opts), C.c_void_p(psi_in.data_ptr() if psi_in is not None else 0),
                                 C.c_void_p(out.data_ptr()), oc.ctypes.data_as(C.POINTER(C.c_uint8)),
                                 probs.ctypes.data_as(C.POINTER(C.c_double)))

@@ -201,6 +201,43 @@ def test_sampled_outcomes_follow_the_oracle_stream(env):
             assert np.max(np.abs(out.cpu().numpy() - ref.psi_out)) <= 1e-12
 
 
+def test_device_sampling_matches_host_sampling(env):
+    """Outcomes drawn on the device (counter-based splitmix64, one graph)
+    equal the per-measurement host draws bit for bit: same outcomes, same
+    probabilities, same output, for complex64 and complex128, with and
+    without a graph; a pattern with X between its measurements takes the
+    host path and still follows the oracle's stream."""
+    torch, owqs = env
+    rng = SplitMix64(106)
+    for p in [workloads.brickwork(12, 16).pattern, workloads.qft(11, with_input=False).pattern,
+              workloads.small_random().pattern]:
+        psi = random_state(rng, len(p.inputs))
+        h = owqs.load(p)
+        h.reorder()
+        for dtype in ("c128", "c64"):
+            for seed in (5, 6):
+                dev_out, dev_oc, dev_p, _ = h.run(_dev(torch, psi, dtype), dtype=dtype, policy="sampled", seed=seed)
+                host_out, host_oc, host_p, _ = h.run(_dev(torch, psi, dtype), dtype=dtype, policy="sampled",
+                                                     seed=seed, host_sampling=True)
+                ng_out, ng_oc, ng_p, _ = h.run(_dev(torch, psi, dtype), dtype=dtype, policy="sampled", seed=seed,
+                                               use_graph=False)
+                assert np.array_equal(dev_oc, host_oc) and np.array_equal(dev_oc, ng_oc)
+                assert np.array_equal(dev_p, host_p) and np.array_equal(dev_p, ng_p)
+                assert torch.equal(dev_out, host_out) and torch.equal(dev_out, ng_out)
+        op = _oracle_for(h, p)
+        ref = substate.run(op, psi, policy="sampled", seed=7)
+        out, oc, probs, _ = h.run(_dev(torch, psi, "c128"), dtype="c128", policy="sampled", seed=7)
+        assert [int(oc[k]) for k in range(p.K)] == [ref.outcomes[q] for q in p.measured()]
+        assert np.max(np.abs(out.cpu().numpy() - ref.psi_out)) <= 1e-12
+    for p in _wild_patterns()[:2]:
+        psi = random_state(rng, len(p.inputs))
+        h = owqs.load(p)
+        out, oc, _, _ = h.run(_dev(torch, psi, "c128"), dtype="c128", policy="sampled", seed=8)
+        ref = substate.run(p, psi, policy="sampled", seed=8)
+        assert [int(oc[k]) for k in range(p.K)] == [ref.outcomes[q] for q in p.measured()]
+        assert np.max(np.abs(out.cpu().numpy() - ref.psi_out)) <= 1e-12
+
+
 def test_host_io_matches_device_io(env):
     torch, owqs = env
     wl = workloads.qft(8)
