@@ -154,7 +154,8 @@ struct PassParams {
 };
 
 enum KernelKind {
-  KK_FAST = 0, KK_GENERIC = 1, KK_FINAL = 2, KK_NORM = 3, KK_PROB = 4, KK_TMA = 5, KK_FUSED = 6, KK_DECIDE = 7
+  KK_FAST = 0, KK_GENERIC = 1, KK_FINAL = 2, KK_NORM = 3, KK_PROB = 4, KK_TMA = 5, KK_FUSED = 6, KK_DECIDE = 7,
+  KK_GROUP = 8
 };
 
 // Two consecutive measure passes run as one sweep (complex64, TMA).  The
@@ -209,6 +210,69 @@ void fast_config(int dtype, int* lg, int* hint);
 int tma_enabled();
 constexpr int kBlock = 256;
 int max_grid();               // grid cap for grid-stride kernels
+
+// A group of 2..kGroupMax consecutive measure passes run as one sweep
+// (complex64, TMA).  Every pass is in star form with no X mask and prepares
+// exactly one qubit, and measures either an input qubit of the group's input
+// array or a qubit prepared earlier in the group.  Then a constant set of M
+// qubits (M = the input qubits the group measures, 1..kGroupRegMax) varies
+// per element of the remaining ("free") input bits: the group is M-qubit
+// register arithmetic per free index.  Slot i of the register starts as
+// input qubit B[i]; the qubit a pass prepares takes the slot of the qubit it
+// measures.  The free bits keep their order and become the low output bits;
+// the surviving register qubits become the top M output bits (outoff).
+//
+// Signs.  Pass j's sign for the element's free index f, output register
+// configuration g and measured value m splits into
+//   m = 0:  c0 ^ par(f & zfree) ^ par(g & zr)
+//   m = 1:  the m = 0 sign ^ zb ^ par(f & afree) ^ par(g & ar)
+// The kernel keeps a scaled register x~ with x[g] = E D(g) x~[g], where E is
+// the element's accumulated sign times the product of the scales and the
+// previous array's 1/sqrt(N), and D(g) = (-1)^par(g & p) a register-diagonal
+// sign whose mask p the host tracks from pass to pass.  A pass then computes
+//   x~'[g] = x~[g0] + ct[g] (-1)^rho w x~[g1]      (g0, g1: g with the
+// measured slot 0 / 1), rho = zb ^ par(f & afree) per element, ct[g] =
+// (-1)^(par(g & ar) ^ p_slot), and the element's sign collects
+// c0 ^ par(f & zfree); the new mask is zr ^ (p without the measured slot).
+// The store multiplies by E and fin[g] = D_final(g) * product of scales.
+// A tile is 2^(12-M) consecutive free indices (2^M input runs of 2^(12-M)
+// amplitudes: 32 KB), so every B[i] must be >= 12 - M.
+// norms[norm_out + j] = squared norm after pass j (no rescaling inside the
+// group): the product of the group's first j+1 outcome probabilities;
+// nscale[j] = product of the first j+1 squared scales.
+constexpr int kGroupMax = 12;
+constexpr int kGroupRegMax = 3;
+struct GroupPass {
+  int slot;                 // register slot measured, then refilled by the new qubit
+  uint32_t c0, zb;
+  uint32_t zr, ar;          // register parts of the sign masks (bit t = slot t)
+  uint32_t zlo, alo;        // zfree, afree within a tile (low 12 - M bits)
+  uint64_t zfree, afree;    // sign masks over the free index
+  double scale, wre, wim;   // scale and (-1)^s e^{-i theta}
+  float ct[1 << kGroupRegMax];  // +-1 per output configuration
+  float fwr, fwi;           // (-1)^s e^{-i theta} in FP32
+};
+struct GroupParams {
+  const void* in;
+  void* out;
+  double* norms;
+  double* partials;
+  unsigned int* counter;
+  unsigned int* errflag;
+  int k, m, lt;             // passes, register qubits, log2 tile (12 - m)
+  int nfree;                // free bits (input bits minus m)
+  int B[kGroupRegMax];      // input bit of each slot's initial qubit
+  uint64_t outoff[1 << kGroupRegMax];
+  float fin[1 << kGroupRegMax];
+  double nscale[kGroupMax];
+  int norm_in, norm_out;
+  double thresh;
+  GroupPass pass[kGroupMax];
+};
+// longest group starting at passes[i] (0 or 1 if none), planned into G
+int plan_group(const std::vector<PassDesc>& passes, size_t i, int dtype, GroupParams& G, LaunchPlan& L);
+cudaError_t launch_group(const GroupParams& G, cudaStream_t s);
+int group_enabled();  // OWQS_GROUP=0 turns group fusion off
 
 bool fusable(const PassDesc& d1, const PassDesc& d2, int dtype);
 void plan_fused(const PassDesc& d1, const PassDesc& d2, FusedParams& F, LaunchPlan& L);

@@ -86,7 +86,7 @@ __device__ __forceinline__ double2 pass_w1(const PassParams& P) {
 // ---------------------------------------------------------------------------
 template <int NV>
 __device__ __forceinline__ void reduce_to_slots(const double (&acc)[NV], double* partials,
-                                                unsigned int* counter, double* norms, int slot) {
+                                                unsigned int* counter, double* norms, int slot, int nv = NV) {
   __shared__ double sh[NV][32];
   __shared__ int am_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -133,7 +133,7 @@ __device__ __forceinline__ void reduce_to_slots(const double (&acc)[NV], double*
     if (threadIdx.x == 0) {
       double tot = 0.0;
       for (int w = 0; w < nwarp; ++w) tot += sh[i][w];
-      norms[slot + i] = tot;
+      if (i < nv) norms[slot + i] = tot;
     }
   }
   if (threadIdx.x == 0) *counter = 0u;
@@ -376,6 +376,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   uint32_t ok;
@@ -841,6 +844,40 @@ static cudaError_t launch_fused_t(const FusedParams& F, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int M>
+__global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G);
+
+template <int M>
+static cudaError_t launch_group_t(const GroupParams& G, cudaStream_t s) {
+  constexpr int STAGE = (1 << M) * (1 << (12 - M)) * 8;
+  constexpr int SMEM = kTmaStages * STAGE + 2 * kTmaStages * 8 + kTmaStages * 4 + 16;
+  static int grid_cap = 0;
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (grid_cap == 0) {
+      cudaError_t e = cudaFuncSetAttribute(k_group<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+      if (e != cudaSuccess) return e;
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group<M>, kBlock, SMEM);
+      if (e != cudaSuccess) return e;
+      grid_cap = std::max(1, per_sm) * (max_grid() / 8);
+    }
+  }
+  const uint64_t tiles = 1ull << (G.nfree - (12 - M));
+  k_group<M><<<(int)std::min<uint64_t>(tiles, (uint64_t)grid_cap), kBlock, SMEM, s>>>(G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group(const GroupParams& G, cudaStream_t s) {
+  switch (G.m) {
+    case 1: return launch_group_t<1>(G, s);
+    case 2: return launch_group_t<2>(G, s);
+    case 3: return launch_group_t<3>(G, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_fused(const FusedParams& F, cudaStream_t s) {
   switch (F.r1 * 2 + F.r2) {
     case 0: return launch_fused_t<0, 0>(F, s);
@@ -848,6 +885,225 @@ cudaError_t launch_fused(const FusedParams& F, cudaStream_t s) {
     case 2: return launch_fused_t<1, 0>(F, s);
     case 3: return launch_fused_t<1, 1>(F, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Group of up to kGroupMax measure passes in one HBM sweep (complex64): per
+// free index the group is arithmetic on an M-qubit register (the contract,
+// including how the signs and scales are carried, is in owqs_internal.h).
+// A tile is 2^(12-M) consecutive free indices; its 2^M input runs (one per
+// configuration of the register's input qubits) arrive by bulk copies into a
+// 3-stage shared-memory ring, 32 KB per stage.  Each thread takes two
+// consecutive elements at a time and holds their 2^M amplitudes in
+// registers.  Per pass and element: one sign bit selecting +-w; per
+// butterfly: one complex product and, per output, one packed FP32x2
+// multiply-add for the amplitude and one for its squared norm.  The
+// element's sign, the previous array's 1/sqrt(N) and the carried scales and
+// register signs are applied once, at the 16-byte stores.
+// Sign bits: the tile's part (two bits per pass) comes from the issuing
+// thread through a shared word; the element's low-bit parities are fixed
+// per thread (a thread always takes the same offsets within a tile), so per
+// tile one XOR gives every sign bit of an element.
+// Pipeline: a stage is refilled once every warp has released it (one
+// arrival per warp on the stage's "empty" mbarrier), so warps run up to
+// kTmaStages - 1 tiles apart instead of meeting at a block barrier per tile.
+// Every wait is bounded; a block that gives up sets the error flag, lets its
+// issued copies land and returns.  Squared norms after every pass are summed
+// per thread in compensated FP32 and reduced once into k slots.
+// ---------------------------------------------------------------------------
+template <int M, int S>
+__device__ __forceinline__ void group_butterfly(float2 (&x)[1 << M], const GroupPass& P, float wr, float wi,
+                                                float2& nacc) {
+#pragma unroll
+  for (int h = 0; h < (1 << (M - 1)); ++h) {
+    const int g0 = ((h >> S) << (S + 1)) | (h & ((1 << S) - 1));
+    const int g1 = g0 | (1 << S);
+    const float2 x0 = x[g0], x1 = x[g1];
+    const float2 v = make_float2(fmaf(wr, x1.x, -wi * x1.y), fmaf(wr, x1.y, wi * x1.x));
+    const float2 y0 = make_float2(fmaf(P.ct[g0], v.x, x0.x), fmaf(P.ct[g0], v.y, x0.y));
+    const float2 y1 = make_float2(fmaf(P.ct[g1], v.x, x0.x), fmaf(P.ct[g1], v.y, x0.y));
+    nacc = __ffma2_rn(y0, y0, nacc);
+    nacc = __ffma2_rn(y1, y1, nacc);
+    x[g0] = y0;
+    x[g1] = y1;
+  }
+}
+
+template <int M, int S>
+__device__ __forceinline__ void group_pass2(float2 (&x)[2][1 << M], const GroupPass& P, uint32_t r0, uint32_t r1,
+                                            float2& nacc) {
+  const float wr0 = r0 ? -P.fwr : P.fwr, wi0 = r0 ? -P.fwi : P.fwi;
+  const float wr1 = r1 ? -P.fwr : P.fwr, wi1 = r1 ? -P.fwi : P.fwi;
+  group_butterfly<M, S>(x[0], P, wr0, wi0, nacc);
+  group_butterfly<M, S>(x[1], P, wr1, wi1, nacc);
+}
+
+template <int M>
+__global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
+  constexpr int LT = 12 - M, TE = 1 << LT, NC = 1 << M, NS = kTmaStages;
+  constexpr int STAGE = NC * TE * 8;
+  constexpr int EPT = TE / kBlock;  // elements per thread per tile (even)
+  constexpr int NWARP = kBlock / 32;
+  static_assert(EPT >= 2 && EPT <= 8, "tile shape");
+  static_assert(2 * kGroupMax <= 32, "two sign bits per pass in one word");
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * STAGE);
+  uint64_t* empty = full + NS;
+  uint32_t* signs = reinterpret_cast<uint32_t*>(smem + NS * STAGE + 2 * NS * 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(signs + NS);
+  const float2* __restrict__ in = reinterpret_cast<const float2*>(G.in);
+  float2* __restrict__ out = reinterpret_cast<float2*>(G.out);
+  double cprev = 1.0;
+  if (G.norm_in >= 0) {
+    const double nv = G.norms[G.norm_in];
+    cprev = (nv >= G.thresh && nv > 0.0) ? 1.0 / sqrt(nv) : 0.0;
+  }
+  const float fprev = (float)cprev;
+  const uint64_t tiles = 1ull << (G.nfree - LT);
+  const uint64_t step = gridDim.x;
+  const uint64_t mine = blockIdx.x < tiles ? (tiles - blockIdx.x + step - 1) / step : 0;
+  constexpr unsigned RUN = TE * sizeof(float2);
+  const int k = G.k;
+  // the element's low-bit sign parities, two bits per pass in the tile word's
+  // layout (element q at offset 2 threadIdx + (q>>1) 2 kBlock + (q&1))
+  uint32_t lowbits[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const uint32_t e = (uint32_t)(threadIdx.x * 2 + (q >> 1) * kBlock * 2 + (q & 1));
+    uint32_t w = 0;
+#pragma unroll
+    for (int j = 0; j < kGroupMax; ++j) {
+      w |= ((uint32_t)__popc(e & G.pass[j].zlo) & 1u) << (2 * j);
+      w |= ((uint32_t)__popc(e & G.pass[j].alo) & 1u) << (2 * j + 1);
+    }
+    lowbits[q] = w;
+  }
+  const uint32_t evenk = 0x55555555u & ((k >= 16) ? 0xffffffffu : ((1u << (2 * k)) - 1u));
+
+  auto issue = [&](uint64_t i) {  // thread 0 only
+    const int st = (int)(i % NS);
+    float2* buf = reinterpret_cast<float2*>(smem + st * STAGE);
+    const uint64_t L0 = (blockIdx.x + i * step) << LT;
+    uint64_t ib = L0;  // free index with zeros inserted at the register inputs (ascending)
+    int sorted[M];
+#pragma unroll
+    for (int q = 0; q < M; ++q) sorted[q] = G.B[q];
+#pragma unroll
+    for (int q = 0; q < M; ++q)
+#pragma unroll
+      for (int r = q + 1; r < M; ++r)
+        if (sorted[r] < sorted[q]) {
+          const int tmp = sorted[q];
+          sorted[q] = sorted[r];
+          sorted[r] = tmp;
+        }
+#pragma unroll
+    for (int q = 0; q < M; ++q) ib = ins0(ib, sorted[q]);
+    uint32_t w = 0;
+    for (int j = 0; j < k; ++j) {
+      w |= ((G.pass[j].c0 ^ par64(L0 & G.pass[j].zfree)) & 1u) << (2 * j);
+      w |= ((G.pass[j].zb ^ par64(L0 & G.pass[j].afree)) & 1u) << (2 * j + 1);
+    }
+    signs[st] = w;
+    mbar_expect_tx(&full[st], NC * RUN);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      uint64_t off = 0;
+#pragma unroll
+      for (int q = 0; q < M; ++q) off += (uint64_t)((c >> q) & 1) << G.B[q];
+      bulk_g2s(buf + c * TE, in + ib + off, RUN, &full[st]);
+    }
+  };
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NS; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], NWARP);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (uint64_t q = 0; q < mine && q < (uint64_t)NS; ++q) issue(q);
+
+  float ks[kGroupMax], kc[kGroupMax];
+#pragma unroll
+  for (int j = 0; j < kGroupMax; ++j) ks[j] = kc[j] = 0.f;
+  uint64_t issued = mine < (uint64_t)NS ? mine : (uint64_t)NS;  // thread 0's count
+  for (uint64_t i = 0; i < mine; ++i) {
+    const int st = (int)(i % NS);
+    if (*abort_flag) break;
+    if (!mbar_wait_bounded(&full[st], (unsigned)((i / NS) & 1u))) {
+      *abort_flag = 1;
+      break;
+    }
+    const float2* buf = reinterpret_cast<const float2*>(smem + st * STAGE);
+    const uint32_t sw = signs[st];
+    const uint64_t L0 = (blockIdx.x + i * step) << LT;
+    float2 tacc[kGroupMax];
+#pragma unroll
+    for (int j = 0; j < kGroupMax; ++j) tacc[j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int it = 0; it < EPT / 2; ++it) {
+      const int e = threadIdx.x * 2 + it * kBlock * 2;
+      float2 x[2][NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const float4 v = *reinterpret_cast<const float4*>(buf + c * TE + e);
+        x[0][c] = make_float2(v.x, v.y);
+        x[1][c] = make_float2(v.z, v.w);
+      }
+      const uint32_t b0 = sw ^ lowbits[2 * it], b1 = sw ^ lowbits[2 * it + 1];
+#pragma unroll
+      for (int j = 0; j < kGroupMax; ++j) {
+        if (j >= k) break;
+        const GroupPass& P = G.pass[j];
+        const uint32_t r0 = (b0 >> (2 * j + 1)) & 1u, r1 = (b1 >> (2 * j + 1)) & 1u;
+        if (M == 1 || P.slot == 0) group_pass2<M, 0>(x, P, r0, r1, tacc[j]);
+        else if (M == 2 || P.slot == 1) group_pass2<M, (M > 1 ? 1 : 0)>(x, P, r0, r1, tacc[j]);
+        else group_pass2<M, (M > 2 ? 2 : 0)>(x, P, r0, r1, tacc[j]);
+      }
+      const float f0 = (__popc(b0 & evenk) & 1) ? -fprev : fprev;
+      const float f1 = (__popc(b1 & evenk) & 1) ? -fprev : fprev;
+#pragma unroll
+      for (int g = 0; g < NC; ++g) {
+        const float s0 = f0 * G.fin[g], s1 = f1 * G.fin[g];
+        *reinterpret_cast<float4*>(out + L0 + G.outoff[g] + e) =
+            make_float4(s0 * x[0][g].x, s0 * x[0][g].y, s1 * x[1][g].x, s1 * x[1][g].y);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kGroupMax; ++j) kahan_add(ks[j], kc[j], tacc[j].x + tacc[j].y);
+    // release the stage; thread 0 refills it once every warp has released it
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[st]);
+    if (threadIdx.x == 0 && issued < mine) {
+      if (!mbar_wait_bounded(&empty[st], (unsigned)((i / NS) & 1u))) {
+        *abort_flag = 1;
+        break;
+      }
+      issue(issued++);
+    }
+  }
+  __syncthreads();
+  if (*abort_flag) {
+    if (threadIdx.x == 0) {
+      atomicExch(G.errflag, 1u);
+      // let every issued copy land before the block's memory goes away
+      for (uint64_t j = issued > (uint64_t)NS ? issued - NS : 0; j < issued; ++j)
+        mbar_wait_bounded(&full[j % NS], (unsigned)((j / NS) & 1u));
+    }
+    __syncthreads();
+    return;
+  }
+  if (G.norm_out >= 0) {
+    const double c2 = cprev * cprev;
+    double a[kGroupMax];
+#pragma unroll
+    for (int j = 0; j < kGroupMax; ++j) a[j] = c2 * G.nscale[j] * ((double)ks[j] - (double)kc[j]);
+    reduce_to_slots<kGroupMax>(a, G.partials, G.counter, G.norms, G.norm_out, k);
   }
 }
 

@@ -101,9 +101,10 @@ struct FixedSource : OutcomeSource {
 // launch list
 // ---------------------------------------------------------------------------
 struct Item {
-  int type = 0;  // 0 pass, 1 norm, 2 fused pair, 3 device-drawn outcome
+  int type = 0;  // 0 pass, 1 norm, 2 fused pair, 3 device-drawn outcome, 4 pass group
   PassParams P;
   FusedParams F;
+  GroupParams G;
   DecideParams D;
   LaunchPlan L;
   const void* norm_in = nullptr;
@@ -181,6 +182,37 @@ class Runner {
     issue(it);
   }
 
+  // a group of k consecutive measure passes as one sweep: slots pass_i+1 ..
+  // pass_i+k get the running products of the group's probabilities
+  void measure_group(const GroupParams& G, const LaunchPlan& L) {
+    Item it;
+    it.type = 4;
+    it.G = G;
+    it.L = L;
+    it.G.norms = rc_.norms;
+    it.G.partials = rc_.partials;
+    it.G.counter = rc_.counter;
+    it.G.errflag = rc_.counter + 1;
+    it.G.thresh = thresh_;
+    it.G.in = cur_in_;
+    it.G.out = rc_.buf[sel_];
+    sel_ ^= 1;
+    it.G.norm_in = prev_slot_;
+    it.G.norm_out = mode_ == OWQS_MODE_OWQS ? pass_i_ + 1 : -1;
+    issue(it);
+    cur_in_ = it.G.out;
+    prev_slot_ = mode_ == OWQS_MODE_OWQS ? pass_i_ + G.k : -1;
+    fused_second.push_back(0);
+    for (int j = 1; j < G.k; ++j) fused_second.push_back(1);
+    pass_i_ += G.k;
+  }
+
+  // longest pass group starting at passes[i] that can run as one sweep (0 if none)
+  int group_at(const std::vector<PassDesc>& passes, size_t i, GroupParams& G, LaunchPlan& L) const {
+    if (cur_in_ == nullptr || !group_enabled()) return 0;
+    return plan_group(passes, i, dtype_, G, L);
+  }
+
   // can the next two measure passes run as one sweep
   bool can_fuse(const PassDesc& d1, const PassDesc& d2) const {
     return cur_in_ != nullptr && fusion_enabled() && fusable(d1, d2, dtype_);
@@ -253,7 +285,9 @@ class Runner {
 
   owqs_status launch(const Item& it, cudaStream_t s) {
     cudaError_t e;
-    if (it.type == 3)
+    if (it.type == 4)
+      e = launch_group(it.G, s);
+    else if (it.type == 3)
       e = launch_decide(it.D, s);
     else if (it.type == 2)
       e = launch_fused(it.F, s);
@@ -394,7 +428,7 @@ static owqs_status prepare(Pattern& p, const owqs_run_opts* o, const void* psi_i
   pr.out_elems = 1ull << p.outputs.size();
   st = ensure_buf((void*&)rc->norms, rc->nnorms, sizeof(double) * (3 * (size_t)K + 8), "norm slots");
   if (st == OWQS_OK)
-    st = ensure_buf((void*&)rc->partials, rc->npartials, sizeof(double) * 2 * (size_t)max_grid(), "partials");
+    st = ensure_buf((void*&)rc->partials, rc->npartials, sizeof(double) * kGroupMax * (size_t)max_grid(), "partials");
   if (st == OWQS_OK && !rc->counter) {  // [0] finished-block counter, [1] error flag
     cudaError_t e = cudaMalloc(&rc->counter, 2 * sizeof(unsigned int));
     if (e != cudaSuccess) return cuda_fail(e, "counter");
@@ -716,8 +750,14 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
     R.begin(pr.in_dev, pr.in_elems, pr.out_dev);
     for (size_t i = 0; i < pr.passes.size(); ++i) {
       const PassDesc& d = pr.passes[i];
+      GroupParams G;
+      LaunchPlan GL;
+      int gk = 0;
       if (d.kind != 0) {
         R.final_pass(d);
+      } else if ((gk = R.group_at(pr.passes, i, G, GL)) >= 2) {
+        R.measure_group(G, GL);
+        i += (size_t)gk - 1;
       } else if (i + 1 < pr.passes.size() && pr.passes[i + 1].kind == 0 && R.can_fuse(d, pr.passes[i + 1])) {
         R.measure_pair(d, pr.passes[i + 1]);
         ++i;

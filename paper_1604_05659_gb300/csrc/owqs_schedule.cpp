@@ -239,6 +239,130 @@ static bool star_mask(const PassDesc& d, uint64_t* amask) {
   return true;
 }
 
+int group_enabled() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = std::getenv("OWQS_GROUP");
+    on = (e && e[0] == '0') ? 0 : 1;
+  }
+  return on;
+}
+
+// Group planning.  A live entry is a free input bit (code >= 0, its input
+// bit while scanning, its free index when planning) or a register slot /
+// prepared qubit (code < 0).
+int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupParams& G, LaunchPlan& L) {
+  if (dtype != OWQS_C64 || i0 >= passes.size() || passes[i0].kind != 0) return 0;
+  const int n0 = passes[i0].n_in;
+  if (n0 < 12 || n0 > 62) return 0;
+  // scan: the longest valid prefix
+  std::vector<int> live(n0);
+  for (int x = 0; x < n0; ++x) live[x] = x;
+  std::vector<int> regs;
+  int best_k = 0;
+  for (size_t i = i0; i < passes.size() && (int)(i - i0) < kGroupMax; ++i) {
+    const PassDesc& d = passes[i];
+    uint64_t a;
+    if (d.kind != 0 || d.xmask || d.r != 1 || d.b >= d.n_in || d.n_in != (int)live.size() || !star_mask(d, &a))
+      break;
+    const int src = live[d.b];
+    if (src >= 0) {
+      if ((int)regs.size() == kGroupRegMax || src < 12 - kGroupRegMax) break;
+      regs.push_back(src);
+    }
+    live.erase(live.begin() + d.b);
+    live.push_back(-1);
+    const int k = (int)(i - i0) + 1, m = (int)regs.size(), lt = 12 - m;
+    bool ok = k >= 2 && n0 - m >= lt;
+    for (int x : regs) ok = ok && x >= lt;
+    if (ok) best_k = k;
+  }
+  if (best_k < 2) return 0;
+  // plan the first best_k passes
+  regs.clear();
+  {
+    std::vector<int> lv(n0);
+    for (int x = 0; x < n0; ++x) lv[x] = x;
+    for (int j = 0; j < best_k; ++j) {
+      const PassDesc& d = passes[i0 + j];
+      if (lv[d.b] >= 0) regs.push_back(lv[d.b]);
+      lv.erase(lv.begin() + d.b);
+      lv.push_back(-1);
+    }
+  }
+  const int m = (int)regs.size();
+  std::memset(&G, 0, sizeof(G));
+  G.k = best_k;
+  G.m = m;
+  G.lt = 12 - m;
+  G.nfree = n0 - m;
+  std::vector<int> slot_of_input(n0, -1), free_of(n0, -1);
+  for (int q = 0; q < m; ++q) slot_of_input[regs[q]] = q, G.B[q] = regs[q];
+  for (int x = 0, f = 0; x < n0; ++x)
+    if (slot_of_input[x] < 0) free_of[x] = f++;
+  std::vector<int> lv(n0);
+  for (int x = 0; x < n0; ++x) lv[x] = slot_of_input[x] >= 0 ? -(1 + slot_of_input[x]) : free_of[x];
+  const uint32_t lomask = (1u << G.lt) - 1u;
+  uint32_t pend = 0;  // register-diagonal sign mask carried by the scaled register
+  double prod = 1.0;
+  for (int j = 0; j < best_k; ++j) {
+    const PassDesc& d = passes[i0 + j];
+    uint64_t A = 0;
+    star_mask(d, &A);
+    GroupPass& P = G.pass[j];
+    const int s = -lv[d.b] - 1;
+    P.slot = s;
+    P.c0 = d.c0 & 1u;
+    P.zb = (uint32_t)((d.zmask >> d.b) & 1u);
+    for (int l = 0; l <= d.n_in; ++l) {  // l = n_in: the prepared qubit, which takes slot s
+      if (l == d.b) continue;
+      const uint32_t zbit = (uint32_t)((d.zmask >> l) & 1u), abit = (uint32_t)((A >> l) & 1u);
+      if (!zbit && !abit) continue;
+      const int code = l < d.n_in ? lv[l] : -(1 + s);
+      if (code >= 0) {
+        P.zfree |= (uint64_t)zbit << code;
+        P.afree |= (uint64_t)abit << code;
+      } else {
+        const int t = -code - 1;
+        P.zr ^= zbit << t;
+        P.ar ^= abit << t;
+      }
+    }
+    P.zlo = (uint32_t)(P.zfree & lomask);
+    P.alo = (uint32_t)(P.afree & lomask);
+    P.scale = d.scale;
+    P.wre = d.w1re;
+    P.wim = d.w1im;
+    const uint32_t ps = (pend >> s) & 1u;
+    for (int g = 0; g < (1 << kGroupRegMax); ++g)
+      P.ct[g] = ((__builtin_popcount(P.ar & (uint32_t)g) & 1u) ^ ps) ? -1.0f : 1.0f;
+    P.fwr = (float)d.w1re;
+    P.fwi = (float)d.w1im;
+    pend = P.zr ^ (pend & ~(1u << s));
+    prod *= d.scale;
+    G.nscale[j] = prod * prod;
+    lv.erase(lv.begin() + d.b);
+    lv.push_back(-(1 + s));
+  }
+  // final order: the free bits in order, then the register slots
+  for (int f = 0; f < G.nfree; ++f)
+    if (lv[f] != f) return 0;  // cannot happen: free bits are never removed and keep their order
+  for (int g = 0; g < (1 << m); ++g) {
+    uint64_t off = 0;
+    for (int l = G.nfree; l < n0; ++l) {
+      const int t = -lv[l] - 1;
+      if ((g >> t) & 1) off |= 1ull << l;
+    }
+    G.outoff[g] = off;
+    G.fin[g] = (float)(((__builtin_popcount(pend & (uint32_t)g) & 1u) ? -1.0 : 1.0) * prod);
+  }
+  G.norm_in = G.norm_out = -1;
+  L.kind = KK_GROUP;
+  L.bytes = (std::ldexp(1.0, n0) + std::ldexp(1.0, passes[i0 + best_k - 1].n_out)) * 8.0;
+  L.grid = 1;
+  return best_k;
+}
+
 bool fusable(const PassDesc& d1, const PassDesc& d2, int dtype) {
   if (dtype != OWQS_C64 || d1.kind != 0 || d2.kind != 0) return false;
   if (d1.xmask || d2.xmask || d1.r > 1 || d2.r > 1) return false;

@@ -316,17 +316,20 @@ def test_brickwork_full_size_properties(env):
     del d
 
 
-def test_fused_measurement_pairs(env):
-    """Consecutive measure passes fused into one sweep (complex64): the
-    output and every per-measurement probability still match the oracle; the
-    profile shows the fused kernel ran."""
+def test_pass_groups(env):
+    """Up to eight consecutive measure passes in one sweep (complex64): the
+    output and every per-measurement probability still match the oracle, in
+    both modes, from the virtual |+> input and from a random input; the
+    profile shows the group kernel ran and covered most measurements."""
     torch, owqs = env
     rng = SplitMix64(105)
-    for rows, cols in ((14, 8), (13, 10)):
-        wl = workloads.brickwork(rows, cols)
+    for wl in (workloads.brickwork(14, 8), workloads.brickwork(13, 10), workloads.qft(12, with_input=False)):
         p = wl.pattern
         bits = rng.bits(p.K)
         h, _ = _compare(env, p, None, bits, "c64", "owqs")
+        psi = random_state(rng, len(p.inputs))
+        _compare(env, p, psi, bits, "c64", "owqs")
+        _compare(env, p, psi, bits, "c64", "eowqs")
         ms, by, kd, _ = h.profile(None, dtype="c64", outcomes=bits)
-        assert (kd == 6).sum() >= 5, sorted(set(kd.tolist()))
-        _compare(env, p, None, bits, "c64", "eowqs")
+        assert (kd == 8).sum() >= 5, sorted(set(kd.tolist()))
+        assert len(kd) < 0.6 * p.K, (len(kd), p.K)
