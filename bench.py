@@ -36,13 +36,20 @@ UNIT = "amplitude-updates/s"
 ROWS, COLS = 28, 40
 WORKLOAD = ("brickwork cluster 28x40 (1120 qubits, 1092 measurements), angles k*pi/4, |+>^28 input, "
             "forced seeded outcomes, greedy reordering (peak 29 live qubits, 2^28 complex64 amplitudes)")
+
+
+def workload_name(rows: int, cols: int) -> str:
+    if (rows, cols) == (ROWS, COLS):
+        return WORKLOAD
+    return (f"brickwork cluster {rows}x{cols} ({rows * cols} qubits), angles k*pi/4, |+>^{rows} input, "
+            f"forced seeded outcomes, greedy reordering (a reduced size of the 28x40 workload)")
 FALLBACK_HBM_GBS = 6800.0
 # ncu DRAM bytes (read + write) per launch of the dominant kernel, keyed by the
 # sha256 prefix of the kernel source they were measured on (a changed kernel
-# reports null).  c64: k_tma<float,1> on the full 2^28-amplitude brickwork
-# pass, mean of three launches (2147.6 MB read + 2101.2 MB written;
-# profiles/k_tma_c64_brickwork28x40_dram.md).
-NCU_TRAFFIC = {("0eaf65b1124c3d4d", "c64"): (2147666432 + 2147585792 + 2147547648 + 2103186944 + 2100009984 + 2100388864) / 3.0}
+# reports null).  c64: k_group<3> on the full brickwork workload (2^28
+# complex64 amplitudes in and out per launch), mean of three launches
+# (2147.8 MB read + 2099.1 MB written; profiles/k_group_c64_brickwork28x40_dram.md).
+NCU_TRAFFIC = {("9906a4202e8fe7c1", "c64"): (2147747840 + 2101385728 + 2147797504 + 2097540608 + 2147803392 + 2098328064) / 3.0}
 # nominal GB300 FP64 rate (no measured FP64 peak exists for this machine)
 FP64_PEAK_TFLOPS = 1.25
 # FP64 flops per output amplitude of the complex128 pass: complex multiply-add
@@ -458,7 +465,8 @@ def run_owqs(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t64 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "rows": args.rows, "cols": args.cols, "measurements": p.K,
+            "config": {"workload": workload_name(args.rows, args.cols), "rows": args.rows, "cols": args.cols,
+                       "measurements": p.K,
                        "peak_m": rinfo["peak_m"], "peak_live": rinfo["peak_live"],
                        "amp_updates_per_step": upd, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "no flush: live arrays of 2 GiB (c64) / 4 GiB (c128) exceed the 129 MB L2",

@@ -235,8 +235,13 @@ int max_grid();               // grid cap for grid-stride kernels
 // (-1)^(par(g & ar) ^ p_slot), and the element's sign collects
 // c0 ^ par(f & zfree); the new mask is zr ^ (p without the measured slot).
 // The store multiplies by E and fin[g] = D_final(g) * product of scales.
-// A tile is 2^(12-M) consecutive free indices (2^M input runs of 2^(12-M)
-// amplitudes: 32 KB), so every B[i] must be >= 12 - M.
+// A tile is 2^(12-M) consecutive free indices (32 KB of input).  Register
+// inputs with input bit below 12 - M + (the number of such bits) are "low":
+// they lie inside the tile's contiguous input block of 2^(12-M+nlow)
+// amplitudes; the others are "high" and select one of 2^(M-nlow) such
+// blocks (runoff).  Configuration c of the register is read at smem offset
+// cbase[c] + spread(e), spread inserting zeros at the low register bits
+// (lowmask) into the element's offset e within the tile.
 // norms[norm_out + j] = squared norm after pass j (no rescaling inside the
 // group): the product of the group's first j+1 outcome probabilities;
 // nscale[j] = product of the first j+1 squared scales.
@@ -262,6 +267,11 @@ struct GroupParams {
   int k, m, lt;             // passes, register qubits, log2 tile (12 - m)
   int nfree;                // free bits (input bits minus m)
   int B[kGroupRegMax];      // input bit of each slot's initial qubit
+  int nruns;                // 2^(number of high register inputs)
+  uint32_t runlen;          // amplitudes per run: 2^(12 - M + nlow)
+  uint32_t lowmask;         // low register input bits (inside the run)
+  uint64_t runoff[1 << kGroupRegMax];  // input offset of run r (high register bits)
+  uint32_t cbase[1 << kGroupRegMax];   // smem offset of configuration c: run * runlen + low bits
   uint64_t outoff[1 << kGroupRegMax];
   float fin[1 << kGroupRegMax];
   double nscale[kGroupMax];

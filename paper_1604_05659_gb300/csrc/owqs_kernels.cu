@@ -966,11 +966,18 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
   constexpr unsigned RUN = TE * sizeof(float2);
   const int k = G.k;
   // the element's low-bit sign parities, two bits per pass in the tile word's
-  // layout (element q at offset 2 threadIdx + (q>>1) 2 kBlock + (q&1))
-  uint32_t lowbits[EPT];
+  // layout (element q at offset 2 threadIdx + (q>>1) 2 kBlock + (q&1)), and
+  // its offset within an input run (zeros inserted at the low register bits)
+  uint32_t lowbits[EPT], spread[EPT];
 #pragma unroll
   for (int q = 0; q < EPT; ++q) {
     const uint32_t e = (uint32_t)(threadIdx.x * 2 + (q >> 1) * kBlock * 2 + (q & 1));
+    uint32_t sp = e;
+    for (uint32_t lm = G.lowmask; lm; lm &= lm - 1) {
+      const int b = __ffs(lm) - 1;
+      sp = ((sp >> b) << (b + 1)) | (sp & ((1u << b) - 1u));
+    }
+    spread[q] = sp;
     uint32_t w = 0;
 #pragma unroll
     for (int j = 0; j < kGroupMax; ++j) {
@@ -980,6 +987,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
     lowbits[q] = w;
   }
   const uint32_t evenk = 0x55555555u & ((k >= 16) ? 0xffffffffu : ((1u << (2 * k)) - 1u));
+  const bool pair_contig = (G.lowmask & 1u) == 0u;  // elements e, e+1 adjacent in every run
 
   auto issue = [&](uint64_t i) {  // thread 0 only
     const int st = (int)(i % NS);
@@ -1007,13 +1015,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
     }
     signs[st] = w;
     mbar_expect_tx(&full[st], NC * RUN);
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      uint64_t off = 0;
-#pragma unroll
-      for (int q = 0; q < M; ++q) off += (uint64_t)((c >> q) & 1) << G.B[q];
-      bulk_g2s(buf + c * TE, in + ib + off, RUN, &full[st]);
-    }
+    const unsigned rbytes = G.runlen * (unsigned)sizeof(float2);
+    for (int r = 0; r < G.nruns; ++r) bulk_g2s(buf + r * G.runlen, in + ib + G.runoff[r], rbytes, &full[st]);
   };
 
   if (threadIdx.x == 0) {
@@ -1049,11 +1052,19 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
     for (int it = 0; it < EPT / 2; ++it) {
       const int e = threadIdx.x * 2 + it * kBlock * 2;
       float2 x[2][NC];
+      if (pair_contig) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const float4 v = *reinterpret_cast<const float4*>(buf + c * TE + e);
-        x[0][c] = make_float2(v.x, v.y);
-        x[1][c] = make_float2(v.z, v.w);
+        for (int c = 0; c < NC; ++c) {
+          const float4 v = *reinterpret_cast<const float4*>(buf + G.cbase[c] + spread[2 * it]);
+          x[0][c] = make_float2(v.x, v.y);
+          x[1][c] = make_float2(v.z, v.w);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          x[0][c] = buf[G.cbase[c] + spread[2 * it]];
+          x[1][c] = buf[G.cbase[c] + spread[2 * it + 1]];
+        }
       }
       const uint32_t b0 = sw ^ lowbits[2 * it], b1 = sw ^ lowbits[2 * it + 1];
 #pragma unroll

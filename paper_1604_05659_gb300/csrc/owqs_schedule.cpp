@@ -267,15 +267,13 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupP
       break;
     const int src = live[d.b];
     if (src >= 0) {
-      if ((int)regs.size() == kGroupRegMax || src < 12 - kGroupRegMax) break;
+      if ((int)regs.size() == kGroupRegMax) break;
       regs.push_back(src);
     }
     live.erase(live.begin() + d.b);
     live.push_back(-1);
     const int k = (int)(i - i0) + 1, m = (int)regs.size(), lt = 12 - m;
-    bool ok = k >= 2 && n0 - m >= lt;
-    for (int x : regs) ok = ok && x >= lt;
-    if (ok) best_k = k;
+    if (k >= 2 && n0 - m >= lt) best_k = k;
   }
   if (best_k < 2) return 0;
   // plan the first best_k passes
@@ -298,6 +296,37 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupP
   G.nfree = n0 - m;
   std::vector<int> slot_of_input(n0, -1), free_of(n0, -1);
   for (int q = 0; q < m; ++q) slot_of_input[regs[q]] = q, G.B[q] = regs[q];
+  {  // low register inputs: inside the tile's contiguous input block
+    std::vector<int> sorted(regs);
+    std::sort(sorted.begin(), sorted.end());
+    int nlow = 0;
+    for (int b : sorted)
+      if (b < G.lt + nlow) ++nlow;
+    std::vector<char> low(m, 0);
+    for (int q = 0; q < m; ++q) low[q] = regs[q] < G.lt + nlow;
+    G.lowmask = 0;
+    for (int q = 0; q < m; ++q)
+      if (low[q]) G.lowmask |= 1u << regs[q];
+    G.nruns = 1 << (m - nlow);
+    G.runlen = 1u << (G.lt + nlow);
+    for (int c = 0; c < (1 << m); ++c) {
+      uint32_t run = 0, lowoff = 0;
+      int rank = 0;
+      for (int q = 0; q < m; ++q) {
+        const uint32_t bit = (c >> q) & 1u;
+        if (low[q]) lowoff |= bit << regs[q];
+        else run |= bit << rank++;
+      }
+      G.cbase[c] = run * G.runlen + lowoff;
+    }
+    for (int r = 0; r < G.nruns; ++r) {
+      uint64_t off = 0;
+      int rank = 0;
+      for (int q = 0; q < m; ++q)
+        if (!low[q]) off |= (uint64_t)((r >> rank++) & 1) << regs[q];
+      G.runoff[r] = off;
+    }
+  }
   for (int x = 0, f = 0; x < n0; ++x)
     if (slot_of_input[x] < 0) free_of[x] = f++;
   std::vector<int> lv(n0);
