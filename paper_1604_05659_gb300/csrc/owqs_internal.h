@@ -154,35 +154,10 @@ struct PassParams {
 };
 
 enum KernelKind {
-  KK_FAST = 0, KK_GENERIC = 1, KK_FINAL = 2, KK_NORM = 3, KK_PROB = 4, KK_TMA = 5, KK_FUSED = 6, KK_DECIDE = 7,
+  KK_FAST = 0, KK_GENERIC = 1, KK_FINAL = 2, KK_NORM = 3, KK_PROB = 4, KK_TMA = 5, KK_DECIDE = 7,
   KK_GROUP = 8
 };
 
-// Two consecutive measure passes run as one sweep (complex64, TMA).  The
-// contract is the composition of the two single passes: y1 = pass1(in) is
-// rebuilt on chip and never stored, out = pass2(y1).  Both passes must be in
-// star form with no X mask, prepare at most one qubit each, measure bits of
-// the input array at or above the tile width, and the second must not
-// measure the first one's new qubit.  norms[norm_out1] = |y1|^2 and
-// norms[norm_out2] = |out|^2 = |y1|^2 |pass2(y1 / |y1|)|^2 (the stored array
-// is not rescaled by 1/|y1| in between).
-struct FusedParams {
-  const void* in;
-  void* out;
-  double* norms;
-  double* partials;
-  unsigned int* counter;
-  unsigned int* errflag;
-  int n1, r1, b1, r2, b2;   // pass coordinates as in PassDesc
-  int B1, B2;               // the two measured bits in input coordinates
-  int nlo, n_out;           // live output bits, output bits
-  int norm_in, norm_out1, norm_out2;
-  double thresh;
-  uint64_t z1, A1, z2, A2;  // sign forms (star at b1 / b2), in each pass's coordinates
-  uint32_t c01, zb1, c02, zb2;
-  double scale1, w1re, w1im, scale2, w2re, w2im;
-};
-constexpr int kFusedLogTile = 10;  // 2^10 outputs per tile, 4 input runs of 8 KB
 
 
 // TMA-pipelined pass (complex64): log2 of the outputs per tile (16 KB of
@@ -284,10 +259,6 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i, int dtype, GroupPa
 cudaError_t launch_group(const GroupParams& G, cudaStream_t s);
 int group_enabled();  // OWQS_GROUP=0 turns group fusion off
 
-bool fusable(const PassDesc& d1, const PassDesc& d2, int dtype);
-void plan_fused(const PassDesc& d1, const PassDesc& d2, FusedParams& F, LaunchPlan& L);
-cudaError_t launch_fused(const FusedParams& F, cudaStream_t s);
-int fusion_enabled();  // OWQS_FUSE=0 turns pass fusion off
 
 // plan + fill the parameter block of one pass (host)
 void plan_pass(const PassDesc& d, int dtype, bool virt_in, PassParams& P, LaunchPlan& L);

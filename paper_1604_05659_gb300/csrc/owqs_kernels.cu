@@ -524,177 +524,6 @@ __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
 }
 
 
-// ---------------------------------------------------------------------------
-// Fused pair of measure passes (complex64): one HBM sweep for two
-// measurements.  A tile is 2^10 consecutive live outputs; its inputs are the
-// four corners (c1, c2) of the two measured bits, staged by four bulk copies
-// per stage into a 3-stage shared-memory ring.  Per element the first pass's
-// two intermediate amplitudes y1(c2) are rebuilt for each value of its new
-// qubit t1 (their squared norms summed, each counted once), then combined
-// into the second pass's outputs for each value of its new qubit t2.  The
-// low 10 bits of an output index are the same bits in every coordinate
-// system involved (both measured bits lie above them), so per-element signs
-// are the tile's base signs XOR parities of those low bits.  The base signs
-// are uniform over the tile: the thread that issues a tile's copies computes
-// them once and leaves them in a shared word beside the stage.  Squared
-// norms are summed per thread in FP32 with compensation (GB300 issues FP64
-// at a small fraction of the FP32 rate) and promoted to FP64 once.
-// R1, R2: qubits the two passes prepare (0 or 1).
-// ---------------------------------------------------------------------------
-constexpr int kFusedTE = 1 << kFusedLogTile;
-constexpr int kFusedStageBytes = 4 * kFusedTE * 8;
-constexpr int kFusedSmem = kTmaStages * kFusedStageBytes + kTmaStages * 8 + kTmaStages * 4;
-
-// bit t1*8 + c2: pz1, t1*8 + 2 + c2: pa1, t1*8 + 4 + t2: pz2, t1*8 + 6 + t2: pa2
-template <int R1, int R2>
-__device__ __forceinline__ uint32_t fused_tile_signs(const FusedParams& F, uint64_t L0, int m2bits) {
-  const uint64_t m2 = (1ull << m2bits) - 1ull;
-  uint32_t w = 0;
-#pragma unroll
-  for (int t1 = 0; t1 < (1 << R1); ++t1) {
-    const uint64_t J1 = L0 | ((uint64_t)t1 << F.nlo);
-#pragma unroll
-    for (int c2 = 0; c2 < 2; ++c2) {
-      const uint64_t I1 = (ins0(J1, F.b2) | ((uint64_t)c2 << F.b2)) & m2;
-      const uint64_t K1 = ins0(I1, F.b1);
-      w |= ((F.c01 ^ par64(K1 & F.z1)) & 1u) << (t1 * 8 + c2);
-      w |= ((F.zb1 ^ par64(K1 & F.A1)) & 1u) << (t1 * 8 + 2 + c2);
-    }
-#pragma unroll
-    for (int t2 = 0; t2 < (1 << R2); ++t2) {
-      const uint64_t K2 = ins0(J1 | ((uint64_t)t2 << (F.nlo + R1)), F.b2);
-      w |= ((F.c02 ^ par64(K2 & F.z2)) & 1u) << (t1 * 8 + 4 + t2);
-      w |= ((F.zb2 ^ par64(K2 & F.A2)) & 1u) << (t1 * 8 + 6 + t2);
-    }
-  }
-  return w;
-}
-
-template <int R1, int R2>
-__global__ void __launch_bounds__(kBlock, 2) k_fused(const FusedParams F) {
-  constexpr int LTE = kFusedLogTile, TE = kFusedTE, NS = kTmaStages;
-  extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * kFusedStageBytes);
-  uint32_t* signs = reinterpret_cast<uint32_t*>(smem + NS * kFusedStageBytes + NS * 8);
-  const float2* __restrict__ in = reinterpret_cast<const float2*>(F.in);
-  float2* __restrict__ out = reinterpret_cast<float2*>(F.out);
-  double cprev = 1.0;
-  if (F.norm_in >= 0) {
-    const double nv = F.norms[F.norm_in];
-    cprev = (nv >= F.thresh && nv > 0.0) ? 1.0 / sqrt(nv) : 0.0;
-  }
-  const float sc1 = (float)(F.scale1 * cprev), w1r = (float)(F.scale1 * cprev * F.w1re),
-              w1i = (float)(F.scale1 * cprev * F.w1im);
-  const float sc2 = (float)F.scale2, w2r = (float)(F.scale2 * F.w2re), w2i = (float)(F.scale2 * F.w2im);
-  const int lo = F.B1 < F.B2 ? F.B1 : F.B2, hi = F.B1 < F.B2 ? F.B2 : F.B1;
-  const int n2 = F.n1 + R1 - 1;
-  const uint64_t inmask = (1ull << F.n1) - 1ull;
-  const uint64_t tiles = 1ull << (F.nlo - LTE);
-  const uint64_t step = gridDim.x;
-  const uint64_t mine = blockIdx.x < tiles ? (tiles - blockIdx.x + step - 1) / step : 0;
-  const uint32_t lomask = (uint32_t)(TE - 1);
-  const uint32_t z1lo = (uint32_t)F.z1 & lomask, a1lo = (uint32_t)F.A1 & lomask;
-  const uint32_t z2lo = (uint32_t)F.z2 & lomask, a2lo = (uint32_t)F.A2 & lomask;
-  constexpr unsigned RUN = TE * sizeof(float2);
-
-  auto issue = [&](uint64_t i) {  // thread 0 only
-    const int st = (int)(i % NS);
-    float2* buf = reinterpret_cast<float2*>(smem + st * kFusedStageBytes);
-    const uint64_t L0 = (blockIdx.x + i * step) << LTE;
-    const uint64_t ib = ins0(ins0(L0, lo), hi) & inmask;
-    signs[st] = fused_tile_signs<R1, R2>(F, L0, n2);
-    mbar_expect_tx(&full[st], 4 * RUN);
-    for (int c = 0; c < 4; ++c) {  // corner c = 2*c1 + c2
-      const uint64_t off = ((uint64_t)(c >> 1) << F.B1) + ((uint64_t)(c & 1) << F.B2);
-      bulk_g2s(buf + c * TE, in + ib + off, RUN, &full[st]);
-    }
-  };
-
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < NS; ++q) mbar_init(&full[q], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (uint64_t q = 0; q < mine && q < (uint64_t)NS; ++q) issue(q);
-
-  float s1 = 0.f, k1 = 0.f, s2 = 0.f, k2 = 0.f;  // compensated per-thread sums
-  uint64_t issued = mine < (uint64_t)NS ? mine : (uint64_t)NS;
-  uint64_t i = 0;
-  bool failed = false;
-  for (; i < mine; ++i) {
-    const int st = (int)(i % NS);
-    const bool ok = mbar_wait_bounded(&full[st], (unsigned)((i / NS) & 1u));
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-    const float2* buf = reinterpret_cast<const float2*>(smem + st * kFusedStageBytes);
-    const uint32_t sg = signs[st];
-    const uint64_t L0 = (blockIdx.x + i * step) << LTE;
-    float t1acc = 0.f, t2acc = 0.f;
-#pragma unroll
-    for (int t1 = 0; t1 < (1 << R1); ++t1) {
-      const uint32_t w = sg >> (t1 * 8);
-#pragma unroll
-      for (int e = threadIdx.x * 2; e < TE; e += kBlock * 2) {
-        float2 y1[2][2];  // [c2][element]
-#pragma unroll
-        for (int c2 = 0; c2 < 2; ++c2) {
-          const float4 a0 = *reinterpret_cast<const float4*>(buf + (0 * 2 + c2) * TE + e);
-          const float4 a1 = *reinterpret_cast<const float4*>(buf + (1 * 2 + c2) * TE + e);
-          const float2 x0[2] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w)};
-          const float2 x1[2] = {make_float2(a1.x, a1.y), make_float2(a1.z, a1.w)};
-#pragma unroll
-          for (int v = 0; v < 2; ++v) {
-            const uint32_t jj = (uint32_t)(e + v);
-            const uint32_t s0 = ((w >> c2) ^ __popc(jj & z1lo)) & 1u;
-            const uint32_t s1 = (s0 ^ (w >> (2 + c2)) ^ __popc(jj & a1lo)) & 1u;
-            const float a = s0 ? -sc1 : sc1;
-            const float br = s1 ? -w1r : w1r, bi = s1 ? -w1i : w1i;
-            y1[c2][v].x = a * x0[v].x + br * x1[v].x - bi * x1[v].y;
-            y1[c2][v].y = a * x0[v].y + br * x1[v].y + bi * x1[v].x;
-            t1acc += y1[c2][v].x * y1[c2][v].x + y1[c2][v].y * y1[c2][v].y;
-          }
-        }
-#pragma unroll
-        for (int t2 = 0; t2 < (1 << R2); ++t2) {
-          float2 o[2];
-#pragma unroll
-          for (int v = 0; v < 2; ++v) {
-            const uint32_t jj = (uint32_t)(e + v);
-            const uint32_t s0 = ((w >> (4 + t2)) ^ __popc(jj & z2lo)) & 1u;
-            const uint32_t s1 = (s0 ^ (w >> (6 + t2)) ^ __popc(jj & a2lo)) & 1u;
-            const float a = s0 ? -sc2 : sc2;
-            const float br = s1 ? -w2r : w2r, bi = s1 ? -w2i : w2i;
-            o[v].x = a * y1[0][v].x + br * y1[1][v].x - bi * y1[1][v].y;
-            o[v].y = a * y1[0][v].y + br * y1[1][v].y + bi * y1[1][v].x;
-            t2acc += o[v].x * o[v].x + o[v].y * o[v].y;
-          }
-          const uint64_t J = L0 | ((uint64_t)t1 << F.nlo) | ((uint64_t)t2 << (F.nlo + R1));
-          *reinterpret_cast<float4*>(out + J + e) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
-        }
-      }
-    }
-    kahan_add(s1, k1, t1acc);
-    kahan_add(s2, k2, t2acc);
-    __syncthreads();
-    if (threadIdx.x == 0 && issued < mine) issue(issued++);
-  }
-  if (failed) {
-    if (threadIdx.x == 0) {
-      atomicExch(F.errflag, 1u);
-      for (uint64_t j = i; j < issued; ++j) mbar_wait_bounded(&full[j % NS], (unsigned)((j / NS) & 1u));
-    }
-    __syncthreads();
-    return;
-  }
-  if (F.norm_out1 >= 0) {
-    const double a2[2] = {(double)s1 - (double)k1, (double)s2 - (double)k2};
-    reduce_to_slots<2>(a2, F.partials, F.counter, F.norms, F.norm_out1);
-  }
-}
-
 // squared norm of an input vector (OWQS divides by it)
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_norm(const void* vin, uint64_t n, double* norms, int slot,
@@ -824,26 +653,6 @@ cudaError_t launch_pass(const PassParams& P, const LaunchPlan& L, int dtype, cud
   return dtype == OWQS_C64 ? launch_t<float>(P, L, s) : launch_t<double>(P, L, s);
 }
 
-template <int R1, int R2>
-static cudaError_t launch_fused_t(const FusedParams& F, cudaStream_t s) {
-  static int grid_cap = 0;
-  static std::mutex mu;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    if (grid_cap == 0) {
-      cudaError_t e = cudaFuncSetAttribute(k_fused<R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem);
-      if (e != cudaSuccess) return e;
-      int per_sm = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<R1, R2>, kBlock, kFusedSmem);
-      if (e != cudaSuccess) return e;
-      grid_cap = std::max(1, per_sm) * (max_grid() / 8);
-    }
-  }
-  const uint64_t tiles = 1ull << (F.nlo - kFusedLogTile);
-  k_fused<R1, R2><<<(int)std::min<uint64_t>(tiles, (uint64_t)grid_cap), kBlock, kFusedSmem, s>>>(F);
-  return cudaGetLastError();
-}
-
 template <int M>
 __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G);
 
@@ -874,16 +683,6 @@ cudaError_t launch_group(const GroupParams& G, cudaStream_t s) {
     case 1: return launch_group_t<1>(G, s);
     case 2: return launch_group_t<2>(G, s);
     case 3: return launch_group_t<3>(G, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t launch_fused(const FusedParams& F, cudaStream_t s) {
-  switch (F.r1 * 2 + F.r2) {
-    case 0: return launch_fused_t<0, 0>(F, s);
-    case 1: return launch_fused_t<0, 1>(F, s);
-    case 2: return launch_fused_t<1, 0>(F, s);
-    case 3: return launch_fused_t<1, 1>(F, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -101,9 +101,8 @@ struct FixedSource : OutcomeSource {
 // launch list
 // ---------------------------------------------------------------------------
 struct Item {
-  int type = 0;  // 0 pass, 1 norm, 2 fused pair, 3 device-drawn outcome, 4 pass group
+  int type = 0;  // 0 pass, 1 norm, 3 device-drawn outcome, 4 pass group
   PassParams P;
-  FusedParams F;
   GroupParams G;
   DecideParams D;
   LaunchPlan L;
@@ -123,7 +122,7 @@ class Runner {
   bool immediate = false;
   int vdiag = 0;  // virtual diagonal input over 2 * vdiag bits (recognition)
   std::vector<Item> items;
-  std::vector<char> fused_second;  // per measurement: second of a fused pair
+  std::vector<char> in_group;  // per measurement: not the first of a pass group
   owqs_status err = OWQS_OK;
 
   void begin(const void* in0, uint64_t in_elems, void* out_final) {
@@ -160,7 +159,7 @@ class Runner {
     issue(it);
     cur_in_ = it.P.out;
     prev_slot_ = it.P.norm_out;
-    fused_second.push_back(0);
+    in_group.push_back(0);
     ++pass_i_;
   }
 
@@ -202,8 +201,8 @@ class Runner {
     issue(it);
     cur_in_ = it.G.out;
     prev_slot_ = mode_ == OWQS_MODE_OWQS ? pass_i_ + G.k : -1;
-    fused_second.push_back(0);
-    for (int j = 1; j < G.k; ++j) fused_second.push_back(1);
+    in_group.push_back(0);
+    for (int j = 1; j < G.k; ++j) in_group.push_back(1);
     pass_i_ += G.k;
   }
 
@@ -211,38 +210,6 @@ class Runner {
   int group_at(const std::vector<PassDesc>& passes, size_t i, GroupParams& G, LaunchPlan& L) const {
     if (cur_in_ == nullptr || !group_enabled()) return 0;
     return plan_group(passes, i, dtype_, G, L);
-  }
-
-  // can the next two measure passes run as one sweep
-  bool can_fuse(const PassDesc& d1, const PassDesc& d2) const {
-    return cur_in_ != nullptr && fusion_enabled() && fusable(d1, d2, dtype_);
-  }
-
-  // two measure passes in one sweep: slot pass_i+1 gets |y1|^2 = p(first),
-  // slot pass_i+2 gets p(first) p(second)
-  void measure_pair(const PassDesc& d1, const PassDesc& d2) {
-    Item it;
-    it.type = 2;
-    plan_fused(d1, d2, it.F, it.L);
-    it.F.norms = rc_.norms;
-    it.F.partials = rc_.partials;
-    it.F.counter = rc_.counter;
-    it.F.errflag = rc_.counter + 1;
-    it.F.thresh = thresh_;
-    it.F.in = cur_in_;
-    it.F.out = rc_.buf[sel_];
-    sel_ ^= 1;
-    it.F.norm_in = prev_slot_;
-    if (mode_ == OWQS_MODE_OWQS) {
-      it.F.norm_out1 = pass_i_ + 1;
-      it.F.norm_out2 = pass_i_ + 2;
-    }
-    issue(it);
-    cur_in_ = it.F.out;
-    prev_slot_ = it.F.norm_out1 >= 0 ? it.F.norm_out2 : -1;
-    fused_second.push_back(0);
-    fused_second.push_back(1);
-    pass_i_ += 2;
   }
 
   // both outcome probabilities of the next measurement into slots
@@ -289,8 +256,6 @@ class Runner {
       e = launch_group(it.G, s);
     else if (it.type == 3)
       e = launch_decide(it.D, s);
-    else if (it.type == 2)
-      e = launch_fused(it.F, s);
     else if (it.type == 1)
       e = launch_norm(it.norm_in, it.norm_n, dtype_, rc_.norms, it.norm_slot, rc_.partials, rc_.counter,
                       it.L.grid, s);
@@ -471,7 +436,7 @@ static owqs_status ensure_pingpong(RunCache* rc, size_t elems, size_t amp) {
 
 static owqs_status finish(Pattern& p, const owqs_run_opts* o, RunCache* rc, const Prepared& pr,
                           cudaStream_t s, uint8_t* outcomes, double* probs, const std::vector<int>& outcome_of_pass,
-                          bool has_input, int vdiag, double* frob2, const std::vector<char>& fused_second) {
+                          bool has_input, int vdiag, double* frob2, const std::vector<char>& in_group) {
   const int K = (int)p.meas_qubit.size();
   rc->h_norms.assign((size_t)K + 2, 0.0);
   unsigned int flag = 0;
@@ -490,8 +455,8 @@ static owqs_status finish(Pattern& p, const owqs_run_opts* o, RunCache* rc, cons
   for (const PassDesc& d : pr.passes) {
     if (d.kind != 0) continue;
     double pv = o->mode == OWQS_MODE_OWQS ? rc->h_norms[mi + 1] : 0.5;
-    if (o->mode == OWQS_MODE_OWQS && (size_t)mi < fused_second.size() && fused_second[mi]) {
-      // second measurement of a fused pair: its slot holds p(first) p(second)
+    if (o->mode == OWQS_MODE_OWQS && (size_t)mi < in_group.size() && in_group[mi]) {
+      // later measurement of a pass group: its slot holds the running product of the group's probabilities
       const double first = rc->h_norms[mi];
       pv = first > 0.0 ? pv / first : 0.0;
     }
@@ -696,7 +661,7 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
   if (st != OWQS_OK) return st;
   const int K = (int)p.meas_qubit.size();
   std::vector<int> outcome_of_pass;
-  std::vector<char> fused_second;
+  std::vector<char> in_group;
 
   if (sampled) {
     if (prof_ms) return set_error(OWQS_ERR_ARG, "profiling needs forced or zero outcomes");
@@ -724,7 +689,7 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
         if (e != cudaSuccess) return cuda_fail(e, "output copy");
       }
       return finish(p, o, rc, pr, s, outcomes, probs, outcome_of_pass, pr.in_dev != nullptr, vdiag, frob2,
-                    fused_second);
+                    in_group);
     }
     Runner R(p, *rc, o->dtype, o->mode, s);
     R.immediate = true;
@@ -758,14 +723,11 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
       } else if ((gk = R.group_at(pr.passes, i, G, GL)) >= 2) {
         R.measure_group(G, GL);
         i += (size_t)gk - 1;
-      } else if (i + 1 < pr.passes.size() && pr.passes[i + 1].kind == 0 && R.can_fuse(d, pr.passes[i + 1])) {
-        R.measure_pair(d, pr.passes[i + 1]);
-        ++i;
       } else {
         R.measure(d);
       }
     }
-    fused_second = R.fused_second;
+    in_group = R.in_group;
     if (o->io == OWQS_IO_HOST && psi_in) {
       cudaError_t e = cudaMemcpyAsync(rc->in_stage, psi_in, pr.in_elems * pr.amp, cudaMemcpyHostToDevice, s);
       if (e != cudaSuccess) return cuda_fail(e, "input copy");
@@ -805,7 +767,7 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
   }
   (void)K;
   return finish(p, o, rc, pr, s, outcomes, probs, outcome_of_pass, pr.in_dev != nullptr, vdiag, frob2,
-                fused_second);
+                in_group);
 }
 
 }  // namespace owqs

@@ -218,14 +218,6 @@ int tma_enabled() {
   return on;
 }
 
-int fusion_enabled() {
-  static int on = -1;
-  if (on < 0) {
-    const char* e = std::getenv("OWQS_FUSE");
-    on = (e && e[0] == '0') ? 0 : 1;
-  }
-  return on;
-}
 
 // star adjacency of the measured bit, or false if some E term misses it
 static bool star_mask(const PassDesc& d, uint64_t* amask) {
@@ -390,49 +382,6 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupP
   L.bytes = (std::ldexp(1.0, n0) + std::ldexp(1.0, passes[i0 + best_k - 1].n_out)) * 8.0;
   L.grid = 1;
   return best_k;
-}
-
-bool fusable(const PassDesc& d1, const PassDesc& d2, int dtype) {
-  if (dtype != OWQS_C64 || d1.kind != 0 || d2.kind != 0) return false;
-  if (d1.xmask || d2.xmask || d1.r > 1 || d2.r > 1) return false;
-  if (d1.b >= d1.n_in || d2.b >= d2.n_in) return false;           // both measure bits already live
-  if (d1.r == 1 && d2.b == d1.n_in - 1) return false;              // not the first pass's new qubit
-  uint64_t a;
-  if (!star_mask(d1, &a) || !star_mask(d2, &a)) return false;
-  const int B1 = d1.b, B2 = d2.b < d1.b ? d2.b : d2.b + 1;
-  const int lt = kFusedLogTile;
-  return B1 >= lt && B2 >= lt && d1.n_in - 2 >= lt;
-}
-
-void plan_fused(const PassDesc& d1, const PassDesc& d2, FusedParams& F, LaunchPlan& L) {
-  std::memset(&F, 0, sizeof(F));
-  F.n1 = d1.n_in;
-  F.r1 = d1.r;
-  F.b1 = d1.b;
-  F.r2 = d2.r;
-  F.b2 = d2.b;
-  F.B1 = d1.b;
-  F.B2 = d2.b < d1.b ? d2.b : d2.b + 1;
-  F.nlo = d1.n_in - 2;
-  F.n_out = d2.n_out;
-  star_mask(d1, &F.A1);
-  star_mask(d2, &F.A2);
-  F.z1 = d1.zmask;
-  F.z2 = d2.zmask;
-  F.c01 = d1.c0;
-  F.c02 = d2.c0;
-  F.zb1 = (uint32_t)((d1.zmask >> d1.b) & 1u);
-  F.zb2 = (uint32_t)((d2.zmask >> d2.b) & 1u);
-  F.scale1 = d1.scale;
-  F.w1re = d1.w1re;
-  F.w1im = d1.w1im;
-  F.scale2 = d2.scale;
-  F.w2re = d2.w1re;
-  F.w2im = d2.w1im;
-  F.norm_in = F.norm_out1 = F.norm_out2 = -1;
-  L.kind = KK_FUSED;
-  L.bytes = (std::ldexp(1.0, d1.n_in) + std::ldexp(1.0, d2.n_out)) * 8.0;
-  L.grid = 1;
 }
 
 static inline uint64_t ins0(uint64_t j, int b) {  // insert a 0 bit at position b

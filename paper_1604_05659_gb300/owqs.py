@@ -27,7 +27,7 @@ RUN_HOST_SAMPLING = 1
 DTYPE = {"c64": 0, "c128": 1}
 POLICY = {"forced": 0, "sampled": 1, "zero": 2}
 KERNEL_KIND = {0: "fast_pass", 1: "generic_pass", 2: "final", 3: "norm", 4: "prob", 5: "tma_pass",
-               6: "fused_pass", 7: "decide", 8: "group_pass"}
+               7: "decide", 8: "group_pass"}
 
 
 class OwqsError(RuntimeError):
