@@ -267,6 +267,17 @@ enum { OWQS_RUN_HOST_SAMPLING = 1 };
 owqs_status owqs_run(owqs_pattern* p, const owqs_run_opts* opts, const void* psi_in,
                      void* psi_out, uint8_t* outcomes, double* probs);
 
+/* Test hook for the device-side wait limits (no real stall is needed to
+ * exercise them).  Every wait inside the bulk-copy pass kernels is bounded:
+ * on expiry the kernel raises an error flag and returns, and the run reports
+ * OWQS_ERR_TIMEOUT with the context still usable.  After this call, the
+ * next `runs` calls of owqs_run (forced or zero outcomes) that contain a
+ * bulk-copy launch make their first such launch wait on a barrier that
+ * nothing arrives at, for `limit_cycles` SM cycles (1 .. 4e9), before any
+ * copy is issued; that run is launched without a graph and returns
+ * OWQS_ERR_TIMEOUT.  runs = 0 cancels.  Not for production use. */
+owqs_status owqs_test_wait_timeout(uint32_t runs, uint64_t limit_cycles);
+
 /* Flows of the pattern's open graph (G, I, O), Section 4.5 with the
  * definitions of ref. [13]; G has an edge u-v iff the pattern holds an odd
  * number of E commands on {u, v}.

@@ -52,6 +52,10 @@ struct Pattern {
   ~Pattern();
 };
 
+// Test hook (owqs_test_wait_timeout): runs left that stall their first
+// bulk-copy launch, and the cycle limit of that stall
+int take_test_stall(long long* limit);
+
 // Section 4.5 pre-check: does the open graph have a gflow (searched once,
 // kept with the pattern; owqs_flow.cpp)
 bool has_gflow(Pattern& p);
@@ -139,6 +143,7 @@ struct PassParams {
   double scale, w1re, w1im, ere, eim, vconst;
   const double* w1dev;   // device (-1)^s e^{-i theta} written by k_decide; nullptr: w1re, w1im
   const double* edev;    // device e^{-i theta} (probability pass); nullptr: ere, eim
+  long long stall_limit; // > 0 (tests only): wait this many cycles on a barrier nothing arrives at, then give up
   int vdiag;             // virtual input: 0 = |+> of value vconst; h > 0 = amplitude 1 where the
                          // low h input bits equal the next h (all basis columns, recognition)
   // fast pass (star form at b, no X): uniform sign tables
@@ -252,6 +257,7 @@ struct GroupParams {
   double nscale[kGroupMax];
   int norm_in, norm_out;
   double thresh;
+  long long stall_limit;    // > 0 (tests only): as PassParams::stall_limit
   GroupPass pass[kGroupMax];
 };
 // longest group starting at passes[i] (0 or 1 if none), planned into G

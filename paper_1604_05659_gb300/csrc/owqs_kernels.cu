@@ -396,6 +396,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     if (clock64() - t0 > kWaitLimitCycles) return false;
   return true;
 }
+// Test path of the bounded waits: thread 0 waits on a barrier that nothing
+// arrives at, gives up after `limit` cycles and raises the error flag; every
+// thread of the block then returns before any copy is issued.
+__device__ __forceinline__ void stall_and_give_up(long long limit, unsigned int* errflag) {
+  __shared__ uint64_t never;
+  if (threadIdx.x == 0) {
+    mbar_init(&never, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bool done = mbar_try_wait(&never, 0u);
+    const long long t0 = clock64();
+    while (!done && clock64() - t0 <= limit) done = mbar_try_wait(&never, 0u);
+    if (!done) atomicExch(errflag, 1u);
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -414,6 +430,10 @@ struct TmaShape {
 
 template <typename T, int CASE>
 __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
+  if (P.stall_limit > 0) {
+    stall_and_give_up(P.stall_limit, P.errflag);
+    return;
+  }
   using V = typename Cplx<T>::V;
   using S = TmaShape<T>;
   constexpr int LTE = S::LTE, TE = S::TE, NS = kTmaStages;
@@ -740,6 +760,10 @@ __device__ __forceinline__ void group_pass2(float2 (&x)[2][1 << M], const GroupP
 
 template <int M>
 __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
+  if (G.stall_limit > 0) {
+    stall_and_give_up(G.stall_limit, G.errflag);
+    return;
+  }
   constexpr int LT = 12 - M, TE = 1 << LT, NC = 1 << M, NS = kTmaStages;
   constexpr int STAGE = NC * TE * 8;
   constexpr int EPT = TE / kBlock;  // elements per thread per tile (even)

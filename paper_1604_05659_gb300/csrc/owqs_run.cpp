@@ -1,6 +1,7 @@
 // Run driver: device workspace, launch list, CUDA-graph capture and replay,
 // sampled outcomes, per-launch profiling, index maps and pass descriptions.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -757,7 +758,21 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
       for (auto& x : ev) cudaEventDestroy(x);
       if (st != OWQS_OK) return st;
     } else {
-      st = replay(rc, R, graph_key(p, o, pr.in_dev, pr.out_dev, outcomes), o->use_graph != 0, s);
+      // test hook: make the first bulk-copy launch give up on a wait
+      Item* stall = nullptr;
+      for (Item& it : R.items)
+        if ((it.type == 0 && it.L.kind == KK_TMA) || it.type == 4) {
+          stall = &it;
+          break;
+        }
+      long long limit = 0;
+      if (stall && take_test_stall(&limit)) {
+        if (stall->type == 4) stall->G.stall_limit = limit;
+        else stall->P.stall_limit = limit;
+        st = replay(rc, R, std::string(), false, s);  // direct launches, no graph
+      } else {
+        st = replay(rc, R, graph_key(p, o, pr.in_dev, pr.out_dev, outcomes), o->use_graph != 0, s);
+      }
       if (st != OWQS_OK) return st;
     }
   }
@@ -775,6 +790,18 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
 using namespace owqs;
 
 namespace owqs {
+static std::atomic<int> g_test_stall_runs{0};
+static std::atomic<long long> g_test_stall_limit{0};
+
+int take_test_stall(long long* limit) {
+  int n = g_test_stall_runs.load();
+  while (n > 0 && !g_test_stall_runs.compare_exchange_weak(n, n - 1)) {
+  }
+  if (n <= 0) return 0;
+  *limit = g_test_stall_limit.load();
+  return 1;
+}
+
 owqs_status run_unchecked(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
                           uint8_t* outcomes, double* probs) {
   clear_error();
@@ -783,6 +810,15 @@ owqs_status run_unchecked(Pattern& p, const owqs_run_opts* o, const void* psi_in
 }  // namespace owqs
 
 extern "C" {
+
+owqs_status owqs_test_wait_timeout(uint32_t runs, uint64_t limit_cycles) {
+  clear_error();
+  if (runs && (limit_cycles == 0 || limit_cycles > 4000000000ull))
+    return set_error(OWQS_ERR_ARG, "limit_cycles must be in 1 .. 4e9");
+  g_test_stall_limit.store((long long)limit_cycles);
+  g_test_stall_runs.store((int)runs);
+  return OWQS_OK;
+}
 
 owqs_status owqs_run(owqs_pattern* h, const owqs_run_opts* o, const void* psi_in, void* psi_out,
                      uint8_t* outcomes, double* probs) {

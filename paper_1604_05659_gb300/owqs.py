@@ -125,6 +125,7 @@ EXPORTS = {
                                    C.c_uint32, C.c_float, C.c_uint64, C.c_void_p, C.c_void_p]),
     "owqs_find_flow": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_int32),
                                  C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32)]),
+    "owqs_test_wait_timeout": (C.c_int, [C.c_uint32, C.c_uint64]),
     "owqs_last_error": (C.c_char_p, []),
     "owqs_abi_version": (C.c_uint32, []),
 }
@@ -383,6 +384,16 @@ class Handle:
                                           C.c_void_p(out.data_ptr()), oc, ms, by, kd, cap, C.byref(n)))
         k = min(n.value, cap)
         return np.array(ms[:k]), np.array(by[:k]), np.array(kd[:k]), out
+
+
+def last_error() -> str:
+    """Message of the library's last error on this thread."""
+    return library().owqs_last_error().decode()
+
+
+def test_wait_timeout(runs: int, limit_cycles: int = 2_000_000):
+    """Make the next `runs` runs give up on a device-side wait (test hook)."""
+    _check(library().owqs_test_wait_timeout(runs, limit_cycles))
 
 
 def run_batch(items, *, dtype: str = "c128", column_block: int = 0, stream=None, use_graph: bool = True,
