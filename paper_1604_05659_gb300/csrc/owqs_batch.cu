@@ -29,6 +29,9 @@ struct BPass {
   int32_t n_in, r, b, n_out;  // b < 0: final pass
   uint64_t xmask, zmask;
   uint32_t c0, nq, q_off, perm_off;
+  uint32_t star;              // measure pass in star form at b with no X mask:
+  uint32_t amask, zb;         //   sign = c0 ^ par(k & zmask) ^ k_b (zb ^ par(k & amask))
+  uint32_t pad_;
   double w1re, w1im, scale;
 };
 struct BQ {
@@ -108,7 +111,26 @@ __global__ void __launch_bounds__(kBlock) k_batch(const BItem* __restrict__ item
       const T sc = (T)ps.scale, wr = (T)(ps.scale * ps.w1re), wi = (T)(ps.scale * ps.w1im);
       const uint32_t n_out = (uint32_t)ps.n_out;
       const uint32_t total = B << n_out;
-      if (ps.b >= 0) {
+      if (ps.b >= 0 && ps.star) {
+        // star form, no X mask, every index below 2^16: 32-bit index math and
+        // both signs from two parities
+        const uint32_t b = (uint32_t)ps.b, z = (uint32_t)ps.zmask;
+        const uint32_t lowm = (1u << b) - 1u, nmask = (1u << n_out) - 1u, inm = (1u << ps.n_in) - 1u;
+        const T nsc = -sc, nwr = -wr, nwi = -wi;
+        for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+          const uint32_t col = idx >> n_out, j = idx & nmask;
+          const uint32_t k0 = ((j >> b) << (b + 1)) | (j & lowm);
+          const V* src = cur + col * stride;
+          const V x0 = src[k0 & inm], x1 = src[(k0 | (1u << b)) & inm];  // prepared qubits: broadcast
+          const uint32_t s0 = (ps.c0 ^ (uint32_t)__popc(k0 & z)) & 1u;
+          const uint32_t s1 = (s0 ^ ps.zb ^ (uint32_t)__popc(k0 & ps.amask)) & 1u;
+          const T a = s0 ? nsc : sc, br = s1 ? nwr : wr, bi = s1 ? nwi : wi;
+          V y;
+          y.x = a * x0.x + br * x1.x - bi * x1.y;
+          y.y = a * x0.y + br * x1.y + bi * x1.x;
+          nxt[col * stride + j] = y;
+        }
+      } else if (ps.b >= 0) {
         const uint64_t bb = 1ull << ps.b;
         for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
           const uint32_t col = idx >> n_out;
@@ -287,6 +309,20 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
       // quadratic terms: one lower endpoint per edge
       for (auto& ed : d.edges) bqs.push_back(BQ{1ull << ed.second, ed.first, 0});
       bp.nq = (uint32_t)(bqs.size() - bp.q_off);
+      if (d.kind == 0 && d.xmask == 0 && d.n_in + d.r <= 16) {
+        uint32_t a = 0;
+        bool star = true;
+        for (auto& ed : d.edges) {
+          if (ed.first == d.b) a |= 1u << ed.second;
+          else if (ed.second == d.b) a |= 1u << ed.first;
+          else star = false;
+        }
+        if (star) {
+          bp.star = 1;
+          bp.amask = a;
+          bp.zb = (uint32_t)((d.zmask >> d.b) & 1u);
+        }
+      }
       bp.perm_off = (uint32_t)bperms.size();
       for (int q : d.perm) bperms.push_back(q);
       bp.w1re = d.w1re;
