@@ -68,9 +68,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rows", type=int, default=ROWS)
     ap.add_argument("--cols", type=int, default=COLS)
-    ap.add_argument("--legs", default="c64,c128,e2e,cpu,rec,learned",
-                    help="comma list of c64 (always run), c128, e2e, cpu, rec, learned; fewer legs for profiler runs")
+    ap.add_argument("--legs", default="c64,c128,e2e,cpu,rec,learned,qft,small",
+                    help="comma list of c64 (always run), c128, e2e, cpu, rec, learned, qft, small; fewer legs for "
+                         "profiler runs")
     ap.add_argument("--learned-count", type=int, default=24, help="held-out patterns in the learned leg")
+    ap.add_argument("--rec-branches", type=int, default=64, help="outcome branches per pattern in the recognition leg")
     ap.add_argument("--rec-count", type=int, default=256, help="patterns in the recognition leg")
     return ap.parse_args()
 
@@ -207,7 +209,10 @@ def recognition_leg(args, owqs, torch):
     complex64.  Items whose arrays fit a shared-memory column block run in one
     persistent launch; wider ones are streamed through the pass kernels with
     one reused output buffer.  The plain complex128 path (owqs_unitary per
-    pattern) is timed on the widths up to 10 with the c64 batch's error."""
+    pattern) is timed on the widths up to 10 with the c64 batch's error.
+    Determinism: 64 random outcome branches per pattern on one random input,
+    complex64 and complex128, one batch call each, with every branch's
+    fidelity to the pattern's first branch computed on the device."""
     import numpy as np
     from owqs_inputs import workloads
     wls = workloads.random_batch(count=args.rec_count)
@@ -267,12 +272,126 @@ def recognition_leg(args, owqs, torch):
     e1.record()
     torch.cuda.synchronize()
     t64_sub = e0.elapsed_time(e1) / 1e3
+    # determinism: 64 random outcome branches of every pattern on one random
+    # input, in one batch call per precision, each branch's output compared
+    # with the pattern's first branch on the device (<ref|out> and norms)
+    from owqs_inputs.rng import SplitMix64, random_state
+    branches = {}
+    handles = [(h, wl) for h, wl in small]
+    for wl in wide:
+        h = owqs.load(wl.pattern)
+        h.reorder()
+        handles.append((h, wl))
+    for dtype, tdt, npdt in (("c64", torch.complex64, np.complex64), ("c128", torch.complex128, np.complex128)):
+        bitems, bufs = [], []
+        rng = SplitMix64(1604)
+        for h, wl in handles:
+            nin, nout = len(wl.pattern.inputs), len(wl.pattern.outputs)
+            psi = torch.from_numpy(random_state(rng, nin).astype(npdt)).cuda()
+            first = len(bitems)
+            for b in range(args.rec_branches):
+                o = torch.empty(1 << nout, dtype=tdt, device="cuda")
+                bufs.append((psi, o))
+                bitems.append({"handle": h, "outcomes": rng.bits(h.K), "psi_in": psi, "out": o,
+                               "ref": -1 if b == 0 else first})
+        owqs.run_batch(bitems[: min(len(bitems), 64)], dtype=dtype, use_graph=False)  # tunes the column block
+        torch.cuda.synchronize()
+        e0.record()
+        # every branch item has its own outcomes: graphs would never be replayed
+        binfo, ov = owqs.run_batch(bitems, dtype=dtype, overlaps=True, use_graph=False)
+        e1.record()
+        torch.cuda.synchronize()
+        tb = e0.elapsed_time(e1) / 1e3
+        fid = [ov[i, 0] ** 2 + ov[i, 1] ** 2 for i, it in enumerate(bitems) if it["ref"] >= 0]
+        fid = [f / (ov[i, 2] * ov[i, 3]) for f, i in zip(fid, [i for i, it in enumerate(bitems) if it["ref"] >= 0])]
+        branches[dtype] = {"items": len(bitems), "seconds": tb, "batch_info": binfo,
+                           "min_branch_fidelity": float(min(fid)), "bound": 1 - 4e-5 if dtype == "c64" else 1 - 1e-12}
+        del bufs, bitems
+    for h, wl in handles[len(small):]:
+        h.close()
     return {"patterns": len(wls), "widths": "6..14", "columns": cols, "amp_updates": upd,
+            "branches_per_pattern": args.rec_branches, "determinism": branches,
             "seconds": t_small + t_wide, "smem_batch_seconds": t_small, "wide_seconds": t_wide,
             "amp_updates_per_s": upd / (t_small + t_wide), "batch_info": info,
             "c128_plain_subset": {"patterns": len(sub), "seconds_c128_per_pattern_calls": t128,
                                   "seconds_c64_batch": t64_sub, "speedup": t128 / t64_sub if t64_sub else None,
                                   "c64_max_abs_err_vs_c128": err, "bound": 2e-5}}
+
+
+def qft_leg(args, owqs, torch):
+    """QFT-shaped pattern on 24 logical qubits (2784 measurements, peak 25
+    live qubits), random normalised input, forced seeded outcomes, complex64
+    and complex128.  The pattern has no final swaps, so the exact output is
+    the inverse DFT (numpy FFT) of the bit-reversed input times 2^(n/2); per
+    output the max-abs error after global-phase alignment and the fidelity
+    |<ref|out>|^2 are reported for both precisions."""
+    import numpy as np
+    from owqs_inputs import workloads
+    wl = workloads.qft(24)
+    h = owqs.load(wl.pattern)
+    _, rinfo = h.reorder()
+    n = 24
+    upd = int(h.info()["amp_updates"])
+    idx = np.arange(1 << n, dtype=np.int64)
+    rev = np.zeros_like(idx)
+    for b in range(n):
+        rev |= ((idx >> b) & 1) << (n - 1 - b)
+    ref = np.fft.ifft(wl.psi_in[rev]) * math.sqrt(1 << n)
+    res = {"workload": "QFT-shaped J/CZ pattern, 24 logical qubits, random normalised input",
+           "measurements": wl.pattern.K, "peak_m": rinfo["peak_m"], "amp_updates_per_run": upd}
+    for dtype, tdt in (("c64", torch.complex64), ("c128", torch.complex128)):
+        psi = torch.from_numpy(wl.psi_in.astype(np.complex64 if dtype == "c64" else np.complex128)).cuda()
+        out = torch.empty(1 << n, dtype=tdt, device="cuda")
+        run = lambda: h.run(psi, dtype=dtype, outcomes=wl.outcomes, out=out)
+        run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = 3
+        e0.record()
+        for _ in range(steps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / steps
+        got = out.cpu().numpy().astype(np.complex128)
+        ov = np.vdot(got, ref)
+        aligned = got * (ov / abs(ov))
+        res[dtype] = {"ms_per_run": 1e3 * t, "amp_updates_per_s": upd / t,
+                      "max_abs_err_vs_exact": float(np.max(np.abs(aligned - ref))),
+                      "fidelity": float(abs(ov) ** 2 / (np.vdot(got, got).real * np.vdot(ref, ref).real))}
+        del out, psi
+    res["c64_speedup_over_c128"] = res["c128"]["ms_per_run"] / res["c64"]["ms_per_run"]
+    h.close()
+    return res
+
+
+def small_leg(args, owqs, torch):
+    """The small case: random 3-wire J/CZ circuit of depth 10 (33 qubits, 30
+    measurements, peak 4 live), complex128, forced seeded outcomes.  Latency
+    of one run replayed from the CUDA graph (host schedule compile included,
+    as in every owqs_run call); its parity with the oracle is a test."""
+    import numpy as np
+    from owqs_inputs import workloads
+    wl = workloads.small_random()
+    h = owqs.load(wl.pattern)
+    h.reorder()
+    psi = torch.from_numpy(wl.psi_in).cuda()
+    out = torch.empty(1 << len(wl.pattern.outputs), dtype=torch.complex128, device="cuda")
+    run = lambda: h.run(psi, dtype="c128", outcomes=wl.outcomes, out=out)
+    for _ in range(5):
+        run()
+    torch.cuda.synchronize()
+    n = 200
+    t0 = time.perf_counter()
+    for _ in range(n):
+        run()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / n
+    ms, _, _, _ = h.profile(psi, dtype="c128", outcomes=wl.outcomes)
+    res = {"workload": "random 3-wire J/CZ circuit, depth 10 (30 measurements)", "us_per_run": 1e6 * dt,
+           "launches_per_run": int(len(ms))}
+    h.close()
+    return res
 
 
 def learned_leg(args, owqs, torch, hbm_gbs):
@@ -458,6 +577,8 @@ def run_owqs(args):
         accuracy = {"c64_vs_c128_max_abs_amp_err": amp_err, "c64_vs_c128_max_prob_err": prob_err, "bound": 2e-5}
 
     rec = recognition_leg(args, owqs, torch) if "rec" in legs else None
+    qft = qft_leg(args, owqs, torch) if "qft" in legs else None
+    small = small_leg(args, owqs, torch) if "small" in legs else None
     learned = learned_leg(args, owqs, torch, hbm) if "learned" in legs else None
 
     cpu = None
@@ -482,6 +603,8 @@ def run_owqs(args):
             "accuracy": accuracy,
             "e2e": e2e,
             "recognition": rec,
+            "qft24": qft,
+            "small": small,
             "learned_reorder": learned,
             "cpu_baseline": cpu,
             "clocks": clocks,
