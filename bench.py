@@ -57,7 +57,7 @@ FP64_PEAK_TFLOPS = 1.25
 FP64_FLOPS_PER_OUTPUT = 14
 
 
-def parse():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--learned-count", type=int, default=24, help="held-out patterns in the learned leg")
     ap.add_argument("--rec-branches", type=int, default=64, help="outcome branches per pattern in the recognition leg")
     ap.add_argument("--rec-count", type=int, default=256, help="patterns in the recognition leg")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -82,6 +82,22 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(t: float, dist=None, device: str = "cpu") -> float:
+    """Slowest rank's time (every rank gets it); t itself without a group."""
+    if dist is None:
+        return t
+    import torch
+    tt = torch.tensor([t], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_throughput(units_per_step: float, steps: int, world: int, t_max: float) -> float:
+    """Whole-job throughput of N independent replicas (weak scaling): the
+    units every rank processed over the slowest rank's time."""
+    return units_per_step * steps * world / t_max
 
 
 def measured_peaks():
@@ -490,12 +506,7 @@ def run_owqs(args):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        t = e0.elapsed_time(e1) / 1e3
-        if dist is not None:
-            tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = tt.item()
-        return t
+        return max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, "cuda")
 
     run64 = lambda: h.run(None, dtype="c64", outcomes=wl.outcomes, out=out64)
     for _ in range(args.warmup):
@@ -505,7 +516,7 @@ def run_owqs(args):
     sampler.start()
     t64 = timed(run64, args.steps)
     clocks = sampler.stop()
-    value = upd * args.steps * world / t64
+    value = replica_throughput(upd, args.steps, world, t64)
 
     # per-launch CUDA-event timing of one run: roofline of the dominant kernel
     hbm, peak_kind = measured_peaks()
@@ -551,7 +562,7 @@ def run_owqs(args):
         sampler_e.start()
         te = timed(run_e2e, args.e2e_steps)
         clocks_e2e = sampler_e.stop()
-        e2e = {"value": upd * args.e2e_steps * world / te, "unit": UNIT,
+        e2e = {"value": replica_throughput(upd, args.e2e_steps, world, te), "unit": UNIT,
                "h2d_bytes_per_step": (1 << nin) * 8, "d2h_bytes_per_step": (1 << nout) * 8 + 8 * (p.K + 2),
                "ms_per_step": 1e3 * te / args.e2e_steps, "clocks": clocks_e2e}
 
@@ -572,7 +583,7 @@ def run_owqs(args):
         amp_err = torch.max(torch.abs(a * (ov / abs(ov)) - out128)).item()
         prob_err = float(np.max(np.abs(p64 - p128)))
         del a, out128
-        fp64 = {"dtype": "c128", "value": upd * args.fp64_steps * world / t128,
+        fp64 = {"dtype": "c128", "value": replica_throughput(upd, args.fp64_steps, world, t128),
                 "ms_per_step": 1e3 * t128 / args.fp64_steps, "roofline": roof128}
         accuracy = {"c64_vs_c128_max_abs_amp_err": amp_err, "c64_vs_c128_max_prob_err": prob_err, "bound": 2e-5}
 
@@ -617,7 +628,7 @@ def run_owqs(args):
 
 
 def main():
-    args = parse()
+    args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     return run_owqs(args)

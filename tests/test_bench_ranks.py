@@ -1,0 +1,63 @@
+"""Host logic of bench.py's N > 1 mode on CPU with two gloo ranks: the path
+runs independent replicas (no data-path collective), the slowest rank's time
+is what every rank reports, and whole-job throughput counts every rank's
+units.  The reference arm runs on rank 0 only."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        r, w, local = bench.dist_env()
+        t = bench.max_over_ranks(1.0 + rank, dist)            # rank 1 is the slower one
+        v = bench.replica_throughput(100.0, 4, w, t)
+        q.put((rank, r, w, t, v))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time():
+    mp = pytest.importorskip("torch.multiprocessing")
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    for rank, r, w, t, v in res:
+        assert (r, w) == (rank, 2)
+        assert t == 2.0                                          # every rank reports the slowest time
+        assert v == 100.0 * 4 * 2 / 2.0                          # all ranks' units over that time
+
+
+def test_single_process_needs_no_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5) == 3.5
+    assert bench.replica_throughput(10.0, 3, 1, 2.0) == 15.0
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    args = bench.parse_args(["--impl", "reference", "--gpus", "2"])
+    assert bench.run_reference(args) == 0          # returns at once, no oracle work
