@@ -267,6 +267,24 @@ enum { OWQS_RUN_HOST_SAMPLING = 1 };
 owqs_status owqs_run(owqs_pattern* p, const owqs_run_opts* opts, const void* psi_in,
                      void* psi_out, uint8_t* outcomes, double* probs);
 
+/* Product input (Section 4.1 and Fig. 8a: the input as separate sub-states).
+ * The inputs are given as nfactors factors: factor f holds sizes[f] input
+ * qubits (1 .. 30), listed in qubits[] (all factors concatenated, each in its
+ * bit order: bit k of factor f's vector is its k-th qubit), and its
+ * 2^sizes[f] amplitudes at the device pointer vecs[f] (the run's dtype,
+ * 16-byte aligned).  Every input qubit is in exactly one factor; each factor
+ * is normalised by the library.  A factor joins the live array (a tensor
+ * product, its qubits becoming the top bits) only at the start of the first
+ * segment whose commands touch one of its qubits, or before the final pass
+ * for an output no command touches, so inputs that a pattern reaches late
+ * stay out of the array until then.
+ *   opts      as owqs_run; policy FORCED or ZERO, io DEVICE
+ *   psi_out, outcomes, probs: as owqs_run
+ * OWQS_ERR_ARG if the factors do not cover the inputs exactly once. */
+owqs_status owqs_run_product(owqs_pattern* p, const owqs_run_opts* opts, uint32_t nfactors, const uint32_t* sizes,
+                             const uint32_t* qubits, const void* const* vecs, void* psi_out, uint8_t* outcomes,
+                             double* probs);
+
 /* Test hook for the device-side wait limits (no real stall is needed to
  * exercise them).  Every wait inside the bulk-copy pass kernels is bounded:
  * on expiry the kernel raises an error flag and returns, and the run reports

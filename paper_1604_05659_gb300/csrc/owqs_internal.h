@@ -107,7 +107,8 @@ owqs_status learned_order(const Pattern& p, const owqs_model* m, bool eowqs, boo
 // s_c = scale / sqrt(norm of the previous array) in OWQS mode, scale in EOWQS.
 // ---------------------------------------------------------------------------
 struct PassDesc {
-  int kind = 0;  // 0 measure, 1 final
+  int kind = 0;  // 0 measure, 1 final, 2 join of an input factor (product input)
+  int factor = -1;  // kind 2: the factor whose qubits become the top r bits
   int n_in = 0, r = 0, b = -1, n_out = 0;
   int outcome = 0;
   uint32_t meas_k = 0;  // K-index (load order) of the measured qubit
@@ -160,7 +161,7 @@ struct PassParams {
 
 enum KernelKind {
   KK_FAST = 0, KK_GENERIC = 1, KK_FINAL = 2, KK_NORM = 3, KK_PROB = 4, KK_TMA = 5, KK_DECIDE = 7,
-  KK_GROUP = 8
+  KK_GROUP = 8, KK_KRON = 9
 };
 
 
@@ -311,9 +312,29 @@ struct OutcomeSource {
 
 // Walk the active order; emits K measure passes then the final pass.  Returns
 // OWQS_OK or an error.  maps (optional) receives bit_of_qubit after each pass.
+// factors (optional, product inputs): the input qubits grouped into factors
+// (each list in the factor's bit order).  No input qubit is live at the start;
+// at the start of each segment, every factor with a qubit that the segment
+// (up to and including its measurement) touches joins the live array as new
+// top bits (a kind-2 pass), and so does every factor holding an output before
+// the final pass.
 owqs_status compile_schedule(const Pattern& p, int mode, OutcomeSource& src,
                              std::vector<PassDesc>& passes,
-                             std::vector<std::vector<int32_t>>* maps = nullptr);
+                             std::vector<std::vector<int32_t>>* maps = nullptr,
+                             const std::vector<std::vector<uint32_t>>* factors = nullptr);
+
+// Join of one input factor (product input): out[j] = s * in[j mod 2^n_in] *
+// phi[j >> n_in], s = 1/sqrt(norms[fnorm]) (the factor normalised) times
+// 1/sqrt(norms[norm_in]) if norm_in >= 0; in == nullptr means the scalar 1.
+struct KronParams {
+  const void* in;
+  void* out;
+  const void* phi;
+  const double* norms;
+  int n_in, q;
+  int norm_in, fnorm;
+};
+cudaError_t launch_kron(const KronParams& K, int dtype, cudaStream_t s);
 
 }  // namespace owqs
 

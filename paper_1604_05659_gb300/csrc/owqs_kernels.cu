@@ -987,6 +987,50 @@ cudaError_t launch_put_u64(uint64_t* dst, uint64_t v, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Join of an input factor (product input, Section 4.1: a tensor product of
+// sub-states): out[j] = s in[j mod 2^n_in] phi[j >> n_in], the factor's
+// qubits becoming the top bits; s normalises the factor (and the previous
+// array in OWQS mode).  Grid-stride over the outputs.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_kron(const KronParams K) {
+  using V = typename Cplx<T>::V;
+  const V* __restrict__ in = reinterpret_cast<const V*>(K.in);
+  const V* __restrict__ phi = reinterpret_cast<const V*>(K.phi);
+  V* __restrict__ out = reinterpret_cast<V*>(K.out);
+  double sc = 1.0;
+  const double nf = K.norms[K.fnorm];
+  sc = nf > 0.0 ? 1.0 / sqrt(nf) : 0.0;
+  if (K.norm_in >= 0) {
+    const double nv = K.norms[K.norm_in];
+    sc = nv > 0.0 ? sc / sqrt(nv) : 0.0;
+  }
+  const T s = (T)sc;
+  const uint64_t n = 1ull << (K.n_in + K.q), lo = (1ull << K.n_in) - 1ull;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    const V f = phi[j >> K.n_in];
+    V a;
+    if (in) {
+      a = in[j & lo];
+    } else {
+      a.x = (T)1;
+      a.y = (T)0;
+    }
+    V y;
+    y.x = s * (a.x * f.x - a.y * f.y);
+    y.y = s * (a.x * f.y + a.y * f.x);
+    out[j] = y;
+  }
+}
+
+cudaError_t launch_kron(const KronParams& K, int dtype, cudaStream_t s) {
+  const uint64_t n = 1ull << (K.n_in + K.q);
+  const int grid = (int)std::min<uint64_t>((n + kBlock - 1) / kBlock, (uint64_t)max_grid());
+  if (dtype == OWQS_C64) k_kron<float><<<grid, kBlock, 0, s>>>(K);
+  else k_kron<double><<<grid, kBlock, 0, s>>>(K);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_norm(const void* in, uint64_t n, int dtype, double* norms, int slot, double* partials,
                         unsigned int* counter, int grid, cudaStream_t s) {
   if (dtype == OWQS_C64) k_norm<float><<<grid, kBlock, 0, s>>>(in, n, norms, slot, partials, counter);

@@ -102,8 +102,9 @@ struct FixedSource : OutcomeSource {
 // launch list
 // ---------------------------------------------------------------------------
 struct Item {
-  int type = 0;  // 0 pass, 1 norm, 3 device-drawn outcome, 4 pass group
+  int type = 0;  // 0 pass, 1 norm, 3 device-drawn outcome, 4 pass group, 5 factor join
   PassParams P;
+  KronParams Kp;
   GroupParams G;
   DecideParams D;
   LaunchPlan L;
@@ -207,6 +208,38 @@ class Runner {
     pass_i_ += G.k;
   }
 
+  // join of an input factor (product input): its norm into slot fslot, then
+  // the tensor product with the live array (normalised), the factor's qubits
+  // becoming the top bits
+  void join(const PassDesc& d, const void* phi, int fslot) {
+    Item nm;
+    nm.type = 1;
+    nm.norm_in = phi;
+    nm.norm_n = 1ull << d.r;
+    nm.norm_slot = fslot;
+    nm.L.grid = (int)std::min<uint64_t>((nm.norm_n + kBlock - 1) / kBlock, (uint64_t)max_grid());
+    nm.L.kind = KK_NORM;
+    nm.L.bytes = std::ldexp(1.0, d.r) * (dtype_ == OWQS_C64 ? 8.0 : 16.0);
+    issue(nm);
+    Item it;
+    it.type = 5;
+    it.Kp.in = cur_in_;
+    it.Kp.out = rc_.buf[sel_];
+    sel_ ^= 1;
+    it.Kp.phi = phi;
+    it.Kp.norms = rc_.norms;
+    it.Kp.n_in = d.n_in;
+    it.Kp.q = d.r;
+    it.Kp.norm_in = prev_slot_;
+    it.Kp.fnorm = fslot;
+    it.L.kind = KK_KRON;
+    it.L.bytes = ((cur_in_ ? std::ldexp(1.0, d.n_in) : 0.0) + std::ldexp(1.0, d.n_out)) *
+                 (dtype_ == OWQS_C64 ? 8.0 : 16.0);
+    issue(it);
+    cur_in_ = it.Kp.out;
+    prev_slot_ = -1;  // the joined array is normalised
+  }
+
   // longest pass group starting at passes[i] that can run as one sweep (0 if none)
   int group_at(const std::vector<PassDesc>& passes, size_t i, GroupParams& G, LaunchPlan& L) const {
     if (cur_in_ == nullptr || !group_enabled()) return 0;
@@ -253,7 +286,9 @@ class Runner {
 
   owqs_status launch(const Item& it, cudaStream_t s) {
     cudaError_t e;
-    if (it.type == 4)
+    if (it.type == 5)
+      e = launch_kron(it.Kp, dtype_, s);
+    else if (it.type == 4)
       e = launch_group(it.G, s);
     else if (it.type == 3)
       e = launch_decide(it.D, s);
@@ -362,6 +397,13 @@ static std::string graph_key(const Pattern& p, const owqs_run_opts* o, const voi
   return k;
 }
 
+// product input: the input qubits grouped into factors and each factor's
+// amplitudes (device)
+struct ProductInput {
+  std::vector<std::vector<uint32_t>> qubits;
+  std::vector<const void*> vecs;
+};
+
 struct Prepared {
   std::vector<PassDesc> passes;
   const void* in_dev = nullptr;
@@ -371,7 +413,8 @@ struct Prepared {
 };
 
 static owqs_status prepare(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
-                           const uint8_t* outcomes, RunCache*& rc, Prepared& pr, bool sampled) {
+                           const uint8_t* outcomes, RunCache*& rc, Prepared& pr, bool sampled,
+                           const ProductInput* prod = nullptr) {
   if (!o || !psi_out) return set_error(OWQS_ERR_ARG, "NULL argument");
   if (o->dtype > OWQS_C128 || o->mode > OWQS_MODE_EOWQS || o->policy > OWQS_OUTCOME_ZERO || o->io > OWQS_IO_HOST)
     return set_error(OWQS_ERR_ARG, "bad option value");
@@ -386,13 +429,14 @@ static owqs_status prepare(Pattern& p, const owqs_run_opts* o, const void* psi_i
   if (st != OWQS_OK) return st;
   if (!sampled) {  // sampled runs compile while they execute
     FixedSource src(p, o->policy == OWQS_OUTCOME_ZERO ? nullptr : outcomes);
-    st = compile_schedule(p, o->mode, src, pr.passes);
+    st = compile_schedule(p, o->mode, src, pr.passes, nullptr, prod ? &prod->qubits : nullptr);
     if (st != OWQS_OK) return st;
   }
   const int K = (int)p.meas_qubit.size();
   pr.in_elems = 1ull << p.inputs.size();
   pr.out_elems = 1ull << p.outputs.size();
-  st = ensure_buf((void*&)rc->norms, rc->nnorms, sizeof(double) * (3 * (size_t)K + 8), "norm slots");
+  const size_t nfac = prod ? prod->qubits.size() : 0;
+  st = ensure_buf((void*&)rc->norms, rc->nnorms, sizeof(double) * (3 * (size_t)K + 8 + nfac), "norm slots");
   if (st == OWQS_OK)
     st = ensure_buf((void*&)rc->partials, rc->npartials, sizeof(double) * kGroupMax * (size_t)max_grid(), "partials");
   if (st == OWQS_OK && !rc->counter) {  // [0] finished-block counter, [1] error flag
@@ -653,12 +697,14 @@ static owqs_status sample_on_device(Pattern& p, const owqs_run_opts* o, RunCache
 static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
                             uint8_t* outcomes, double* probs, float* prof_ms, double* prof_bytes,
                             uint32_t* prof_kind, uint32_t prof_cap, uint32_t* prof_n, int vdiag = 0,
-                            double* frob2 = nullptr) {
+                            double* frob2 = nullptr, const ProductInput* prod = nullptr) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(o ? o->stream : nullptr);
   RunCache* rc = nullptr;
   Prepared pr;
   const bool sampled = o && o->policy == OWQS_OUTCOME_SAMPLED;
-  owqs_status st = prepare(p, o, psi_in, psi_out, outcomes, rc, pr, sampled);
+  if (prod && (sampled || (o && o->io != OWQS_IO_DEVICE) || vdiag || psi_in))
+    return set_error(OWQS_ERR_UNSUPPORTED, "product inputs take device vectors and forced or zero outcomes");
+  owqs_status st = prepare(p, o, psi_in, psi_out, outcomes, rc, pr, sampled, prod);
   if (st != OWQS_OK) return st;
   const int K = (int)p.meas_qubit.size();
   std::vector<int> outcome_of_pass;
@@ -675,7 +721,7 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
     if (st != OWQS_OK) return st;
     size_t wmax = 1;
     for (const PassDesc& d : tmp)
-      if (d.kind == 0) wmax = std::max<size_t>(wmax, (size_t)1 << d.n_out);
+      if (d.kind != 1) wmax = std::max<size_t>(wmax, (size_t)1 << d.n_out);
     st = ensure_pingpong(rc, wmax, pr.amp);
     if (st != OWQS_OK) return st;
     if (o->io == OWQS_IO_HOST && psi_in) {
@@ -706,7 +752,7 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
   } else {
     size_t wmax = 1;
     for (const PassDesc& d : pr.passes)
-      if (d.kind == 0) wmax = std::max<size_t>(wmax, (size_t)1 << d.n_out);
+      if (d.kind != 1) wmax = std::max<size_t>(wmax, (size_t)1 << d.n_out);
     st = ensure_pingpong(rc, wmax, pr.amp);
     if (st != OWQS_OK) return st;
     for (const PassDesc& d : pr.passes)
@@ -719,7 +765,9 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
       GroupParams G;
       LaunchPlan GL;
       int gk = 0;
-      if (d.kind != 0) {
+      if (d.kind == 2) {
+        R.join(d, prod->vecs[d.factor], 3 * K + 8 + d.factor);
+      } else if (d.kind != 0) {
         R.final_pass(d);
       } else if ((gk = R.group_at(pr.passes, i, G, GL)) >= 2) {
         R.measure_group(G, GL);
@@ -771,7 +819,10 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
         else stall->P.stall_limit = limit;
         st = replay(rc, R, std::string(), false, s);  // direct launches, no graph
       } else {
-        st = replay(rc, R, graph_key(p, o, pr.in_dev, pr.out_dev, outcomes), o->use_graph != 0, s);
+        std::string key = graph_key(p, o, pr.in_dev, pr.out_dev, outcomes);
+        if (prod)
+          for (const void* v : prod->vecs) key.append(reinterpret_cast<const char*>(&v), sizeof(v));
+        st = replay(rc, R, key, o->use_graph != 0, s);
       }
       if (st != OWQS_OK) return st;
     }
@@ -810,6 +861,36 @@ owqs_status run_unchecked(Pattern& p, const owqs_run_opts* o, const void* psi_in
 }  // namespace owqs
 
 extern "C" {
+
+owqs_status owqs_run_product(owqs_pattern* h, const owqs_run_opts* o, uint32_t nfactors, const uint32_t* sizes,
+                             const uint32_t* qubits, const void* const* vecs, void* psi_out, uint8_t* outcomes,
+                             double* probs) {
+  clear_error();
+  if (!h || !o || (nfactors && (!sizes || !qubits || !vecs))) return set_error(OWQS_ERR_ARG, "NULL argument");
+  const Pattern& p = h->p;
+  ProductInput prod;
+  std::vector<char> seen(p.n, 0), is_in(p.n, 0);
+  for (uint32_t q : p.inputs) is_in[q] = 1;
+  size_t at = 0, covered = 0;
+  for (uint32_t f = 0; f < nfactors; ++f) {
+    if (sizes[f] == 0 || sizes[f] > 30) return set_error(OWQS_ERR_ARG, "factor sizes must be 1 .. 30 qubits");
+    if (!vecs[f] || ((uintptr_t)vecs[f] % 16)) return set_error(OWQS_ERR_ARG, "factor vectors must be 16-byte aligned");
+    std::vector<uint32_t> qs(qubits + at, qubits + at + sizes[f]);
+    at += sizes[f];
+    for (uint32_t q : qs) {
+      if (q >= p.n || !is_in[q] || seen[q]) return set_error(OWQS_ERR_ARG, "every input must be in exactly one factor");
+      seen[q] = 1;
+      ++covered;
+    }
+    prod.qubits.push_back(std::move(qs));
+    prod.vecs.push_back(vecs[f]);
+  }
+  if (covered != p.inputs.size()) return set_error(OWQS_ERR_ARG, "every input must be in exactly one factor");
+  if (o->mode == OWQS_MODE_EOWQS && !has_gflow(h->p))
+    return set_error(OWQS_ERR_NOT_DETERMINISTIC, "EOWQS: the open graph has no gflow (Section 4.5)");
+  return run_impl(h->p, o, nullptr, psi_out, outcomes, probs, nullptr, nullptr, nullptr, 0, nullptr, 0, nullptr,
+                  &prod);
+}
 
 owqs_status owqs_test_wait_timeout(uint32_t runs, uint64_t limit_cycles) {
   clear_error();

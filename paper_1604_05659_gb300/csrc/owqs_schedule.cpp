@@ -32,7 +32,8 @@ static inline double pow2_half(int h) {
 
 owqs_status compile_schedule(const Pattern& p, int mode, OutcomeSource& src,
                              std::vector<PassDesc>& passes,
-                             std::vector<std::vector<int32_t>>* maps) {
+                             std::vector<std::vector<int32_t>>* maps,
+                             const std::vector<std::vector<uint32_t>>* factors) {
   passes.clear();
   const uint32_t n = p.n;
   std::vector<int32_t> bit_of(n, -1);
@@ -41,9 +42,17 @@ owqs_status compile_schedule(const Pattern& p, int mode, OutcomeSource& src,
   const bool upfront = src.known_upfront(outcome);
   if (!upfront && !p.deps_ok)
     return set_error(OWQS_ERR_ARG, "sampled outcomes need an order that measures every domain first");
-  for (uint32_t q : p.inputs) {
-    bit_of[q] = (int32_t)at_bit.size();
-    at_bit.push_back(q);
+  std::vector<int32_t> factor_of(n, -1);
+  std::vector<char> joined;
+  if (factors) {
+    joined.assign(factors->size(), 0);
+    for (size_t f = 0; f < factors->size(); ++f)
+      for (uint32_t q : (*factors)[f]) factor_of[q] = (int32_t)f;
+  } else {
+    for (uint32_t q : p.inputs) {
+      bit_of[q] = (int32_t)at_bit.size();
+      at_bit.push_back(q);
+    }
   }
   if ((int)at_bit.size() > kMaxLive) return set_error(OWQS_ERR_OOM, "more than 62 input qubits");
   int n_in = (int)at_bit.size();
@@ -52,6 +61,38 @@ owqs_status compile_schedule(const Pattern& p, int mode, OutcomeSource& src,
   uint64_t z = 0, x = 0;
   uint32_t c0 = 0;
   if (maps) maps->push_back(bit_of);
+
+  // product input: make factor f live as the top bits (a kind-2 pass)
+  auto join = [&](int f) -> bool {
+    if (joined[f]) return true;
+    joined[f] = 1;
+    const std::vector<uint32_t>& qs = (*factors)[f];
+    if ((int)(at_bit.size() + qs.size()) > kMaxLive) return false;
+    PassDesc d;
+    d.kind = 2;
+    d.factor = f;
+    d.n_in = n_in;
+    d.r = (int)qs.size();
+    d.n_out = n_in + (int)qs.size();
+    for (uint32_t q : qs) {
+      bit_of[q] = (int32_t)at_bit.size();
+      at_bit.push_back(q);
+    }
+    n_in = (int)at_bit.size();
+    passes.push_back(std::move(d));
+    return true;
+  };
+  // at a segment start: join every factor that the segment touches
+  auto join_ahead = [&](size_t from) -> bool {
+    for (size_t ai = from; ai < p.active.size(); ++ai) {
+      const Cmd& c = p.cmds[p.active[ai]];
+      const uint32_t q0 = c.q0, q1 = c.kind == OWQS_CMD_E ? c.q1 : c.q0;
+      for (uint32_t q : {q0, q1})
+        if (factor_of[q] >= 0 && !join(factor_of[q])) return false;
+      if (c.kind == OWQS_CMD_M) break;
+    }
+    return true;
+  };
 
   bool overflow = false;
   auto touch = [&](uint32_t q) -> int {
@@ -75,8 +116,13 @@ owqs_status compile_schedule(const Pattern& p, int mode, OutcomeSource& src,
     }
   };
 
-  for (uint32_t idx : p.active) {
-    const Cmd& c = p.cmds[idx];
+  bool seg_start = true;
+  for (size_t ai = 0; ai < p.active.size(); ++ai) {
+    const Cmd& c = p.cmds[p.active[ai]];
+    if (factors && seg_start) {
+      if (!join_ahead(ai)) return set_error(OWQS_ERR_OOM, "live width above 62 qubits");
+      seg_start = false;
+    }
     switch (c.kind) {
       case OWQS_CMD_N:
         break;  // prepared at first touch
@@ -143,6 +189,7 @@ owqs_status compile_schedule(const Pattern& p, int mode, OutcomeSource& src,
         z = x = 0;
         c0 = 0;
         if (maps) maps->push_back(bit_of);
+        seg_start = true;
         break;
       }
       default:
@@ -150,6 +197,9 @@ owqs_status compile_schedule(const Pattern& p, int mode, OutcomeSource& src,
     }
     if (overflow) return set_error(OWQS_ERR_OOM, "live width above 62 qubits; reorder the pattern");
   }
+  if (factors)  // input qubits that no command touches: outputs, joined before the final pass
+    for (uint32_t q : p.outputs)
+      if (factor_of[q] >= 0 && !join(factor_of[q])) return set_error(OWQS_ERR_OOM, "live width above 62 qubits");
   for (uint32_t q : p.outputs) touch(q);
   if (overflow) return set_error(OWQS_ERR_OOM, "live width above 62 qubits");
   if (at_bit.size() != p.outputs.size())

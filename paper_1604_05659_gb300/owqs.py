@@ -27,7 +27,7 @@ RUN_HOST_SAMPLING = 1
 DTYPE = {"c64": 0, "c128": 1}
 POLICY = {"forced": 0, "sampled": 1, "zero": 2}
 KERNEL_KIND = {0: "fast_pass", 1: "generic_pass", 2: "final", 3: "norm", 4: "prob", 5: "tma_pass",
-               7: "decide", 8: "group_pass"}
+               7: "decide", 8: "group_pass", 9: "factor_join"}
 
 
 class OwqsError(RuntimeError):
@@ -126,6 +126,9 @@ EXPORTS = {
     "owqs_find_flow": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_int32),
                                  C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32)]),
     "owqs_test_wait_timeout": (C.c_int, [C.c_uint32, C.c_uint64]),
+    "owqs_run_product": (C.c_int, [C.c_void_p, C.POINTER(owqs_run_opts), C.c_uint32, C.POINTER(C.c_uint32),
+                                   C.POINTER(C.c_uint32), C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(C.c_uint8),
+                                   C.POINTER(C.c_double)]),
     "owqs_last_error": (C.c_char_p, []),
     "owqs_abi_version": (C.c_uint32, []),
 }
@@ -300,6 +303,37 @@ class Handle:
                                 C.c_void_p(out.data_ptr()), oc.ctypes.data_as(C.POINTER(C.c_uint8)),
                                 probs.ctypes.data_as(C.POINTER(C.c_double)))
         if check and st not in (OK,):
+            _check(st)
+        return out, oc[: self.K].copy(), probs[: self.K].copy(), st
+
+    def run_product(self, factors, *, dtype: str = "c128", mode: str = "owqs", policy: str = "forced",
+                    outcomes=None, stream=None, use_graph: bool = True, out=None, check: bool = True):
+        """Run with a product input: factors is a list of (qubits, CUDA
+        tensor) pairs, tensor bit k = qubits[k]; returns as run()."""
+        import torch
+        tdt = torch.complex64 if dtype == "c64" else torch.complex128
+        sizes, qubits, vecs = [], [], []
+        for qs, v in factors:
+            if not v.is_cuda or v.dtype != tdt or not v.is_contiguous() or v.numel() != (1 << len(qs)):
+                raise ValueError("each factor must be a contiguous CUDA tensor of the run's dtype, 2^len(qubits) long")
+            sizes.append(len(qs))
+            qubits += list(qs)
+            vecs.append(v.data_ptr())
+        dev = factors[0][1].device if factors else torch.device("cuda", torch.cuda.current_device())
+        if out is None:
+            out = torch.empty(1 << self.nout, dtype=tdt, device=dev)
+        oc = np.zeros(max(1, self.K), dtype=np.uint8)
+        if outcomes is not None:
+            oc[: self.K] = np.asarray(outcomes, dtype=np.uint8)[: self.K]
+        probs = np.zeros(max(1, self.K), dtype=np.float64)
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        opts = owqs_run_opts(DTYPE[dtype], MODE[mode], POLICY[policy], 0, 0, C.c_void_p(s.cuda_stream),
+                             int(use_graph), 0)
+        vp = (C.c_void_p * max(1, len(vecs)))(*vecs)
+        st = library().owqs_run_product(self._h, C.byref(opts), len(sizes), _u32(sizes), _u32(qubits), vp,
+                                        C.c_void_p(out.data_ptr()), oc.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                        probs.ctypes.data_as(C.POINTER(C.c_double)))
+        if check and st != OK:
             _check(st)
         return out, oc[: self.K].copy(), probs[: self.K].copy(), st
 
