@@ -9,9 +9,12 @@ PROA with measurement dependencies (OWQS), ranked by (peak live width,
 amplitude updates) -- the quantities that set GPU memory and time.  The
 network learns to score the target's choice lowest among the ready
 candidates at every step (features from owqs_reorder_features, training by
-owqs_model_train: the library's own forward and backward kernels).  The
-held-out patterns are then reordered in EOWQS mode with the proposal, which
-the greedy order judges, and the comparison is stored next to the weights.
+owqs_model_train: the library's own forward and backward kernels).  For a
+seeded subset the target is instead the fastest of the library's candidate
+orders as simulated and timed on the GPU.  The held-out patterns are then
+reordered in EOWQS mode with the proposal, which the greedy order judges,
+the kept orders of a subset are timed against the greedy orders that fit the
+device, and the comparison is stored next to the weights.
 """
 from __future__ import annotations
 
@@ -40,34 +43,112 @@ def target_order(h):
     return best[1]
 
 
-def build_dataset(handles, cands, seed):
-    """handles: iterable of loaded patterns (consumed one at a time)."""
+def gpu_seconds(h, reps: int = 3) -> float:
+    """Median CUDA-event time of one EOWQS run (complex64, all-zero branch,
+    graph replay) under the handle's active order."""
+    import torch
+    out = torch.empty(1 << h.nout, dtype=torch.complex64, device="cuda")
+    h.run(None, dtype="c64", mode="eowqs", policy="zero", out=out)
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h.run(None, dtype="c64", mode="eowqs", policy="zero", out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    del out
+    return sorted(ts)[len(ts) // 2]
+
+
+def timed_target(h, max_live: int = 24):
+    """Candidate orders generated by the library (greedy OWQS sweep, greedy
+    EOWQS, the circuit's own order), each simulated and timed on the GPU when
+    its widest array fits max_live qubits; returns the fastest among those of
+    the smallest peak, and whether the modelled choice (peak, then amplitude
+    updates) agrees with the measured one."""
+    k = float(max(1, h.nout))
+    w = (k, k, 0.5, k)
+    cands = []
+    for label in ("owqs_sweep", "eowqs_greedy", "circuit"):
+        if label == "owqs_sweep":
+            order, info = h.reorder(mode="owqs", sweep=True, weights=w)
+        elif label == "eowqs_greedy":
+            order, info = h.reorder(mode="eowqs", sweep=False, weights=w)
+        else:
+            order = h.pattern.measured()
+            h.set_order(order)
+            info = h.info()
+        if info["peak_live"] > max_live:
+            continue
+        cands.append({"label": label, "order": list(order), "peak": info["peak_live"],
+                      "updates": info["amp_updates"], "seconds": gpu_seconds(h)})
+    if not cands:
+        return None
+    best = min(cands, key=lambda c: (c["peak"], c["seconds"]))
+    modelled = min(cands, key=lambda c: (c["peak"], c["updates"]))
+    return best, modelled
+
+
+def build_dataset(handles, cands, seed, timed: int = 0, timed_width: int = 22):
+    """handles: iterable of loaded patterns (consumed one at a time).  The
+    first `timed` patterns of at most timed_width inputs take their target
+    from GPU timings (timed_target); the others from the modelled cost."""
     feats, firsts, targets = [], [0], []
     row = 0
+    stats = {"timed": 0, "agree": 0, "modelled_over_measured": []}
     for i, h in enumerate(handles):
-        order = target_order(h)
+        order = None
+        if stats["timed"] < timed and h.nin <= timed_width:
+            tt = timed_target(h)
+            if tt is not None:
+                best, modelled = tt
+                order = best["order"]
+                stats["timed"] += 1
+                stats["agree"] += best["label"] == modelled["label"]
+                stats["modelled_over_measured"].append(modelled["seconds"] / best["seconds"])
+        if order is None:
+            order = target_order(h)
         f, first, tgt = h.features(order, mode="eowqs", max_cands=cands, seed=seed + i)
         feats.append(f)
         firsts.extend((first[1:] + row).tolist())
         targets.extend((tgt + row).tolist())
         row += f.shape[0]
-    return (np.concatenate(feats).astype(np.float32), np.array(firsts, dtype=np.uint32),
-            np.array(targets, dtype=np.uint32))
+    X = (np.concatenate(feats).astype(np.float32), np.array(firsts, dtype=np.uint32),
+         np.array(targets, dtype=np.uint32))
+    return X if timed == 0 else (X, stats)
 
 
-def evaluate(handles, model, sweep):
+def evaluate(handles, model, sweep, timed: int = 0, timed_width: int = 22):
     """EOWQS reordering of each pattern, greedy alone and with the proposal
     (without the sweep the Eq. 18 weights are Section 5's first run,
-    a = b = d = |O|, g = 0.5)."""
+    a = b = d = |O|, g = 0.5).  For the first `timed` patterns of at most
+    timed_width inputs, the kept order's GPU time is measured against the
+    fastest greedy order that fits the device (greedy EOWQS, else the greedy
+    OWQS sweep; EOWQS runs, complex64, all-zero branch)."""
     rows = []
+    ntimed = 0
     for h in handles:
         k = float(max(1, h.nout))
         w = (k, k, 0.5, k)
         _, g = h.reorder(mode="eowqs", sweep=sweep, weights=w)
         _, l = h.reorder(mode="eowqs", sweep=sweep, weights=w, model=model)
-        rows.append({"n": h.nin, "K": h.K, "greedy_peak": l["greedy_peak_live"],
-                     "greedy_updates": l["greedy_amp_updates"], "learned_peak": l["learned_peak_live"],
-                     "learned_updates": l["learned_amp_updates"], "accepted": l["learned_accepted"]})
+        row = {"n": h.nin, "K": h.K, "greedy_peak": l["greedy_peak_live"],
+               "greedy_updates": l["greedy_amp_updates"], "learned_peak": l["learned_peak_live"],
+               "learned_updates": l["learned_amp_updates"], "accepted": l["learned_accepted"]}
+        if ntimed < timed and h.nin <= timed_width and l["peak_live"] <= 24:
+            row["kept_seconds"] = gpu_seconds(h)
+            best = None
+            for mode, sw in (("eowqs", sweep), ("owqs", True)):
+                _, gi = h.reorder(mode=mode, sweep=sw, weights=w)
+                if gi["peak_live"] <= 24:
+                    t = gpu_seconds(h)
+                    if best is None or t < best[0]:
+                        best = (t, mode, gi["peak_live"])
+            if best is not None:
+                row["greedy_seconds"], row["greedy_timed_mode"], row["greedy_timed_peak"] = best
+            ntimed += 1
+        rows.append(row)
     return rows
 
 
@@ -83,7 +164,17 @@ def summary(rows):
     exact = [r for r in rows if r["greedy_updates"] < SATURATED]
     ratio = (float(np.exp(np.mean([np.log(r["greedy_updates"] / r["learned_updates"]) for r in exact])))
              if exact else None)
+    tr = [r for r in rows if "greedy_seconds" in r]
+    timing = None
+    if tr:
+        timing = {"patterns": len(tr),
+                  "geomean_greedy_over_kept_seconds": float(np.exp(np.mean(
+                      [np.log(r["greedy_seconds"] / r["kept_seconds"]) for r in tr]))),
+                  "kept_seconds_total": float(sum(r["kept_seconds"] for r in tr)),
+                  "greedy_seconds_total": float(sum(r["greedy_seconds"] for r in tr)),
+                  "greedy_modes": {m: sum(r["greedy_timed_mode"] == m for r in tr) for m in ("eowqs", "owqs")}}
     return {"patterns": len(rows), "accepted": acc, "mean_greedy_peak_live": gp, "mean_learned_peak_live": lp,
+            "gpu_time": timing,
             "max_greedy_peak_live": max(r["greedy_peak"] for r in rows),
             "max_learned_peak_live": max(r["learned_peak"] for r in rows),
             "greedy_updates_saturated": len(rows) - len(exact),
@@ -109,6 +200,8 @@ def main(argv=None):
     ap.add_argument("--batch-steps", type=int, default=2048)
     ap.add_argument("--eval-sweep", action="store_true", help="judge with the full Section 5 sweep")
     ap.add_argument("--out", default=DEFAULT_OUT)
+    ap.add_argument("--timed", type=int, default=64, help="training patterns labelled by GPU timings")
+    ap.add_argument("--timed-eval", type=int, default=48, help="held-out patterns whose kept order is GPU-timed")
     ap.add_argument("--eval-only", action="store_true",
                     help="re-evaluate the weights already in --out on the held-out set and rewrite its summary")
     a = ap.parse_args(argv)
@@ -123,7 +216,7 @@ def main(argv=None):
     if a.eval_only:
         res = json.load(open(a.out))
         model = owqs.Model(weights=np.array(res["params"], dtype=np.float32))
-        rows = evaluate(handles(a.heldout, 1_000_000), model, a.eval_sweep)
+        rows = evaluate(handles(a.heldout, 1_000_000), model, a.eval_sweep, timed=a.timed_eval)
         res["heldout"] = summary(rows)
         res.setdefault("seconds", {})["eval"] = time.time() - t0
         with open(a.out, "w") as f:
@@ -131,7 +224,7 @@ def main(argv=None):
         print(json.dumps({k: v for k, v in res.items() if k != "params"}))
         return
 
-    X, first, target = build_dataset(handles(a.train, 0), a.cands, seed=4)
+    (X, first, target), tstats = build_dataset(handles(a.train, 0), a.cands, seed=4, timed=a.timed)
     t_data = time.time() - t0
     Xd = torch.from_numpy(X).cuda()
     Fd = torch.from_numpy(first.astype(np.int32)).cuda()
@@ -142,13 +235,17 @@ def main(argv=None):
     torch.cuda.synchronize()
     t_train = time.time() - t1
     t2 = time.time()
-    rows = evaluate(handles(a.heldout, 1_000_000), model, a.eval_sweep)
+    rows = evaluate(handles(a.heldout, 1_000_000), model, a.eval_sweep, timed=a.timed_eval)
     t_eval = time.time() - t2
     res = {"params": [float(x) for x in model.weights()],
            "trained_on": {"patterns": a.train, "widths": [a.wmin, a.wmax], "depths": [a.dmin, a.dmax],
                           "candidates_per_step": a.cands, "rows": int(X.shape[0]), "steps": int(len(target)),
                           "epochs": a.epochs, "lr": a.lr, "batch_steps": a.batch_steps,
-                          "epoch_losses": [float(x) for x in losses]},
+                          "epoch_losses": [float(x) for x in losses],
+                          "gpu_timed_targets": {"patterns": tstats["timed"], "measured_equals_modelled": tstats["agree"],
+                                                "geomean_modelled_over_measured_seconds": float(np.exp(np.mean(
+                                                    np.log(tstats["modelled_over_measured"]))))
+                                                if tstats["modelled_over_measured"] else None}},
            "heldout": summary(rows),
            "seconds": {"data": t_data, "train": t_train, "eval": t_eval}}
     with open(a.out, "w") as f:
