@@ -59,6 +59,10 @@ FP64_PEAK_TFLOPS = 1.25
 # FP64 flops per output amplitude of the complex128 pass: complex multiply-add
 # (2 DMUL + 4 DFMA = 10 flops) and the squared-norm sum (DMUL + DFMA + DADD = 4)
 FP64_FLOPS_PER_OUTPUT = 14
+# inside a pass group: per butterfly (two outputs) the complex product
+# (2 DMUL + 2 DFMA = 6 flops), two amplitude updates (4 DFMA = 8) and the
+# squared norms (4 DFMA = 8): 11 flops per output
+FP64_FLOPS_PER_GROUP_OUTPUT = 11
 
 
 def parse_args(argv=None):
@@ -537,9 +541,14 @@ def run_owqs(args):
         common = {"kernel": owqs.KERNEL_KIND[dom], "launches": int(sel.sum()), "share_of_step": share,
                   "bytes_per_launch": float(by[sel].mean()), "avg_launch_ms": float(ms[sel].mean())}
         if dtype == "c128":
-            # FP64-bound on GB300: every pass here reads and writes 2^n amplitudes
-            outputs = float(by[sel].sum()) / 32.0
-            achieved = outputs * FP64_FLOPS_PER_OUTPUT / secs / 1e12
+            # FP64-bound on GB300.  A launch of k measurements on 2^n amplitudes
+            # (in and out) produces k 2^n outputs: FP64 flops per output are
+            # FP64_FLOPS_PER_OUTPUT for a single pass and FP64_FLOPS_PER_GROUP_OUTPUT
+            # inside a pass group (scales and signs carried, not multiplied)
+            nm = h.profile_meas[sel].astype(np.float64)
+            outputs = by[sel] / 32.0 * nm
+            fpo = FP64_FLOPS_PER_GROUP_OUTPUT if owqs.KERNEL_KIND[dom] == "group_pass" else FP64_FLOPS_PER_OUTPUT
+            achieved = float(outputs.sum()) * fpo / secs / 1e12
             return dict({"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get((kernel_source_hash(), dtype)),
                          "hbm_gbs": float(by[sel].sum()) / secs / 1e9,

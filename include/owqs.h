@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define OWQS_ABI_VERSION 1
+#define OWQS_ABI_VERSION 2
 
 typedef enum {
   OWQS_OK = 0,
@@ -418,13 +418,16 @@ owqs_status owqs_run_static(owqs_pattern* p, const owqs_run_opts* opts, const vo
 
 /* Per-kernel timing of one run (instrumentation).  Runs the same schedule
  * without a graph, with a CUDA event pair around every launch on opts->stream,
- * and fills ms[i] (i < *nlaunch, at most cap) with each launch's duration,
- * bytes[i] with its algorithmic bytes (amplitudes read + written) and kind[i]
- * with 0 = fast pass kernel, 1 = generic pass kernel, 2 = final kernel,
- * 3 = norm kernel.  Device IO only; the forced or zero policy.             */
+ * and fills, for launch i (i < *nlaunch, at most cap): ms[i] its duration,
+ * bytes[i] its algorithmic bytes (amplitudes read + written), kind[i] its
+ * kernel (0 register-tiled pass, 1 generic pass, 2 final pass, 3 norm,
+ * 4 outcome probabilities, 5 bulk-copy pass, 7 device-drawn outcome, 8 pass
+ * group, 9 factor join) and, when nmeas is not NULL, nmeas[i] the number of
+ * measurements it performs (1 for a measure pass, k for a group of k, 0
+ * otherwise).  Device IO only; the forced or zero policy.                  */
 owqs_status owqs_profile_run(owqs_pattern* p, const owqs_run_opts* opts, const void* psi_in,
                              void* psi_out, const uint8_t* outcomes, float* ms, double* bytes,
-                             uint32_t* kind, uint32_t cap, uint32_t* nlaunch);
+                             uint32_t* kind, uint32_t* nmeas, uint32_t cap, uint32_t* nlaunch);
 
 /* Bit position of every qubit in the live array after pass `pass` of the
  * active order (-1 if the qubit is not live), for pass = 0 .. K (pass K is

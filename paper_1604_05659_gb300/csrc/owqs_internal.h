@@ -175,6 +175,7 @@ constexpr long long kWaitLimitCycles = 4000000000ll;
 
 struct LaunchPlan {
   int kind = KK_GENERIC;
+  int meas = 0;          // measurements the launch performs (1 for a measure pass, k for a group)
   int variant = 0;       // fast: measured-bit case (b < lg: b; lg: middle bit; lg+1: new qubit)
   int lg = 2;            // fast: log2 of consecutive outputs per thread tile
   int hint = 0;          // fast: 1 = streaming (evict-first) loads and stores
@@ -216,9 +217,10 @@ int max_grid();               // grid cap for grid-stride kernels
 // (-1)^(par(g & ar) ^ p_slot), and the element's sign collects
 // c0 ^ par(f & zfree); the new mask is zr ^ (p without the measured slot).
 // The store multiplies by E and fin[g] = D_final(g) * product of scales.
-// A tile is 2^(12-M) consecutive free indices (32 KB of input).  Register
+// A tile is 2^(T-M) consecutive free indices (32 KB of input; T = 12 for
+// complex64, 11 for complex128).  Register
 // inputs with input bit below 12 - M + (the number of such bits) are "low":
-// they lie inside the tile's contiguous input block of 2^(12-M+nlow)
+// they lie inside the tile's contiguous input block of 2^(T-M+nlow)
 // amplitudes; the others are "high" and select one of 2^(M-nlow) such
 // blocks (runoff).  Configuration c of the register is read at smem offset
 // cbase[c] + spread(e), spread inserting zeros at the low register bits
@@ -237,6 +239,7 @@ struct GroupPass {
   double scale, wre, wim;   // scale and (-1)^s e^{-i theta}
   float ct[1 << kGroupRegMax];  // +-1 per output configuration
   float fwr, fwi;           // (-1)^s e^{-i theta} in FP32
+  double ctd[1 << kGroupRegMax];  // ct in FP64 (complex128 groups)
 };
 struct GroupParams {
   const void* in;
@@ -255,6 +258,7 @@ struct GroupParams {
   uint32_t cbase[1 << kGroupRegMax];   // smem offset of configuration c: run * runlen + low bits
   uint64_t outoff[1 << kGroupRegMax];
   float fin[1 << kGroupRegMax];
+  double find[1 << kGroupRegMax];  // fin in FP64 (complex128 groups)
   double nscale[kGroupMax];
   int norm_in, norm_out;
   double thresh;
@@ -263,7 +267,7 @@ struct GroupParams {
 };
 // longest group starting at passes[i] (0 or 1 if none), planned into G
 int plan_group(const std::vector<PassDesc>& passes, size_t i, int dtype, GroupParams& G, LaunchPlan& L);
-cudaError_t launch_group(const GroupParams& G, cudaStream_t s);
+cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s);
 int group_enabled();  // OWQS_GROUP=0 turns group fusion off
 
 

@@ -158,6 +158,7 @@ class Runner {
     it.P.norm_in = prev_slot_;
     it.P.norm_out = mode_ == OWQS_MODE_OWQS ? pass_i_ + 1 : -1;
     it.P.w1dev = w1dev_;
+    it.L.meas = 1;
     issue(it);
     cur_in_ = it.P.out;
     prev_slot_ = it.P.norm_out;
@@ -190,6 +191,7 @@ class Runner {
     it.type = 4;
     it.G = G;
     it.L = L;
+    it.L.meas = G.k;
     it.G.norms = rc_.norms;
     it.G.partials = rc_.partials;
     it.G.counter = rc_.counter;
@@ -289,7 +291,7 @@ class Runner {
     if (it.type == 5)
       e = launch_kron(it.Kp, dtype_, s);
     else if (it.type == 4)
-      e = launch_group(it.G, s);
+      e = launch_group(it.G, dtype_, s);
     else if (it.type == 3)
       e = launch_decide(it.D, s);
     else if (it.type == 1)
@@ -697,7 +699,8 @@ static owqs_status sample_on_device(Pattern& p, const owqs_run_opts* o, RunCache
 static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
                             uint8_t* outcomes, double* probs, float* prof_ms, double* prof_bytes,
                             uint32_t* prof_kind, uint32_t prof_cap, uint32_t* prof_n, int vdiag = 0,
-                            double* frob2 = nullptr, const ProductInput* prod = nullptr) {
+                            double* frob2 = nullptr, const ProductInput* prod = nullptr,
+                            uint32_t* prof_meas = nullptr) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(o ? o->stream : nullptr);
   RunCache* rc = nullptr;
   Prepared pr;
@@ -801,6 +804,7 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
         prof_ms[i] = ms;
         if (prof_bytes) prof_bytes[i] = R.items[i].L.bytes;
         if (prof_kind) prof_kind[i] = (uint32_t)R.items[i].L.kind;
+        if (prof_meas) prof_meas[i] = (uint32_t)R.items[i].L.meas;
       }
       if (prof_n) *prof_n = (uint32_t)R.items.size();
       for (auto& x : ev) cudaEventDestroy(x);
@@ -952,8 +956,8 @@ owqs_status owqs_unitary(owqs_pattern* h, const owqs_run_opts* o, const uint8_t*
 }
 
 owqs_status owqs_profile_run(owqs_pattern* h, const owqs_run_opts* o, const void* psi_in, void* psi_out,
-                             const uint8_t* outcomes, float* ms, double* bytes, uint32_t* kind, uint32_t cap,
-                             uint32_t* nlaunch) {
+                             const uint8_t* outcomes, float* ms, double* bytes, uint32_t* kind, uint32_t* nmeas,
+                             uint32_t cap, uint32_t* nlaunch) {
   clear_error();
   if (!h || !o || !ms || !nlaunch) return set_error(OWQS_ERR_ARG, "NULL argument");
   if (o->io != OWQS_IO_DEVICE) return set_error(OWQS_ERR_ARG, "profiling takes device vectors");
@@ -962,7 +966,7 @@ owqs_status owqs_profile_run(owqs_pattern* h, const owqs_run_opts* o, const void
   std::vector<uint8_t> oc;
   if (outcomes) oc.assign(outcomes, outcomes + h->p.meas_qubit.size());
   return run_impl(h->p, o, psi_in, psi_out, oc.empty() ? nullptr : oc.data(), nullptr, ms, bytes, kind, cap,
-                  nlaunch);
+                  nlaunch, 0, nullptr, nullptr, nmeas);
 }
 
 owqs_status owqs_get_index_map(const owqs_pattern* h, uint32_t pass, int32_t* bit_of_qubit) {

@@ -294,9 +294,10 @@ int group_enabled() {
 // bit while scanning, its free index when planning) or a register slot /
 // prepared qubit (code < 0).
 int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupParams& G, LaunchPlan& L) {
-  if (dtype != OWQS_C64 || i0 >= passes.size() || passes[i0].kind != 0) return 0;
+  if (i0 >= passes.size() || passes[i0].kind != 0) return 0;
+  const int tb = dtype == OWQS_C64 ? 12 : 11;  // log2 of a 32 KB stage in amplitudes
   const int n0 = passes[i0].n_in;
-  if (n0 < 12 || n0 > 62) return 0;
+  if (n0 < tb || n0 > 62) return 0;
   // scan: the longest valid prefix
   std::vector<int> live(n0);
   for (int x = 0; x < n0; ++x) live[x] = x;
@@ -314,7 +315,7 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupP
     }
     live.erase(live.begin() + d.b);
     live.push_back(-1);
-    const int k = (int)(i - i0) + 1, m = (int)regs.size(), lt = 12 - m;
+    const int k = (int)(i - i0) + 1, m = (int)regs.size(), lt = tb - m;
     if (k >= 2 && n0 - m >= lt) best_k = k;
   }
   if (best_k < 2) return 0;
@@ -334,7 +335,7 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupP
   std::memset(&G, 0, sizeof(G));
   G.k = best_k;
   G.m = m;
-  G.lt = 12 - m;
+  G.lt = tb - m;
   G.nfree = n0 - m;
   std::vector<int> slot_of_input(n0, -1), free_of(n0, -1);
   for (int q = 0; q < m; ++q) slot_of_input[regs[q]] = q, G.B[q] = regs[q];
@@ -405,8 +406,10 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupP
     P.wre = d.w1re;
     P.wim = d.w1im;
     const uint32_t ps = (pend >> s) & 1u;
-    for (int g = 0; g < (1 << kGroupRegMax); ++g)
+    for (int g = 0; g < (1 << kGroupRegMax); ++g) {
       P.ct[g] = ((__builtin_popcount(P.ar & (uint32_t)g) & 1u) ^ ps) ? -1.0f : 1.0f;
+      P.ctd[g] = P.ct[g];
+    }
     P.fwr = (float)d.w1re;
     P.fwi = (float)d.w1im;
     pend = P.zr ^ (pend & ~(1u << s));
@@ -425,11 +428,12 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupP
       if ((g >> t) & 1) off |= 1ull << l;
     }
     G.outoff[g] = off;
-    G.fin[g] = (float)(((__builtin_popcount(pend & (uint32_t)g) & 1u) ? -1.0 : 1.0) * prod);
+    G.find[g] = ((__builtin_popcount(pend & (uint32_t)g) & 1u) ? -1.0 : 1.0) * prod;
+    G.fin[g] = (float)G.find[g];
   }
   G.norm_in = G.norm_out = -1;
   L.kind = KK_GROUP;
-  L.bytes = (std::ldexp(1.0, n0) + std::ldexp(1.0, passes[i0 + best_k - 1].n_out)) * 8.0;
+  L.bytes = (std::ldexp(1.0, n0) + std::ldexp(1.0, passes[i0 + best_k - 1].n_out)) * (dtype == OWQS_C64 ? 8.0 : 16.0);
   L.grid = 1;
   return best_k;
 }

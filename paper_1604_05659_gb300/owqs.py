@@ -108,7 +108,7 @@ EXPORTS = {
                                   C.POINTER(C.c_uint8), C.POINTER(C.c_double)]),
     "owqs_profile_run": (C.c_int, [C.c_void_p, C.POINTER(owqs_run_opts), C.c_void_p, C.c_void_p,
                                    C.POINTER(C.c_uint8), C.POINTER(C.c_float), C.POINTER(C.c_double),
-                                   C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32)]),
+                                   C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32)]),
     "owqs_get_index_map": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_int32)]),
     "owqs_describe_passes": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_uint8), C.POINTER(owqs_pass_desc),
                                        C.c_uint32, C.POINTER(C.c_uint32)]),
@@ -409,14 +409,16 @@ class Handle:
         ms = (C.c_float * cap)()
         by = (C.c_double * cap)()
         kd = (C.c_uint32 * cap)()
+        nm = (C.c_uint32 * cap)()
         n = C.c_uint32()
         s = stream if stream is not None else torch.cuda.current_stream(dev)
         opts = owqs_run_opts(DTYPE[dtype], MODE[mode], POLICY[policy], 0, 0, C.c_void_p(s.cuda_stream), 0, 0)
         oc = _outcome_buf(outcomes, self.K)
         _check(library().owqs_profile_run(self._h, C.byref(opts),
                                           C.c_void_p(psi_in.data_ptr() if psi_in is not None else 0),
-                                          C.c_void_p(out.data_ptr()), oc, ms, by, kd, cap, C.byref(n)))
+                                          C.c_void_p(out.data_ptr()), oc, ms, by, kd, nm, cap, C.byref(n)))
         k = min(n.value, cap)
+        self.profile_meas = np.array(nm[:k])  # measurements per launch of the last profile
         return np.array(ms[:k]), np.array(by[:k]), np.array(kd[:k]), out
 
 

@@ -37,7 +37,7 @@ def test_exports_every_declared_symbol(owqs):
     exported = set(re.findall(r"\bT (owqs_[a-z_]+)\b", out))
     assert declared <= exported, declared - exported
     lib = owqs.library()
-    assert lib.owqs_abi_version() == 1
+    assert lib.owqs_abi_version() == 2
 
 
 def test_validation_errors(owqs):

@@ -316,20 +316,21 @@ def test_brickwork_full_size_properties(env):
     del d
 
 
-def test_pass_groups(env):
-    """Up to eight consecutive measure passes in one sweep (complex64): the
-    output and every per-measurement probability still match the oracle, in
-    both modes, from the virtual |+> input and from a random input; the
-    profile shows the group kernel ran and covered most measurements."""
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_pass_groups(env, dtype):
+    """Up to twelve consecutive measure passes in one sweep: the output and
+    every per-measurement probability still match the oracle, in both modes,
+    from the virtual |+> input and from a random input; the profile shows the
+    group kernel ran and covered most measurements."""
     torch, owqs = env
     rng = SplitMix64(105)
     for wl in (workloads.brickwork(14, 8), workloads.brickwork(13, 10), workloads.qft(12, with_input=False)):
         p = wl.pattern
         bits = rng.bits(p.K)
-        h, _ = _compare(env, p, None, bits, "c64", "owqs")
+        h, _ = _compare(env, p, None, bits, dtype, "owqs")
         psi = random_state(rng, len(p.inputs))
-        _compare(env, p, psi, bits, "c64", "owqs")
-        _compare(env, p, psi, bits, "c64", "eowqs")
-        ms, by, kd, _ = h.profile(None, dtype="c64", outcomes=bits)
+        _compare(env, p, psi, bits, dtype, "owqs")
+        _compare(env, p, psi, bits, dtype, "eowqs")
+        ms, by, kd, _ = h.profile(None, dtype=dtype, outcomes=bits)
         assert (kd == 8).sum() >= 5, sorted(set(kd.tolist()))
         assert len(kd) < 0.6 * p.K, (len(kd), p.K)
