@@ -46,14 +46,13 @@ def workload_name(rows: int, cols: int) -> str:
 FALLBACK_HBM_GBS = 6800.0
 # ncu DRAM bytes (read + write) per launch of the dominant kernel, keyed by the
 # sha256 prefix of the kernel source they were measured on (a changed kernel
-# reports null).  c64: k_group<3> on the full brickwork workload (2^28
-# complex64 amplitudes in and out per launch), mean of three launches
-# (2147.8 MB read + 2099.1 MB written; profiles/k_group_c64_brickwork28x40_dram.md).
-# c128: k_fast<double,2,2,0> on the same workload (2^28 complex128 amplitudes
-# in and out), mean of three launches (4309.3 MB read + 4252.2 MB written;
-# profiles/k_fast_c128_brickwork26x4.md).
-NCU_TRAFFIC = {("8f93290039fc8797", "c64"): (2147747840 + 2101385728 + 2147797504 + 2097540608 + 2147803392 + 2098328064) / 3.0,
-               ("ae8e117312fcecbf", "c128"): (4309097984 + 4254342656 + 4308605440 + 4251319040 + 4310056448 + 4250811904) / 3.0}
+# reports null).  Both are pass groups on the full brickwork workload, mean of
+# three launches: c64 k_group<3> (2^28 complex64 amplitudes in and out;
+# 2148.1 MB read + 2098.8 MB written) and c128 k_group64<3> (2^28 complex128;
+# 4299.1 MB read + 4247.6 MB written).  profiles/k_group_c64_brickwork28x40_dram.md,
+# profiles/k_group64_c128_brickwork26x8.md.
+NCU_TRAFFIC = {("de93c85d9c9e343a", "c64"): (2147829760 + 2100831488 + 2148685056 + 2097812736 + 2147732480 + 2097788672) / 3.0,
+               ("de93c85d9c9e343a", "c128"): (4298769152 + 4249655808 + 4298641664 + 4246542336 + 4299995648 + 4246735872) / 3.0}
 # nominal GB300 FP64 rate (no measured FP64 peak exists for this machine)
 FP64_PEAK_TFLOPS = 1.25
 # FP64 flops per output amplitude of the complex128 pass: complex multiply-add
