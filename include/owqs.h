@@ -416,6 +416,16 @@ owqs_status owqs_run_batch(const owqs_batch_item* items, uint32_t n, const owqs_
 owqs_status owqs_run_static(owqs_pattern* p, const owqs_run_opts* opts, const void* psi_in,
                             void* psi_out, uint8_t* outcomes, double* probs);
 
+/* The launches owqs_run would make (host only, no GPU needed): for launch i
+ * (i < *nlaunch, at most cap), kind[i] as in owqs_profile_run, first_meas[i]
+ * the index (execution order) of its first measurement and nmeas[i] the
+ * number of measurements it performs.  real_input: the run reads an input
+ * vector (0: the virtual |+> input; the first measurement then runs alone).
+ * outcomes: forced outcome bits (load order) or NULL for all zero. */
+owqs_status owqs_describe_launches(const owqs_pattern* p, uint32_t dtype, uint32_t mode, uint32_t real_input,
+                                   const uint8_t* outcomes, uint32_t* kind, uint32_t* first_meas, uint32_t* nmeas,
+                                   uint32_t cap, uint32_t* nlaunch);
+
 /* Per-kernel timing of one run (instrumentation).  Runs the same schedule
  * without a graph, with a CUDA event pair around every launch on opts->stream,
  * and fills, for launch i (i < *nlaunch, at most cap): ms[i] its duration,

@@ -242,11 +242,8 @@ class Runner {
     prev_slot_ = -1;  // the joined array is normalised
   }
 
-  // longest pass group starting at passes[i] that can run as one sweep (0 if none)
-  int group_at(const std::vector<PassDesc>& passes, size_t i, GroupParams& G, LaunchPlan& L) const {
-    if (cur_in_ == nullptr || !group_enabled()) return 0;
-    return plan_group(passes, i, dtype_, G, L);
-  }
+  // the array the next launch reads is materialised (not the virtual |+> input)
+  bool real_input() const { return cur_in_ != nullptr; }
 
   // both outcome probabilities of the next measurement into slots
   // prob_slot(i), prob_slot(i)+1 (sampled outcomes)
@@ -405,6 +402,26 @@ struct ProductInput {
   std::vector<std::vector<uint32_t>> qubits;
   std::vector<const void*> vecs;
 };
+
+// What the launch for passes[i] is: a factor join, the final pass, a group
+// of k measure passes (k >= 2; needs a materialised input array) or a single
+// measure pass.  The run driver and owqs_describe_launches both use it.
+enum { LAUNCH_SINGLE = 0, LAUNCH_GROUP = 1, LAUNCH_FINAL = 2, LAUNCH_JOIN = 3 };
+static int decide_launch(const std::vector<PassDesc>& passes, size_t i, int dtype, bool real_input, GroupParams& G,
+                         LaunchPlan& GL, int& k) {
+  const PassDesc& d = passes[i];
+  k = 1;
+  if (d.kind == 2) return LAUNCH_JOIN;
+  if (d.kind != 0) return LAUNCH_FINAL;
+  if (real_input && group_enabled()) {
+    const int g = plan_group(passes, i, dtype, G, GL);
+    if (g >= 2) {
+      k = g;
+      return LAUNCH_GROUP;
+    }
+  }
+  return LAUNCH_SINGLE;
+}
 
 struct Prepared {
   std::vector<PassDesc> passes;
@@ -768,15 +785,19 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
       GroupParams G;
       LaunchPlan GL;
       int gk = 0;
-      if (d.kind == 2) {
-        R.join(d, prod->vecs[d.factor], 3 * K + 8 + d.factor);
-      } else if (d.kind != 0) {
-        R.final_pass(d);
-      } else if ((gk = R.group_at(pr.passes, i, G, GL)) >= 2) {
-        R.measure_group(G, GL);
-        i += (size_t)gk - 1;
-      } else {
-        R.measure(d);
+      switch (decide_launch(pr.passes, i, o->dtype, R.real_input(), G, GL, gk)) {
+        case LAUNCH_JOIN:
+          R.join(d, prod->vecs[d.factor], 3 * K + 8 + d.factor);
+          break;
+        case LAUNCH_FINAL:
+          R.final_pass(d);
+          break;
+        case LAUNCH_GROUP:
+          R.measure_group(G, GL);
+          i += (size_t)gk - 1;
+          break;
+        default:
+          R.measure(d);
       }
     }
     in_group = R.in_group;
@@ -967,6 +988,57 @@ owqs_status owqs_profile_run(owqs_pattern* h, const owqs_run_opts* o, const void
   if (outcomes) oc.assign(outcomes, outcomes + h->p.meas_qubit.size());
   return run_impl(h->p, o, psi_in, psi_out, oc.empty() ? nullptr : oc.data(), nullptr, ms, bytes, kind, cap,
                   nlaunch, 0, nullptr, nullptr, nmeas);
+}
+
+owqs_status owqs_describe_launches(const owqs_pattern* h, uint32_t dtype, uint32_t mode, uint32_t real_input,
+                                   const uint8_t* outcomes, uint32_t* kind, uint32_t* first_meas, uint32_t* nmeas,
+                                   uint32_t cap, uint32_t* nlaunch) {
+  clear_error();
+  if (!h || !nlaunch) return set_error(OWQS_ERR_ARG, "NULL argument");
+  if (dtype > OWQS_C128 || mode > OWQS_MODE_EOWQS) return set_error(OWQS_ERR_ARG, "bad option value");
+  FixedSource src(h->p, outcomes);
+  std::vector<PassDesc> passes;
+  owqs_status st = compile_schedule(h->p, (int)mode, src, passes);
+  if (st != OWQS_OK) return st;
+  uint32_t n = 0, mi = 0;
+  auto put = [&](uint32_t kd, uint32_t first, uint32_t m) {
+    if (n < cap) {
+      if (kind) kind[n] = kd;
+      if (first_meas) first_meas[n] = first;
+      if (nmeas) nmeas[n] = m;
+    }
+    ++n;
+  };
+  bool real = real_input != 0;
+  if (real) put(KK_NORM, 0, 0);  // the input norm (OWQS divides by it, EOWQS checks the output against it)
+  for (size_t i = 0; i < passes.size(); ++i) {
+    GroupParams G;
+    LaunchPlan GL;
+    int k = 0;
+    switch (decide_launch(passes, i, (int)dtype, real, G, GL, k)) {
+      case LAUNCH_GROUP:
+        put(KK_GROUP, mi, (uint32_t)k);
+        mi += (uint32_t)k;
+        i += (size_t)k - 1;
+        break;
+      case LAUNCH_FINAL:
+        put(KK_FINAL, mi, 0);
+        break;
+      case LAUNCH_JOIN:
+        put(KK_KRON, mi, 0);
+        break;
+      default: {
+        PassParams P;
+        LaunchPlan L;
+        plan_pass(passes[i], (int)dtype, !real, P, L);
+        put((uint32_t)L.kind, mi, 1);
+        ++mi;
+      }
+    }
+    real = true;
+  }
+  *nlaunch = n;
+  return OWQS_OK;
 }
 
 owqs_status owqs_get_index_map(const owqs_pattern* h, uint32_t pass, int32_t* bit_of_qubit) {

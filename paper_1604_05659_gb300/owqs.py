@@ -126,6 +126,9 @@ EXPORTS = {
     "owqs_find_flow": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_int32),
                                  C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32)]),
     "owqs_test_wait_timeout": (C.c_int, [C.c_uint32, C.c_uint64]),
+    "owqs_describe_launches": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.POINTER(C.c_uint8),
+                                         C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                         C.c_uint32, C.POINTER(C.c_uint32)]),
     "owqs_run_product": (C.c_int, [C.c_void_p, C.POINTER(owqs_run_opts), C.c_uint32, C.POINTER(C.c_uint32),
                                    C.POINTER(C.c_uint32), C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(C.c_uint8),
                                    C.POINTER(C.c_double)]),
@@ -261,6 +264,19 @@ class Handle:
         outs = set(self.pattern.outputs)
         g = {v: list(members[first[v]:first[v + 1]]) for v in range(n) if v not in outs}
         return list(layer), g
+
+    def describe_launches(self, outcomes=None, *, dtype: str = "c64", mode: str = "owqs", real_input: bool = False):
+        """The launches a run would make (host only): list of (kind name,
+        first measurement, measurements)."""
+        cap = 2 * self.K + 16
+        kd = (C.c_uint32 * cap)()
+        fm = (C.c_uint32 * cap)()
+        nm = (C.c_uint32 * cap)()
+        n = C.c_uint32()
+        oc = _outcome_buf(outcomes, self.K) if outcomes is not None else None
+        _check(library().owqs_describe_launches(self._h, DTYPE[dtype], MODE[mode], int(real_input), oc, kd, fm, nm,
+                                                cap, C.byref(n)))
+        return [(KERNEL_KIND[kd[i]], fm[i], nm[i]) for i in range(min(n.value, cap))]
 
     def index_map(self, pass_index: int):
         out = (C.c_int32 * self.pattern.nqubits)()

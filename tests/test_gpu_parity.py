@@ -334,3 +334,7 @@ def test_pass_groups(env, dtype):
         ms, by, kd, _ = h.profile(None, dtype=dtype, outcomes=bits)
         assert (kd == 8).sum() >= 5, sorted(set(kd.tolist()))
         assert len(kd) < 0.6 * p.K, (len(kd), p.K)
+        # the run launched exactly what the host planner describes
+        plan = h.describe_launches(bits, dtype=dtype)
+        assert [owqs.KERNEL_KIND[int(k)] for k in kd] == [x[0] for x in plan]
+        assert list(h.profile_meas) == [x[2] for x in plan]

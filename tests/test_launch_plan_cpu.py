@@ -1,0 +1,73 @@
+"""Launch planning on the host (owqs_describe_launches, no GPU): which
+measurements run as pass groups, which as single passes, in what order.
+These are the decisions the run driver makes; the GPU tests check that a
+profiled run launches exactly these kernels."""
+import pytest
+
+from owqs_inputs import workloads
+from owqs_inputs.rng import SplitMix64
+
+
+@pytest.fixture(scope="module")
+def owqs():
+    from paper_1604_05659_gb300 import build, owqs as mod
+    build.ensure_built()
+    mod.library()
+    return mod
+
+
+def _check_cover(launches, K):
+    """Every measurement once, in order; groups of 2..12 measurements."""
+    at = 0
+    for kind, first, n in launches:
+        if n:
+            assert first == at, (kind, first, at)
+            at += n
+        if kind == "group_pass":
+            assert 2 <= n <= 12
+        elif kind in ("fast_pass", "tma_pass", "generic_pass"):
+            assert n == 1
+        else:
+            assert n == 0
+    assert at == K
+    assert launches[-1][0] == "final"
+
+
+def test_brickwork_full_size_plan(owqs):
+    wl = workloads.brickwork(28, 40)
+    h = owqs.load(wl.pattern)
+    h.reorder()
+    for dtype in ("c64", "c128"):
+        lv = h.describe_launches(wl.outcomes, dtype=dtype)        # virtual |+> input
+        _check_cover(lv, wl.pattern.K)
+        groups = [x for x in lv if x[0] == "group_pass"]
+        assert lv[0] == ("generic_pass", 0, 1)                   # the first measurement reads the virtual input
+        assert len(lv) <= 120 and sum(x[2] for x in groups) >= 1085, (dtype, len(lv))
+        lr = h.describe_launches(wl.outcomes, dtype=dtype, real_input=True)
+        assert lr[0] == ("norm", 0, 0)
+        _check_cover(lr, wl.pattern.K)
+
+
+def test_qft_plan_and_small_arrays(owqs):
+    wl = workloads.qft(24, with_input=False)
+    h = owqs.load(wl.pattern)
+    h.reorder()
+    lr = h.describe_launches(wl.outcomes, real_input=True)
+    _check_cover(lr, wl.pattern.K)
+    assert len(lr) <= 260, len(lr)
+    # live arrays narrower than one 32 KB tile never group
+    small = workloads.small_random()
+    hs = owqs.load(small.pattern)
+    hs.reorder()
+    ls = hs.describe_launches(small.outcomes, real_input=True)
+    _check_cover(ls, small.pattern.K)
+    assert not any(k == "group_pass" for k, _, _ in ls)
+
+
+def test_random_patterns_cover_every_measurement(owqs):
+    for wl in workloads.random_batch(12, 10, 16, 5, 20, config_index=4, start=50):
+        h = owqs.load(wl.pattern)
+        h.reorder()
+        for dtype in ("c64", "c128"):
+            for real in (False, True):
+                _check_cover(h.describe_launches(wl.outcomes, dtype=dtype, real_input=real), wl.pattern.K)
