@@ -372,7 +372,8 @@ typedef struct {
   uint32_t dtype;           /* OWQS_C64 or OWQS_C128                                 */
   uint32_t column_block;    /* columns per task (power of two); 0 = tuned            */
   void* stream;             /* cudaStream_t; NULL = legacy default stream            */
-  uint32_t use_graph;       /* for the items run through the pass kernels            */
+  uint32_t use_graph;       /* 1: the persistent launch and the items run through the
+                               pass kernels are replayed from CUDA graphs            */
   uint32_t pad_;
   double* overlaps;         /* optional host array of 4n doubles: for items with
                                ref >= 0, Re and Im of <out_ref|out>, |out|^2 and

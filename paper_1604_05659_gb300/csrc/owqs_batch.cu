@@ -210,6 +210,11 @@ struct DevBuf {
 struct BatchCache {
   int device = -1;
   DevBuf items, passes, qs, perms, tasks, counter, ov_ptrs, ov_res;
+  // the persistent launch (counter reset + kernel) as a CUDA graph, replayed
+  // while the launch shape and the buffers stay the same
+  std::string gkey;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap = nullptr;
   std::map<std::string, int> tuned;  // signature -> shared-memory budget (bytes per CTA)
 };
 
@@ -367,7 +372,8 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
   };
 
   auto kernel = dtype == OWQS_C64 ? (const void*)k_batch<float> : (const void*)k_batch<double>;
-  auto launch_batch = [&](size_t budget, const std::vector<BTask>& tasks, uint32_t cap) -> owqs_status {
+  auto launch_batch = [&](size_t budget, const std::vector<BTask>& tasks, uint32_t cap,
+                          bool graph) -> owqs_status {
     if (tasks.empty()) return OWQS_OK;
     owqs_status st = upload(bc.items, bitems.data(), bitems.size() * sizeof(BItem), s, "batch items");
     if (st == OWQS_OK) st = upload(bc.passes, bpasses.data(), bpasses.size() * sizeof(BPass), s, "batch passes");
@@ -388,21 +394,65 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
     e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, smem);
     if (e2 != cudaSuccess) return bfail(e2, "batch occupancy");
     const int grid = std::max(1, std::min<int>(std::max(1, per_sm) * (max_grid() / 8), (int)tasks.size()));
-    e2 = cudaMemsetAsync(bc.counter.p, 0, sizeof(unsigned int), s);
-    if (e2 != cudaSuccess) return bfail(e2, "batch counter reset");
     auto* ip = static_cast<const BItem*>(bc.items.p);
     auto* pp = static_cast<const BPass*>(bc.passes.p);
     auto* qp = static_cast<const BQ*>(bc.qs.p);
     auto* mp = static_cast<const int32_t*>(bc.perms.p);
     auto* tp = static_cast<const BTask*>(bc.tasks.p);
     auto* cp = static_cast<unsigned int*>(bc.counter.p);
-    if (dtype == OWQS_C64)
-      k_batch<float><<<grid, kBlock, smem, s>>>(ip, pp, qp, mp, tp, (uint32_t)tasks.size(), cp, cap);
-    else
-      k_batch<double><<<grid, kBlock, smem, s>>>(ip, pp, qp, mp, tp, (uint32_t)tasks.size(), cp, cap);
-    e2 = cudaGetLastError();
+    const uint32_t nt = (uint32_t)tasks.size();
+    auto enqueue = [&](cudaStream_t st) -> cudaError_t {
+      cudaError_t e3 = cudaMemsetAsync(cp, 0, sizeof(unsigned int), st);
+      if (e3 != cudaSuccess) return e3;
+      if (dtype == OWQS_C64)
+        k_batch<float><<<grid, kBlock, smem, st>>>(ip, pp, qp, mp, tp, nt, cp, cap);
+      else
+        k_batch<double><<<grid, kBlock, smem, st>>>(ip, pp, qp, mp, tp, nt, cp, cap);
+      return cudaGetLastError();
+    };
     (void)budget;
-    return e2 == cudaSuccess ? OWQS_OK : bfail(e2, "batch kernel launch");
+    if (!graph) {
+      e2 = enqueue(s);
+      return e2 == cudaSuccess ? OWQS_OK : bfail(e2, "batch kernel launch");
+    }
+    // one persistent launch under a captured graph
+    std::string key;
+    auto add = [&](const void* v, size_t nb) { key.append(reinterpret_cast<const char*>(v), nb); };
+    const void* ptrs[6] = {ip, pp, qp, mp, tp, cp};
+    add(&dtype, sizeof(dtype));
+    add(&grid, sizeof(grid));
+    add(&smem, sizeof(smem));
+    add(&nt, sizeof(nt));
+    add(&cap, sizeof(cap));
+    add(ptrs, sizeof(ptrs));
+    if (!bc.gexec || key != bc.gkey) {
+      if (bc.gexec) {
+        cudaGraphExecDestroy(bc.gexec);
+        bc.gexec = nullptr;
+      }
+      if (!bc.cap) {
+        e2 = cudaStreamCreateWithFlags(&bc.cap, cudaStreamNonBlocking);
+        if (e2 != cudaSuccess) return bfail(e2, "batch capture stream");
+      }
+      e2 = cudaStreamBeginCapture(bc.cap, cudaStreamCaptureModeThreadLocal);
+      if (e2 != cudaSuccess) return bfail(e2, "batch begin capture");
+      const cudaError_t el = enqueue(bc.cap);
+      cudaGraph_t g = nullptr;
+      e2 = cudaStreamEndCapture(bc.cap, &g);
+      if (el != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bfail(el != cudaSuccess ? el : e2, "batch capture");
+      }
+      e2 = cudaGraphInstantiate(&bc.gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e2 != cudaSuccess) {
+        bc.gexec = nullptr;
+        return bfail(e2, "batch graph instantiate");
+      }
+      bc.gkey = key;
+    }
+    e2 = cudaGraphLaunch(bc.gexec, s);
+    return e2 == cudaSuccess ? OWQS_OK : bfail(e2, "batch graph launch");
   };
 
   std::vector<BTask> tasks;
@@ -426,7 +476,7 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
         for (size_t bud : budgets) {
           make_tasks(bud, tasks, cap);
           cudaEventRecord(e0, s);
-          owqs_status st = launch_batch(bud, tasks, cap);
+          owqs_status st = launch_batch(bud, tasks, cap, false);  // timed without graph capture
           cudaEventRecord(e1, s);
           if (st != OWQS_OK) {
             cudaEventDestroy(e0);
@@ -449,7 +499,7 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
       }
     }
     make_tasks(budget, tasks, cap);
-    owqs_status st = launch_batch(budget, tasks, cap);
+    owqs_status st = launch_batch(budget, tasks, cap, o->use_graph != 0);
     if (st != OWQS_OK) return st;
     ++launches;
   }
