@@ -51,6 +51,31 @@ def circuit_unitary(nwires: int, gates) -> np.ndarray:
     return U
 
 
+def apply_circuit(nwires: int, gates, vec: np.ndarray) -> np.ndarray:
+    """The circuit applied to one state vector, gate by gate (first gate
+    first), without forming any 2^n x 2^n matrix: a J on wire w mixes the
+    amplitude pairs that differ in bit w with the 2x2 matrix; a CZ negates
+    the amplitudes whose two bits are 1.  For widths where the dense product
+    is too large."""
+    v = np.asarray(vec, dtype=np.complex128).copy()
+    idx = np.arange(1 << nwires)
+    for g in gates:
+        if g[0] == "J":
+            w = g[1]
+            m = J(g[2])
+            lo = idx[((idx >> w) & 1) == 0]
+            hi = lo | (1 << w)
+            a, b = v[lo].copy(), v[hi].copy()
+            v[lo] = m[0, 0] * a + m[0, 1] * b
+            v[hi] = m[1, 0] * a + m[1, 1] * b
+        elif g[0] == "CZ":
+            both = ((idx >> g[1]) & 1) & ((idx >> g[2]) & 1)
+            v[both == 1] *= -1
+        else:
+            raise ValueError(g[0])
+    return v
+
+
 def align_phase(ref: np.ndarray, x: np.ndarray) -> np.ndarray:
     """x multiplied by the unit phase that best aligns it with ref."""
     ov = np.vdot(x, ref)
