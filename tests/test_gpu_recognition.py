@@ -160,3 +160,34 @@ def test_batch_determinism_branches(env, dtype):
         re, im, nx, na = ov[i]
         assert abs((re * re + im * im) / (nx * na) - 1) <= tol, (i, ov[i])
         assert abs(nx - 1) <= tol and abs(na - 1) <= tol
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_batch_unitaries_full_widths_against_circuits(env, dtype):
+    """Recognition at the full widths of the batched configuration (11..14
+    logical qubits): eight sampled columns of each matrix equal the J/CZ
+    circuit applied to those basis vectors (the textbook reduction), up to
+    the branch's global phase, common to all columns."""
+    torch, owqs = env
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    items, meta = [], []
+    for i, n in enumerate((11, 12, 13, 14)):
+        rng = SplitMix64(600 + i)
+        gates = random_jcz_circuit(n, 12, rng, cz_per_layer=(n + 3) // 4)
+        p = circuit_to_pattern(n, gates, f"full{n}")
+        h = owqs.load(p)
+        h.reorder()
+        out = torch.empty(1 << (2 * n), dtype=tdt, device="cuda")
+        items.append({"handle": h, "outcomes": rng.bits(p.K), "psi_in": None, "out": out, "ref": -1})
+        meta.append((n, gates, rng))
+    owqs.run_batch(items, dtype=dtype)
+    tol = 1e-11 if dtype == "c128" else 2e-5
+    for it, (n, gates, rng) in zip(items, meta):
+        cols = sorted({rng.randint(1 << n) for _ in range(8)})
+        ref = np.stack([circuit.apply_circuit(n, gates, np.eye(1, 1 << n, c, dtype=np.complex128)[0]) for c in cols],
+                       axis=1)
+        # column c of the column-major matrix is the contiguous slice [c 2^n, (c+1) 2^n)
+        sub = np.stack([it["out"][c << n:(c + 1) << n].cpu().numpy().astype(np.complex128) for c in cols], axis=1)
+        ov = np.vdot(sub.reshape(-1), ref.reshape(-1))
+        assert np.max(np.abs(sub * (ov / abs(ov)) - ref)) <= tol, (n, dtype)
+
