@@ -51,8 +51,8 @@ FALLBACK_HBM_GBS = 6800.0
 # 2148.1 MB read + 2098.8 MB written) and c128 k_group64<3> (2^28 complex128;
 # 4299.1 MB read + 4247.6 MB written).  profiles/k_group_c64_brickwork28x40_dram.md,
 # profiles/k_group64_c128_brickwork26x8.md.
-NCU_TRAFFIC = {("de93c85d9c9e343a", "c64"): (2147829760 + 2100831488 + 2148685056 + 2097812736 + 2147732480 + 2097788672) / 3.0,
-               ("de93c85d9c9e343a", "c128"): (4298769152 + 4249655808 + 4298641664 + 4246542336 + 4299995648 + 4246735872) / 3.0}
+NCU_TRAFFIC = {("d1d48e887adff9c0", "c64"): (2147812352 + 2097959936 + 2147715584 + 2095019008 + 2147740160 + 2094754048) / 3.0,
+               ("d1d48e887adff9c0", "c128"): (4298868992 + 4249040640 + 4298602496 + 4246573568 + 4299443456 + 4246392320) / 3.0}
 # nominal GB300 FP64 rate (no measured FP64 peak exists for this machine)
 FP64_PEAK_TFLOPS = 1.25
 # FP64 flops per output amplitude of the complex128 pass: complex multiply-add

@@ -194,7 +194,7 @@ constexpr int kBlock = 256;
 int max_grid();               // grid cap for grid-stride kernels
 
 // A group of 2..kGroupMax consecutive measure passes run as one sweep
-// (complex64, TMA).  Every pass is in star form with no X mask and prepares
+// (bulk copies into shared memory).  Every pass is in star form with no X mask and prepares
 // exactly one qubit, and measures either an input qubit of the group's input
 // array or a qubit prepared earlier in the group.  Then a constant set of M
 // qubits (M = the input qubits the group measures, 1..kGroupRegMax) varies
@@ -217,9 +217,9 @@ int max_grid();               // grid cap for grid-stride kernels
 // (-1)^(par(g & ar) ^ p_slot), and the element's sign collects
 // c0 ^ par(f & zfree); the new mask is zr ^ (p without the measured slot).
 // The store multiplies by E and fin[g] = D_final(g) * product of scales.
-// A tile is 2^(T-M) consecutive free indices (32 KB of input; T = 12 for
-// complex64, 11 for complex128).  Register
-// inputs with input bit below 12 - M + (the number of such bits) are "low":
+// A tile is 2^(T-M) consecutive free indices (T = 9 for complex64: 4 KB of
+// input per warp; T = 11 for complex128: 32 KB per block).  Register
+// inputs with input bit below T - M + (the number of such bits) are "low":
 // they lie inside the tile's contiguous input block of 2^(T-M+nlow)
 // amplitudes; the others are "high" and select one of 2^(M-nlow) such
 // blocks (runoff).  Configuration c of the register is read at smem offset
@@ -234,7 +234,7 @@ struct GroupPass {
   int slot;                 // register slot measured, then refilled by the new qubit
   uint32_t c0, zb;
   uint32_t zr, ar;          // register parts of the sign masks (bit t = slot t)
-  uint32_t zlo, alo;        // zfree, afree within a tile (low 12 - M bits)
+  uint32_t zlo, alo;        // zfree, afree within a tile (low T - M bits)
   uint64_t zfree, afree;    // sign masks over the free index
   double scale, wre, wim;   // scale and (-1)^s e^{-i theta}
   float ct[1 << kGroupRegMax];  // +-1 per output configuration
@@ -248,11 +248,11 @@ struct GroupParams {
   double* partials;
   unsigned int* counter;
   unsigned int* errflag;
-  int k, m, lt;             // passes, register qubits, log2 tile (12 - m)
+  int k, m, lt;             // passes, register qubits, log2 tile (T - m)
   int nfree;                // free bits (input bits minus m)
   int B[kGroupRegMax];      // input bit of each slot's initial qubit
   int nruns;                // 2^(number of high register inputs)
-  uint32_t runlen;          // amplitudes per run: 2^(12 - M + nlow)
+  uint32_t runlen;          // amplitudes per run: 2^(T - M + nlow)
   uint32_t lowmask;         // low register input bits (inside the run)
   uint64_t runoff[1 << kGroupRegMax];  // input offset of run r (high register bits)
   uint32_t cbase[1 << kGroupRegMax];   // smem offset of configuration c: run * runlen + low bits

@@ -679,12 +679,14 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G);
 template <int M>
 __global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G);
 
-// one 32 KB stage of 2^(TB-M) free indices x 2^M configurations (TB = 12 for
-// complex64, 11 for complex128); the kernel pointer selects the precision
+// a tile of 2^(TB-M) free indices x 2^M configurations: TB = 9 for complex64
+// (4 KB, one per warp), 11 for complex128 (32 KB, one per block); the kernel
+// pointer selects the precision
 template <int M, int TB>
 static cudaError_t launch_group_t(void (*kern)(const GroupParams), const GroupParams& G, cudaStream_t s) {
-  constexpr int STAGE = 32768;
-  constexpr int SMEM = kTmaStages * STAGE + 2 * kTmaStages * 8 + kTmaStages * 4 + 16;
+  constexpr int STAGE = 32768;  // one block-wide stage, or eight warps' 4 KB stages
+  // stages, barriers, the sign table and the abort flag
+  constexpr int SMEM = kTmaStages * STAGE + 1024;
   static int grid_cap = 0;
   static std::mutex mu;
   {
@@ -699,16 +701,17 @@ static cudaError_t launch_group_t(void (*kern)(const GroupParams), const GroupPa
     }
   }
   const uint64_t tiles = 1ull << (G.nfree - (TB - M));
-  kern<<<(int)std::min<uint64_t>(tiles, (uint64_t)grid_cap), kBlock, SMEM, s>>>(G);
+  const uint64_t blocks = TB == 9 ? (tiles + kBlock / 32 - 1) / (kBlock / 32) : tiles;  // c64: one tile per warp
+  kern<<<(int)std::min<uint64_t>(blocks, (uint64_t)grid_cap), kBlock, SMEM, s>>>(G);
   return cudaGetLastError();
 }
 
 cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s) {
   if (dtype == OWQS_C64) {
     switch (G.m) {
-      case 1: return launch_group_t<1, 12>(k_group<1>, G, s);
-      case 2: return launch_group_t<2, 12>(k_group<2>, G, s);
-      case 3: return launch_group_t<3, 12>(k_group<3>, G, s);
+      case 1: return launch_group_t<1, 9>(k_group<1>, G, s);
+      case 2: return launch_group_t<2, 9>(k_group<2>, G, s);
+      case 3: return launch_group_t<3, 9>(k_group<3>, G, s);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -724,29 +727,31 @@ cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s) {
 // Group of up to kGroupMax measure passes in one HBM sweep (complex64): per
 // free index the group is arithmetic on an M-qubit register (the contract,
 // including how the signs and scales are carried, is in owqs_internal.h).
-// A tile is 2^(12-M) consecutive free indices; its 2^M input runs (one per
-// configuration of the register's input qubits) arrive by bulk copies into a
-// 3-stage shared-memory ring, 32 KB per stage.  Each thread takes two
-// consecutive elements at a time and holds their 2^M amplitudes in
-// registers.  Per pass and element: one sign bit selecting +-w; per
-// butterfly: one complex product and, per output, one packed FP32x2
-// multiply-add for the amplitude and one for its squared norm.  The
-// element's sign, the previous array's 1/sqrt(N) and the carried scales and
-// register signs are applied once, at the 16-byte stores.
-// Sign bits: the tile's part (two bits per pass) comes from the issuing
-// thread through a shared word; the element's low-bit parities are fixed
-// per thread (a thread always takes the same offsets within a tile), so per
-// tile one XOR gives every sign bit of an element.
-// Pipeline: a stage is refilled once every warp has released it (one
-// arrival per warp on the stage's "empty" mbarrier), so warps run up to
-// kTmaStages - 1 tiles apart instead of meeting at a block barrier per tile.
-// Every wait is bounded; a block that gives up sets the error flag, lets its
-// issued copies land and returns.  Squared norms after every pass are summed
-// per thread in compensated FP32 and reduced once into k slots.
+// Pipelines are warp-private: a warp's tile is 2^(9-M) consecutive free
+// indices, whose 2^M input runs (one per configuration of the register's
+// input qubits) arrive by bulk copies into the warp's own 3-stage ring of
+// 4 KB stages.  The warp refills a stage as soon as its own lanes have read
+// it, so no warp ever waits for another (a block-wide ring, refilled once
+// every warp had released a stage, left the fastest warps waiting for the
+// slowest warp's release plus a DRAM round trip).
+// Each lane takes two consecutive elements at a time and holds their 2^M
+// amplitudes in registers.  Per pass and element: one sign bit XORed into w;
+// per butterfly: one complex product and, per output, two FP32 multiply-adds
+// for the amplitude and one packed FP32x2 multiply-add for its squared norm
+// (the tile's first product starts each pass's accumulator).  The element's
+// sign, the previous array's 1/sqrt(N) and the carried scales and register
+// signs are applied once, at the 16-byte stores.
+// Sign bits: the tile's part (two bits per pass) is evaluated by lanes
+// 0..k-1, one pass each, and OR-reduced across the warp; the element's
+// low-bit parities are fixed per lane (a lane always takes the same offsets
+// within a tile), so per tile one XOR gives every sign bit of an element.
+// Every wait is bounded; a warp that gives up raises the block's abort flag,
+// lets its issued copies land and returns.  Squared norms after every pass
+// are summed per thread in compensated FP32 and reduced once into k slots.
 // ---------------------------------------------------------------------------
 template <int M, int S>
 __device__ __forceinline__ void group_butterfly(float2 (&x)[1 << M], const GroupPass& P, float wr, float wi,
-                                                float2& nacc) {
+                                                float2& nacc, bool first) {
 #pragma unroll
   for (int h = 0; h < (1 << (M - 1)); ++h) {
     const int g0 = ((h >> S) << (S + 1)) | (h & ((1 << S) - 1));
@@ -755,20 +760,22 @@ __device__ __forceinline__ void group_butterfly(float2 (&x)[1 << M], const Group
     const float2 v = make_float2(fmaf(wr, x1.x, -wi * x1.y), fmaf(wr, x1.y, wi * x1.x));
     const float2 y0 = make_float2(fmaf(P.ct[g0], v.x, x0.x), fmaf(P.ct[g0], v.y, x0.y));
     const float2 y1 = make_float2(fmaf(P.ct[g1], v.x, x0.x), fmaf(P.ct[g1], v.y, x0.y));
-    nacc = __ffma2_rn(y0, y0, nacc);
+    // the tile's first product starts the pass's accumulator (no zeroing)
+    nacc = (first && h == 0) ? __fmul2_rn(y0, y0) : __ffma2_rn(y0, y0, nacc);
     nacc = __ffma2_rn(y1, y1, nacc);
     x[g0] = y0;
     x[g1] = y1;
   }
 }
 
+// r0, r1: the two elements' sign bits for this pass, at bit 31 (one XOR
+// gives +-w)
 template <int M, int S>
 __device__ __forceinline__ void group_pass2(float2 (&x)[2][1 << M], const GroupPass& P, uint32_t r0, uint32_t r1,
-                                            float2& nacc) {
-  const float wr0 = r0 ? -P.fwr : P.fwr, wi0 = r0 ? -P.fwi : P.fwi;
-  const float wr1 = r1 ? -P.fwr : P.fwr, wi1 = r1 ? -P.fwi : P.fwi;
-  group_butterfly<M, S>(x[0], P, wr0, wi0, nacc);
-  group_butterfly<M, S>(x[1], P, wr1, wi1, nacc);
+                                            float2& nacc, bool first) {
+  const uint32_t ur = __float_as_uint(P.fwr), ui = __float_as_uint(P.fwi);
+  group_butterfly<M, S>(x[0], P, __uint_as_float(ur ^ r0), __uint_as_float(ui ^ r0), nacc, first);
+  group_butterfly<M, S>(x[1], P, __uint_as_float(ur ^ r1), __uint_as_float(ui ^ r1), nacc, false);
 }
 
 template <int M>
@@ -777,17 +784,20 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
     stall_and_give_up(G.stall_limit, G.errflag);
     return;
   }
-  constexpr int LT = 12 - M, TE = 1 << LT, NC = 1 << M, NS = kTmaStages;
+  constexpr int LT = 9 - M, TE = 1 << LT, NC = 1 << M, NS = kTmaStages;
   constexpr int STAGE = NC * TE * 8;
-  constexpr int EPT = TE / kBlock;  // elements per thread per tile (even)
+  constexpr int EPT = TE / 32;  // elements per lane per tile (even)
   constexpr int NWARP = kBlock / 32;
   static_assert(EPT >= 2 && EPT <= 8, "tile shape");
   static_assert(2 * kGroupMax <= 32, "two sign bits per pass in one word");
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * STAGE);
-  uint64_t* empty = full + NS;
-  uint32_t* signs = reinterpret_cast<uint32_t*>(smem + NS * STAGE + 2 * NS * 8);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(signs + NS);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* wsm = smem + warp * NS * STAGE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NWARP * NS * STAGE) + warp * NS;
+  uint64_t* zf = reinterpret_cast<uint64_t*>(smem + NWARP * NS * STAGE + NWARP * NS * 8);
+  uint64_t* af = zf + kGroupMax;
+  uint32_t* cz = reinterpret_cast<uint32_t*>(af + kGroupMax);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(cz + kGroupMax);
   const float2* __restrict__ in = reinterpret_cast<const float2*>(G.in);
   float2* __restrict__ out = reinterpret_cast<float2*>(G.out);
   double cprev = 1.0;
@@ -797,17 +807,14 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
   }
   const float fprev = (float)cprev;
   const uint64_t tiles = 1ull << (G.nfree - LT);
-  const uint64_t step = gridDim.x;
-  const uint64_t mine = blockIdx.x < tiles ? (tiles - blockIdx.x + step - 1) / step : 0;
-  constexpr unsigned RUN = TE * sizeof(float2);
+  const uint64_t gw = (uint64_t)blockIdx.x * NWARP + warp;
+  const uint64_t step = (uint64_t)gridDim.x * NWARP;
+  const uint64_t mine = gw < tiles ? (tiles - gw + step - 1) / step : 0;
   const int k = G.k;
-  // the element's low-bit sign parities, two bits per pass in the tile word's
-  // layout (element q at offset 2 threadIdx + (q>>1) 2 kBlock + (q&1)), and
-  // its offset within an input run (zeros inserted at the low register bits)
   uint32_t lowbits[EPT], spread[EPT];
 #pragma unroll
   for (int q = 0; q < EPT; ++q) {
-    const uint32_t e = (uint32_t)(threadIdx.x * 2 + (q >> 1) * kBlock * 2 + (q & 1));
+    const uint32_t e = (uint32_t)(lane * 2 + (q >> 1) * 64 + (q & 1));
     uint32_t sp = e;
     for (uint32_t lm = G.lowmask; lm; lm &= lm - 1) {
       const int b = __ffs(lm) - 1;
@@ -823,13 +830,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
     lowbits[q] = w;
   }
   const uint32_t evenk = 0x55555555u & ((k >= 16) ? 0xffffffffu : ((1u << (2 * k)) - 1u));
-  const bool pair_contig = (G.lowmask & 1u) == 0u;  // elements e, e+1 adjacent in every run
+  const bool pair_contig = (G.lowmask & 1u) == 0u;
 
-  auto issue = [&](uint64_t i) {  // thread 0 only
+  auto issue = [&](uint64_t i) {  // lane 0 of the warp
     const int st = (int)(i % NS);
-    float2* buf = reinterpret_cast<float2*>(smem + st * STAGE);
-    const uint64_t L0 = (blockIdx.x + i * step) << LT;
-    uint64_t ib = L0;  // free index with zeros inserted at the register inputs (ascending)
+    float2* buf = reinterpret_cast<float2*>(wsm + st * STAGE);
+    const uint64_t L0 = (gw + i * step) << LT;
+    uint64_t ib = L0;
     int sorted[M];
 #pragma unroll
     for (int q = 0; q < M; ++q) sorted[q] = G.B[q];
@@ -844,33 +851,28 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
         }
 #pragma unroll
     for (int q = 0; q < M; ++q) ib = ins0(ib, sorted[q]);
-    uint32_t w = 0;
-    for (int j = 0; j < k; ++j) {
-      w |= ((G.pass[j].c0 ^ par64(L0 & G.pass[j].zfree)) & 1u) << (2 * j);
-      w |= ((G.pass[j].zb ^ par64(L0 & G.pass[j].afree)) & 1u) << (2 * j + 1);
-    }
-    signs[st] = w;
-    mbar_expect_tx(&full[st], NC * RUN);
+    mbar_expect_tx(&full[st], (unsigned)STAGE);
     const unsigned rbytes = G.runlen * (unsigned)sizeof(float2);
     for (int r = 0; r < G.nruns; ++r) bulk_g2s(buf + r * G.runlen, in + ib + G.runoff[r], rbytes, &full[st]);
   };
 
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < NS; ++q) {
-      mbar_init(&full[q], 1);
-      mbar_init(&empty[q], NWARP);
-    }
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (threadIdx.x < kGroupMax) {
+    zf[threadIdx.x] = G.pass[threadIdx.x].zfree;
+    af[threadIdx.x] = G.pass[threadIdx.x].afree;
+    cz[threadIdx.x] = (G.pass[threadIdx.x].c0 & 1u) | ((G.pass[threadIdx.x].zb & 1u) << 1);
   }
+  if (lane == 0)
+    for (int q = 0; q < NS; ++q) mbar_init(&full[q], 1);
+  if (threadIdx.x == 0) *abort_flag = 0;
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
-  if (threadIdx.x == 0)
+  if (lane == 0)
     for (uint64_t q = 0; q < mine && q < (uint64_t)NS; ++q) issue(q);
 
   float ks[kGroupMax], kc[kGroupMax];
 #pragma unroll
   for (int j = 0; j < kGroupMax; ++j) ks[j] = kc[j] = 0.f;
-  uint64_t issued = mine < (uint64_t)NS ? mine : (uint64_t)NS;  // thread 0's count
+  uint64_t issued = mine < (uint64_t)NS ? mine : (uint64_t)NS;
   for (uint64_t i = 0; i < mine; ++i) {
     const int st = (int)(i % NS);
     if (*abort_flag) break;
@@ -878,15 +880,18 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
       *abort_flag = 1;
       break;
     }
-    const float2* buf = reinterpret_cast<const float2*>(smem + st * STAGE);
-    const uint32_t sw = signs[st];
-    const uint64_t L0 = (blockIdx.x + i * step) << LT;
+    const float2* buf = reinterpret_cast<const float2*>(wsm + st * STAGE);
+    const uint64_t L0 = (gw + i * step) << LT;
+    // the tile's sign word: lane j < k evaluates pass j's two tile parities
+    uint32_t mybits = 0;
+    if (lane < k)
+      mybits = (((cz[lane] & 1u) ^ par64(L0 & zf[lane])) << (2 * lane)) |
+               ((((cz[lane] >> 1) & 1u) ^ par64(L0 & af[lane])) << (2 * lane + 1));
+    const uint32_t sw = __reduce_or_sync(0xffffffffu, mybits);
     float2 tacc[kGroupMax];
 #pragma unroll
-    for (int j = 0; j < kGroupMax; ++j) tacc[j] = make_float2(0.f, 0.f);
-#pragma unroll
     for (int it = 0; it < EPT / 2; ++it) {
-      const int e = threadIdx.x * 2 + it * kBlock * 2;
+      const int e = lane * 2 + it * 64;
       float2 x[2][NC];
       if (pair_contig) {
 #pragma unroll
@@ -907,10 +912,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
       for (int j = 0; j < kGroupMax; ++j) {
         if (j >= k) break;
         const GroupPass& P = G.pass[j];
-        const uint32_t r0 = (b0 >> (2 * j + 1)) & 1u, r1 = (b1 >> (2 * j + 1)) & 1u;
-        if (M == 1 || P.slot == 0) group_pass2<M, 0>(x, P, r0, r1, tacc[j]);
-        else if (M == 2 || P.slot == 1) group_pass2<M, (M > 1 ? 1 : 0)>(x, P, r0, r1, tacc[j]);
-        else group_pass2<M, (M > 2 ? 2 : 0)>(x, P, r0, r1, tacc[j]);
+        const uint32_t r0 = (b0 << (30 - 2 * j)) & 0x80000000u, r1 = (b1 << (30 - 2 * j)) & 0x80000000u;
+        if (M == 1 || P.slot == 0) group_pass2<M, 0>(x, P, r0, r1, tacc[j], it == 0);
+        else if (M == 2 || P.slot == 1) group_pass2<M, (M > 1 ? 1 : 0)>(x, P, r0, r1, tacc[j], it == 0);
+        else group_pass2<M, (M > 2 ? 2 : 0)>(x, P, r0, r1, tacc[j], it == 0);
       }
       const float f0 = (__popc(b0 & evenk) & 1) ? -fprev : fprev;
       const float f1 = (__popc(b1 & evenk) & 1) ? -fprev : fprev;
@@ -922,23 +927,18 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
       }
     }
 #pragma unroll
-    for (int j = 0; j < kGroupMax; ++j) kahan_add(ks[j], kc[j], tacc[j].x + tacc[j].y);
-    // release the stage; thread 0 refills it once every warp has released it
+    for (int j = 0; j < kGroupMax; ++j)
+      if (j < k) kahan_add(ks[j], kc[j], tacc[j].x + tacc[j].y);
+    // every lane has read the stage: refill it with this warp's tile i + NS
     __syncwarp();
-    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[st]);
-    if (threadIdx.x == 0 && issued < mine) {
-      if (!mbar_wait_bounded(&empty[st], (unsigned)((i / NS) & 1u))) {
-        *abort_flag = 1;
-        break;
-      }
-      issue(issued++);
-    }
+    if (lane == 0 && issued < mine) issue(issued);
+    if (issued < mine) ++issued;
   }
   __syncthreads();
   if (*abort_flag) {
-    if (threadIdx.x == 0) {
-      atomicExch(G.errflag, 1u);
-      // let every issued copy land before the block's memory goes away
+    if (lane == 0) {
+      if (threadIdx.x == 0) atomicExch(G.errflag, 1u);
+      // let every copy this warp issued land before the block's memory goes away
       for (uint64_t j = issued > (uint64_t)NS ? issued - NS : 0; j < issued; ++j)
         mbar_wait_bounded(&full[j % NS], (unsigned)((j / NS) & 1u));
     }

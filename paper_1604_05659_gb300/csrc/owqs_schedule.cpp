@@ -295,7 +295,9 @@ int group_enabled() {
 // prepared qubit (code < 0).
 int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupParams& G, LaunchPlan& L) {
   if (i0 >= passes.size() || passes[i0].kind != 0) return 0;
-  const int tb = dtype == OWQS_C64 ? 12 : 11;  // log2 of a 32 KB stage in amplitudes
+  // log2 of a tile in amplitudes: a warp's 4 KB stage (complex64), a block's
+  // 32 KB stage (complex128)
+  const int tb = dtype == OWQS_C64 ? 9 : 11;
   const int n0 = passes[i0].n_in;
   if (n0 < tb || n0 > 62) return 0;
   // scan: the longest valid prefix
