@@ -262,11 +262,14 @@ struct GroupParams {
   double nscale[kGroupMax];
   int norm_in, norm_out;
   double thresh;
+  double vconst;            // in == nullptr: the value of every input amplitude (virtual |+> input)
   long long stall_limit;    // > 0 (tests only): as PassParams::stall_limit
   GroupPass pass[kGroupMax];
 };
 // longest group starting at passes[i] (0 or 1 if none), planned into G
-int plan_group(const std::vector<PassDesc>& passes, size_t i, int dtype, GroupParams& G, LaunchPlan& L);
+// virt_in: the group reads the virtual |+> input (no input array)
+int plan_group(const std::vector<PassDesc>& passes, size_t i, int dtype, GroupParams& G, LaunchPlan& L,
+               bool virt_in = false);
 cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s);
 int group_enabled();  // OWQS_GROUP=0 turns group fusion off
 

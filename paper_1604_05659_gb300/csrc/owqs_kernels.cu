@@ -673,16 +673,18 @@ cudaError_t launch_pass(const PassParams& P, const LaunchPlan& L, int dtype, cud
   return dtype == OWQS_C64 ? launch_t<float>(P, L, s) : launch_t<double>(P, L, s);
 }
 
-template <int M>
+// VIRT: the group reads the virtual |+> input (G.in == nullptr); a separate
+// instantiation keeps the array-reading kernel free of the test
+template <int M, bool VIRT>
 __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G);
 
-template <int M>
+template <int M, bool VIRT>
 __global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G);
 
 // a tile of 2^(TB-M) free indices x 2^M configurations: TB = 9 for complex64
 // (4 KB, one per warp), 11 for complex128 (32 KB, one per block); the kernel
 // pointer selects the precision
-template <int M, int TB>
+template <int M, int TB, bool VIRT>
 static cudaError_t launch_group_t(void (*kern)(const GroupParams), const GroupParams& G, cudaStream_t s) {
   constexpr int STAGE = 32768;  // one block-wide stage, or eight warps' 4 KB stages
   // stages, barriers, the sign table and the abort flag
@@ -707,18 +709,25 @@ static cudaError_t launch_group_t(void (*kern)(const GroupParams), const GroupPa
 }
 
 cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s) {
+  const bool v = G.in == nullptr;
   if (dtype == OWQS_C64) {
     switch (G.m) {
-      case 1: return launch_group_t<1, 9>(k_group<1>, G, s);
-      case 2: return launch_group_t<2, 9>(k_group<2>, G, s);
-      case 3: return launch_group_t<3, 9>(k_group<3>, G, s);
+      case 1: return v ? launch_group_t<1, 9, true>(k_group<1, true>, G, s)
+                       : launch_group_t<1, 9, false>(k_group<1, false>, G, s);
+      case 2: return v ? launch_group_t<2, 9, true>(k_group<2, true>, G, s)
+                       : launch_group_t<2, 9, false>(k_group<2, false>, G, s);
+      case 3: return v ? launch_group_t<3, 9, true>(k_group<3, true>, G, s)
+                       : launch_group_t<3, 9, false>(k_group<3, false>, G, s);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (G.m) {
-    case 1: return launch_group_t<1, 11>(k_group64<1>, G, s);
-    case 2: return launch_group_t<2, 11>(k_group64<2>, G, s);
-    case 3: return launch_group_t<3, 11>(k_group64<3>, G, s);
+    case 1: return v ? launch_group_t<1, 11, true>(k_group64<1, true>, G, s)
+                     : launch_group_t<1, 11, false>(k_group64<1, false>, G, s);
+    case 2: return v ? launch_group_t<2, 11, true>(k_group64<2, true>, G, s)
+                     : launch_group_t<2, 11, false>(k_group64<2, false>, G, s);
+    case 3: return v ? launch_group_t<3, 11, true>(k_group64<3, true>, G, s)
+                     : launch_group_t<3, 11, false>(k_group64<3, false>, G, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -778,7 +787,7 @@ __device__ __forceinline__ void group_pass2(float2 (&x)[2][1 << M], const GroupP
   group_butterfly<M, S>(x[1], P, __uint_as_float(ur ^ r1), __uint_as_float(ui ^ r1), nacc, false);
 }
 
-template <int M>
+template <int M, bool VIRT>
 __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
   if (G.stall_limit > 0) {
     stall_and_give_up(G.stall_limit, G.errflag);
@@ -806,6 +815,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
     cprev = (nv >= G.thresh && nv > 0.0) ? 1.0 / sqrt(nv) : 0.0;
   }
   const float fprev = (float)cprev;
+  // no input array: every input amplitude is vconst (the virtual |+> input);
+  // the ring then carries no data and only paces the loop
+  constexpr bool virt = VIRT;
+  const float vc = (float)G.vconst;
   const uint64_t tiles = 1ull << (G.nfree - LT);
   const uint64_t gw = (uint64_t)blockIdx.x * NWARP + warp;
   const uint64_t step = (uint64_t)gridDim.x * NWARP;
@@ -851,6 +864,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
         }
 #pragma unroll
     for (int q = 0; q < M; ++q) ib = ins0(ib, sorted[q]);
+    if (virt) {
+      mbar_arrive(&full[st]);
+      return;
+    }
     mbar_expect_tx(&full[st], (unsigned)STAGE);
     const unsigned rbytes = G.runlen * (unsigned)sizeof(float2);
     for (int r = 0; r < G.nruns; ++r) bulk_g2s(buf + r * G.runlen, in + ib + G.runoff[r], rbytes, &full[st]);
@@ -893,7 +910,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
     for (int it = 0; it < EPT / 2; ++it) {
       const int e = lane * 2 + it * 64;
       float2 x[2][NC];
-      if (pair_contig) {
+      if (virt) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) x[0][c] = x[1][c] = make_float2(vc, 0.f);
+      } else if (pair_contig) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const float4 v = *reinterpret_cast<const float4*>(buf + G.cbase[c] + spread[2 * it]);
@@ -981,7 +1001,7 @@ __device__ __forceinline__ void group_butterfly64(double2 (&x)[1 << M], const Gr
   }
 }
 
-template <int M>
+template <int M, bool VIRT>
 __global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G) {
   if (G.stall_limit > 0) {
     stall_and_give_up(G.stall_limit, G.errflag);
@@ -1004,6 +1024,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G) {
     const double nv = G.norms[G.norm_in];
     cprev = (nv >= G.thresh && nv > 0.0) ? 1.0 / sqrt(nv) : 0.0;
   }
+  constexpr bool virt = VIRT;  // virtual |+> input, as in k_group
   const uint64_t tiles = 1ull << (G.nfree - LT);
   const uint64_t step = gridDim.x;
   const uint64_t mine = blockIdx.x < tiles ? (tiles - blockIdx.x + step - 1) / step : 0;
@@ -1054,6 +1075,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G) {
       w |= ((G.pass[j].zb ^ par64(L0 & G.pass[j].afree)) & 1u) << (2 * j + 1);
     }
     signs[st] = w;
+    if (virt) {
+      mbar_arrive(&full[st]);
+      return;
+    }
     mbar_expect_tx(&full[st], NC * RUN);
     const unsigned rbytes = G.runlen * (unsigned)sizeof(double2);
     for (int r = 0; r < G.nruns; ++r) bulk_g2s(buf + r * G.runlen, in + ib + G.runoff[r], rbytes, &full[st]);
@@ -1090,7 +1115,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G) {
       const int e = threadIdx.x + q * kBlock;
       double2 x[NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) x[c] = buf[G.cbase[c] + spread[q]];
+      for (int c = 0; c < NC; ++c) x[c] = virt ? make_double2(G.vconst, 0.0) : buf[G.cbase[c] + spread[q]];
       const uint32_t b = sw ^ lowbits[q];
 #pragma unroll
       for (int j = 0; j < kGroupMax; ++j) {

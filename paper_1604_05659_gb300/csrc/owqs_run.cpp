@@ -404,17 +404,18 @@ struct ProductInput {
 };
 
 // What the launch for passes[i] is: a factor join, the final pass, a group
-// of k measure passes (k >= 2; needs a materialised input array) or a single
+// of k measure passes (k >= 2; reads a materialised input array or the
+// virtual |+> input, not the diagonal input of a unitary) or a single
 // measure pass.  The run driver and owqs_describe_launches both use it.
 enum { LAUNCH_SINGLE = 0, LAUNCH_GROUP = 1, LAUNCH_FINAL = 2, LAUNCH_JOIN = 3 };
-static int decide_launch(const std::vector<PassDesc>& passes, size_t i, int dtype, bool real_input, GroupParams& G,
-                         LaunchPlan& GL, int& k) {
+static int decide_launch(const std::vector<PassDesc>& passes, size_t i, int dtype, bool real_input, bool diag_input,
+                         GroupParams& G, LaunchPlan& GL, int& k) {
   const PassDesc& d = passes[i];
   k = 1;
   if (d.kind == 2) return LAUNCH_JOIN;
   if (d.kind != 0) return LAUNCH_FINAL;
-  if (real_input && group_enabled()) {
-    const int g = plan_group(passes, i, dtype, G, GL);
+  if ((real_input || !diag_input) && group_enabled()) {
+    const int g = plan_group(passes, i, dtype, G, GL, !real_input);
     if (g >= 2) {
       k = g;
       return LAUNCH_GROUP;
@@ -785,7 +786,7 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
       GroupParams G;
       LaunchPlan GL;
       int gk = 0;
-      switch (decide_launch(pr.passes, i, o->dtype, R.real_input(), G, GL, gk)) {
+      switch (decide_launch(pr.passes, i, o->dtype, R.real_input(), vdiag > 0, G, GL, gk)) {
         case LAUNCH_JOIN:
           R.join(d, prod->vecs[d.factor], 3 * K + 8 + d.factor);
           break;
@@ -1015,7 +1016,7 @@ owqs_status owqs_describe_launches(const owqs_pattern* h, uint32_t dtype, uint32
     GroupParams G;
     LaunchPlan GL;
     int k = 0;
-    switch (decide_launch(passes, i, (int)dtype, real, G, GL, k)) {
+    switch (decide_launch(passes, i, (int)dtype, real, false, G, GL, k)) {
       case LAUNCH_GROUP:
         put(KK_GROUP, mi, (uint32_t)k);
         mi += (uint32_t)k;

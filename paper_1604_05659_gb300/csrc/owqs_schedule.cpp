@@ -293,7 +293,8 @@ int group_enabled() {
 // Group planning.  A live entry is a free input bit (code >= 0, its input
 // bit while scanning, its free index when planning) or a register slot /
 // prepared qubit (code < 0).
-int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupParams& G, LaunchPlan& L) {
+int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupParams& G, LaunchPlan& L,
+               bool virt_in) {
   if (i0 >= passes.size() || passes[i0].kind != 0) return 0;
   // log2 of a tile in amplitudes: a warp's 4 KB stage (complex64), a block's
   // 32 KB stage (complex128)
@@ -435,7 +436,9 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupP
   }
   G.norm_in = G.norm_out = -1;
   L.kind = KK_GROUP;
-  L.bytes = (std::ldexp(1.0, n0) + std::ldexp(1.0, passes[i0 + best_k - 1].n_out)) * (dtype == OWQS_C64 ? 8.0 : 16.0);
+  G.vconst = virt_in ? std::ldexp((n0 & 1) ? M_SQRT1_2 : 1.0, -(n0 / 2)) : 0.0;
+  L.bytes = ((virt_in ? 0.0 : std::ldexp(1.0, n0)) + std::ldexp(1.0, passes[i0 + best_k - 1].n_out)) *
+            (dtype == OWQS_C64 ? 8.0 : 16.0);
   L.grid = 1;
   return best_k;
 }

@@ -41,7 +41,7 @@ def test_brickwork_full_size_plan(owqs):
         lv = h.describe_launches(wl.outcomes, dtype=dtype)        # virtual |+> input
         _check_cover(lv, wl.pattern.K)
         groups = [x for x in lv if x[0] == "group_pass"]
-        assert lv[0] == ("generic_pass", 0, 1)                   # the first measurement reads the virtual input
+        assert lv[0] == ("group_pass", 0, 12)                    # the first group reads the virtual input
         assert len(lv) <= 120 and sum(x[2] for x in groups) >= 1085, (dtype, len(lv))
         lr = h.describe_launches(wl.outcomes, dtype=dtype, real_input=True)
         assert lr[0] == ("norm", 0, 0)
@@ -55,7 +55,7 @@ def test_qft_plan_and_small_arrays(owqs):
     lr = h.describe_launches(wl.outcomes, real_input=True)
     _check_cover(lr, wl.pattern.K)
     assert len(lr) <= 260, len(lr)
-    # live arrays narrower than one 32 KB tile never group
+    # live arrays narrower than one tile (2^9 amplitudes for complex64) never group
     small = workloads.small_random()
     hs = owqs.load(small.pattern)
     hs.reorder()
