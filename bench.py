@@ -51,8 +51,8 @@ FALLBACK_HBM_GBS = 6800.0
 # 2148.1 MB read + 2098.8 MB written) and c128 k_group64<3> (2^28 complex128;
 # 4299.1 MB read + 4247.6 MB written).  profiles/k_group_c64_brickwork28x40_dram.md,
 # profiles/k_group64_c128_brickwork26x8.md.
-NCU_TRAFFIC = {("d1d48e887adff9c0", "c64"): (2147812352 + 2097959936 + 2147715584 + 2095019008 + 2147740160 + 2094754048) / 3.0,
-               ("d1d48e887adff9c0", "c128"): (4298868992 + 4249040640 + 4298602496 + 4246573568 + 4299443456 + 4246392320) / 3.0}
+NCU_TRAFFIC = {("ee3688961c6d8a2d", "c64"): (2147736320 + 2097301248 + 2147706624 + 2094425088 + 2147719168 + 2094294272) / 3.0,
+               ("ee3688961c6d8a2d", "c128"): (4298717696 + 4249130752 + 4298062848 + 4245649664 + 4298588416 + 4246102016) / 3.0}
 # nominal GB300 FP64 rate (no measured FP64 peak exists for this machine)
 FP64_PEAK_TFLOPS = 1.25
 # FP64 flops per output amplitude of the complex128 pass: complex multiply-add
