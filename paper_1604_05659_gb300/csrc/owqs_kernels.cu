@@ -80,9 +80,10 @@ __device__ __forceinline__ double2 pass_w1(const PassParams& P) {
 // ---------------------------------------------------------------------------
 // Block reduction of NV FP64 values into norms[slot .. slot+NV).  Each block
 // stores its partial; the last block to finish (counted with one atomic)
-// adds the partials in block order with Neumaier compensation, so the result
-// does not depend on block scheduling.  The counter is reset for the next
-// launch.  No thread ever waits on another block.
+// adds the partials, one warp per value: lane-strided Neumaier sums in block
+// order, then a fixed shuffle tree, so the result does not depend on block
+// scheduling.  The counter is reset for the next launch.  No thread ever
+// waits on another block.
 // ---------------------------------------------------------------------------
 template <int NV>
 __device__ __forceinline__ void reduce_to_slots(const double (&acc)[NV], double* partials,
@@ -115,10 +116,11 @@ __device__ __forceinline__ void reduce_to_slots(const double (&acc)[NV], double*
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
+  // one warp per slot: lane-strided Neumaier sums over the block partials,
+  // then a fixed shuffle tree (the order does not depend on scheduling)
+  for (int i = warp; i < nv; i += nwarp) {
     double s = 0.0, c = 0.0;
-    for (unsigned blk = threadIdx.x; blk < gridDim.x; blk += blockDim.x) {
+    for (unsigned blk = lane; blk < gridDim.x; blk += 32) {
       const double x = __ldcg(&partials[(size_t)i * gridDim.x + blk]);
       const double t = s + x;
       c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
@@ -126,16 +128,10 @@ __device__ __forceinline__ void reduce_to_slots(const double (&acc)[NV], double*
     }
     s += c;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    __syncthreads();
-    if (lane == 0) sh[i][warp] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double tot = 0.0;
-      for (int w = 0; w < nwarp; ++w) tot += sh[i][w];
-      if (i < nv) norms[slot + i] = tot;
-    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) norms[slot + i] = s;
   }
+  __syncthreads();
   if (threadIdx.x == 0) *counter = 0u;
 }
 
