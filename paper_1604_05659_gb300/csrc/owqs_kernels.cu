@@ -85,11 +85,11 @@ __device__ __forceinline__ double2 pass_w1(const PassParams& P) {
 // scheduling.  The counter is reset for the next launch.  No thread ever
 // waits on another block.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void finish_slots(double* partials, unsigned int* counter, double* norms, int slot, int nv);
 template <int NV>
 __device__ __forceinline__ void reduce_to_slots(const double (&acc)[NV], double* partials,
                                                 unsigned int* counter, double* norms, int slot, int nv = NV) {
   __shared__ double sh[NV][32];
-  __shared__ int am_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
@@ -108,6 +108,16 @@ __device__ __forceinline__ void reduce_to_slots(const double (&acc)[NV], double*
       if (lane == 0) partials[(size_t)i * gridDim.x + blockIdx.x] = v;
     }
   }
+  finish_slots(partials, counter, norms, slot, nv);
+}
+
+// Second half of the slot reduction: every block's partials are stored (and
+// fenced by the threads that wrote them); the last block to finish adds them
+// into norms[slot ..).
+__device__ __forceinline__ void finish_slots(double* partials, unsigned int* counter, double* norms, int slot, int nv) {
+  __shared__ int am_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned prev = atomicAdd(counter, 1u);
@@ -754,6 +764,35 @@ cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s) {
 // lets its issued copies land and returns.  Squared norms after every pass
 // are summed per thread in compensated FP32 and reduced once into k slots.
 // ---------------------------------------------------------------------------
+// Block stage of a complex64 group's slot sums (red: the threads'
+// compensated sums, slot-major).  Slot j is summed by warp j % 8 in FP32:
+// lane-strided Kahan sums, then a shuffle tree that carries each step's
+// rounding error (TwoSum); only the block's total goes to FP64, which on
+// GB300 runs at 1/64 of the FP32 rate (a per-thread FP64 tree over twelve
+// slots cost about 15 us per launch).  Out of line, so that the main loop's
+// code does not change with it.
+__device__ __noinline__ void group_slot_sums(const float* red, int k, double c2, const double* nscale,
+                                             double* partials, unsigned int* counter, double* norms, int slot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int j = warp; j < k; j += nwarp) {
+    float s = 0.f, c = 0.f;
+    for (int t = lane; t < (int)blockDim.x; t += 32) kahan_add(s, c, red[j * blockDim.x + t]);
+    float e = -c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float so = __shfl_xor_sync(0xffffffffu, s, o), eo = __shfl_xor_sync(0xffffffffu, e, o);
+      const float t = s + so, bp = t - s, err = (s - (t - bp)) + (so - bp);
+      s = t;
+      e = e + eo + err;
+    }
+    if (lane == 0) {
+      partials[(size_t)j * gridDim.x + blockIdx.x] = c2 * nscale[j] * ((double)s + (double)e);
+      __threadfence();
+    }
+  }
+  finish_slots(partials, counter, norms, slot, k);
+}
+
 template <int M, int S>
 __device__ __forceinline__ void group_butterfly(float2 (&x)[1 << M], const GroupPass& P, float wr, float wi,
                                                 float2& nacc, bool first) {
@@ -962,11 +1001,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
     return;
   }
   if (G.norm_out >= 0) {
-    const double c2 = cprev * cprev;
-    double a[kGroupMax];
+    // every copy has landed and been read: the stage memory now holds the
+    // threads' compensated sums, slot-major
+    float* red = reinterpret_cast<float*>(smem);
 #pragma unroll
-    for (int j = 0; j < kGroupMax; ++j) a[j] = c2 * G.nscale[j] * ((double)ks[j] - (double)kc[j]);
-    reduce_to_slots<kGroupMax>(a, G.partials, G.counter, G.norms, G.norm_out, k);
+    for (int j = 0; j < kGroupMax; ++j) red[j * kBlock + threadIdx.x] = ks[j] - kc[j];
+    __syncthreads();
+    group_slot_sums(red, k, cprev * cprev, G.nscale, G.partials, G.counter, G.norms, G.norm_out);
   }
 }
 
