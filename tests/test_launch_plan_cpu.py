@@ -71,3 +71,25 @@ def test_random_patterns_cover_every_measurement(owqs):
         for dtype in ("c64", "c128"):
             for real in (False, True):
                 _check_cover(h.describe_launches(wl.outcomes, dtype=dtype, real_input=real), wl.pattern.K)
+
+
+def test_group_eligibility_follows_the_tile_width(owqs):
+    """A group needs at least one tile of free indices: 2^9 input amplitudes
+    for complex64 (a warp's 4 KB tile), 2^11 for complex128 (a block's 32 KB
+    tile).  Brickworks of 7..11 rows have live arrays of rows or rows + 1
+    qubits; below the boundary the measurements run as single passes and
+    the first one reads the virtual input in the generic kernel, from it on
+    the first group reads the virtual input itself."""
+    first = {"c64": 9, "c128": 11}
+    for rows in (7, 8, 9, 10, 11):
+        wl = workloads.brickwork(rows, 6)
+        h = owqs.load(wl.pattern)
+        h.reorder()
+        for dtype in ("c64", "c128"):
+            for real in (False, True):
+                plan = h.describe_launches(wl.outcomes, dtype=dtype, real_input=real)
+                _check_cover(plan, wl.pattern.K)
+                ngroups = sum(1 for k, _, _ in plan if k == "group_pass")
+                assert (ngroups > 0) == (rows >= first[dtype]), (rows, dtype, real, plan[:3])
+                if not real:
+                    assert plan[0][0] == ("group_pass" if rows >= first[dtype] else "generic_pass"), (rows, dtype)
