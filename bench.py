@@ -51,8 +51,8 @@ FALLBACK_HBM_GBS = 6800.0
 # 2148.1 MB read + 2098.8 MB written) and c128 k_group64<3> (2^28 complex128;
 # 4299.1 MB read + 4247.6 MB written).  profiles/k_group_c64_brickwork28x40_dram.md,
 # profiles/k_group64_c128_brickwork26x8.md.
-NCU_TRAFFIC = {("66bbbc5904ee172d", "c64"): (2147650560 + 2097494784 + 2147630848 + 2094420992 + 2147755776 + 2094493440) / 3.0,
-               ("66bbbc5904ee172d", "c128"): (4299849216 + 4249496320 + 4298870272 + 4245908224 + 4298921984 + 4246132736) / 3.0}
+NCU_TRAFFIC = {("96c287f5e75f9e0d", "c64"): (2147819776 + 2097235968 + 2147815936 + 2094480128 + 2147635712 + 2094625536) / 3.0,
+               ("96c287f5e75f9e0d", "c128"): (4299899136 + 4249785088 + 4299558656 + 4246345216 + 4298472704 + 4245789952) / 3.0}
 # nominal GB300 FP64 rate (no measured FP64 peak exists for this machine)
 FP64_PEAK_TFLOPS = 1.25
 # FP64 flops per output amplitude of the complex128 pass: complex multiply-add

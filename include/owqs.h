@@ -296,6 +296,16 @@ owqs_status owqs_run_product(owqs_pattern* p, const owqs_run_opts* opts, uint32_
  * OWQS_ERR_TIMEOUT.  runs = 0 cancels.  Not for production use. */
 owqs_status owqs_test_wait_timeout(uint32_t runs, uint64_t limit_cycles);
 
+/* Test hook for the bounds-checked build (libowqs_checked.so, compiled with
+ * OWQS_BOUNDS_CHECK, in which every global access of the pass kernels is
+ * first checked against the extent of the buffer it touches): the next
+ * `runs` owqs_run calls launch without a graph with every buffer extent
+ * `elems` amplitudes short.  The checked build then skips the accesses
+ * beyond the shortened extents and the run returns OWQS_ERR_CUDA ("outside
+ * its buffer"); the release build ignores extents.  runs = 0 cancels.
+ * Not for production use. */
+owqs_status owqs_test_shrink_extents(uint32_t runs, uint64_t elems);
+
 /* Flows of the pattern's open graph (G, I, O), Section 4.5 with the
  * definitions of ref. [13]; G has an edge u-v iff the pattern holds an odd
  * number of E commands on {u, v}.

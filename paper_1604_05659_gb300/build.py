@@ -4,6 +4,11 @@ Host C++ goes through g++, the kernels through nvcc with
 -gencode arch=compute_103a,code=sm_103a; the objects are linked into one
 shared library with the CUDA runtime linked statically, so the library has
 no dependency beyond the driver.  Objects go to _build/ next to this file.
+
+build(bounds_check=True) makes the debug library libowqs_checked.so
+(objects in _build_checked/): the kernels compiled with OWQS_BOUNDS_CHECK,
+which checks every global access of the pass kernels against the extent of
+its buffer and reports a failed check as an error of the run.
 """
 from __future__ import annotations
 
@@ -19,6 +24,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libowqs.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libowqs_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -45,44 +52,47 @@ def _run(cmd):
     return r.stdout + r.stderr
 
 
-def build(verbose: bool = False, ptxas_info: bool = False) -> str:
+def build(verbose: bool = False, ptxas_info: bool = False, bounds_check: bool = False) -> str:
     cuda = cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
-    os.makedirs(BUILD, exist_ok=True)
+    bdir, lib = (BUILD_CHECKED, LIB_CHECKED) if bounds_check else (BUILD, LIB)
+    os.makedirs(bdir, exist_ok=True)
     cpp, cu = sources()
     inc = ["-I", INCLUDE, "-I", CSRC, "-I", os.path.join(cuda, "include")]
+    defs = ["-DOWQS_BOUNDS_CHECK"] if bounds_check else []
     jobs = []
     for f in cpp:
-        obj = os.path.join(BUILD, f[:-4] + ".o")
-        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function", *inc, "-c",
+        obj = os.path.join(bdir, f[:-4] + ".o")
+        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function", *defs, *inc, "-c",
                      os.path.join(CSRC, f), "-o", obj])
     for f in cu:
-        obj = os.path.join(BUILD, f[:-3] + ".o")
+        obj = os.path.join(bdir, f[:-3] + ".o")
         extra = ["-Xptxas", "-v"] if ptxas_info else []
         jobs.append([nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-                     "--expt-relaxed-constexpr", *extra, *inc, "-c", os.path.join(CSRC, f), "-o", obj])
+                     "--expt-relaxed-constexpr", *defs, *extra, *inc, "-c", os.path.join(CSRC, f), "-o", obj])
     logs = []
     with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
         for out in ex.map(_run, jobs):
             logs.append(out)
-    objs = [os.path.join(BUILD, f[:-4] + ".o") for f in cpp] + [os.path.join(BUILD, f[:-3] + ".o") for f in cu]
-    tmp = LIB + ".tmp"
+    objs = [os.path.join(bdir, f[:-4] + ".o") for f in cpp] + [os.path.join(bdir, f[:-3] + ".o") for f in cu]
+    tmp = lib + ".tmp"
     logs.append(_run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread", "-ldl", "-lrt"]))
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     text = "\n".join(x for x in logs if x.strip())
     if verbose and text:
         print(text)
     return text
 
 
-def ensure_built() -> str:
+def ensure_built(bounds_check: bool = False) -> str:
     """Build if the library is missing or older than a source file."""
     cpp, cu = sources()
     srcs = [os.path.join(CSRC, f) for f in cpp + cu + os.listdir(CSRC) if f.endswith(".h")]
     srcs.append(os.path.join(INCLUDE, "owqs.h"))
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(s) for s in srcs):
-        build()
-    return LIB
+    lib = LIB_CHECKED if bounds_check else LIB
+    if not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(s) for s in srcs):
+        build(bounds_check=bounds_check)
+    return lib
 
 
 if __name__ == "__main__":

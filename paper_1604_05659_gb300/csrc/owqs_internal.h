@@ -55,6 +55,7 @@ struct Pattern {
 // Test hook (owqs_test_wait_timeout): runs left that stall their first
 // bulk-copy launch, and the cycle limit of that stall
 int take_test_stall(long long* limit);
+int take_test_shrink(uint64_t* elems);
 
 // Section 4.5 pre-check: does the open graph have a gflow (searched once,
 // kept with the pattern; owqs_flow.cpp)
@@ -131,7 +132,7 @@ struct PassParams {
   double* norms;         // device norm slots
   double* partials;      // per-block partial sums (2 * grid)
   unsigned int* counter; // finished-block counter, left at 0
-  unsigned int* errflag; // set to a nonzero code if a device-side wait gives up
+  unsigned int* errflag; // bit 0: a device-side wait gave up; bit 1: a bounds check failed
   int n_in, r, b, n_out;
   int norm_in;           // slot whose value N gives s_c = scale / sqrt(N); -1: s_c = scale
   int norm_out;          // slot written with sum |out|^2 (prob pass: norm_out, norm_out+1); -1: none
@@ -157,6 +158,9 @@ struct PassParams {
   // final pass
   int identity_perm;
   int perm[64];
+  // elements in the buffers read and written; checked only in builds with
+  // OWQS_BOUNDS_CHECK (0: not checked)
+  uint64_t in_cap, out_cap;
 };
 
 enum KernelKind {
@@ -265,6 +269,7 @@ struct GroupParams {
   double vconst;            // in == nullptr: the value of every input amplitude (virtual |+> input)
   long long stall_limit;    // > 0 (tests only): as PassParams::stall_limit
   GroupPass pass[kGroupMax];
+  uint64_t in_cap, out_cap;  // as PassParams
 };
 // longest group starting at passes[i] (0 or 1 if none), planned into G
 // virt_in: the group reads the virtual |+> input (no input array)
@@ -340,6 +345,8 @@ struct KronParams {
   const double* norms;
   int n_in, q;
   int norm_in, fnorm;
+  unsigned int* errflag;
+  uint64_t in_cap, out_cap;  // as PassParams
 };
 cudaError_t launch_kron(const KronParams& K, int dtype, cudaStream_t s);
 

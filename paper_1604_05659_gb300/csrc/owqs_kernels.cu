@@ -53,6 +53,23 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
   sum = t;
 }
 
+// Bounds-checked builds (-DOWQS_BOUNDS_CHECK): a global access of the pass
+// kernels is first checked against the extent of the buffer it touches (cap
+// elements; 0: not checked); an access outside it is skipped and raises bit
+// 1 of the run's error flag, which the host reports.  Release builds compile
+// the checks away.
+#ifdef OWQS_BOUNDS_CHECK
+__device__ __forceinline__ bool in_extent(uint64_t first, uint64_t count, uint64_t cap, unsigned int* flag) {
+  if (cap == 0 || (first <= cap && count <= cap - first)) return true;
+  atomicOr(flag, 2u);
+  return false;
+}
+#define OWQS_IF_IN_EXTENT(first, count, cap, flag) if (in_extent((first), (count), (cap), (flag)))
+#else
+__device__ __forceinline__ bool in_extent(uint64_t, uint64_t, uint64_t, unsigned int*) { return true; }
+#define OWQS_IF_IN_EXTENT(first, count, cap, flag)
+#endif
+
 // Per-thread running sum of squared norms: compensated FP32 for complex64
 // passes, plain FP64 for complex128
 template <typename T>
@@ -177,7 +194,13 @@ __global__ void __launch_bounds__(kBlock) k_generic(const PassParams P) {
       x.x = ((i & dmask) == (i >> P.vdiag)) ? (T)1 : (T)0;
       x.y = (T)0;
     } else {
-      x = in[(k ^ P.xmask) & inmask];
+      const uint64_t i = (k ^ P.xmask) & inmask;
+      if (in_extent(i, 1, P.in_cap, P.errflag)) {
+        x = in[i];
+      } else {
+        x.x = (T)0;
+        x.y = (T)0;
+      }
     }
     if (qsign(P, k)) x.x = -x.x, x.y = -x.y;
     return x;
@@ -197,7 +220,7 @@ __global__ void __launch_bounds__(kBlock) k_generic(const PassParams P) {
       V y;
       y.x = sc * x.x;
       y.y = sc * x.y;
-      out[j] = y;
+      if (in_extent(j, 1, P.out_cap, P.errflag)) out[j] = y;
       part[0] += y.x * y.x + y.y * y.y;
     } else {
       const uint64_t k0 = ins0(j, P.b), k1 = k0 | bb;
@@ -206,7 +229,7 @@ __global__ void __launch_bounds__(kBlock) k_generic(const PassParams P) {
         V y;
         y.x = sc * x0.x + wr * x1.x - wi * x1.y;
         y.y = sc * x0.y + wr * x1.y + wi * x1.x;
-        out[j] = y;
+        if (in_extent(j, 1, P.out_cap, P.errflag)) out[j] = y;
         part[0] += y.x * y.x + y.y * y.y;
       } else {
         const T ex = er * x1.x - ei * x1.y, ey = er * x1.y + ei * x1.x;
@@ -312,6 +335,9 @@ __global__ void __launch_bounds__(kBlock) k_fast(const PassParams P) {
     const uint32_t pa = P.zb ^ par64(K0 & P.amask);
     const uint64_t ib = K0 & inmask;
     V v0[NL], v1[NL];
+    if (!in_extent(ib, BM == L ? (1ull << b) + NL : (BM < L ? 2 * NL : NL), P.in_cap, P.errflag) ||
+        !in_extent(J, ((uint64_t)((1 << rt) - 1) << nlo) + NL, P.out_cap, P.errflag))
+      continue;
     if constexpr (BM < L) {
       V run[2 * NL];
       ld_run<HINT>(run, in + ib);
@@ -413,7 +439,7 @@ __device__ __forceinline__ void stall_and_give_up(long long limit, unsigned int*
     bool done = mbar_try_wait(&never, 0u);
     const long long t0 = clock64();
     while (!done && clock64() - t0 <= limit) done = mbar_try_wait(&never, 0u);
-    if (!done) atomicExch(errflag, 1u);
+    if (!done) atomicOr(errflag, 1u);
   }
   __syncthreads();
 }
@@ -466,6 +492,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
     V* buf = reinterpret_cast<V*>(smem + st * S::STAGE_BYTES);
     const uint64_t tile = blockIdx.x + i * step;
     const uint64_t ib = ins0(tile << LTE, b) & inmask;
+    if (!in_extent(ib, CASE == 1 ? (1ull << b) + TE : IN_BYTES / sizeof(V), P.in_cap, P.errflag)) {
+      mbar_arrive(&full[st]);  // no copy: the stage keeps stale data, the run reports the error
+      return;
+    }
     mbar_expect_tx(&full[st], IN_BYTES);
     if constexpr (CASE == 1) {
       bulk_g2s(buf, in + ib, TE * sizeof(V), &full[st]);
@@ -506,6 +536,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
       const uint32_t s0t = pz ^ par64(dt & P.zmask);
       const uint32_t s1t = s0t ^ pa ^ par64(dt & P.amask);
       V* o = out + J + (t << nlo);
+      if (!in_extent(J + (t << nlo), TE, P.out_cap, P.errflag)) continue;
 #pragma unroll 2
       for (int e = threadIdx.x * VE; e < TE; e += kBlock * VE) {
         V x0[VE], x1[VE], y[VE];
@@ -536,7 +567,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
   }
   if (failed) {
     if (threadIdx.x == 0) {
-      atomicExch(P.errflag, 1u);
+      atomicOr(P.errflag, 1u);
       // let copies already issued land before the block's memory goes away
       for (uint64_t j = i; j < issued; ++j) mbar_wait_bounded(&full[j % NS], (unsigned)((j / NS) & 1u));
     }
@@ -899,7 +930,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
         }
 #pragma unroll
     for (int q = 0; q < M; ++q) ib = ins0(ib, sorted[q]);
-    if (virt) {
+#ifdef OWQS_BOUNDS_CHECK
+    bool ok = !virt;
+    for (int r = 0; r < G.nruns && ok; ++r) ok = in_extent(ib + G.runoff[r], G.runlen, G.in_cap, G.errflag);
+#else
+    const bool ok = !virt;
+#endif
+    if (!ok) {  // the virtual input, or (checked builds) a run outside the input: no copy
       mbar_arrive(&full[st]);
       return;
     }
@@ -977,6 +1014,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
 #pragma unroll
       for (int g = 0; g < NC; ++g) {
         const float s0 = f0 * G.fin[g], s1 = f1 * G.fin[g];
+        OWQS_IF_IN_EXTENT(L0 + G.outoff[g] + e, 2, G.out_cap, G.errflag)
         *reinterpret_cast<float4*>(out + L0 + G.outoff[g] + e) =
             make_float4(s0 * x[0][g].x, s0 * x[0][g].y, s1 * x[1][g].x, s1 * x[1][g].y);
       }
@@ -992,7 +1030,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
   __syncthreads();
   if (*abort_flag) {
     if (lane == 0) {
-      if (threadIdx.x == 0) atomicExch(G.errflag, 1u);
+      if (threadIdx.x == 0) atomicOr(G.errflag, 1u);
       // let every copy this warp issued land before the block's memory goes away
       for (uint64_t j = issued > (uint64_t)NS ? issued - NS : 0; j < issued; ++j)
         mbar_wait_bounded(&full[j % NS], (unsigned)((j / NS) & 1u));
@@ -1112,7 +1150,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G) {
       w |= ((G.pass[j].zb ^ par64(L0 & G.pass[j].afree)) & 1u) << (2 * j + 1);
     }
     signs[st] = w;
-    if (virt) {
+#ifdef OWQS_BOUNDS_CHECK
+    bool ok = !virt;
+    for (int r = 0; r < G.nruns && ok; ++r) ok = in_extent(ib + G.runoff[r], G.runlen, G.in_cap, G.errflag);
+#else
+    const bool ok = !virt;
+#endif
+    if (!ok) {  // as in k_group
       mbar_arrive(&full[st]);
       return;
     }
@@ -1168,6 +1212,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G) {
 #pragma unroll
       for (int g = 0; g < NC; ++g) {
         const double sc = f * G.find[g];
+        OWQS_IF_IN_EXTENT(L0 + G.outoff[g] + e, 1, G.out_cap, G.errflag)
         out[L0 + G.outoff[g] + e] = make_double2(sc * x[g].x, sc * x[g].y);
       }
     }
@@ -1184,7 +1229,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G) {
   __syncthreads();
   if (*abort_flag) {
     if (threadIdx.x == 0) {
-      atomicExch(G.errflag, 1u);
+      atomicOr(G.errflag, 1u);
       for (uint64_t j = issued > (uint64_t)NS ? issued - NS : 0; j < issued; ++j)
         mbar_wait_bounded(&full[j % NS], (unsigned)((j / NS) & 1u));
     }
@@ -1270,6 +1315,7 @@ __global__ void __launch_bounds__(kBlock) k_kron(const KronParams K) {
     const V f = phi[j >> K.n_in];
     V a;
     if (in) {
+      if (!in_extent(j & lo, 1, K.in_cap, K.errflag)) continue;
       a = in[j & lo];
     } else {
       a.x = (T)1;
@@ -1278,7 +1324,7 @@ __global__ void __launch_bounds__(kBlock) k_kron(const KronParams K) {
     V y;
     y.x = s * (a.x * f.x - a.y * f.y);
     y.y = s * (a.x * f.y + a.y * f.x);
-    out[j] = y;
+    if (in_extent(j, 1, K.out_cap, K.errflag)) out[j] = y;
   }
 }
 

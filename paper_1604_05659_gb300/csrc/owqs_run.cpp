@@ -127,9 +127,15 @@ class Runner {
   std::vector<char> in_group;  // per measurement: not the first of a pass group
   owqs_status err = OWQS_OK;
 
-  void begin(const void* in0, uint64_t in_elems, void* out_final) {
+  // in0: the input array (nullptr: virtual input) of in_elems amplitudes;
+  // out_final: the output array of out_elems amplitudes
+  void begin(const void* in0, uint64_t in_elems, void* out_final, uint64_t out_elems) {
     cur_in_ = in0;
     out_final_ = out_final;
+    in0_ = in0;
+    in0_cap_ = in_elems;
+    out_cap_ = out_elems;
+    buf_cap_ = rc_.buf_bytes / (dtype_ == OWQS_C64 ? 8 : 16);
     pass_i_ = 0;
     sel_ = 0;
     prev_slot_ = -1;
@@ -154,6 +160,8 @@ class Runner {
     if (!cur_in_) it.P.vdiag = vdiag;
     it.P.in = cur_in_;
     it.P.out = rc_.buf[sel_];
+    it.P.in_cap = in_cap();
+    it.P.out_cap = buf_cap_;
     sel_ ^= 1;
     it.P.norm_in = prev_slot_;
     it.P.norm_out = mode_ == OWQS_MODE_OWQS ? pass_i_ + 1 : -1;
@@ -199,6 +207,8 @@ class Runner {
     it.G.thresh = thresh_;
     it.G.in = cur_in_;
     it.G.out = rc_.buf[sel_];
+    it.G.in_cap = in_cap();
+    it.G.out_cap = buf_cap_;
     sel_ ^= 1;
     it.G.norm_in = prev_slot_;
     it.G.norm_out = mode_ == OWQS_MODE_OWQS ? pass_i_ + 1 : -1;
@@ -227,6 +237,9 @@ class Runner {
     it.type = 5;
     it.Kp.in = cur_in_;
     it.Kp.out = rc_.buf[sel_];
+    it.Kp.in_cap = in_cap();
+    it.Kp.out_cap = buf_cap_;
+    it.Kp.errflag = rc_.counter + 1;
     sel_ ^= 1;
     it.Kp.phi = phi;
     it.Kp.norms = rc_.norms;
@@ -256,6 +269,7 @@ class Runner {
     it.L.bytes = (cur_in_ ? std::ldexp(1.0, d.n_in) : 0.0) * (dtype_ == OWQS_C64 ? 8.0 : 16.0);
     it.P.in = cur_in_;
     it.P.out = nullptr;
+    it.P.in_cap = in_cap();
     it.P.norm_in = prev_slot_;
     it.P.norm_out = K_ + 2 + 2 * pass_i_;
     it.P.edev = edev_;
@@ -278,6 +292,8 @@ class Runner {
     if (!cur_in_) it.P.vdiag = vdiag;
     it.P.in = cur_in_;
     it.P.out = out_final_;
+    it.P.in_cap = in_cap();
+    it.P.out_cap = out_cap_;
     it.P.norm_in = mode_ == OWQS_MODE_OWQS ? prev_slot_ : -1;
     it.P.norm_out = K_ + 1;
     issue(it);
@@ -301,6 +317,8 @@ class Runner {
   }
 
  private:
+  // elements of the array the next launch reads (0: virtual input)
+  uint64_t in_cap() const { return cur_in_ == nullptr ? 0 : (cur_in_ == in0_ ? in0_cap_ : buf_cap_); }
   void fill_common(PassParams& P) {
     P.norms = rc_.norms;
     P.partials = rc_.partials;
@@ -329,6 +347,8 @@ class Runner {
   const double* w1dev_ = nullptr;
   const double* edev_ = nullptr;
   int prev_slot_ = -1;
+  const void* in0_ = nullptr;
+  uint64_t in0_cap_ = 0, out_cap_ = 0, buf_cap_ = 0;  // buffer extents (bounds-checked builds)
 };
 
 // sampled outcomes: the previous measure pass is launched, then the two
@@ -509,9 +529,11 @@ static owqs_status finish(Pattern& p, const owqs_run_opts* o, RunCache* rc, cons
   if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, rc->counter + 1, sizeof(flag), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "run");
-  if (flag) {  // a device-side wait gave up: blocks skipped the reduction
+  if (flag) {  // a device-side wait gave up (bit 0; blocks skipped the reduction) or a bounds check failed (bit 1)
     cudaMemsetAsync(rc->counter, 0, 2 * sizeof(unsigned int), s);
     cudaStreamSynchronize(s);
+    if (flag & 2u)
+      return set_error(OWQS_ERR_CUDA, "a kernel access fell outside its buffer (bounds-checked build); results are invalid");
     return set_error(OWQS_ERR_TIMEOUT, "a device-side wait in a pass kernel gave up; results are invalid");
   }
   const double thresh = o->dtype == OWQS_C128 ? 1e-24 : 1e-12;
@@ -664,7 +686,7 @@ static owqs_status sample_on_device(Pattern& p, const owqs_run_opts* o, RunCache
   if (ce != cudaSuccess) return cuda_fail(ce, "sampling tables");
 
   Runner R(p, *rc, o->dtype, o->mode, s);
-  R.begin(pr.in_dev, pr.in_elems, pr.out_dev);
+  R.begin(pr.in_dev, pr.in_elems, pr.out_dev, pr.out_elems);
   for (size_t i = 0; i < meas.size(); ++i) {
     const PassDesc& d = *meas[i];
     DecideParams D;
@@ -761,7 +783,7 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
     }
     Runner R(p, *rc, o->dtype, o->mode, s);
     R.immediate = true;
-    R.begin(pr.in_dev, pr.in_elems, pr.out_dev);
+    R.begin(pr.in_dev, pr.in_elems, pr.out_dev, pr.out_elems);
     SampledSource src(R, *rc, s, o->seed);
     st = compile_schedule(p, o->mode, src, pr.passes);
     if (st != OWQS_OK) return st;
@@ -780,7 +802,7 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
       if (d.kind == 0) outcome_of_pass.push_back(d.outcome);
     Runner R(p, *rc, o->dtype, o->mode, s);
     R.vdiag = vdiag;
-    R.begin(pr.in_dev, pr.in_elems, pr.out_dev);
+    R.begin(pr.in_dev, pr.in_elems, pr.out_dev, pr.out_elems);
     for (size_t i = 0; i < pr.passes.size(); ++i) {
       const PassDesc& d = pr.passes[i];
       GroupParams G;
@@ -840,10 +862,26 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
           break;
         }
       long long limit = 0;
+      uint64_t shrink = 0;
       if (stall && take_test_stall(&limit)) {
         if (stall->type == 4) stall->G.stall_limit = limit;
         else stall->P.stall_limit = limit;
         st = replay(rc, R, std::string(), false, s);  // direct launches, no graph
+      } else if (take_test_shrink(&shrink)) {
+        // test hook: every buffer extent the launches carry is `shrink`
+        // amplitudes short (only bounds-checked builds read the extents)
+        auto cut = [shrink](uint64_t& cap) {
+          if (cap) cap = cap > shrink ? cap - shrink : 1;
+        };
+        for (Item& it : R.items) {
+          cut(it.P.in_cap);
+          cut(it.P.out_cap);
+          cut(it.G.in_cap);
+          cut(it.G.out_cap);
+          cut(it.Kp.in_cap);
+          cut(it.Kp.out_cap);
+        }
+        st = replay(rc, R, std::string(), false, s);
       } else {
         std::string key = graph_key(p, o, pr.in_dev, pr.out_dev, outcomes);
         if (prod)
@@ -869,6 +907,17 @@ using namespace owqs;
 namespace owqs {
 static std::atomic<int> g_test_stall_runs{0};
 static std::atomic<long long> g_test_stall_limit{0};
+static std::atomic<int> g_test_shrink_runs{0};
+static std::atomic<uint64_t> g_test_shrink_elems{0};
+
+int take_test_shrink(uint64_t* elems) {
+  int n = g_test_shrink_runs.load();
+  while (n > 0 && !g_test_shrink_runs.compare_exchange_weak(n, n - 1)) {
+  }
+  if (n <= 0) return 0;
+  *elems = g_test_shrink_elems.load();
+  return 1;
+}
 
 int take_test_stall(long long* limit) {
   int n = g_test_stall_runs.load();
@@ -916,6 +965,14 @@ owqs_status owqs_run_product(owqs_pattern* h, const owqs_run_opts* o, uint32_t n
     return set_error(OWQS_ERR_NOT_DETERMINISTIC, "EOWQS: the open graph has no gflow (Section 4.5)");
   return run_impl(h->p, o, nullptr, psi_out, outcomes, probs, nullptr, nullptr, nullptr, 0, nullptr, 0, nullptr,
                   &prod);
+}
+
+owqs_status owqs_test_shrink_extents(uint32_t runs, uint64_t elems) {
+  clear_error();
+  if (runs && elems == 0) return set_error(OWQS_ERR_ARG, "elems must be positive");
+  g_test_shrink_elems.store(elems);
+  g_test_shrink_runs.store((int)runs);
+  return OWQS_OK;
 }
 
 owqs_status owqs_test_wait_timeout(uint32_t runs, uint64_t limit_cycles) {

@@ -138,14 +138,17 @@ static owqs_status run_static(Pattern& p, const owqs_run_opts* o, const void* ps
     P.errflag = counter + 1;
     P.thresh = thresh;
     P.in = cur;
+    P.in_cap = cur == nullptr ? 0 : (cur == psi_in ? in_elems : max_elems);
     if (d.kind == 0) {
       P.out = buf[i & 1];
+      P.out_cap = max_elems;
       P.norm_in = prev;
       P.norm_out = mode == OWQS_MODE_OWQS ? i + 1 : -1;
       prev = P.norm_out;
       ++i;
     } else {
       P.out = psi_out;
+      P.out_cap = 1ull << p.outputs.size();
       P.norm_in = mode == OWQS_MODE_OWQS ? prev : -1;
       P.norm_out = K + 1;
     }
@@ -159,6 +162,8 @@ static owqs_status run_static(Pattern& p, const owqs_run_opts* o, const void* ps
   if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, counter + 1, sizeof(flag), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_err(e, "static run");
+  if (flag & 2u)
+    return set_error(OWQS_ERR_CUDA, "a kernel access fell outside its buffer (bounds-checked build); results are invalid");
   if (flag) return set_error(OWQS_ERR_TIMEOUT, "a device-side wait in a pass kernel gave up; results are invalid");
 
   st = OWQS_OK;

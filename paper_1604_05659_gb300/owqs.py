@@ -126,6 +126,7 @@ EXPORTS = {
     "owqs_find_flow": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_int32),
                                  C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32)]),
     "owqs_test_wait_timeout": (C.c_int, [C.c_uint32, C.c_uint64]),
+    "owqs_test_shrink_extents": (C.c_int, [C.c_uint32, C.c_uint64]),
     "owqs_describe_launches": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.POINTER(C.c_uint8),
                                          C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                          C.c_uint32, C.POINTER(C.c_uint32)]),
@@ -446,6 +447,12 @@ def last_error() -> str:
 def test_wait_timeout(runs: int, limit_cycles: int = 2_000_000):
     """Make the next `runs` runs give up on a device-side wait (test hook)."""
     _check(library().owqs_test_wait_timeout(runs, limit_cycles))
+
+
+def test_shrink_extents(runs: int, elems: int):
+    """Make the next `runs` runs carry buffer extents `elems` amplitudes short
+    (test hook; only the bounds-checked build reads them)."""
+    _check(library().owqs_test_shrink_extents(runs, elems))
 
 
 def run_batch(items, *, dtype: str = "c128", column_block: int = 0, stream=None, use_graph: bool = True,
