@@ -526,7 +526,7 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
       st = owqs_unitary(items[i].pattern, &ro, items[i].outcomes, items[i].out, nullptr);
     }
     if (st != OWQS_OK) return st;
-    launches += 1 + (uint32_t)items[i].pattern->p.meas_qubit.size();
+    launches += last_launch_count(items[i].pattern->p, items[i].psi_in == nullptr);
   }
 
   // overlaps with reference items

@@ -65,6 +65,9 @@ bool has_gflow(Pattern& p);
 // the branch overlaps themselves)
 owqs_status run_unchecked(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
                           uint8_t* outcomes, double* probs);
+// kernels launched by the pattern's last forced-outcome run (unitary: of its
+// last owqs_unitary call)
+uint32_t last_launch_count(Pattern& p, bool unitary);
 
 // peak live width and amplitude updates of the active order (host)
 void order_stats(const Pattern& p, uint32_t* peak_live, uint64_t* amp_updates);

@@ -1020,6 +1020,15 @@ static owqs::Pattern& augmented(owqs::Pattern& p) {
   return *a;
 }
 
+extern "C++" {
+namespace owqs {
+uint32_t last_launch_count(Pattern& p, bool unitary) {
+  Pattern& q = unitary ? augmented(p) : p;
+  return q.cache ? q.cache->last_launches : 0u;
+}
+}  // namespace owqs
+}
+
 owqs_status owqs_unitary(owqs_pattern* h, const owqs_run_opts* o, const uint8_t* outcomes, void* U,
                          double* frob2) {
   clear_error();
