@@ -13,17 +13,23 @@
 // owqs_run / owqs_unitary.  An optional overlap kernel reduces <out_ref|out>
 // per item on the device.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "owqs_internal.h"
 
 namespace owqs {
+
+// host threads (each with its own stream) that run the wide items of
+// different patterns side by side
+constexpr size_t kWideWorkers = 8;
 
 struct BPass {
   int32_t n_in, r, b, n_out;  // b < 0: final pass
@@ -504,18 +510,35 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
     ++launches;
   }
 
-  // wide items: the pass kernels
+  // wide items: the pass kernels.  Items of different patterns are
+  // independent (each pattern has its own workspace), so they run on up to
+  // kWideWorkers host threads, each with its own stream: the many small
+  // launches of items just too wide for shared memory then overlap on the
+  // GPU.  The items of one pattern stay in order on one thread.
   uint32_t hbm = 0;
-  for (uint32_t i = 0; i < n; ++i) {
-    if (on_chip[i]) continue;
-    ++hbm;
+  std::vector<std::vector<uint32_t>> by_pattern;
+  {
+    std::map<const owqs_pattern*, size_t> slot;
+    for (uint32_t i = 0; i < n; ++i) {
+      if (on_chip[i]) continue;
+      ++hbm;
+      auto it = slot.find(items[i].pattern);
+      if (it == slot.end()) {
+        slot[items[i].pattern] = by_pattern.size();
+        by_pattern.push_back({i});
+      } else {
+        by_pattern[it->second].push_back(i);
+      }
+    }
+  }
+  auto run_wide = [&](uint32_t i, cudaStream_t ws) -> owqs_status {
     owqs_run_opts ro;
     std::memset(&ro, 0, sizeof(ro));
     ro.dtype = o->dtype;
     ro.mode = OWQS_MODE_EOWQS;
     ro.policy = items[i].outcomes ? OWQS_OUTCOME_FORCED : OWQS_OUTCOME_ZERO;
     ro.io = OWQS_IO_DEVICE;
-    ro.stream = o->stream;
+    ro.stream = ws;
     ro.use_graph = o->use_graph;
     owqs_status st;
     if (items[i].psi_in) {
@@ -525,8 +548,68 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
     } else {
       st = owqs_unitary(items[i].pattern, &ro, items[i].outcomes, items[i].out, nullptr);
     }
-    if (st != OWQS_OK) return st;
-    launches += last_launch_count(items[i].pattern->p, items[i].psi_in == nullptr);
+    return st;
+  };
+  const int nworkers = (int)std::min<size_t>(kWideWorkers, by_pattern.size());
+  if (nworkers <= 1) {
+    for (const auto& grp : by_pattern)
+      for (uint32_t i : grp) {
+        owqs_status st = run_wide(i, s);
+        if (st != OWQS_OK) return st;
+        launches += last_launch_count(items[i].pattern->p, items[i].psi_in == nullptr);
+      }
+  } else {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    cudaEvent_t start = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(start, s);  // work queued before this call comes first
+    if (e != cudaSuccess) {
+      if (start) cudaEventDestroy(start);
+      return bfail(e, "wide item streams");
+    }
+    // launch settings that are read lazily, read once here before the workers
+    int lg = 0, hint = 0;
+    (void)max_grid();
+    (void)tma_enabled();
+    (void)group_enabled();
+    fast_config(OWQS_C64, &lg, &hint);
+    fast_config(OWQS_C128, &lg, &hint);
+    std::atomic<size_t> next{0};
+    std::atomic<uint32_t> wl{0};
+    std::vector<owqs_status> wst((size_t)nworkers, OWQS_OK);
+    std::vector<std::string> wmsg((size_t)nworkers);
+    auto worker = [&](int w) {
+      cudaStream_t ws = nullptr;
+      cudaError_t we = cudaSetDevice(dev);
+      if (we == cudaSuccess) we = cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking);
+      if (we == cudaSuccess) we = cudaStreamWaitEvent(ws, start, 0);
+      if (we != cudaSuccess) {
+        wst[(size_t)w] = we == cudaErrorMemoryAllocation ? OWQS_ERR_OOM : OWQS_ERR_CUDA;
+        wmsg[(size_t)w] = std::string("wide item stream: ") + cudaGetErrorString(we);
+      }
+      for (size_t g; wst[(size_t)w] == OWQS_OK && (g = next.fetch_add(1)) < by_pattern.size();)
+        for (uint32_t i : by_pattern[g]) {
+          const owqs_status st = run_wide(i, ws);
+          if (st != OWQS_OK) {
+            wst[(size_t)w] = st;
+            wmsg[(size_t)w] = owqs_last_error();
+            break;
+          }
+          wl += last_launch_count(items[i].pattern->p, items[i].psi_in == nullptr);
+        }
+      if (ws) {
+        cudaStreamSynchronize(ws);
+        cudaStreamDestroy(ws);
+      }
+    };
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nworkers; ++w) pool.emplace_back(worker, w);
+    for (auto& t : pool) t.join();
+    cudaEventDestroy(start);
+    for (int w = 0; w < nworkers; ++w)
+      if (wst[(size_t)w] != OWQS_OK) return set_error(wst[(size_t)w], wmsg[(size_t)w]);
+    launches += wl.load();
   }
 
   // overlaps with reference items
