@@ -240,9 +240,12 @@ typedef struct {
   uint32_t flags;     /* OWQS_RUN_HOST_SAMPLING: draw sampled outcomes on the host,
                          one device-to-host read per measurement (otherwise they are
                          drawn on the device whenever no X or Z with a signal comes
-                         before the last measurement, e.g. standard form)            */
+                         before the last measurement, e.g. standard form).
+                         OWQS_RUN_PER_PASS: one kernel per pass even when every array
+                         of a forced or zero-outcome run fits 2^8 amplitudes (such
+                         runs otherwise execute in one single-block kernel)          */
 } owqs_run_opts;
-enum { OWQS_RUN_HOST_SAMPLING = 1 };
+enum { OWQS_RUN_HOST_SAMPLING = 1, OWQS_RUN_PER_PASS = 2 };
 
 /* Simulate the pattern under its active order and return the output state.
  *   psi_in    2^|I| amplitudes (bit k = inputs[k]); NULL = |+> on every input

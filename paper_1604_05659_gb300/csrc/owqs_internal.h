@@ -168,7 +168,7 @@ struct PassParams {
 
 enum KernelKind {
   KK_FAST = 0, KK_GENERIC = 1, KK_FINAL = 2, KK_NORM = 3, KK_PROB = 4, KK_TMA = 5, KK_DECIDE = 7,
-  KK_GROUP = 8, KK_KRON = 9
+  KK_GROUP = 8, KK_KRON = 9, KK_SMALL = 10
 };
 
 
@@ -287,6 +287,15 @@ void plan_pass(const PassDesc& d, int dtype, bool virt_in, PassParams& P, Launch
 
 // device launches (owqs_kernels.cu)
 cudaError_t launch_pass(const PassParams& P, const LaunchPlan& L, int dtype, cudaStream_t s);
+
+// A whole run in one block when every array of the run has at most
+// 2^kSmallLog amplitudes and it has at most kSmallMaxPasses passes (k_small): passes_dev holds the run's passes, the
+// final pass last, planned as for the per-pass kernels (norm slots, scales,
+// the first pass's input, the final pass's output); input_norm: slot 0 first
+// gets the input vector's squared norm.
+constexpr int kSmallLog = 8;
+constexpr int kSmallMaxPasses = 160;  // the passes sit in shared memory
+cudaError_t launch_small(const PassParams* passes_dev, int npass, int input_norm, int dtype, cudaStream_t s);
 
 // Device-drawn outcome of one measurement (sampled policy, k_decide)
 struct DecideParams {

@@ -169,12 +169,15 @@ __device__ __forceinline__ void finish_slots(double* partials, unsigned int* cou
 // of a unitary at once).  MODE 0 measure, 1 the two outcome probabilities
 // only, 2 final pass (corrections + output order).
 // ---------------------------------------------------------------------------
+// One sweep of the generic pass over outputs j0, j0 + stride, ... (in and
+// out may point to global or shared memory); the squared norms (MODE 1: of
+// both outcomes) are added to acc.  c: the previous array's 1/sqrt(N).
 template <typename T, int MODE, int VIRT>
-__global__ void __launch_bounds__(kBlock) k_generic(const PassParams P) {
+__device__ __forceinline__ void generic_sweep(const PassParams& P, const typename Cplx<T>::V* __restrict__ in,
+                                              typename Cplx<T>::V* __restrict__ out, uint64_t j0, uint64_t stride,
+                                              double c, double (&acc)[2]) {
   using V = typename Cplx<T>::V;
-  const V* __restrict__ in = reinterpret_cast<const V*>(P.in);
-  V* __restrict__ out = reinterpret_cast<V*>(P.out);
-  const double c = prev_scale(P);
+  if (j0 >= (1ull << P.n_out)) return;
   const T sc = (T)(P.scale * c);
   const double2 w1 = pass_w1(P);
   const T wr = (T)(P.scale * c * w1.x), wi = (T)(P.scale * c * w1.y);
@@ -205,11 +208,9 @@ __global__ void __launch_bounds__(kBlock) k_generic(const PassParams P) {
     if (qsign(P, k)) x.x = -x.x, x.y = -x.y;
     return x;
   };
-  double acc[2] = {0.0, 0.0};
   T part[2] = {(T)0, (T)0};
   int cnt = 0;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nout; j += stride) {
+  for (uint64_t j = j0; j < nout; j += stride) {
     if (MODE == 2) {
       uint64_t k = j;
       if (!P.identity_perm) {
@@ -247,6 +248,15 @@ __global__ void __launch_bounds__(kBlock) k_generic(const PassParams P) {
   }
   acc[0] += (double)part[0];
   acc[1] += (double)part[1];
+}
+
+template <typename T, int MODE, int VIRT>
+__global__ void __launch_bounds__(kBlock) k_generic(const PassParams P) {
+  using V = typename Cplx<T>::V;
+  double acc[2] = {0.0, 0.0};
+  generic_sweep<T, MODE, VIRT>(P, reinterpret_cast<const V*>(P.in), reinterpret_cast<V*>(P.out),
+                               (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x,
+                               prev_scale(P), acc);
   if (P.norm_out >= 0) {
     if (MODE == 1) {
       reduce_to_slots<2>(acc, P.partials, P.counter, P.norms, P.norm_out);
@@ -255,6 +265,102 @@ __global__ void __launch_bounds__(kBlock) k_generic(const PassParams P) {
       reduce_to_slots<1>(a1, P.partials, P.counter, P.norms, P.norm_out);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// A whole run of a small pattern in one warp (every array of the run at most
+// 2^kSmallLog amplitudes and at most kSmallMaxPasses passes, where one launch
+// per pass would be mostly launch latency).  The passes (planned exactly as
+// for the per-pass kernels) are first copied into shared memory; each pass
+// reads the previous pass's output from shared memory (the first reads the
+// input vector or the virtual input) and writes shared memory (the final
+// pass writes the output vector).  After each measurement the warp adds the
+// squared norms in FP64 (a shuffle tree: every lane holds the total), lane 0
+// stores the slot and every lane keeps the next pass's 1/sqrt(N).  One warp:
+// the arrays are at most a few hundred amplitudes, the complex128 arithmetic
+// is bound by the SM's FP64 pipe, not by warps, and no block barrier is
+// needed.  input_norm: slot 0 first gets the input vector's squared norm.
+// ---------------------------------------------------------------------------
+constexpr int kSmallBlock = 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSmallBlock) k_small(const PassParams* __restrict__ passes, int npass,
+                                                        int input_norm) {
+  using V = typename Cplx<T>::V;
+  static_assert(sizeof(PassParams) % 16 == 0, "copied as 16-byte words");
+  extern __shared__ __align__(16) unsigned char dsm[];
+  PassParams* sp = reinterpret_cast<PassParams*>(dsm);  // npass entries
+  __shared__ V buf[2][1 << kSmallLog];
+  const int lane = threadIdx.x;
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(passes);
+    uint4* dst = reinterpret_cast<uint4*>(sp);
+    const int nw = npass * (int)(sizeof(PassParams) / 16);
+    for (int k = lane; k < nw; k += 32) dst[k] = src[k];
+  }
+  __syncwarp();
+  int slast = -1;      // the last stored slot
+  double cnext = 1.0;  // and its 1/sqrt(N)
+  auto keep = [&](const PassParams& P, int slot, double t) {
+    if (lane == 0) P.norms[slot] = t;
+    cnext = (t >= P.thresh && t > 0.0) ? 1.0 / sqrt(t) : 0.0;
+    slast = slot;
+  };
+  if (input_norm) {
+    const PassParams& P0 = sp[0];
+    const V* in = reinterpret_cast<const V*>(P0.in);
+    double a = 0.0;
+    for (uint64_t i = lane; i < (1ull << P0.n_in); i += 32)
+      a += (double)in[i].x * (double)in[i].x + (double)in[i].y * (double)in[i].y;
+    keep(P0, 0, warp_sum(a));
+  }
+  for (int p = 0; p < npass; ++p) {
+    const PassParams& P = sp[p];
+    const bool last = p == npass - 1;
+    const V* in = p == 0 ? reinterpret_cast<const V*>(P.in) : buf[(p - 1) & 1];
+    V* out = last ? reinterpret_cast<V*>(P.out) : buf[p & 1];
+    const double c = P.norm_in < 0 ? 1.0 : (P.norm_in == slast ? cnext : prev_scale(P));
+    double acc[2] = {0.0, 0.0};
+    const int virt = (p == 0 && P.in == nullptr) ? (P.vdiag ? 2 : 1) : 0;
+    if (last) {
+      if (virt == 0) generic_sweep<T, 2, 0>(P, in, out, lane, 32, c, acc);
+      else if (virt == 1) generic_sweep<T, 2, 1>(P, in, out, lane, 32, c, acc);
+      else generic_sweep<T, 2, 2>(P, in, out, lane, 32, c, acc);
+    } else {
+      if (virt == 0) generic_sweep<T, 0, 0>(P, in, out, lane, 32, c, acc);
+      else if (virt == 1) generic_sweep<T, 0, 1>(P, in, out, lane, 32, c, acc);
+      else generic_sweep<T, 0, 2>(P, in, out, lane, 32, c, acc);
+    }
+    const double t = warp_sum(acc[0]);
+    if (P.norm_out >= 0) keep(P, P.norm_out, t);
+    __syncwarp();  // this pass's outputs are visible to the next
+  }
+}
+
+cudaError_t launch_small(const PassParams* passes_dev, int npass, int input_norm, int dtype, cudaStream_t s) {
+  constexpr int kMaxDyn = kSmallMaxPasses * (int)sizeof(PassParams);
+  static bool ready = false;
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ready) {
+      cudaError_t e = cudaFuncSetAttribute(k_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn);
+      if (e != cudaSuccess) return e;
+      ready = true;
+    }
+  }
+  if (npass < 1 || npass > kSmallMaxPasses) return cudaErrorInvalidValue;
+  const size_t dyn = (size_t)npass * sizeof(PassParams);
+  if (dtype == OWQS_C64) k_small<float><<<1, kSmallBlock, dyn, s>>>(passes_dev, npass, input_norm);
+  else k_small<double><<<1, kSmallBlock, dyn, s>>>(passes_dev, npass, input_norm);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

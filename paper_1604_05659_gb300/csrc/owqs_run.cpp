@@ -30,6 +30,9 @@ struct RunCache {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::string gkey;
+  void* small_dev = nullptr;  // the passes of a single-block run, and their host copy
+  size_t small_bytes = 0;
+  std::vector<unsigned char> small_host;
   std::vector<double> h_norms;
   uint32_t last_launches = 0;
 
@@ -39,7 +42,8 @@ struct RunCache {
     if (device >= 0 && cur != device) cudaSetDevice(device);
     if (gexec) cudaGraphExecDestroy(gexec);
     if (cap) cudaStreamDestroy(cap);
-    for (void* p : {buf[0], buf[1], in_stage, out_stage, (void*)norms, (void*)partials, (void*)counter, samp})
+    for (void* p : {buf[0], buf[1], in_stage, out_stage, (void*)norms, (void*)partials, (void*)counter, samp,
+                    small_dev})
       if (p) cudaFree(p);
     if (device >= 0 && cur >= 0 && cur != device) cudaSetDevice(cur);
   }
@@ -423,6 +427,16 @@ struct ProductInput {
   std::vector<const void*> vecs;
 };
 
+// A forced or zero-outcome run whose arrays all fit 2^kSmallLog amplitudes,
+// with at most kSmallMaxPasses passes, runs in one single-block kernel
+// (k_small) instead of one kernel per pass.
+static bool small_run_ok(const std::vector<PassDesc>& passes) {
+  if (passes.empty() || passes.size() > (size_t)kSmallMaxPasses) return false;
+  for (const PassDesc& d : passes)
+    if (d.kind == 2 || d.n_in > kSmallLog || d.n_out > kSmallLog) return false;
+  return true;
+}
+
 // What the launch for passes[i] is: a factor join, the final pass, a group
 // of k measure passes (k >= 2; reads a materialised input array or the
 // virtual |+> input, not the diagonal input of a unitary) or a single
@@ -803,8 +817,14 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
     Runner R(p, *rc, o->dtype, o->mode, s);
     R.vdiag = vdiag;
     R.begin(pr.in_dev, pr.in_elems, pr.out_dev, pr.out_elems);
+    const bool small = !prod && !(o->flags & OWQS_RUN_PER_PASS) && small_run_ok(pr.passes);
     for (size_t i = 0; i < pr.passes.size(); ++i) {
       const PassDesc& d = pr.passes[i];
+      if (small) {  // planned one pass at a time, run in one kernel below
+        if (d.kind == 1) R.final_pass(d);
+        else R.measure(d);
+        continue;
+      }
       GroupParams G;
       LaunchPlan GL;
       int gk = 0;
@@ -829,7 +849,51 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
       if (e != cudaSuccess) return cuda_fail(e, "input copy");
     }
     rc->last_launches = (uint32_t)R.items.size();
-    if (prof_ms) {
+    if (small) {
+      std::vector<PassParams> ps;
+      int input_norm = 0;
+      for (const Item& it : R.items) {
+        if (it.type == 1) input_norm = 1;
+        else ps.push_back(it.P);
+      }
+      const size_t bytes = ps.size() * sizeof(PassParams);
+      if (rc->small_host.size() != bytes || std::memcmp(rc->small_host.data(), ps.data(), bytes) != 0) {
+        st = ensure_buf(rc->small_dev, rc->small_bytes, bytes, "small-run passes");
+        if (st != OWQS_OK) return st;
+        cudaError_t e = cudaMemcpyAsync(rc->small_dev, ps.data(), bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "small-run passes");
+        rc->small_host.assign(reinterpret_cast<const unsigned char*>(ps.data()),
+                              reinterpret_cast<const unsigned char*>(ps.data()) + bytes);
+      }
+      rc->last_launches = 1;
+      const PassParams* pd = reinterpret_cast<const PassParams*>(rc->small_dev);
+      if (prof_ms) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = launch_small(pd, (int)ps.size(), input_norm, o->dtype, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        float ms = 0;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (e != cudaSuccess) return cuda_fail(e, "profiled small run");
+        if (prof_cap > 0) {
+          prof_ms[0] = ms;
+          double by = 0.0;
+          for (const Item& it : R.items) by += it.L.bytes;
+          if (prof_bytes) prof_bytes[0] = by;
+          if (prof_kind) prof_kind[0] = (uint32_t)KK_SMALL;
+          if (prof_meas) prof_meas[0] = (uint32_t)K;
+        }
+        if (prof_n) *prof_n = 1;
+      } else {
+        cudaError_t e = launch_small(pd, (int)ps.size(), input_norm, o->dtype, s);
+        if (e != cudaSuccess) return cuda_fail(e, "small run");
+      }
+    } else if (prof_ms) {
       std::vector<cudaEvent_t> ev(2 * R.items.size());
       for (auto& x : ev)
         if (cudaEventCreate(&x) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaEventCreate");
@@ -1077,6 +1141,11 @@ owqs_status owqs_describe_launches(const owqs_pattern* h, uint32_t dtype, uint32
     ++n;
   };
   bool real = real_input != 0;
+  if (small_run_ok(passes)) {  // one single-block kernel for the whole run
+    put(KK_SMALL, 0, (uint32_t)h->p.meas_qubit.size());
+    *nlaunch = n;
+    return OWQS_OK;
+  }
   if (real) put(KK_NORM, 0, 0);  // the input norm (OWQS divides by it, EOWQS checks the output against it)
   for (size_t i = 0; i < passes.size(); ++i) {
     GroupParams G;

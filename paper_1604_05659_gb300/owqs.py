@@ -24,9 +24,10 @@ CMD_KIND = {"N": 0, "E": 1, "M": 2, "X": 3, "Z": 4}
 MODE = {"owqs": 0, "eowqs": 1}
 FLOW_CAUSAL, FLOW_GFLOW = 0, 1
 RUN_HOST_SAMPLING = 1
+RUN_PER_PASS = 2
 DTYPE = {"c64": 0, "c128": 1}
 POLICY = {"forced": 0, "sampled": 1, "zero": 2}
-KERNEL_KIND = {0: "fast_pass", 1: "generic_pass", 2: "final", 3: "norm", 4: "prob", 5: "tma_pass",
+KERNEL_KIND = {0: "fast_pass", 1: "generic_pass", 2: "final", 3: "norm", 4: "prob", 5: "tma_pass", 10: "small_run",
                7: "decide", 8: "group_pass", 9: "factor_join"}
 
 
@@ -295,12 +296,13 @@ class Handle:
     # -- device calls ----------------------------------------------------
     def run(self, psi_in=None, *, dtype: str = "c128", mode: str = "owqs", policy: str = "forced",
             outcomes=None, seed: int = 0, stream=None, use_graph: bool = True, out=None,
-            check: bool = True, host_sampling: bool = False):
+            check: bool = True, host_sampling: bool = False, per_pass: bool = False):
         """Run on the GPU.  psi_in: torch tensor on the GPU (complex64 for
         c64, complex128 for c128) or None for |+> inputs; returns
         (psi_out tensor, outcomes array, probs array, status).
         host_sampling: draw sampled outcomes on the host (one device read per
-        measurement) instead of on the device."""
+        measurement) instead of on the device.  per_pass: one kernel per pass
+        even for a run that fits the single-block kernel."""
         import torch
         tdt = torch.complex64 if dtype == "c64" else torch.complex128
         if psi_in is not None:
@@ -315,7 +317,8 @@ class Handle:
         probs = np.zeros(max(1, self.K), dtype=np.float64)
         s = stream if stream is not None else torch.cuda.current_stream(dev)
         opts = owqs_run_opts(DTYPE[dtype], MODE[mode], POLICY[policy], 0, seed, C.c_void_p(s.cuda_stream),
-                             int(use_graph), RUN_HOST_SAMPLING if host_sampling else 0)
+                             int(use_graph), (RUN_HOST_SAMPLING if host_sampling else 0) |
+                             (RUN_PER_PASS if per_pass else 0))
         st = library().owqs_run(self._h, C.byref(opts), C.c_void_p(psi_in.data_ptr() if psi_in is not None else 0),
                                 C.c_void_p(out.data_ptr()), oc.ctypes.data_as(C.POINTER(C.c_uint8)),
                                 probs.ctypes.data_as(C.POINTER(C.c_double)))
@@ -354,7 +357,8 @@ class Handle:
             _check(st)
         return out, oc[: self.K].copy(), probs[: self.K].copy(), st
 
-    def unitary(self, *, dtype: str = "c128", outcomes=None, stream=None, use_graph: bool = True, out=None):
+    def unitary(self, *, dtype: str = "c128", outcomes=None, stream=None, use_graph: bool = True, out=None,
+                per_pass: bool = False):
         """All basis columns of the forced branch as a matrix (2^|O| x 2^|I|,
         column-major as a flat tensor); returns (U, ||U||_F^2 / 2^|I|)."""
         import torch
@@ -364,7 +368,7 @@ class Handle:
         s = stream if stream is not None else torch.cuda.current_stream()
         policy = "zero" if outcomes is None else "forced"
         opts = owqs_run_opts(DTYPE[dtype], MODE["eowqs"], POLICY[policy], 0, 0, C.c_void_p(s.cuda_stream),
-                             int(use_graph), 0)
+                             int(use_graph), RUN_PER_PASS if per_pass else 0)
         f2 = C.c_double()
         _check(library().owqs_unitary(self._h, C.byref(opts), _outcome_buf(outcomes, self.K),
                                       C.c_void_p(out.data_ptr()), C.byref(f2)))

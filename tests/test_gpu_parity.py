@@ -46,13 +46,14 @@ def _oracle_for(h, p):
     return proa.reorder_commands(p, order) if p.is_standard() else p
 
 
-def _compare(env, p, psi, bits, dtype, mode, reorder=True, graph=True):
+def _compare(env, p, psi, bits, dtype, mode, reorder=True, graph=True, per_pass=False):
     torch, owqs = env
     h = owqs.load(p)
     if reorder and p.is_standard():
         h.reorder()
     op = _oracle_for(h, p) if reorder and p.is_standard() else p
-    out, oc, probs, st = h.run(_dev(torch, psi, dtype), dtype=dtype, mode=mode, outcomes=bits, use_graph=graph)
+    out, oc, probs, st = h.run(_dev(torch, psi, dtype), dtype=dtype, mode=mode, outcomes=bits, use_graph=graph,
+                               per_pass=per_pass)
     torch.cuda.synchronize()
     ref = substate.run(op, psi, outcomes=outcomes_by_label(p, bits), mode=mode)
     got = out.cpu().numpy().astype(np.complex128)
@@ -75,13 +76,48 @@ def _small_cases():
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("mode", ["owqs", "eowqs"])
-def test_small_patterns(env, dtype, mode):
+@pytest.mark.parametrize("per_pass", [False, True], ids=["one_kernel", "per_pass"])
+def test_small_patterns(env, dtype, mode, per_pass):
+    """Patterns whose arrays fit 2^8 amplitudes run in one single-block
+    kernel; per_pass forces one kernel per pass.  Both against the oracle."""
     rng = SplitMix64(101)
     for p in _small_cases():
         psi = random_state(rng, len(p.inputs))
         bits = rng.bits(p.K)
-        _compare(env, p, psi, bits, dtype, mode)
-        _compare(env, p, None, bits, dtype, mode)
+        _compare(env, p, psi, bits, dtype, mode, per_pass=per_pass)
+        _compare(env, p, None, bits, dtype, mode, per_pass=per_pass)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_small_run_is_one_launch(env, dtype):
+    """The single-block run: one launch where the planner says so, the same
+    outputs and probabilities as one kernel per pass, and the same for a
+    small unitary (the diagonal virtual input)."""
+    torch, owqs = env
+    rng = SplitMix64(111)
+    tol = 1e-13 if dtype == "c128" else 1e-6
+    for p in _small_cases():
+        h = owqs.load(p)
+        if p.is_standard():
+            h.reorder()
+        psi = _dev(torch, random_state(rng, len(p.inputs)), dtype)
+        bits = rng.bits(p.K)
+        plan = h.describe_launches(bits, dtype=dtype, real_input=True)
+        ms, _, kd, _ = h.profile(psi, dtype=dtype, outcomes=bits)
+        assert [owqs.KERNEL_KIND[int(k)] for k in kd] == [x[0] for x in plan], p.name
+        a, _, pa, _ = h.run(psi, dtype=dtype, outcomes=bits)
+        b, _, pb, _ = h.run(psi, dtype=dtype, outcomes=bits, per_pass=True)
+        assert torch.max(torch.abs(a - b)).item() <= tol and np.max(np.abs(pa - pb)) <= tol, p.name
+        if plan[0][0] == "small_run":
+            assert len(kd) == 1
+    p = circuit_to_pattern(3, random_jcz_circuit(3, 6, rng, cz_per_layer=1), "u3")
+    h = owqs.load(p)
+    h.reorder()
+    bits = rng.bits(p.K)
+    assert h.describe_launches(bits, dtype=dtype)[0][0] == "small_run"
+    ua, _ = h.unitary(dtype=dtype, outcomes=bits)
+    ub, _ = h.unitary(dtype=dtype, outcomes=bits, per_pass=True)
+    assert torch.max(torch.abs(ua - ub)).item() <= tol
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])

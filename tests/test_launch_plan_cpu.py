@@ -17,7 +17,11 @@ def owqs():
 
 
 def _check_cover(launches, K):
-    """Every measurement once, in order; groups of 2..12 measurements."""
+    """Every measurement once, in order; groups of 2..12 measurements; or the
+    whole run in one single-block kernel."""
+    if launches[0][0] == "small_run":
+        assert launches == [("small_run", 0, K)], launches
+        return
     at = 0
     for kind, first, n in launches:
         if n:
@@ -78,8 +82,10 @@ def test_group_eligibility_follows_the_tile_width(owqs):
     for complex64 (a warp's 4 KB tile), 2^11 for complex128 (a block's 32 KB
     tile).  Brickworks of 7..11 rows have live arrays of rows or rows + 1
     qubits; below the boundary the measurements run as single passes and
-    the first one reads the virtual input in the generic kernel, from it on
-    the first group reads the virtual input itself."""
+    the first one reads the virtual input in the generic kernel (or, with
+    every array at most 2^8 amplitudes, the whole run is one single-block
+    kernel); from the boundary on the first group reads the virtual input
+    itself."""
     first = {"c64": 9, "c128": 11}
     for rows in (7, 8, 9, 10, 11):
         wl = workloads.brickwork(rows, 6)
@@ -92,4 +98,8 @@ def test_group_eligibility_follows_the_tile_width(owqs):
                 ngroups = sum(1 for k, _, _ in plan if k == "group_pass")
                 assert (ngroups > 0) == (rows >= first[dtype]), (rows, dtype, real, plan[:3])
                 if not real:
-                    assert plan[0][0] == ("group_pass" if rows >= first[dtype] else "generic_pass"), (rows, dtype)
+                    # every array at most 2^8 amplitudes: the whole run is one kernel
+                    widest = max(max(d.n_in, d.n_out) for d in h.describe_passes(wl.outcomes))
+                    expect = ("group_pass" if rows >= first[dtype] else
+                              "small_run" if widest <= 8 else "generic_pass")
+                    assert plan[0][0] == expect, (rows, dtype, plan[:2])
