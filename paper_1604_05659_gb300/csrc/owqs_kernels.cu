@@ -1019,6 +1019,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
 
   auto issue = [&](uint64_t i) {  // lane 0 of the warp
     const int st = (int)(i % NS);
+    if (virt) {  // no input array: the stage only paces the loop
+      mbar_arrive(&full[st]);
+      return;
+    }
     float2* buf = reinterpret_cast<float2*>(wsm + st * STAGE);
     const uint64_t L0 = (gw + i * step) << LT;
     uint64_t ib = L0;
@@ -1037,15 +1041,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
 #pragma unroll
     for (int q = 0; q < M; ++q) ib = ins0(ib, sorted[q]);
 #ifdef OWQS_BOUNDS_CHECK
-    bool ok = !virt;
+    bool ok = true;
     for (int r = 0; r < G.nruns && ok; ++r) ok = in_extent(ib + G.runoff[r], G.runlen, G.in_cap, G.errflag);
-#else
-    const bool ok = !virt;
-#endif
-    if (!ok) {  // the virtual input, or (checked builds) a run outside the input: no copy
+    if (!ok) {  // a run outside the input: no copy, the run reports the error
       mbar_arrive(&full[st]);
       return;
     }
+#endif
     mbar_expect_tx(&full[st], (unsigned)STAGE);
     const unsigned rbytes = G.runlen * (unsigned)sizeof(float2);
     for (int r = 0; r < G.nruns; ++r) bulk_g2s(buf + r * G.runlen, in + ib + G.runoff[r], rbytes, &full[st]);
@@ -1256,16 +1258,18 @@ __global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G) {
       w |= ((G.pass[j].zb ^ par64(L0 & G.pass[j].afree)) & 1u) << (2 * j + 1);
     }
     signs[st] = w;
-#ifdef OWQS_BOUNDS_CHECK
-    bool ok = !virt;
-    for (int r = 0; r < G.nruns && ok; ++r) ok = in_extent(ib + G.runoff[r], G.runlen, G.in_cap, G.errflag);
-#else
-    const bool ok = !virt;
-#endif
-    if (!ok) {  // as in k_group
+    if (virt) {  // as in k_group
       mbar_arrive(&full[st]);
       return;
     }
+#ifdef OWQS_BOUNDS_CHECK
+    bool ok = true;
+    for (int r = 0; r < G.nruns && ok; ++r) ok = in_extent(ib + G.runoff[r], G.runlen, G.in_cap, G.errflag);
+    if (!ok) {
+      mbar_arrive(&full[st]);
+      return;
+    }
+#endif
     mbar_expect_tx(&full[st], NC * RUN);
     const unsigned rbytes = G.runlen * (unsigned)sizeof(double2);
     for (int r = 0; r < G.nruns; ++r) bulk_g2s(buf + r * G.runlen, in + ib + G.runoff[r], rbytes, &full[st]);
