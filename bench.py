@@ -51,8 +51,8 @@ FALLBACK_HBM_GBS = 6800.0
 # 2148.1 MB read + 2098.8 MB written) and c128 k_group64<3> (2^28 complex128;
 # 4299.1 MB read + 4247.6 MB written).  profiles/k_group_c64_brickwork28x40_dram.md,
 # profiles/k_group64_c128_brickwork26x8.md.
-NCU_TRAFFIC = {("96c287f5e75f9e0d", "c64"): (2147819776 + 2097235968 + 2147815936 + 2094480128 + 2147635712 + 2094625536) / 3.0,
-               ("96c287f5e75f9e0d", "c128"): (4299899136 + 4249785088 + 4299558656 + 4246345216 + 4298472704 + 4245789952) / 3.0}
+NCU_TRAFFIC = {("c22f4cb3373f8725", "c64"): (2147997184 + 2097326848 + 2148010496 + 2095295488 + 2148358912 + 2094445312) / 3.0,
+               ("c22f4cb3373f8725", "c128"): (4298644992 + 4248933120 + 4302609920 + 4246514176 + 4298497280 + 4245665536) / 3.0}
 # nominal GB300 FP64 rate (no measured FP64 peak exists for this machine)
 FP64_PEAK_TFLOPS = 1.25
 # FP64 flops per output amplitude of the complex128 pass: complex multiply-add
