@@ -103,3 +103,22 @@ def test_group_eligibility_follows_the_tile_width(owqs):
                     expect = ("group_pass" if rows >= first[dtype] else
                               "small_run" if widest <= 8 else "generic_pass")
                     assert plan[0][0] == expect, (rows, dtype, plan[:2])
+
+
+def test_small_run_boundary(owqs):
+    """The single-block run takes at most 160 passes (its pass table sits in
+    shared memory) and arrays of at most 2^8 amplitudes; beyond either the
+    run has one kernel per pass."""
+    from owqs_inputs.patterns import circuit_to_pattern, random_jcz_circuit
+    for depth, small in ((53, True), (54, False)):
+        p = circuit_to_pattern(3, random_jcz_circuit(3, depth, SplitMix64(5), cz_per_layer=1), "r3")
+        h = owqs.load(p)
+        h.reorder()
+        assert len(h.describe_passes(None)) == p.K + 1
+        plan = h.describe_launches(None, dtype="c64")
+        _check_cover(plan, p.K)
+        assert (plan[0][0] == "small_run") == small and (p.K + 1 <= 160) == small, (depth, p.K, plan[:2])
+    wl = workloads.brickwork(9, 4)   # arrays of 2^9 amplitudes
+    h = owqs.load(wl.pattern)
+    h.reorder()
+    assert h.describe_launches(wl.outcomes, dtype="c128")[0][0] != "small_run"
