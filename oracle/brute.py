@@ -44,7 +44,11 @@ def run(pattern, psi_in: Optional[np.ndarray] = None, outcomes=None, mode: str =
         tin = vin.reshape([2] * len(I))
         in_axes = [I[len(I) - 1 - a] for a in range(len(I))]
     else:
+        # no input qubit: a one-amplitude input multiplies the whole state
         tin = np.array(1.0 + 0j)
+        if psi_in is not None:
+            c = complex(np.asarray(psi_in, dtype=np.complex128).reshape(-1)[0])
+            tin = np.array(c / abs(c) if mode == "owqs" else c)
         in_axes = []
     # full register: axis q <-> label q
     others = [q for q in range(n) if q not in I]

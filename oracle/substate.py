@@ -149,6 +149,14 @@ def run(pattern, psi_in: Optional[np.ndarray] = None, outcomes=None, mode: str =
         s = from_flat(I, vec)
         for q in I:
             owner[q] = s
+    elif psi_in is not None:
+        # no input qubit: the input is a state over no qubit, one amplitude,
+        # and the initial state is that amplitude times |+> on every qubit
+        # (Section 4.1); normalised in OWQS like any input
+        vec = np.asarray(psi_in, dtype=np.complex128).reshape(-1)
+        if vec.size != 1:
+            raise ValueError("psi_in has the wrong length")
+        gfactor *= vec[0] / abs(vec[0]) if mode == "owqs" else vec[0]
 
     def ensure(q):
         if q not in owner:

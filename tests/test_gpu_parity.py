@@ -374,3 +374,36 @@ def test_pass_groups(env, dtype):
         plan = h.describe_launches(bits, dtype=dtype)
         assert [owqs.KERNEL_KIND[int(k)] for k in kd] == [x[0] for x in plan]
         assert list(h.profile_meas) == [x[2] for x in plan]
+
+
+def _degenerate_patterns():
+    """No measurement (E only; no command at all with permuted outputs; a
+    new qubit entangled and kept), and no input (the first pass has a
+    one-amplitude input)."""
+    return [Pattern(2, [0, 1], [0, 1], [E(0, 1)], "cz_only"),
+            Pattern(3, [0, 1, 2], [2, 0, 1], [], "permutation_only"),
+            Pattern(3, [0, 1], [0, 1, 2], [N(2), E(0, 2), E(1, 2)], "prepare_only"),
+            Pattern(2, [], [1], [N(0), N(1), E(0, 1), M(0, 0.3)], "no_input"),
+            Pattern(3, [], [2], [N(0), N(1), N(2), E(0, 1), E(1, 2), M(0, 1.1), M(1, -0.4, sdom=(0,))],
+                    "no_input_two_measurements")]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("per_pass", [False, True], ids=["one_kernel", "per_pass"])
+def test_degenerate_patterns(env, dtype, per_pass):
+    torch, owqs = env
+    rng = SplitMix64(121)
+    for p in _degenerate_patterns():
+        h = owqs.load(p)
+        bits = rng.bits(p.K)
+        outs = outcomes_by_label(p, bits)
+        for psi in (random_state(rng, len(p.inputs)), None):
+            ref = substate.run(p, psi, outcomes=outs)
+            out, _, probs, st = h.run(_dev(torch, psi, dtype), dtype=dtype, outcomes=bits, per_pass=per_pass)
+            assert st == owqs.OK
+            got = out.cpu().numpy().astype(np.complex128)
+            err = phase_aligned_maxabs(ref.psi_out, got) if dtype == "c64" else float(np.max(np.abs(ref.psi_out - got)))
+            assert err <= TOL[dtype], (p.name, dtype, per_pass, err)
+            if p.K:
+                ref_p = np.array([ref.probs[q] for q in p.measured()])
+                assert np.max(np.abs(probs - ref_p)) <= (1e-12 if dtype == "c128" else 1e-5), p.name

@@ -452,3 +452,22 @@ def test_amplitude_update_count_closed_form():
         p = circuit_to_pattern(1, [("J", 0, 0.1 * k) for k in range(L)])
         pr = proa.reorder_commands(p, p.measured())
         assert counting.amplitude_updates(pr) == 12 * L + 2 + (2 if L >= 2 else 0)
+
+
+def test_no_input_qubit_takes_a_one_amplitude_input():
+    """A pattern without input qubits: its input is a state over no qubit,
+    one amplitude c, and the initial state is c times |+> on every qubit
+    (Section 4.1).  Both oracles then give c/|c| (OWQS: the input is
+    normalised, Eq. 4) or c (EOWQS) times the result from the default
+    input, and agree with each other."""
+    p = Pattern(3, [], [2], [N(0), N(1), N(2), E(0, 1), E(1, 2), M(0, 1.1), M(1, -0.4, sdom=(0,))], "no_input")
+    c = 0.6 - 0.8j
+    for mode in ("owqs", "eowqs"):
+        for bits in ([0, 0], [1, 0], [0, 1], [1, 1]):
+            outs = outcomes_by_label(p, bits)
+            base = substate.run(p, None, outcomes=outs, mode=mode).psi_out
+            ra = substate.run(p, np.array([c * 2.5]), outcomes=outs, mode=mode).psi_out
+            ob, _, _ = brute.run(p, np.array([c * 2.5]), outcomes=outs, mode=mode)
+            factor = c if mode == "owqs" else c * 2.5
+            assert np.allclose(ra, factor * base, atol=1e-14, rtol=0), (mode, bits)
+            assert np.allclose(ob, ra, atol=1e-13, rtol=0), (mode, bits)
