@@ -168,7 +168,7 @@ struct PassParams {
 
 enum KernelKind {
   KK_FAST = 0, KK_GENERIC = 1, KK_FINAL = 2, KK_NORM = 3, KK_PROB = 4, KK_TMA = 5, KK_DECIDE = 7,
-  KK_GROUP = 8, KK_KRON = 9, KK_SMALL = 10
+  KK_GROUP = 8, KK_KRON = 9, KK_SMALL = 10, KK_PROB_TMA = 11
 };
 
 

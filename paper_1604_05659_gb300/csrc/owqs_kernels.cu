@@ -566,7 +566,11 @@ struct TmaShape {
   static constexpr int SMEM = kTmaStages * STAGE_BYTES + kTmaStages * 8;
 };
 
-template <typename T, int CASE>
+// PROB: instead of the outputs, both outcome probabilities of the
+// measurement (sampled outcomes): the squared norms of x0' + e x1' and
+// x0' - e x1' (x0', x1' the sign-applied pair, e = e^{-i theta}) into slots
+// norm_out and norm_out + 1, as k_generic<T, 1, .> computes them.
+template <typename T, int CASE, bool PROB>
 __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
   if (P.stall_limit > 0) {
     stall_and_give_up(P.stall_limit, P.errflag);
@@ -584,6 +588,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
   const T sc = (T)(P.scale * c);
   const double2 w1 = pass_w1(P);
   const T wr = (T)(P.scale * c * w1.x), wi = (T)(P.scale * c * w1.y);
+  const T er = (T)(P.edev ? P.edev[0] : P.ere), ei = (T)(P.edev ? P.edev[1] : P.eim);
   const int b = P.b, nlo = P.nlo, nbc = P.n_out - P.nlo;
   const uint64_t inmask = (1ull << P.n_in) - 1ull;
   const uint64_t tiles = 1ull << (nlo - LTE);
@@ -619,7 +624,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
   if (threadIdx.x == 0)
     for (uint64_t i = 0; i < mine && i < (uint64_t)NS; ++i) issue(i);
 
-  NormAcc<T> acc;
+  NormAcc<T> acc, acc1;  // acc1: outcome 1 (PROB)
   uint64_t issued = mine < (uint64_t)NS ? mine : (uint64_t)NS;
   uint64_t i = 0;
   bool failed = false;
@@ -636,13 +641,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
     const uint64_t K0 = ins0(J, b);
     const uint32_t pz = P.c0 ^ par64(K0 & P.zmask);
     const uint32_t pa = P.zb ^ par64(K0 & P.amask);
-    T tacc = (T)0;
+    T tacc = (T)0, tacc1 = (T)0;
     for (uint64_t t = 0; t < (1ull << nbc); ++t) {
       const uint64_t dt = ins0(t << nlo, b);
       const uint32_t s0t = pz ^ par64(dt & P.zmask);
       const uint32_t s1t = s0t ^ pa ^ par64(dt & P.amask);
       V* o = out + J + (t << nlo);
-      if (!in_extent(J + (t << nlo), TE, P.out_cap, P.errflag)) continue;
+      if (!PROB && !in_extent(J + (t << nlo), TE, P.out_cap, P.errflag)) continue;
 #pragma unroll 2
       for (int e = threadIdx.x * VE; e < TE; e += kBlock * VE) {
         V x0[VE], x1[VE], y[VE];
@@ -654,20 +659,32 @@ __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
           x1[v] = CASE == 0 ? buf[d0 | (1 << b)] : (CASE == 1 ? buf[TE + jj] : buf[jj]);
           const uint32_t s0 = (s0t ^ __popc((uint32_t)d0 & zlo)) & 1u;
           const uint32_t s1 = (s1t ^ __popc((uint32_t)d0 & zlo) ^ __popc((uint32_t)d0 & alo)) & 1u;
-          const T a = s0 ? -sc : sc;
-          const T br = s1 ? -wr : wr, bi = s1 ? -wi : wi;
-          y[v].x = a * x0[v].x + br * x1[v].x - bi * x1[v].y;
-          y[v].y = a * x0[v].y + br * x1[v].y + bi * x1[v].x;
-          tacc += y[v].x * y[v].x + y[v].y * y[v].y;
+          if constexpr (PROB) {
+            const T v0x = s0 ? -x0[v].x : x0[v].x, v0y = s0 ? -x0[v].y : x0[v].y;
+            T ux = er * x1[v].x - ei * x1[v].y, uy = er * x1[v].y + ei * x1[v].x;
+            if (s1) ux = -ux, uy = -uy;
+            const T a0x = v0x + ux, a0y = v0y + uy, a1x = v0x - ux, a1y = v0y - uy;
+            tacc += a0x * a0x + a0y * a0y;
+            tacc1 += a1x * a1x + a1y * a1y;
+          } else {
+            const T a = s0 ? -sc : sc;
+            const T br = s1 ? -wr : wr, bi = s1 ? -wi : wi;
+            y[v].x = a * x0[v].x + br * x1[v].x - bi * x1[v].y;
+            y[v].y = a * x0[v].y + br * x1[v].y + bi * x1[v].x;
+            tacc += y[v].x * y[v].x + y[v].y * y[v].y;
+          }
         }
-        if constexpr (VE == 2) {
-          *reinterpret_cast<float4*>(o + e) = make_float4(y[0].x, y[0].y, y[1].x, y[1].y);
-        } else {
-          o[e] = y[0];
+        if constexpr (!PROB) {
+          if constexpr (VE == 2) {
+            *reinterpret_cast<float4*>(o + e) = make_float4(y[0].x, y[0].y, y[1].x, y[1].y);
+          } else {
+            o[e] = y[0];
+          }
         }
       }
     }
     acc.add(tacc);
+    if (PROB) acc1.add(tacc1);
     __syncthreads();  // every thread is done with stage st
     if (threadIdx.x == 0 && issued < mine) issue(issued++);
   }
@@ -681,8 +698,14 @@ __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
     return;  // the block partial is skipped; the host reports the error
   }
   if (P.norm_out >= 0) {
-    const double a1[1] = {acc.value()};
-    reduce_to_slots<1>(a1, P.partials, P.counter, P.norms, P.norm_out);
+    if constexpr (PROB) {
+      const double s2 = (P.scale * c) * (P.scale * c);
+      const double a2[2] = {s2 * acc.value(), s2 * acc1.value()};
+      reduce_to_slots<2>(a2, P.partials, P.counter, P.norms, P.norm_out);
+    } else {
+      const double a1[1] = {acc.value()};
+      reduce_to_slots<1>(a1, P.partials, P.counter, P.norms, P.norm_out);
+    }
   }
 }
 
@@ -745,10 +768,10 @@ static cudaError_t launch_fast(const PassParams& P, const LaunchPlan& Lp, cudaSt
   return cudaSuccess;
 }
 
-template <typename T, int CASE>
+template <typename T, int CASE, bool PROB>
 static cudaError_t launch_tma_case(const PassParams& P, cudaStream_t s) {
   using S = TmaShape<T>;
-  auto kernel = k_tma<T, CASE>;
+  auto kernel = k_tma<T, CASE, PROB>;
   static int grid_cap = 0;
   static std::mutex mu;
   {
@@ -775,8 +798,18 @@ static cudaError_t launch_t(const PassParams& P, const LaunchPlan& L, cudaStream
     case KK_TMA: {  // planned for complex64 only
       cudaError_t e = cudaErrorInvalidValue;
       if constexpr (sizeof(T) == 4)
-        e = L.variant == 0 ? launch_tma_case<T, 0>(P, s)
-                           : (L.variant == 1 ? launch_tma_case<T, 1>(P, s) : launch_tma_case<T, 2>(P, s));
+        e = L.variant == 0 ? launch_tma_case<T, 0, false>(P, s)
+                           : (L.variant == 1 ? launch_tma_case<T, 1, false>(P, s)
+                                             : launch_tma_case<T, 2, false>(P, s));
+      if (e != cudaSuccess) return e;
+      break;
+    }
+    case KK_PROB_TMA: {  // both outcome probabilities, the bulk-copy pass's tiles (complex64)
+      cudaError_t e = cudaErrorInvalidValue;
+      if constexpr (sizeof(T) == 4)
+        e = L.variant == 0 ? launch_tma_case<T, 0, true>(P, s)
+                           : (L.variant == 1 ? launch_tma_case<T, 1, true>(P, s)
+                                             : launch_tma_case<T, 2, true>(P, s));
       if (e != cudaSuccess) return e;
       break;
     }

@@ -268,7 +268,8 @@ class Runner {
     Item it;
     plan_pass(d, dtype_, cur_in_ == nullptr, it.P, it.L);
     fill_common(it.P);
-    it.L.kind = KK_PROB;
+    // passes the bulk-copy kernel takes read their probabilities the same way
+    it.L.kind = it.L.kind == KK_TMA ? KK_PROB_TMA : KK_PROB;
     it.L.grid = (int)std::min<uint64_t>(((1ull << d.n_out) + kBlock - 1) / kBlock, (uint64_t)max_grid());
     it.L.bytes = (cur_in_ ? std::ldexp(1.0, d.n_in) : 0.0) * (dtype_ == OWQS_C64 ? 8.0 : 16.0);
     it.P.in = cur_in_;

@@ -28,7 +28,7 @@ RUN_PER_PASS = 2
 DTYPE = {"c64": 0, "c128": 1}
 POLICY = {"forced": 0, "sampled": 1, "zero": 2}
 KERNEL_KIND = {0: "fast_pass", 1: "generic_pass", 2: "final", 3: "norm", 4: "prob", 5: "tma_pass", 10: "small_run",
-               7: "decide", 8: "group_pass", 9: "factor_join"}
+               7: "decide", 8: "group_pass", 9: "factor_join", 11: "tma_prob"}
 
 
 class OwqsError(RuntimeError):

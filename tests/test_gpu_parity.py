@@ -237,6 +237,28 @@ def test_sampled_outcomes_follow_the_oracle_stream(env):
             assert np.max(np.abs(out.cpu().numpy() - ref.psi_out)) <= 1e-12
 
 
+def test_sampled_complex64_on_bulk_copy_tiles(env):
+    """complex64 sampled runs on arrays wide enough for the bulk-copy pass
+    (at least 2^11 live outputs): the outcome probabilities come from that
+    kernel's probability mode.  Outcomes follow the oracle's stream, the
+    probabilities and the output match within the complex64 tolerance."""
+    torch, owqs = env
+    rng = SplitMix64(131)
+    for p in [workloads.brickwork(13, 6).pattern, workloads.qft(12, with_input=False).pattern]:
+        psi = random_state(rng, len(p.inputs))
+        h = owqs.load(p)
+        h.reorder()
+        op = _oracle_for(h, p)
+        for seed in (11, 12):
+            out, oc, probs, _ = h.run(_dev(torch, psi, "c64"), dtype="c64", policy="sampled", seed=seed)
+            ref = substate.run(op, psi, policy="sampled", seed=seed)
+            assert [int(oc[k]) for k in range(p.K)] == [ref.outcomes[q] for q in p.measured()], (p.name, seed)
+            ref_p = np.array([ref.probs[q] for q in p.measured()])
+            assert np.max(np.abs(probs - ref_p)) <= 1e-5, p.name
+            got = out.cpu().numpy().astype(np.complex128)
+            assert phase_aligned_maxabs(ref.psi_out, got) <= TOL["c64"], p.name
+
+
 def test_device_sampling_matches_host_sampling(env):
     """Outcomes drawn on the device (counter-based splitmix64, one graph)
     equal the per-measurement host draws bit for bit: same outcomes, same
