@@ -230,8 +230,12 @@ enum { OWQS_IO_DEVICE = 0, OWQS_IO_HOST = 1 };
 typedef struct {
   uint32_t dtype;     /* OWQS_C64 (complex64 amplitudes, FP64 reductions) or OWQS_C128 */
   uint32_t mode;      /* OWQS_MODE_OWQS or OWQS_MODE_EOWQS                            */
-  uint32_t policy;    /* forced outcomes, sampled (outcome 0 iff u <= prob_0, u from
-                         splitmix64(seed) in [0,1)), or all zero                      */
+  uint32_t policy;    /* forced outcomes, sampled, or all zero.  Sampled: outcome 0
+                         iff u <= prob_0, u the k-th splitmix64(seed) uniform in
+                         [0,1) for the k-th measurement in execution order; OWQS
+                         computes prob_0 (Eq. 13), EOWQS takes it as 1/2 (Section
+                         4.5), so an EOWQS sampled run draws every outcome first
+                         and then runs as a forced one                             */
   uint32_t io;        /* OWQS_IO_DEVICE: psi_in/psi_out are device pointers;
                          OWQS_IO_HOST: host pointers, copies done inside the call    */
   uint64_t seed;      /* sampled policy only                                          */

@@ -10,7 +10,8 @@ in the given order:
   M      the projective measurement of Section 2.3 with
          P_s = |+-theta><+-theta| (Eqs. 9-10), theta from Eq. 2:
          prob_s = <psi|P_s|psi> (Eq. 3), psi -> P_s psi / sqrt(prob_s) (Eq. 4).
-         In EOWQS mode the probability is taken as 1/2.
+         In EOWQS mode the probability is taken as 1/2, also for a sampled
+         outcome.
 The measured qubit stays in the register in state |+-theta>; at the end it is
 contracted with <+-theta| to read the state of the outputs.
 """
@@ -97,8 +98,8 @@ def run(pattern, psi_in: Optional[np.ndarray] = None, outcomes=None, mode: str =
                 s = int(outcomes[v]) & 1
             elif policy == "zero":
                 s = 0
-            else:
-                s = 0 if rng.uniform() <= p[0] else 1
+            else:  # EOWQS draws against the 1/2 of Section 4.5
+                s = 0 if rng.uniform() <= (p[0] if mode == "owqs" else 0.5) else 1
             if mode == "owqs":
                 if p[s] <= 0.0:
                     raise PatternError("forced outcome has probability 0")

@@ -24,7 +24,8 @@ qubit, which is the ordering Fig. 8 prints (|q3 q2>, |q4 q3 q1>).
 
 Probabilities: a sampled outcome is 0 iff u <= prob_0 with u uniform in
 [0, 1) from a splitmix64 stream (reading of the `rand(0,1) <= prob` test of
-Fig. 6).  A scalar left over when a whole sub-state is measured away is a
+Fig. 6); in EOWQS mode prob_0 is the 1/2 of Section 4.5 there too, so the
+draws do not depend on the state.  A scalar left over when a whole sub-state is measured away is a
 global factor; it is kept, so results carry the exact branch phase.
 """
 from __future__ import annotations
@@ -214,7 +215,7 @@ def run(pattern, psi_in: Optional[np.ndarray] = None, outcomes=None, mode: str =
             a0 = np.take(sub.tensor, 0, axis=ax)
             a1 = np.take(sub.tensor, 1, axis=ax)
             half = [(a0 + e * a1) / SQRT2, (a0 - e * a1) / SQRT2]   # rows of M_0, M_1
-            if mode == "owqs" or policy == "sampled":
+            if mode == "owqs":
                 norm2 = float(np.vdot(sub.tensor, sub.tensor).real)
                 p = [float(np.vdot(h, h).real) / norm2 for h in half]
             else:

@@ -356,6 +356,17 @@ class Runner {
   uint64_t in0_cap_ = 0, out_cap_ = 0, buf_cap_ = 0;  // buffer extents (bounds-checked builds)
 };
 
+// next uniform in [0, 1) of a splitmix64 stream: the state advances by the
+// golden-ratio increment, the finaliser mixes it, the top 53 bits are kept
+static double splitmix_uniform(uint64_t& state) {
+  state += 0x9E3779B97F4A7C15ull;
+  uint64_t z = state;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
 // sampled outcomes: the previous measure pass is launched, then the two
 // probabilities of this measurement are reduced and read back, and the
 // outcome is 0 iff u <= prob_0 with u the next splitmix64 uniform
@@ -367,14 +378,7 @@ struct SampledSource : OutcomeSource {
   bool have_pending = false;
   PassDesc pending;
   SampledSource(Runner& r, RunCache& c, cudaStream_t st, uint64_t seed) : R(r), rc(c), s(st), state(seed) {}
-  double uniform() {
-    state += 0x9E3779B97F4A7C15ull;
-    uint64_t z = state;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
-  }
+  double uniform() { return splitmix_uniform(state); }
   void flush() {
     if (have_pending) {
       R.measure(pending);
@@ -751,11 +755,10 @@ static owqs_status sample_on_device(Pattern& p, const owqs_run_opts* o, RunCache
   return OWQS_OK;
 }
 
-static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
+static owqs_status run_core(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
                             uint8_t* outcomes, double* probs, float* prof_ms, double* prof_bytes,
-                            uint32_t* prof_kind, uint32_t prof_cap, uint32_t* prof_n, int vdiag = 0,
-                            double* frob2 = nullptr, const ProductInput* prod = nullptr,
-                            uint32_t* prof_meas = nullptr) {
+                            uint32_t* prof_kind, uint32_t prof_cap, uint32_t* prof_n, int vdiag,
+                            double* frob2, const ProductInput* prod, uint32_t* prof_meas) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(o ? o->stream : nullptr);
   RunCache* rc = nullptr;
   Prepared pr;
@@ -963,6 +966,35 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
   (void)K;
   return finish(p, o, rc, pr, s, outcomes, probs, outcome_of_pass, pr.in_dev != nullptr, vdiag, frob2,
                 in_group);
+}
+
+// Sampled outcomes in EOWQS mode (Section 4.5): a pattern with a gflow is
+// strongly deterministic, so every measurement gives either outcome with
+// probability 1/2 whatever came before, and no probability is computed.  The
+// outcomes are drawn before the run, outcome 0 iff u <= 1/2 with u the k-th
+// splitmix64 uniform for the k-th measurement in execution order, and the run
+// is then a forced one (pass groups, one graph).  Any other policy or mode
+// goes straight to run_core.
+static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
+                            uint8_t* outcomes, double* probs, float* prof_ms, double* prof_bytes,
+                            uint32_t* prof_kind, uint32_t prof_cap, uint32_t* prof_n, int vdiag = 0,
+                            double* frob2 = nullptr, const ProductInput* prod = nullptr,
+                            uint32_t* prof_meas = nullptr) {
+  if (!o || o->policy != OWQS_OUTCOME_SAMPLED || o->mode != OWQS_MODE_EOWQS || prod || vdiag)
+    return run_core(p, o, psi_in, psi_out, outcomes, probs, prof_ms, prof_bytes, prof_kind, prof_cap, prof_n,
+                    vdiag, frob2, prod, prof_meas);
+  std::vector<uint8_t> drawn(std::max<size_t>(p.meas_qubit.size(), 1), 0);
+  uint64_t state = o->seed;
+  for (uint32_t ci : p.active) {
+    const Cmd& c = p.cmds[ci];
+    if (c.kind == OWQS_CMD_M) drawn[(size_t)p.k_of_qubit[c.q0]] = splitmix_uniform(state) <= 0.5 ? 0 : 1;
+  }
+  owqs_run_opts fo = *o;
+  fo.policy = OWQS_OUTCOME_FORCED;
+  owqs_status st = run_core(p, &fo, psi_in, psi_out, drawn.data(), probs, prof_ms, prof_bytes, prof_kind,
+                            prof_cap, prof_n, vdiag, frob2, prod, prof_meas);
+  if (st == OWQS_OK && outcomes) std::memcpy(outcomes, drawn.data(), p.meas_qubit.size());
+  return st;
 }
 
 }  // namespace owqs

@@ -259,6 +259,35 @@ def test_sampled_complex64_on_bulk_copy_tiles(env):
             assert phase_aligned_maxabs(ref.psi_out, got) <= TOL["c64"], p.name
 
 
+def test_eowqs_sampled_is_a_forced_run_of_fair_coins(env):
+    """EOWQS with sampled outcomes (Section 4.5: every probability is 1/2):
+    the outcomes are the oracle's fair-coin stream, every reported
+    probability is 1/2, the output matches the oracle and is bit-identical
+    to the forced EOWQS run of the same outcomes, and the run takes the
+    forced run's launches (pass groups, no probability sweep)."""
+    torch, owqs = env
+    rng = SplitMix64(133)
+    for p in [workloads.brickwork(13, 6).pattern, workloads.qft(10, with_input=False).pattern]:
+        psi = random_state(rng, len(p.inputs))
+        h = owqs.load(p)
+        h.reorder()
+        op = _oracle_for(h, p)
+        for dtype in ("c64", "c128"):
+            for seed in (21, 22):
+                out, oc, probs, _ = h.run(_dev(torch, psi, dtype), dtype=dtype, mode="eowqs", policy="sampled",
+                                          seed=seed)
+                ref = substate.run(op, psi, mode="eowqs", policy="sampled", seed=seed)
+                assert [int(oc[k]) for k in range(p.K)] == [ref.outcomes[q] for q in p.measured()], (p.name, seed)
+                assert np.all(probs == 0.5)
+                got = out.cpu().numpy().astype(np.complex128)
+                assert phase_aligned_maxabs(ref.psi_out, got) <= TOL[dtype], (p.name, dtype)
+                fout, _, _, _ = h.run(_dev(torch, psi, dtype), dtype=dtype, mode="eowqs", outcomes=oc)
+                assert torch.equal(fout, out), (p.name, dtype, seed)
+            _, _, kinds, _ = h.profile(_dev(torch, psi, dtype), dtype=dtype, mode="eowqs", policy="sampled")
+            names = {owqs.KERNEL_KIND.get(int(k), str(k)) for k in kinds}
+            assert not any("prob" in n or "decide" in n for n in names), names
+
+
 def test_device_sampling_matches_host_sampling(env):
     """Outcomes drawn on the device (counter-based splitmix64, one graph)
     equal the per-measurement host draws bit for bit: same outcomes, same

@@ -416,6 +416,36 @@ def test_bruteforce_agrees_with_substate():
         assert np.allclose(ra.psi_out, ob, atol=1e-13, rtol=0)
 
 
+def test_eowqs_sampled_draws_fair_coins():
+    """Section 4.5: with a flow every branch has probability 1/2, so EOWQS
+    draws a sampled outcome against 1/2 without computing anything.  The
+    outcome of the k-th measurement in execution order is then fixed by the
+    k-th splitmix64 uniform alone (0 iff u <= 1/2), the output is the OWQS
+    output of the same branch, OWQS sampling with the same seed draws the
+    same outcomes (its probabilities are 1/2 up to rounding), and the
+    brute-force oracle agrees."""
+    for n, gates, rng in _small_circuits()[:5]:
+        p = circuit_to_pattern(n, gates)
+        psi = random_state(rng, n)
+        order = [c.q0 for c in p.cmds if c.kind == "M"]
+        for seed in (3, 4, 5):
+            stream = SplitMix64(seed)
+            u = [stream.uniform() for _ in order]
+            want = {q: (0 if uk <= 0.5 else 1) for q, uk in zip(order, u)}
+            e = substate.run(p, psi, mode="eowqs", policy="sampled", seed=seed)
+            assert e.outcomes == want
+            assert all(v == 0.5 for v in e.probs.values())
+            f = substate.run(p, psi, outcomes=want)
+            assert np.allclose(e.psi_out, f.psi_out, atol=1e-13, rtol=0)
+            if min(abs(uk - 0.5) for uk in u) > 1e-9:
+                o = substate.run(p, psi, policy="sampled", seed=seed)
+                assert o.outcomes == want
+            if p.nqubits <= 14:
+                ob, meas, _ = brute.run(p, psi, mode="eowqs", policy="sampled", seed=seed)
+                assert meas == want
+                assert np.allclose(ob, e.psi_out, atol=1e-13, rtol=0)
+
+
 def test_well_formedness_rules():
     with pytest.raises(basis.PatternError):   # D0: depends on unmeasured
         basis.validate(Pattern(3, [0], [2], [E(0, 1), E(1, 2), M(0, 0.0, [1]), M(1, 0.0)]))
