@@ -48,11 +48,11 @@ FALLBACK_HBM_GBS = 6800.0
 # sha256 prefix of the kernel source they were measured on (a changed kernel
 # reports null).  Both are pass groups on the full brickwork workload, mean of
 # three launches: c64 k_group<3> (2^28 complex64 amplitudes in and out;
-# 2148.1 MB read + 2098.8 MB written) and c128 k_group64<3> (2^28 complex128;
-# 4299.1 MB read + 4247.6 MB written).  profiles/k_group_c64_brickwork28x40_dram.md,
+# 2147.9 MB read + 2095.4 MB written) and c128 k_group64<3> (2^28 complex128;
+# 4298.5 MB read + 4246.7 MB written).  profiles/k_group_c64_brickwork28x40_dram.md,
 # profiles/k_group64_c128_brickwork26x8.md.
-NCU_TRAFFIC = {("c22f4cb3373f8725", "c64"): (2147997184 + 2097326848 + 2148010496 + 2095295488 + 2148358912 + 2094445312) / 3.0,
-               ("c22f4cb3373f8725", "c128"): (4298644992 + 4248933120 + 4302609920 + 4246514176 + 4298497280 + 4245665536) / 3.0}
+NCU_TRAFFIC = {("68309cd2b9084767", "c64"): (2147674880 + 2097199360 + 2148430080 + 2094572032 + 2147639552 + 2094421504) / 3.0,
+               ("68309cd2b9084767", "c128"): (4299186432 + 4248895232 + 4298526720 + 4245655808 + 4297742336 + 4245464320) / 3.0}
 # nominal GB300 FP64 rate (no measured FP64 peak exists for this machine)
 FP64_PEAK_TFLOPS = 1.25
 # FP64 flops per output amplitude of the complex128 pass: complex multiply-add
