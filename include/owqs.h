@@ -241,15 +241,23 @@ typedef struct {
   uint64_t seed;      /* sampled policy only                                          */
   void* stream;       /* cudaStream_t to run on; NULL = the legacy default stream    */
   uint32_t use_graph; /* 1: replay the pass sequence as a CUDA graph                */
-  uint32_t flags;     /* OWQS_RUN_HOST_SAMPLING: draw sampled outcomes on the host,
-                         one device-to-host read per measurement (otherwise they are
-                         drawn on the device whenever no X or Z with a signal comes
-                         before the last measurement, e.g. standard form).
+  uint32_t flags;     /* Sampled OWQS runs first guess every outcome as u > 1/2 (the
+                         probability of a gflow pattern, Section 4.5), run the
+                         guesses as forced outcomes, and keep that run iff every
+                         draw u_k <= prob_0 it computed reproduces its guess (then
+                         the one-at-a-time draw takes the same branch); otherwise
+                         they draw one measurement at a time:
+                         OWQS_RUN_SEQUENTIAL_SAMPLING: draw one measurement at a
+                         time from the start, on the device whenever no X or Z with
+                         a signal comes before the last measurement (e.g. standard
+                         form), else on the host.
+                         OWQS_RUN_HOST_SAMPLING: draw one measurement at a time on
+                         the host, one device-to-host read per measurement.
                          OWQS_RUN_PER_PASS: one kernel per pass even when every array
                          of a forced or zero-outcome run fits 2^8 amplitudes (such
                          runs otherwise execute in one single-block kernel)          */
 } owqs_run_opts;
-enum { OWQS_RUN_HOST_SAMPLING = 1, OWQS_RUN_PER_PASS = 2 };
+enum { OWQS_RUN_HOST_SAMPLING = 1, OWQS_RUN_PER_PASS = 2, OWQS_RUN_SEQUENTIAL_SAMPLING = 4 };
 
 /* Simulate the pattern under its active order and return the output state.
  *   psi_in    2^|I| amplitudes (bit k = inputs[k]); NULL = |+> on every input

@@ -968,32 +968,68 @@ static owqs_status run_core(Pattern& p, const owqs_run_opts* o, const void* psi_
                 in_group);
 }
 
-// Sampled outcomes in EOWQS mode (Section 4.5): a pattern with a gflow is
-// strongly deterministic, so every measurement gives either outcome with
-// probability 1/2 whatever came before, and no probability is computed.  The
-// outcomes are drawn before the run, outcome 0 iff u <= 1/2 with u the k-th
-// splitmix64 uniform for the k-th measurement in execution order, and the run
-// is then a forced one (pass groups, one graph).  Any other policy or mode
-// goes straight to run_core.
+// Sampled outcomes as a forced run.
+//
+// EOWQS (Section 4.5): a pattern with a gflow is strongly deterministic, so
+// every measurement gives either outcome with probability 1/2 whatever came
+// before, and no probability is computed.  The outcomes are drawn before the
+// run, outcome 0 iff u <= 1/2 with u the k-th splitmix64 uniform for the k-th
+// measurement in execution order, and the run is then a forced one (pass
+// groups, one graph).
+//
+// OWQS: the outcomes are guessed the same way, the forced run computes the
+// probability of every guessed outcome on the branch of the guesses before
+// it, and the guess is kept iff every draw, u_k <= prob_0 of measurement k,
+// reproduces it.  Then, by induction over k, the one-at-a-time draw would
+// have taken the same branch, so the result is that draw's.  On a pattern
+// with a gflow every prob_0 is 1/2 (Section 4.5) and the guess holds unless
+// a draw lies within rounding of 1/2; otherwise (or on a guessed branch of
+// probability 0) the run is repeated one measurement at a time.
+//
+// Any other policy or mode, and sampling with OWQS_RUN_HOST_SAMPLING or
+// OWQS_RUN_SEQUENTIAL_SAMPLING, goes straight to run_core.
 static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
                             uint8_t* outcomes, double* probs, float* prof_ms, double* prof_bytes,
                             uint32_t* prof_kind, uint32_t prof_cap, uint32_t* prof_n, int vdiag = 0,
                             double* frob2 = nullptr, const ProductInput* prod = nullptr,
                             uint32_t* prof_meas = nullptr) {
-  if (!o || o->policy != OWQS_OUTCOME_SAMPLED || o->mode != OWQS_MODE_EOWQS || prod || vdiag)
+  const bool eowqs = o && o->mode == OWQS_MODE_EOWQS;
+  if (!o || o->policy != OWQS_OUTCOME_SAMPLED || prod || vdiag ||
+      (!eowqs && (prof_ms || !p.deps_ok || (o->flags & (OWQS_RUN_HOST_SAMPLING | OWQS_RUN_SEQUENTIAL_SAMPLING)))))
     return run_core(p, o, psi_in, psi_out, outcomes, probs, prof_ms, prof_bytes, prof_kind, prof_cap, prof_n,
                     vdiag, frob2, prod, prof_meas);
-  std::vector<uint8_t> drawn(std::max<size_t>(p.meas_qubit.size(), 1), 0);
+  const size_t K = p.meas_qubit.size();
+  std::vector<uint8_t> drawn(std::max<size_t>(K, 1), 0);
+  std::vector<double> u(std::max<size_t>(K, 1), 0.0);
   uint64_t state = o->seed;
   for (uint32_t ci : p.active) {
     const Cmd& c = p.cmds[ci];
-    if (c.kind == OWQS_CMD_M) drawn[(size_t)p.k_of_qubit[c.q0]] = splitmix_uniform(state) <= 0.5 ? 0 : 1;
+    if (c.kind != OWQS_CMD_M) continue;
+    const size_t k = (size_t)p.k_of_qubit[c.q0];
+    u[k] = splitmix_uniform(state);
+    drawn[k] = u[k] <= 0.5 ? 0 : 1;
   }
   owqs_run_opts fo = *o;
   fo.policy = OWQS_OUTCOME_FORCED;
-  owqs_status st = run_core(p, &fo, psi_in, psi_out, drawn.data(), probs, prof_ms, prof_bytes, prof_kind,
+  std::vector<double> pk(std::max<size_t>(K, 1), 0.0);
+  owqs_status st = run_core(p, &fo, psi_in, psi_out, drawn.data(), pk.data(), prof_ms, prof_bytes, prof_kind,
                             prof_cap, prof_n, vdiag, frob2, prod, prof_meas);
-  if (st == OWQS_OK && outcomes) std::memcpy(outcomes, drawn.data(), p.meas_qubit.size());
+  bool kept = st == OWQS_OK;
+  if (!eowqs) {
+    for (size_t k = 0; kept && k < K; ++k) {
+      const double p0 = drawn[k] ? 1.0 - pk[k] : pk[k];
+      kept = (u[k] <= p0 ? 0 : 1) == drawn[k];
+    }
+    if (!kept && (st == OWQS_OK || st == OWQS_ERR_IMPOSSIBLE_BRANCH)) {
+      clear_error();
+      return run_core(p, o, psi_in, psi_out, outcomes, probs, prof_ms, prof_bytes, prof_kind, prof_cap, prof_n,
+                      vdiag, frob2, prod, prof_meas);
+    }
+  }
+  if (kept) {
+    if (outcomes) std::memcpy(outcomes, drawn.data(), K);
+    if (probs) std::memcpy(probs, pk.data(), K * sizeof(double));
+  }
   return st;
 }
 

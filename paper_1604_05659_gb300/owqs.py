@@ -25,6 +25,7 @@ MODE = {"owqs": 0, "eowqs": 1}
 FLOW_CAUSAL, FLOW_GFLOW = 0, 1
 RUN_HOST_SAMPLING = 1
 RUN_PER_PASS = 2
+RUN_SEQUENTIAL_SAMPLING = 4
 DTYPE = {"c64": 0, "c128": 1}
 POLICY = {"forced": 0, "sampled": 1, "zero": 2}
 KERNEL_KIND = {0: "fast_pass", 1: "generic_pass", 2: "final", 3: "norm", 4: "prob", 5: "tma_pass", 10: "small_run",
@@ -296,13 +297,17 @@ class Handle:
     # -- device calls ----------------------------------------------------
     def run(self, psi_in=None, *, dtype: str = "c128", mode: str = "owqs", policy: str = "forced",
             outcomes=None, seed: int = 0, stream=None, use_graph: bool = True, out=None,
-            check: bool = True, host_sampling: bool = False, per_pass: bool = False):
+            check: bool = True, host_sampling: bool = False, per_pass: bool = False,
+            sequential_sampling: bool = False):
         """Run on the GPU.  psi_in: torch tensor on the GPU (complex64 for
         c64, complex128 for c128) or None for |+> inputs; returns
         (psi_out tensor, outcomes array, probs array, status).
         host_sampling: draw sampled outcomes on the host (one device read per
         measurement) instead of on the device.  per_pass: one kernel per pass
-        even for a run that fits the single-block kernel."""
+        even for a run that fits the single-block kernel.
+        sequential_sampling: draw sampled OWQS outcomes one measurement at a
+        time from the start, instead of first checking the guess u > 1/2 with
+        one forced run."""
         import torch
         tdt = torch.complex64 if dtype == "c64" else torch.complex128
         if psi_in is not None:
@@ -318,7 +323,8 @@ class Handle:
         s = stream if stream is not None else torch.cuda.current_stream(dev)
         opts = owqs_run_opts(DTYPE[dtype], MODE[mode], POLICY[policy], 0, seed, C.c_void_p(s.cuda_stream),
                              int(use_graph), (RUN_HOST_SAMPLING if host_sampling else 0) |
-                             (RUN_PER_PASS if per_pass else 0))
+                             (RUN_PER_PASS if per_pass else 0) |
+                             (RUN_SEQUENTIAL_SAMPLING if sequential_sampling else 0))
         st = library().owqs_run(self._h, C.byref(opts), C.c_void_p(psi_in.data_ptr() if psi_in is not None else 0),
                                 C.c_void_p(out.data_ptr()), oc.ctypes.data_as(C.POINTER(C.c_uint8)),
                                 probs.ctypes.data_as(C.POINTER(C.c_double)))

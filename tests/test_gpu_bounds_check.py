@@ -4,8 +4,9 @@ against the extent of the buffer it touches.
 
 - Runs that take every launch kind (pass groups from a materialised and from
   the virtual input, bulk-copy and register-tiled single passes, generic and
-  final passes, the input norm, factor joins, unitaries, device-sampled
-  outcomes, EOWQS, the allocation-free entry point) finish with no failed
+  final passes, the input norm, factor joins, unitaries, sampled outcomes
+  by a checked guess and one measurement at a time on the device, EOWQS, the
+  allocation-free entry point) finish with no failed
   check and give the release library's results.
 - With every extent shortened through the test hook, the checked build
   reports the accesses beyond them (skipping them, so nothing outside a
@@ -60,6 +61,8 @@ def run_cases(out_path):
         h.reorder()
         out, oc, probs, st = h.run(None, dtype=dtype, policy="sampled", seed=9, check=False)
         res[f"{{dtype}}:sampled"] = (st, out.cpu().numpy(), probs)
+        out, oc, probs, st = h.run(None, dtype=dtype, policy="sampled", seed=9, check=False, sequential_sampling=True)
+        res[f"{{dtype}}:sampled_seq"] = (st, out.cpu().numpy(), probs)
         p = circuit_to_pattern(6, random_jcz_circuit(6, 5, SplitMix64(1302), cz_per_layer=2), "r6")
         h = owqs.load(p)
         h.reorder()
@@ -119,7 +122,7 @@ def test_every_launch_kind_passes_the_checks_and_matches_release(libs):
     rel = _child(script, build.LIB, "cases", d / "release.npz")
     chk = _child(script, checked, "cases", d / "checked.npz")
     keys = sorted(k[:-3] for k in rel.files if k.endswith("|st"))
-    assert len(keys) == 2 * (7 * 2 + 4)
+    assert len(keys) == 2 * (7 * 2 + 5)
     for k in keys:
         assert int(chk[k + "|st"]) == 0, (k, int(chk[k + "|st"]))
         assert int(rel[k + "|st"]) == int(chk[k + "|st"]), k

@@ -78,9 +78,10 @@ def test_run_writes_only_its_output(env, dtype, name, pattern, nin):
     buf2, view2 = _guarded(torch, nout, tdt)
     h.run(None, dtype=dtype, outcomes=oc, out=view2)
     assert _guards_intact(torch, buf2, nout)
-    buf3, view3 = _guarded(torch, nout, tdt)
-    h.run(psi, dtype=dtype, policy="sampled", seed=5, out=view3)
-    assert _guards_intact(torch, buf3, nout)
+    for seq in (False, True):  # checked guess, one measurement at a time
+        buf3, view3 = _guarded(torch, nout, tdt)
+        h.run(psi, dtype=dtype, policy="sampled", seed=5, out=view3, sequential_sampling=seq)
+        assert _guards_intact(torch, buf3, nout)
     assert torch.equal(psi, psi_copy)
 
 

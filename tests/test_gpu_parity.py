@@ -250,7 +250,8 @@ def test_sampled_complex64_on_bulk_copy_tiles(env):
         h.reorder()
         op = _oracle_for(h, p)
         for seed in (11, 12):
-            out, oc, probs, _ = h.run(_dev(torch, psi, "c64"), dtype="c64", policy="sampled", seed=seed)
+            out, oc, probs, _ = h.run(_dev(torch, psi, "c64"), dtype="c64", policy="sampled", seed=seed,
+                                      sequential_sampling=True)
             ref = substate.run(op, psi, policy="sampled", seed=seed)
             assert [int(oc[k]) for k in range(p.K)] == [ref.outcomes[q] for q in p.measured()], (p.name, seed)
             ref_p = np.array([ref.probs[q] for q in p.measured()])
@@ -303,11 +304,12 @@ def test_device_sampling_matches_host_sampling(env):
         h.reorder()
         for dtype in ("c128", "c64"):
             for seed in (5, 6):
-                dev_out, dev_oc, dev_p, _ = h.run(_dev(torch, psi, dtype), dtype=dtype, policy="sampled", seed=seed)
+                dev_out, dev_oc, dev_p, _ = h.run(_dev(torch, psi, dtype), dtype=dtype, policy="sampled", seed=seed,
+                                                  sequential_sampling=True)
                 host_out, host_oc, host_p, _ = h.run(_dev(torch, psi, dtype), dtype=dtype, policy="sampled",
                                                      seed=seed, host_sampling=True)
                 ng_out, ng_oc, ng_p, _ = h.run(_dev(torch, psi, dtype), dtype=dtype, policy="sampled", seed=seed,
-                                               use_graph=False)
+                                               use_graph=False, sequential_sampling=True)
                 assert np.array_equal(dev_oc, host_oc) and np.array_equal(dev_oc, ng_oc)
                 assert np.array_equal(dev_p, host_p) and np.array_equal(dev_p, ng_p)
                 assert torch.equal(dev_out, host_out) and torch.equal(dev_out, ng_out)
@@ -323,6 +325,55 @@ def test_device_sampling_matches_host_sampling(env):
         ref = substate.run(p, psi, policy="sampled", seed=8)
         assert [int(oc[k]) for k in range(p.K)] == [ref.outcomes[q] for q in p.measured()]
         assert np.max(np.abs(out.cpu().numpy() - ref.psi_out)) <= 1e-12
+
+
+def test_sampling_by_a_checked_guess(env):
+    """Sampled OWQS runs first run the guesses u > 1/2 as forced outcomes and
+    keep that run iff every draw u_k <= prob_0 against the probabilities it
+    computed reproduces its guess; otherwise they draw one measurement at a
+    time.  Either way the outcomes are the one-at-a-time draw's (the oracle's
+    stream): on flow patterns, where every probability is 1/2 (Section 4.5);
+    on a measured input with prob_0 != 1/2, where the guess fails for u
+    between prob_0 and 1/2; and where the guess is a branch of probability 0."""
+    torch, owqs = env
+    rng = SplitMix64(134)
+    for p in [workloads.brickwork(12, 16).pattern, workloads.qft(11, with_input=False).pattern]:
+        psi = random_state(rng, len(p.inputs))
+        h = owqs.load(p)
+        h.reorder()
+        for dtype in ("c128", "c64"):
+            for seed in (5, 6):
+                g_out, g_oc, g_p, _ = h.run(_dev(torch, psi, dtype), dtype=dtype, policy="sampled", seed=seed)
+                s_out, s_oc, s_p, _ = h.run(_dev(torch, psi, dtype), dtype=dtype, policy="sampled", seed=seed,
+                                            sequential_sampling=True)
+                assert np.array_equal(g_oc, s_oc), (p.name, dtype, seed)
+                assert np.max(np.abs(g_p - s_p)) <= (1e-12 if dtype == "c128" else 1e-5)
+                d = phase_aligned_maxabs(s_out.cpu().numpy().astype(np.complex128),
+                                         g_out.cpu().numpy().astype(np.complex128))
+                assert d <= TOL[dtype], (p.name, dtype, d)
+    # one measured input qubit: prob_0 = |<+_a|psi>|^2
+    p = Pattern(2, [0], [1], [N(1), M(0, 0.3)])
+    h = owqs.load(p)
+    psi = np.array([0.8, 0.6j])
+    failed = 0
+    for seed in range(40):
+        ref = substate.run(p, psi, policy="sampled", seed=seed)
+        u = SplitMix64(seed).uniform()
+        failed += int(ref.outcomes[0] != (0 if u <= 0.5 else 1))
+        out, oc, probs, _ = h.run(_dev(torch, psi, "c128"), dtype="c128", policy="sampled", seed=seed)
+        assert int(oc[0]) == ref.outcomes[0], seed
+        assert abs(probs[0] - ref.probs[0]) <= 1e-12
+        assert np.max(np.abs(out.cpu().numpy() - ref.psi_out)) <= 1e-12
+    assert failed >= 2   # the failed-guess path ran
+    # |+> measured at angle 0: outcome 1 has probability 0
+    p = Pattern(2, [0], [1], [N(1), M(0, 0.0)])
+    h = owqs.load(p)
+    plus = np.array([1, 1]) / math.sqrt(2)
+    seeds = [sd for sd in range(16) if SplitMix64(sd).uniform() > 0.5]
+    assert seeds
+    for seed in seeds:
+        out, oc, probs, st = h.run(_dev(torch, plus, "c128"), dtype="c128", policy="sampled", seed=seed)
+        assert st == owqs.OK and int(oc[0]) == 0 and abs(probs[0] - 1.0) <= 1e-12
 
 
 def test_host_io_matches_device_io(env):
