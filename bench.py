@@ -75,9 +75,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rows", type=int, default=ROWS)
     ap.add_argument("--cols", type=int, default=COLS)
-    ap.add_argument("--legs", default="c64,c128,e2e,cpu,rec,learned,qft,small",
-                    help="comma list of c64 (always run), c128, e2e, cpu, rec, learned, qft, small; fewer legs for "
-                         "profiler runs")
+    ap.add_argument("--legs", default="c64,c128,e2e,sampled,cpu,rec,learned,qft,small",
+                    help="comma list of c64 (always run), c128, e2e, sampled, cpu, rec, learned, qft, small; fewer "
+                         "legs for profiler runs")
+    ap.add_argument("--sampled-steps", type=int, default=3, help="sampled-outcome runs per mode")
     ap.add_argument("--learned-count", type=int, default=24, help="held-out patterns in the learned leg")
     ap.add_argument("--rec-branches", type=int, default=64, help="outcome branches per pattern in the recognition leg")
     ap.add_argument("--rec-count", type=int, default=256, help="patterns in the recognition leg")
@@ -580,6 +581,25 @@ def run_owqs(args):
 
     roof64, launches_per_step = roofline("c64")
 
+    sampled = None
+    if "sampled" in legs:
+        # sampled outcomes on the same workload, a new seed (a new branch,
+        # schedule and graph) every run: OWQS (the guess u > 1/2 checked
+        # against the probabilities the run computes) and EOWQS (drawn first)
+        sampled = {"runs": args.sampled_steps, "seeds": "1000 + run index"}
+        for mode in ("owqs", "eowqs"):
+            seeds = iter(range(1000, 2000))
+            dev = []
+
+            def run_s():
+                _, _, ps, _ = h.run(None, dtype="c64", mode=mode, policy="sampled", seed=next(seeds), out=out64)
+                dev.append(float(np.max(np.abs(ps - 0.5))) if len(ps) else 0.0)
+
+            run_s()
+            ts = timed(run_s, args.sampled_steps)
+            sampled[mode] = {"value": replica_throughput(upd, args.sampled_steps, world, ts), "unit": UNIT,
+                             "ms_per_run": 1e3 * ts / args.sampled_steps, "max_abs_prob_minus_half": max(dev)}
+
     fp64, accuracy = None, None
     if "c128" in legs:
         # FP64 (complex128) path on the same workload
@@ -625,6 +645,7 @@ def run_owqs(args):
             "fp64": fp64,
             "accuracy": accuracy,
             "e2e": e2e,
+            "sampled": sampled,
             "recognition": rec,
             "qft24": qft,
             "small": small,
