@@ -458,9 +458,11 @@ owqs_status owqs_describe_launches(const owqs_pattern* p, uint32_t dtype, uint32
  * bytes[i] its algorithmic bytes (amplitudes read + written), kind[i] its
  * kernel (0 register-tiled pass, 1 generic pass, 2 final pass, 3 norm,
  * 4 outcome probabilities, 5 bulk-copy pass, 7 device-drawn outcome, 8 pass
- * group, 9 factor join) and, when nmeas is not NULL, nmeas[i] the number of
- * measurements it performs (1 for a measure pass, k for a group of k, 0
- * otherwise).  Device IO only; the forced or zero policy.                  */
+ * group, 9 factor join, 10 a whole small run in one launch, 11 outcome
+ * probabilities on bulk-copy tiles) and, when nmeas is not NULL, nmeas[i]
+ * the number of measurements it performs (1 for a measure pass, k for a
+ * group of k, 0 otherwise).  Device IO only; the forced or zero policy, or
+ * sampled in EOWQS mode (drawn first, then run as forced).                 */
 owqs_status owqs_profile_run(owqs_pattern* p, const owqs_run_opts* opts, const void* psi_in,
                              void* psi_out, const uint8_t* outcomes, float* ms, double* bytes,
                              uint32_t* kind, uint32_t* nmeas, uint32_t cap, uint32_t* nlaunch);

@@ -40,6 +40,26 @@ def test_exports_every_declared_symbol(owqs):
     assert lib.owqs_abi_version() == 2
 
 
+def test_binding_constants_match_the_header(owqs):
+    """Every enum value the binding passes or decodes is the header's: status
+    codes, command kinds, modes, dtypes, outcome policies, run flags, flow
+    kinds, and the kernel kinds owqs_profile_run documents."""
+    header = open(os.path.join(ROOT, "include", "owqs.h")).read()
+    enum = {k: int(v) for k, v in re.findall(r"\b(OWQS_[A-Z0-9_]+)\s*=\s*(\d+)", header)}
+    assert [enum["OWQS_" + n] for n in owqs.STATUS_NAMES] == list(range(len(owqs.STATUS_NAMES)))
+    assert enum["OWQS_ERR_UNSUPPORTED"] == owqs.ERR_UNSUPPORTED and enum["OWQS_ERR_CUDA"] == owqs.ERR_CUDA
+    assert {k: enum["OWQS_CMD_" + k] for k in owqs.CMD_KIND} == owqs.CMD_KIND
+    assert {k: enum["OWQS_MODE_" + k.upper()] for k in owqs.MODE} == owqs.MODE
+    assert {k: enum["OWQS_" + k.upper()] for k in owqs.DTYPE} == owqs.DTYPE
+    assert {k: enum["OWQS_OUTCOME_" + k.upper()] for k in owqs.POLICY} == owqs.POLICY
+    for flag in ("HOST_SAMPLING", "PER_PASS", "SEQUENTIAL_SAMPLING"):
+        assert enum["OWQS_RUN_" + flag] == getattr(owqs, "RUN_" + flag)
+    assert (enum["OWQS_FLOW_CAUSAL"], enum["OWQS_FLOW_GFLOW"]) == (owqs.FLOW_CAUSAL, owqs.FLOW_GFLOW)
+    doc = header[header.index("kind[i] its"):header.index("owqs_status owqs_profile_run")]
+    documented = {int(k) for k in re.findall(r"\b(\d+) [a-z]", doc.replace("\n *", " ")) if int(k) < 32}
+    assert documented == set(owqs.KERNEL_KIND), (documented, set(owqs.KERNEL_KIND))
+
+
 def test_validation_errors(owqs):
     bad = {
         "D0": Pattern(3, [0], [2], [E(0, 1), E(1, 2), M(0, 0.0, [1]), M(1, 0.0)]),
