@@ -100,6 +100,16 @@ class Result:
         self.measurements_done = 0
 
 
+def outcome_probabilities(mode: str, tensor: np.ndarray, half) -> List[float]:
+    """[prob_0, prob_1] of a measurement: the squared norms of the two halves
+    over the sub-state's (Eq. 13) in OWQS mode; 1/2 each in EOWQS mode
+    (Section 4.5), which computes nothing."""
+    if mode == "owqs":
+        norm2 = float(np.vdot(tensor, tensor).real)
+        return [float(np.vdot(h, h).real) / norm2 for h in half]
+    return [0.5, 0.5]
+
+
 def run(pattern, psi_in: Optional[np.ndarray] = None, outcomes=None, mode: str = "owqs",
         policy: str = "forced", seed: int = 0,
         trace: Optional[Callable[[int, object, List[SubState]], None]] = None,
@@ -215,11 +225,7 @@ def run(pattern, psi_in: Optional[np.ndarray] = None, outcomes=None, mode: str =
             a0 = np.take(sub.tensor, 0, axis=ax)
             a1 = np.take(sub.tensor, 1, axis=ax)
             half = [(a0 + e * a1) / SQRT2, (a0 - e * a1) / SQRT2]   # rows of M_0, M_1
-            if mode == "owqs":
-                norm2 = float(np.vdot(sub.tensor, sub.tensor).real)
-                p = [float(np.vdot(h, h).real) / norm2 for h in half]
-            else:
-                p = [0.5, 0.5]
+            p = outcome_probabilities(mode, sub.tensor, half)
             if policy == "forced":
                 s = int(outcomes[v]) & 1
             elif policy == "zero":

@@ -63,3 +63,11 @@ def test_proa_flag_inverted_is_caught(monkeypatch):
 
     monkeypatch.setattr(proa, "greedy", bad)
     assert _fails(pins.test_table1_proa_trace)
+
+
+def test_eowqs_sampling_against_computed_probability_is_caught(monkeypatch):
+    """EOWQS drawing a sampled outcome against the computed probability
+    instead of the 1/2 of Section 4.5."""
+    orig = substate.outcome_probabilities
+    monkeypatch.setattr(substate, "outcome_probabilities", lambda mode, t, half: orig("owqs", t, half))
+    assert _fails(pins.test_eowqs_sampled_draws_fair_coins)

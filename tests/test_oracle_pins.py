@@ -444,6 +444,23 @@ def test_eowqs_sampled_draws_fair_coins():
                 ob, meas, _ = brute.run(p, psi, mode="eowqs", policy="sampled", seed=seed)
                 assert meas == want
                 assert np.allclose(ob, e.psi_out, atol=1e-13, rtol=0)
+    # where prob_0 is not 1/2 (one measured input, no flow), EOWQS still draws
+    # against 1/2 and OWQS against prob_0 = |<+_a|psi>|^2: they differ exactly
+    # for u between the two
+    p = Pattern(2, [0], [1], [N(1), M(0, 0.3)])
+    psi = np.array([0.8, 0.6j])
+    p0 = substate.run(p, psi, outcomes={0: 0}).pairs[0][0]
+    assert abs(p0 - 0.5) > 0.1
+    differ = 0
+    for seed in range(40):
+        u = SplitMix64(seed).uniform()
+        e = substate.run(p, psi, mode="eowqs", policy="sampled", seed=seed)
+        o = substate.run(p, psi, policy="sampled", seed=seed)
+        _, eb, _ = brute.run(p, psi, mode="eowqs", policy="sampled", seed=seed)
+        assert e.outcomes[0] == eb[0] == (0 if u <= 0.5 else 1)
+        assert o.outcomes[0] == (0 if u <= p0 else 1)
+        differ += int(e.outcomes[0] != o.outcomes[0])
+    assert differ >= 2
 
 
 def test_well_formedness_rules():
