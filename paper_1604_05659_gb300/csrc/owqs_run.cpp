@@ -765,6 +765,10 @@ static owqs_status run_core(Pattern& p, const owqs_run_opts* o, const void* psi_
   const bool sampled = o && o->policy == OWQS_OUTCOME_SAMPLED;
   if (prod && (sampled || (o && o->io != OWQS_IO_DEVICE) || vdiag || psi_in))
     return set_error(OWQS_ERR_UNSUPPORTED, "product inputs take device vectors and forced or zero outcomes");
+  // host-decided refusals of a one-at-a-time draw, before any device work
+  if (sampled && prof_ms) return set_error(OWQS_ERR_ARG, "profiling needs forced or zero outcomes");
+  if (sampled && !p.deps_ok)
+    return set_error(OWQS_ERR_ARG, "sampled outcomes need an order that measures every domain first");
   owqs_status st = prepare(p, o, psi_in, psi_out, outcomes, rc, pr, sampled, prod);
   if (st != OWQS_OK) return st;
   const int K = (int)p.meas_qubit.size();
@@ -772,12 +776,9 @@ static owqs_status run_core(Pattern& p, const owqs_run_opts* o, const void* psi_
   std::vector<char> in_group;
 
   if (sampled) {
-    if (prof_ms) return set_error(OWQS_ERR_ARG, "profiling needs forced or zero outcomes");
     // structure pass (outcome-independent widths) to size the buffers
     FixedSource zero(p, nullptr);
     std::vector<PassDesc> tmp;
-    if (!p.deps_ok)
-      return set_error(OWQS_ERR_ARG, "sampled outcomes need an order that measures every domain first");
     st = compile_schedule(p, o->mode, zero, tmp);
     if (st != OWQS_OK) return st;
     size_t wmax = 1;

@@ -1,6 +1,7 @@
 """Error paths of the C ABI that are decided on the host (no GPU needed):
 live width above the compiler's limit, the EOWQS gflow pre-check (which runs
-before any device work), and argument errors of the newer entry points."""
+before any device work), sampled OWQS runs that cannot draw one measurement
+at a time, and argument errors of the newer entry points."""
 import ctypes as C
 
 import pytest
@@ -53,3 +54,28 @@ def test_argument_errors_of_newer_entry_points(owqs):
     vecs = (C.c_void_p * 1)(addr)
     st = lib.owqs_run_product(h._h, C.byref(opts), 1, sizes, qubits, vecs, None, None, None)
     assert st == owqs.ERR_ARG
+
+
+def test_sampled_owqs_refusals_come_before_device_work(owqs):
+    """A sampled OWQS run under an order that measures a qubit before its
+    domain (an EOWQS order) cannot draw one measurement at a time, and a
+    profile of such a draw is refused; both are ERR_ARG before any device
+    work.  The same order runs sampled in EOWQS mode, where every outcome is
+    drawn first (not run here: that needs a GPU)."""
+    from owqs_inputs import workloads
+    p = workloads.brickwork(4, 4).pattern
+    h = owqs.load(p)
+    order, _ = h.reorder(mode="eowqs")
+    pos = {q: i for i, q in enumerate(order)}
+    assert any(pos[d] > pos[c.q0] for c in p.cmds if c.kind == "M" for d in list(c.sdom) + list(c.tdom))
+    lib = owqs.library()
+    for flags in (0, owqs.RUN_SEQUENTIAL_SAMPLING, owqs.RUN_HOST_SAMPLING):
+        opts = owqs.owqs_run_opts(owqs.DTYPE["c64"], owqs.MODE["owqs"], owqs.POLICY["sampled"], 0, 7, None, 0, flags)
+        assert lib.owqs_run(h._h, C.byref(opts), None, None, None, None) == owqs.ERR_ARG
+        assert "domain first" in owqs.last_error()
+    h.reset_order()
+    opts = owqs.owqs_run_opts(owqs.DTYPE["c64"], owqs.MODE["owqs"], owqs.POLICY["sampled"], 0, 7, None, 0, 0)
+    ms = (C.c_float * 64)()
+    n = C.c_uint32()
+    st = lib.owqs_profile_run(h._h, C.byref(opts), None, None, None, ms, None, None, None, 64, C.byref(n))
+    assert st == owqs.ERR_ARG and "profiling" in owqs.last_error()
