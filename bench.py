@@ -71,7 +71,9 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["owqs", "reference"], default="owqs")
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end calls timed (0: --steps)")
+    ap.add_argument("--cpu-meas", type=int, default=3,
+                    help="measurements of the workload in each CPU-oracle sample (all host cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rows", type=int, default=ROWS)
     ap.add_argument("--cols", type=int, default=COLS)
@@ -202,26 +204,62 @@ def oracle_sample(rows: int, cols: int, target_s: float):
     return upd / dt, desc, dt
 
 
+class OraclePrefix:
+    """The first `nmeas` measurements of the brickwork rows x cols pattern
+    itself, under the oracle's own PROA order, as a workload for the C oracle
+    (O-A with its amplitude loops on every host core): the pattern, the
+    forced outcomes by label and the amplitude updates of the prefix."""
+
+    def __init__(self, rows: int, cols: int, nmeas: int):
+        from oracle import counting, proa
+        from owqs_inputs import workloads
+        from owqs_inputs.patterns import Pattern
+        wl = workloads.brickwork(rows, cols)
+        p = wl.pattern
+        order, _, _ = proa.proa(p)
+        self.pattern = proa.reorder_commands(p, order)
+        self.outcomes = {q: int(wl.outcomes[k]) for k, q in enumerate(p.measured())}
+        self.nmeas = min(nmeas, p.K)
+        cut, seen = 0, 0
+        for i, c in enumerate(self.pattern.cmds):
+            if c.kind == "M":
+                seen += 1
+                if seen == self.nmeas:
+                    cut = i + 1
+                    break
+        prefix = Pattern(self.pattern.nqubits, list(self.pattern.inputs), [], self.pattern.cmds[:cut])
+        self.updates = counting.amplitude_updates(prefix)
+        self.desc = (f"FP64 oracle (C sub-state simulator, OpenMP loops) on brickwork {rows}x{cols} itself, "
+                     f"first {self.nmeas} of {p.K} measurements under PROA (live width {rows + 1}), "
+                     f"{self.updates} amplitude updates")
+
+    def time(self, threads: int = 0) -> float:
+        from oracle import substate_c
+        t0 = time.perf_counter()
+        substate_c.run(self.pattern, None, outcomes=self.outcomes, stop_after=self.nmeas, threads=threads)
+        return time.perf_counter() - t0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    rows = min(args.rows, 22)
-    vals = []
-    desc = ""
+    from oracle import substate_c
+    cores = substate_c.max_threads()
+    wl = OraclePrefix(args.rows, args.cols, args.cpu_meas)
+    times = []
     for i in range(args.warmup + args.steps):
-        v, desc, dt = oracle_sample(rows, args.cols, target_s=6.0)
+        dt = wl.time()
         if i >= args.warmup:
-            vals.append((v, dt))
-    tot_upd = sum(v * dt for v, dt in vals)
-    tot_t = sum(dt for _, dt in vals)
-    value = tot_upd / tot_t
+            times.append(dt)
+    tot_t = sum(times)
+    value = wl.updates * len(times) / tot_t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(vals),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": desc},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "config": {"workload": workload_name(args.rows, args.cols), "sample": wl.desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": wl.desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -571,13 +609,28 @@ def run_owqs(args):
         host_out = torch.empty(1 << nout, dtype=torch.complex64).pin_memory()
         run_e2e = lambda: h.run_host(host_in, host_out, dtype="c64", outcomes=wl.outcomes)
         run_e2e()
+        e2e_steps = args.e2e_steps or args.steps
         sampler_e = ClockSampler(gpu_id)
         sampler_e.start()
-        te = timed(run_e2e, args.e2e_steps)
+        te = timed(run_e2e, e2e_steps)
         clocks_e2e = sampler_e.stop()
-        e2e = {"value": replica_throughput(upd, args.e2e_steps, world, te), "unit": UNIT,
+        # the host link of this machine, measured on the same pinned buffers: one
+        # plain copy each way (the end-to-end call moves these bytes before
+        # its first launch and after its last)
+        dev_in = torch.empty(1 << nin, dtype=torch.complex64, device="cuda")
+        link = {}
+        for name, fn in (("h2d", lambda: dev_in.copy_(host_in, non_blocking=True)),
+                         ("d2h", lambda: host_out.copy_(out64, non_blocking=True))):
+            fn()
+            tl = timed(fn, 3) / 3
+            nbytes = (1 << nin) * 8 if name == "h2d" else (1 << nout) * 8
+            link[name] = {"GBps": nbytes / tl / 1e9, "ms": 1e3 * tl}
+        del dev_in
+        e2e = {"value": replica_throughput(upd, e2e_steps, world, te), "unit": UNIT,
                "h2d_bytes_per_step": (1 << nin) * 8, "d2h_bytes_per_step": (1 << nout) * 8 + 8 * (p.K + 2),
-               "ms_per_step": 1e3 * te / args.e2e_steps, "clocks": clocks_e2e}
+               "ms_per_step": 1e3 * te / e2e_steps, "steps": e2e_steps, "clocks": clocks_e2e,
+               "host_link": link,
+               "device_step_plus_copies_ms": 1e3 * t64 / args.steps + link["h2d"]["ms"] + link["d2h"]["ms"]}
 
     roof64, launches_per_step = roofline("c64")
 
@@ -626,8 +679,17 @@ def run_owqs(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and "cpu" in legs:
-        v, desc, dt = oracle_sample(22, args.cols, target_s=15.0)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "seconds": dt}
+        # the C oracle on every host core, on a prefix of this workload; beside
+        # it the numpy oracle on one core (a prefix of a 22-row brickwork: its
+        # first 29-qubit measurement alone would take minutes on one core)
+        from oracle import substate_c
+        pre = OraclePrefix(args.rows, args.cols, args.cpu_meas)
+        dt = pre.time()
+        v1, desc1, dt1 = oracle_sample(22, args.cols, target_s=8.0)
+        cpu = {"value": pre.updates / dt, "unit": UNIT, "cores": substate_c.max_threads(), "kind": "oracle",
+               "sample": pre.desc, "seconds": dt,
+               "one_core": {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc1,
+                            "seconds": dt1}}
 
     if rank == 0:
         line = {

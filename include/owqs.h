@@ -244,9 +244,12 @@ typedef struct {
   uint32_t flags;     /* Sampled OWQS runs first guess every outcome as u > 1/2 (the
                          probability of a gflow pattern, Section 4.5), run the
                          guesses as forced outcomes, and keep that run iff every
-                         draw u_k <= prob_0 it computed reproduces its guess (then
-                         the one-at-a-time draw takes the same branch); otherwise
-                         they draw one measurement at a time:
+                         draw u_k <= prob_0 it computed reproduces its guess and
+                         lies more than a tie margin (1e-6 for OWQS_C64, 1e-12
+                         for OWQS_C128) from that prob_0 (then the one-at-a-time
+                         draw, whose prob_0 differs only by rounding, takes the
+                         same branch); otherwise they draw one measurement at a
+                         time:
                          OWQS_RUN_SEQUENTIAL_SAMPLING: draw one measurement at a
                          time from the start, on the device whenever no X or Z with
                          a signal comes before the last measurement (e.g. standard
@@ -320,6 +323,14 @@ owqs_status owqs_test_wait_timeout(uint32_t runs, uint64_t limit_cycles);
  * its buffer"); the release build ignores extents.  runs = 0 cancels.
  * Not for production use. */
 owqs_status owqs_test_shrink_extents(uint32_t runs, uint64_t elems);
+
+/* Test hook: every later launch of the pass kernels (single passes, pass
+ * groups, norms and joins) uses at most `blocks` thread blocks, so that a
+ * small array still makes every warp of a persistent kernel loop over many
+ * tiles and wrap its shared-memory ring of stages (the path full-size
+ * arrays take).  The cap is part of the CUDA-graph key.  blocks = 0 removes
+ * the cap.  Not for production use. */
+owqs_status owqs_test_grid_cap(uint32_t blocks);
 
 /* Flows of the pattern's open graph (G, I, O), Section 4.5 with the
  * definitions of ref. [13]; G has an edge u-v iff the pattern holds an odd
@@ -419,9 +430,10 @@ owqs_status owqs_run_batch(const owqs_batch_item* items, uint32_t n, const owqs_
 
 /* owqs_run without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc, such as
- * code running while a CUDA stream is being captured into a graph (where
- * allocation calls are not allowed), or a host program whose device memory
- * is entirely owned by another allocator or held to a fixed budget.  The
+ * a host program whose device memory is entirely owned by another
+ * allocator (a framework's caching pool, an embedding application) or held
+ * to a fixed budget, where an allocation inside the library could fail or
+ * fragment memory that the caller has planned.  The
  * caller passes the input and output vectors exactly as for owqs_run; the
  * library's scratch (two state buffers, the norm slots, the reduction
  * partials and a counter) lives in one statically sized device array of
@@ -438,7 +450,8 @@ owqs_status owqs_run_batch(const owqs_batch_item* items, uint32_t n, const owqs_
  * Every call uses the same array and leaves its contents behind (the counter
  * that must start at zero is cleared at the start of each call), so calls
  * whose work overlaps on the GPU (other streams, other threads) race: issue
- * them one after another.  Returns after the device work has finished.     */
+ * them one after another.  Returns after the device work has finished: the
+ * call reads the norm slots back to the host and synchronises the stream.  */
 owqs_status owqs_run_static(owqs_pattern* p, const owqs_run_opts* opts, const void* psi_in,
                             void* psi_out, uint8_t* outcomes, double* probs);
 

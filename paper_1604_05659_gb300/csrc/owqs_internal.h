@@ -125,6 +125,14 @@ struct PassDesc {
   std::vector<int> perm;                   // final pass
 };
 
+// true if the byte ranges [a, a + na) and [b, b + nb) share a byte (an
+// input and an output vector that overlap would let the first pass read
+// what the final pass overwrites)
+inline bool byte_ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return na && nb && x < y + nb && y < x + na;
+}
+
 constexpr int kMaxLive = 62;   // widest extended index the compiler accepts
 constexpr int kQMax = 64;      // quadratic lower endpoints (a vertex cover of any graph on 62 bits fits)
 
@@ -199,6 +207,10 @@ void fast_config(int dtype, int* lg, int* hint);
 int tma_enabled();
 constexpr int kBlock = 256;
 int max_grid();               // grid cap for grid-stride kernels
+// the grid a launch uses: `want`, or the test hook's cap (owqs_test_grid_cap) when smaller
+int capped_grid(int want);
+int test_grid_cap();          // the test hook's cap, 0 for none
+void set_test_grid_cap(int blocks);
 
 // A group of 2..kGroupMax consecutive measure passes run as one sweep
 // (bulk copies into shared memory).  Every pass is in star form with no X mask and prepares
@@ -245,6 +257,7 @@ struct GroupPass {
   uint64_t zfree, afree;    // sign masks over the free index
   double scale, wre, wim;   // scale and (-1)^s e^{-i theta}
   float ct[1 << kGroupRegMax];  // +-1 per output configuration
+  float2 ct2[1 << kGroupRegMax];  // (ct, ct): the same factor for both elements of a packed pair
   float fwr, fwi;           // (-1)^s e^{-i theta} in FP32
   double ctd[1 << kGroupRegMax];  // ct in FP64 (complex128 groups)
 };
@@ -267,6 +280,8 @@ struct GroupParams {
   float fin[1 << kGroupRegMax];
   double find[1 << kGroupRegMax];  // fin in FP64 (complex128 groups)
   double nscale[kGroupMax];
+  uint64_t zall;            // XOR of the passes' zfree: the element's accumulated Z sign is
+  uint32_t zall_lo, c0all;  // c0all ^ par(f & zall); zall_lo = its low (tile) bits
   int norm_in, norm_out;
   double thresh;
   double vconst;            // in == nullptr: the value of every input amplitude (virtual |+> input)

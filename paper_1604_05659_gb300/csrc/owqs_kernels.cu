@@ -751,7 +751,7 @@ static int resident_grid(K kernel, int want) {
 
 template <typename K>
 static void go(K kernel, const PassParams& P, int want, cudaStream_t s) {
-  kernel<<<resident_grid(kernel, want), kBlock, 0, s>>>(P);
+  kernel<<<capped_grid(resident_grid(kernel, want)), kBlock, 0, s>>>(P);
 }
 
 template <typename T, int L, int HINT>
@@ -786,7 +786,7 @@ static cudaError_t launch_tma_case(const PassParams& P, cudaStream_t s) {
     }
   }
   const uint64_t tiles = 1ull << (P.nlo - S::LTE);
-  const int grid = (int)std::min<uint64_t>(tiles, (uint64_t)grid_cap);
+  const int grid = capped_grid((int)std::min<uint64_t>(tiles, (uint64_t)grid_cap));
   kernel<<<grid, kBlock, S::SMEM, s>>>(P);
   return cudaSuccess;
 }
@@ -880,7 +880,7 @@ static cudaError_t launch_group_t(void (*kern)(const GroupParams), const GroupPa
   }
   const uint64_t tiles = 1ull << (G.nfree - (TB - M));
   const uint64_t blocks = TB == 9 ? (tiles + kBlock / 32 - 1) / (kBlock / 32) : tiles;  // c64: one tile per warp
-  kern<<<(int)std::min<uint64_t>(blocks, (uint64_t)grid_cap), kBlock, SMEM, s>>>(G);
+  kern<<<capped_grid((int)std::min<uint64_t>(blocks, (uint64_t)grid_cap)), kBlock, SMEM, s>>>(G);
   return cudaGetLastError();
 }
 
@@ -1474,15 +1474,15 @@ __global__ void __launch_bounds__(kBlock) k_kron(const KronParams K) {
 cudaError_t launch_kron(const KronParams& K, int dtype, cudaStream_t s) {
   const uint64_t n = 1ull << (K.n_in + K.q);
   const int grid = (int)std::min<uint64_t>((n + kBlock - 1) / kBlock, (uint64_t)max_grid());
-  if (dtype == OWQS_C64) k_kron<float><<<grid, kBlock, 0, s>>>(K);
-  else k_kron<double><<<grid, kBlock, 0, s>>>(K);
+  if (dtype == OWQS_C64) k_kron<float><<<capped_grid(grid), kBlock, 0, s>>>(K);
+  else k_kron<double><<<capped_grid(grid), kBlock, 0, s>>>(K);
   return cudaGetLastError();
 }
 
 cudaError_t launch_norm(const void* in, uint64_t n, int dtype, double* norms, int slot, double* partials,
                         unsigned int* counter, int grid, cudaStream_t s) {
-  if (dtype == OWQS_C64) k_norm<float><<<grid, kBlock, 0, s>>>(in, n, norms, slot, partials, counter);
-  else k_norm<double><<<grid, kBlock, 0, s>>>(in, n, norms, slot, partials, counter);
+  if (dtype == OWQS_C64) k_norm<float><<<capped_grid(grid), kBlock, 0, s>>>(in, n, norms, slot, partials, counter);
+  else k_norm<double><<<capped_grid(grid), kBlock, 0, s>>>(in, n, norms, slot, partials, counter);
   return cudaGetLastError();
 }
 

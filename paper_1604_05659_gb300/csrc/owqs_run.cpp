@@ -422,6 +422,8 @@ static std::string graph_key(const Pattern& p, const owqs_run_opts* o, const voi
   for (uint32_t i : p.active) h = (h ^ i) * 1099511628211ull;
   add(&h, 8);
   if (o->policy == OWQS_OUTCOME_FORCED && outcomes) add(outcomes, p.meas_qubit.size());
+  const int cap = test_grid_cap();
+  add(&cap, sizeof(cap));
   return k;
 }
 
@@ -480,9 +482,13 @@ static owqs_status prepare(Pattern& p, const owqs_run_opts* o, const void* psi_i
   if (o->policy == OWQS_OUTCOME_FORCED && !outcomes && !p.meas_qubit.empty())
     return set_error(OWQS_ERR_ARG, "forced outcomes need the outcomes array");
   pr.amp = o->dtype == OWQS_C64 ? 8 : 16;
-  if (o->io == OWQS_IO_DEVICE) {
+  pr.in_elems = 1ull << p.inputs.size();
+  pr.out_elems = 1ull << p.outputs.size();
+  if (o->io == OWQS_IO_DEVICE) {  // refused before any device work
     if (((uintptr_t)psi_in % 16) || ((uintptr_t)psi_out % 16))
       return set_error(OWQS_ERR_ARG, "device vectors must be 16-byte aligned");
+    if (psi_in && byte_ranges_overlap(psi_in, pr.in_elems * pr.amp, psi_out, pr.out_elems * pr.amp))
+      return set_error(OWQS_ERR_ARG, "psi_in and psi_out must not overlap");
   }
   owqs_status st = get_cache(p, rc);
   if (st != OWQS_OK) return st;
@@ -492,8 +498,6 @@ static owqs_status prepare(Pattern& p, const owqs_run_opts* o, const void* psi_i
     if (st != OWQS_OK) return st;
   }
   const int K = (int)p.meas_qubit.size();
-  pr.in_elems = 1ull << p.inputs.size();
-  pr.out_elems = 1ull << p.outputs.size();
   const size_t nfac = prod ? prod->qubits.size() : 0;
   st = ensure_buf((void*&)rc->norms, rc->nnorms, sizeof(double) * (3 * (size_t)K + 8 + nfac), "norm slots");
   if (st == OWQS_OK)
@@ -517,7 +521,6 @@ static owqs_status prepare(Pattern& p, const owqs_run_opts* o, const void* psi_i
   } else {
     pr.in_dev = psi_in;
     pr.out_dev = psi_out;
-    if (psi_in && psi_in == psi_out) return set_error(OWQS_ERR_ARG, "psi_in and psi_out must not overlap");
   }
   return OWQS_OK;
 }
@@ -984,8 +987,10 @@ static owqs_status run_core(Pattern& p, const owqs_run_opts* o, const void* psi_
 // reproduces it.  Then, by induction over k, the one-at-a-time draw would
 // have taken the same branch, so the result is that draw's.  On a pattern
 // with a gflow every prob_0 is 1/2 (Section 4.5) and the guess holds unless
-// a draw lies within rounding of 1/2; otherwise (or on a guessed branch of
-// probability 0) the run is repeated one measurement at a time.
+// a draw lies within a tie margin of 1/2 (1e-6 for complex64, 1e-12 for
+// complex128: the two ways of computing prob_0 differ by rounding); otherwise
+// (or on a guessed branch of probability 0) the run is repeated one
+// measurement at a time.
 //
 // Any other policy or mode, and sampling with OWQS_RUN_HOST_SAMPLING or
 // OWQS_RUN_SEQUENTIAL_SAMPLING, goes straight to run_core.
@@ -1017,9 +1022,14 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
                             prof_cap, prof_n, vdiag, frob2, prod, prof_meas);
   bool kept = st == OWQS_OK;
   if (!eowqs) {
+    // The guessed run computes prob_0 as 1 - prob_1 where it guessed 1, and
+    // with other kernels than a one-at-a-time run: the two agree only up to
+    // rounding.  A draw within tie_margin of that prob_0 could go either way,
+    // so the guess is kept only when every draw clears it by more.
+    const double tie_margin = o->dtype == OWQS_C64 ? 1e-6 : 1e-12;
     for (size_t k = 0; kept && k < K; ++k) {
       const double p0 = drawn[k] ? 1.0 - pk[k] : pk[k];
-      kept = (u[k] <= p0 ? 0 : 1) == drawn[k];
+      kept = (u[k] <= p0 ? 0 : 1) == drawn[k] && std::fabs(u[k] - p0) > tie_margin;
     }
     if (!kept && (st == OWQS_OK || st == OWQS_ERR_IMPOSSIBLE_BRANCH)) {
       clear_error();
@@ -1099,6 +1109,12 @@ owqs_status owqs_run_product(owqs_pattern* h, const owqs_run_opts* o, uint32_t n
     return set_error(OWQS_ERR_NOT_DETERMINISTIC, "EOWQS: the open graph has no gflow (Section 4.5)");
   return run_impl(h->p, o, nullptr, psi_out, outcomes, probs, nullptr, nullptr, nullptr, 0, nullptr, 0, nullptr,
                   &prod);
+}
+
+owqs_status owqs_test_grid_cap(uint32_t blocks) {
+  clear_error();
+  set_test_grid_cap((int)std::min<uint32_t>(blocks, 1u << 30));
+  return OWQS_OK;
 }
 
 owqs_status owqs_test_shrink_extents(uint32_t runs, uint64_t elems) {

@@ -10,6 +10,7 @@
 // measured bit into one output amplitude.  The surviving qubits keep their
 // relative order; bits above the measured one shift down.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -238,6 +239,16 @@ int max_grid() {
   return g_max_grid;
 }
 
+static std::atomic<int> g_test_grid_cap{0};
+
+int test_grid_cap() { return g_test_grid_cap.load(); }
+void set_test_grid_cap(int blocks) { g_test_grid_cap.store(blocks > 0 ? blocks : 0); }
+
+int capped_grid(int want) {
+  const int cap = g_test_grid_cap.load();
+  return (cap > 0 && want > cap) ? cap : want;
+}
+
 void fast_config(int dtype, int* lg, int* hint) {
   static int cfg[2][2] = {{-1, -1}, {-1, -1}};
   int d = dtype == OWQS_C64 ? 0 : 1;
@@ -411,16 +422,20 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupP
     const uint32_t ps = (pend >> s) & 1u;
     for (int g = 0; g < (1 << kGroupRegMax); ++g) {
       P.ct[g] = ((__builtin_popcount(P.ar & (uint32_t)g) & 1u) ^ ps) ? -1.0f : 1.0f;
+      P.ct2[g] = make_float2(P.ct[g], P.ct[g]);
       P.ctd[g] = P.ct[g];
     }
     P.fwr = (float)d.w1re;
     P.fwi = (float)d.w1im;
+    G.zall ^= P.zfree;
+    G.c0all ^= P.c0;
     pend = P.zr ^ (pend & ~(1u << s));
     prod *= d.scale;
     G.nscale[j] = prod * prod;
     lv.erase(lv.begin() + d.b);
     lv.push_back(-(1 + s));
   }
+  G.zall_lo = (uint32_t)(G.zall & lomask);
   // final order: the free bits in order, then the register slots
   for (int f = 0; f < G.nfree; ++f)
     if (lv[f] != f) return 0;  // cannot happen: free bits are never removed and keep their order

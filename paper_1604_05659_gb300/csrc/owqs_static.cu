@@ -79,9 +79,10 @@ static owqs_status run_static(Pattern& p, const owqs_run_opts* o, const void* ps
     return set_error(OWQS_ERR_ARG, "forced outcomes need the outcomes array");
   if (((uintptr_t)psi_in % 16) || ((uintptr_t)psi_out % 16))
     return set_error(OWQS_ERR_ARG, "device vectors must be 16-byte aligned");
-  if (psi_in && psi_in == psi_out) return set_error(OWQS_ERR_ARG, "psi_in and psi_out must not overlap");
   const int dtype = (int)o->dtype, mode = (int)o->mode;
   const size_t amp = dtype == OWQS_C64 ? 8 : 16;
+  if (psi_in && byte_ranges_overlap(psi_in, amp << p.inputs.size(), psi_out, amp << p.outputs.size()))
+    return set_error(OWQS_ERR_ARG, "psi_in and psi_out must not overlap");
   const int K = (int)p.meas_qubit.size();
 
   StaticSource src(p, o->policy == OWQS_OUTCOME_ZERO ? nullptr : outcomes);

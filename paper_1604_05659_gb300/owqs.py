@@ -129,6 +129,7 @@ EXPORTS = {
                                  C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32)]),
     "owqs_test_wait_timeout": (C.c_int, [C.c_uint32, C.c_uint64]),
     "owqs_test_shrink_extents": (C.c_int, [C.c_uint32, C.c_uint64]),
+    "owqs_test_grid_cap": (C.c_int, [C.c_uint32]),
     "owqs_describe_launches": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.POINTER(C.c_uint8),
                                          C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                          C.c_uint32, C.POINTER(C.c_uint32)]),
@@ -161,6 +162,53 @@ def library(path: str = LIB_PATH):
 def _check(st: int):
     if st != OK:
         raise OwqsError(st, library().owqs_last_error().decode())
+
+
+def _check_vectors(psi_in, out, tdt, nin: int, nout: int, out_elems: Optional[int] = None):
+    """The library takes raw device pointers and trusts their extents, so a
+    wrongly sized, typed or placed tensor is refused here, before any call:
+    psi_in (when given) must hold exactly 2^nin amplitudes, out at least
+    2^nout (out_elems when given), both contiguous CUDA tensors of the run's
+    dtype on one device."""
+    if psi_in is not None:
+        if not psi_in.is_cuda or psi_in.dtype != tdt or not psi_in.is_contiguous():
+            raise ValueError("psi_in must be a contiguous CUDA tensor of the run's dtype")
+        if psi_in.numel() != (1 << nin):
+            raise ValueError(f"psi_in holds {psi_in.numel()} amplitudes; the pattern has {nin} input qubits "
+                             f"(2^{nin} = {1 << nin} amplitudes)")
+    if out is not None:
+        need = (1 << nout) if out_elems is None else out_elems
+        if not out.is_cuda or out.dtype != tdt or not out.is_contiguous():
+            raise ValueError("out must be a contiguous CUDA tensor of the run's dtype")
+        if out.numel() < need:
+            raise ValueError(f"out holds {out.numel()} amplitudes; the run writes {need}")
+        if psi_in is not None and out.device != psi_in.device:
+            raise ValueError("psi_in and out must be on the same device")
+
+
+def _check_host_vectors(psi_in, out, dtype: str, nin: int, nout: int):
+    """run_host's counterpart of _check_vectors: numpy arrays or CPU torch
+    tensors (pinned for full-speed copies) of the run's dtype, contiguous,
+    psi_in exactly 2^nin amplitudes and out at least 2^nout."""
+    ndt = np.complex64 if dtype == "c64" else np.complex128
+    for name, a, n, exact in (("psi_in", psi_in, nin, True), ("out", out, nout, False)):
+        if a is None:
+            continue
+        if isinstance(a, np.ndarray):
+            ok = a.dtype == ndt and a.flags["C_CONTIGUOUS"] and (name != "out" or a.flags["WRITEABLE"])
+            size = a.size
+        elif hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+            import torch
+            tdt = torch.complex64 if dtype == "c64" else torch.complex128
+            ok = (not a.is_cuda) and a.dtype == tdt and a.is_contiguous()
+            size = a.numel()
+        else:
+            ok, size = False, 0
+        if not ok:
+            raise ValueError(f"{name} must be a contiguous, writeable host array (numpy or CPU torch) of "
+                             f"{np.dtype(ndt).name}")
+        if (size != (1 << n)) if exact else (size < (1 << n)):
+            raise ValueError(f"{name} holds {size} amplitudes; the run needs {1 << n}")
 
 
 def _u32(a: Sequence[int]):
@@ -310,9 +358,7 @@ class Handle:
         one forced run."""
         import torch
         tdt = torch.complex64 if dtype == "c64" else torch.complex128
-        if psi_in is not None:
-            if not psi_in.is_cuda or psi_in.dtype != tdt or not psi_in.is_contiguous():
-                raise ValueError("psi_in must be a contiguous CUDA tensor of the run's dtype")
+        _check_vectors(psi_in, out, tdt, self.nin, self.nout)
         dev = psi_in.device if psi_in is not None else torch.device("cuda", torch.cuda.current_device())
         if out is None:
             out = torch.empty(1 << self.nout, dtype=tdt, device=dev)
@@ -346,6 +392,7 @@ class Handle:
             qubits += list(qs)
             vecs.append(v.data_ptr())
         dev = factors[0][1].device if factors else torch.device("cuda", torch.cuda.current_device())
+        _check_vectors(None, out, tdt, 0, self.nout)
         if out is None:
             out = torch.empty(1 << self.nout, dtype=tdt, device=dev)
         oc = np.zeros(max(1, self.K), dtype=np.uint8)
@@ -369,6 +416,7 @@ class Handle:
         column-major as a flat tensor); returns (U, ||U||_F^2 / 2^|I|)."""
         import torch
         tdt = torch.complex64 if dtype == "c64" else torch.complex128
+        _check_vectors(None, out, tdt, 0, self.nout + self.nin)
         if out is None:
             out = torch.empty(1 << (self.nout + self.nin), dtype=tdt, device="cuda")
         s = stream if stream is not None else torch.cuda.current_stream()
@@ -386,9 +434,7 @@ class Handle:
         the library (scratch in a fixed device array; small patterns only)."""
         import torch
         tdt = torch.complex64 if dtype == "c64" else torch.complex128
-        if psi_in is not None:
-            if not psi_in.is_cuda or psi_in.dtype != tdt or not psi_in.is_contiguous():
-                raise ValueError("psi_in must be a contiguous CUDA tensor of the run's dtype")
+        _check_vectors(psi_in, out, tdt, self.nin, self.nout)
         dev = psi_in.device if psi_in is not None else torch.device("cuda", torch.cuda.current_device())
         if out is None:
             out = torch.empty(1 << self.nout, dtype=tdt, device=dev)
@@ -411,6 +457,7 @@ class Handle:
                  use_graph: bool = True):
         """Run with host vectors; the library copies them in and out."""
         import torch
+        _check_host_vectors(psi_in, out, dtype, self.nin, self.nout)
         oc = np.zeros(max(1, self.K), dtype=np.uint8)
         if outcomes is not None:
             oc[: self.K] = np.asarray(outcomes, dtype=np.uint8)[: self.K]
@@ -429,6 +476,7 @@ class Handle:
         """Per-launch CUDA-event durations of one run (no graph)."""
         import torch
         tdt = torch.complex64 if dtype == "c64" else torch.complex128
+        _check_vectors(psi_in, out, tdt, self.nin, self.nout)
         dev = torch.device("cuda", torch.cuda.current_device())
         if out is None:
             out = torch.empty(1 << self.nout, dtype=tdt, device=dev)
@@ -457,6 +505,13 @@ def last_error() -> str:
 def test_wait_timeout(runs: int, limit_cycles: int = 2_000_000):
     """Make the next `runs` runs give up on a device-side wait (test hook)."""
     _check(library().owqs_test_wait_timeout(runs, limit_cycles))
+
+
+def test_grid_cap(blocks: int):
+    """Cap every later pass-kernel launch at `blocks` thread blocks (test
+    hook; 0 removes the cap), so that small arrays make the persistent
+    kernels loop over many tiles per warp."""
+    _check(library().owqs_test_grid_cap(int(blocks)))
 
 
 def test_shrink_extents(runs: int, elems: int):

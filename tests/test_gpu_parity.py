@@ -1,9 +1,10 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
 Tolerances: complex128 amplitudes and probabilities within 1e-12 max-abs of
-the oracle, complex64 within 2e-5 max-abs after global-phase alignment
-(forced-outcome results carry no phase freedom, so the alignment is a no-op
-up to rounding).  Outcome bits and index maps are compared exactly.
+the oracle, complex64 amplitudes within 2e-5 max-abs after global-phase
+alignment (forced-outcome results carry no phase freedom, so the alignment
+is a no-op up to rounding) and complex64 probabilities within 1e-6.  Outcome
+bits and index maps are compared exactly.
 """
 import math
 
@@ -21,6 +22,10 @@ from test_oracle_pins import _wild_patterns, cnot_eq22
 pytestmark = pytest.mark.gpu
 
 TOL = {"c128": 1e-12, "c64": 2e-5}
+# outcome probabilities: FP64 reductions of the complex64 amplitudes keep them
+# within about 1e-7 of the oracle (observed at 2^28 amplitudes); 1e-6 leaves
+# headroom for the rounding of the FP32 amplitudes themselves
+PROB_TOL = {"c128": 1e-12, "c64": 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -61,7 +66,7 @@ def _compare(env, p, psi, bits, dtype, mode, reorder=True, graph=True, per_pass=
     assert err <= TOL[dtype], (p.name, dtype, mode, err)
     if mode == "owqs":
         ref_p = np.array([ref.probs[q] for q in p.measured()])
-        assert np.max(np.abs(probs - ref_p)) <= (1e-12 if dtype == "c128" else 1e-5)
+        assert np.max(np.abs(probs - ref_p)) <= PROB_TOL[dtype]
     else:
         assert np.all(probs == 0.5)
     return h, got
@@ -255,7 +260,7 @@ def test_sampled_complex64_on_bulk_copy_tiles(env):
             ref = substate.run(op, psi, policy="sampled", seed=seed)
             assert [int(oc[k]) for k in range(p.K)] == [ref.outcomes[q] for q in p.measured()], (p.name, seed)
             ref_p = np.array([ref.probs[q] for q in p.measured()])
-            assert np.max(np.abs(probs - ref_p)) <= 1e-5, p.name
+            assert np.max(np.abs(probs - ref_p)) <= PROB_TOL["c64"], p.name
             got = out.cpu().numpy().astype(np.complex128)
             assert phase_aligned_maxabs(ref.psi_out, got) <= TOL["c64"], p.name
 
@@ -347,7 +352,7 @@ def test_sampling_by_a_checked_guess(env):
                 s_out, s_oc, s_p, _ = h.run(_dev(torch, psi, dtype), dtype=dtype, policy="sampled", seed=seed,
                                             sequential_sampling=True)
                 assert np.array_equal(g_oc, s_oc), (p.name, dtype, seed)
-                assert np.max(np.abs(g_p - s_p)) <= (1e-12 if dtype == "c128" else 1e-5)
+                assert np.max(np.abs(g_p - s_p)) <= PROB_TOL[dtype]
                 d = phase_aligned_maxabs(s_out.cpu().numpy().astype(np.complex128),
                                          g_out.cpu().numpy().astype(np.complex128))
                 assert d <= TOL[dtype], (p.name, dtype, d)
@@ -425,7 +430,7 @@ def test_qft24_full_size_closed_form(env):
         got = out.cpu().numpy().astype(np.complex128)
         err = phase_aligned_maxabs(ref, got)
         assert err <= (1e-11 if dtype == "c128" else 2e-5), (dtype, err)
-        assert np.max(np.abs(probs - 0.5)) <= (1e-12 if dtype == "c128" else 1e-5)
+        assert np.max(np.abs(probs - 0.5)) <= PROB_TOL[dtype]
 
 
 def test_brickwork_full_size_properties(env):
@@ -441,7 +446,7 @@ def test_brickwork_full_size_properties(env):
     o128, _, p128, _ = h.run(None, dtype="c128", outcomes=wl.outcomes)
     assert np.max(np.abs(p128 - 0.5)) <= 1e-12
     o64, _, p64, _ = h.run(None, dtype="c64", outcomes=wl.outcomes)
-    assert np.max(np.abs(p64 - 0.5)) <= 1e-5
+    assert np.max(np.abs(p64 - 0.5)) <= PROB_TOL["c64"]
     d = (o64.to(torch.complex128) - o128)
     ov = torch.vdot(o64.to(torch.complex128), o128)
     assert abs(abs(ov.item()) - 1) < 1e-5
@@ -508,4 +513,4 @@ def test_degenerate_patterns(env, dtype, per_pass):
             assert err <= TOL[dtype], (p.name, dtype, per_pass, err)
             if p.K:
                 ref_p = np.array([ref.probs[q] for q in p.measured()])
-                assert np.max(np.abs(probs - ref_p)) <= (1e-12 if dtype == "c128" else 1e-5), p.name
+                assert np.max(np.abs(probs - ref_p)) <= PROB_TOL[dtype], p.name

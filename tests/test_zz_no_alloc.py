@@ -1,9 +1,9 @@
 """owqs_run_static, the entry point that allocates no device memory, against
 owqs_run on the same patterns.
 
-Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-being captured into a graph, or a program whose device memory belongs to
-another allocator or a fixed budget.  owqs_run_static keeps its scratch in a
+Some callers cannot call cudaMalloc: a program whose device memory belongs
+to another allocator (a framework's caching pool, an embedding application)
+or is held to a fixed budget.  owqs_run_static keeps its scratch in a
 fixed device array, so it must give owqs_run's results; it is called twice
 in a row because the array keeps the previous call's contents.  This file is
 collected last so that a failure here, in a run that stops at the first
@@ -59,7 +59,7 @@ def test_static_entry_matches_owqs_run(env, dtype):
             got = out.cpu().numpy().astype(np.complex128)
             err = float(np.max(np.abs(got - ref)))
             assert err <= TOL[dtype], (p.name, dtype, mode, call, err)
-            assert np.max(np.abs(probs - ref_probs)) <= (1e-12 if dtype == "c128" else 1e-5)
+            assert np.max(np.abs(probs - ref_probs)) <= (1e-12 if dtype == "c128" else 1e-6)
 
 
 def test_static_entry_rejects_patterns_beyond_its_scratch(env):
