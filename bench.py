@@ -77,9 +77,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rows", type=int, default=ROWS)
     ap.add_argument("--cols", type=int, default=COLS)
-    ap.add_argument("--legs", default="c64,c128,e2e,sampled,cpu,rec,learned,qft,small",
-                    help="comma list of c64 (always run), c128, e2e, sampled, cpu, rec, learned, qft, small; fewer "
-                         "legs for profiler runs")
+    ap.add_argument("--legs", default="c64,c128,e2e,sampled,cpu,rec,learned,qft,small,substates,m",
+                    help="comma list of c64 (always run), c128, e2e, sampled, cpu, rec, learned, qft, small, "
+                         "substates, m; fewer legs for profiler runs")
     ap.add_argument("--sampled-steps", type=int, default=3, help="sampled-outcome runs per mode")
     ap.add_argument("--learned-count", type=int, default=24, help="held-out patterns in the learned leg")
     ap.add_argument("--rec-branches", type=int, default=64, help="outcome branches per pattern in the recognition leg")
@@ -167,8 +167,12 @@ class ClockSampler:
 
 
 def kernel_source_hash():
-    with open(os.path.join(ROOT, "paper_1604_05659_gb300", "csrc", "owqs_kernels.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """sha256 prefix of the pass-group sources (the dominant kernels)."""
+    h = hashlib.sha256()
+    for name in ("owqs_group.cu", "owqs_device.cuh", "owqs_group_sequences.inc"):
+        with open(os.path.join(ROOT, "paper_1604_05659_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def oracle_sample(rows: int, cols: int, target_s: float):
@@ -263,6 +267,40 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def table3_leg(owqs):
+    """The paper's m (peak sub-state at a measurement, Table III) of the
+    greedy PROA order with OWQS dependencies and with every qubit ready
+    (EOWQS, Section 4.5), side by side, with the width of one array over
+    every live qubit, on the synthetic pattern families (host only)."""
+    from owqs_inputs import workloads
+    fams = {"3-wire depth-10 circuit": [workloads.small_random()],
+            "brickwork 28x40": [workloads.brickwork(28, 40)],
+            "QFT-24": [workloads.qft(24, with_input=False)],
+            "random J/CZ 6-14 wires": workloads.random_batch(16, 6, 14, 10, 40),
+            "random J/CZ 16-30 wires": workloads.random_batch(16, 16, 30, 20, 60, config_index=4, start=2000,
+                                                              with_input=False)}
+    out = {}
+    for name, wls in fams.items():
+        rows = []
+        for wl in wls:
+            h = owqs.load(wl.pattern)
+            n = max(1, h.nout)
+            r = {}
+            for mode in ("owqs", "eowqs"):
+                _, info = h.reorder(mode=mode, sweep=(mode == "owqs"),
+                                    weights=(float(n), float(n), 0.5, float(n)))
+                r[mode] = (info["peak_m"], info["peak_live"])
+            rows.append(r)
+        out[name] = {"patterns": len(rows),
+                     "owqs_m_mean": statistics.mean(r["owqs"][0] for r in rows),
+                     "eowqs_m_mean": statistics.mean(r["eowqs"][0] for r in rows),
+                     "owqs_m_max": max(r["owqs"][0] for r in rows),
+                     "eowqs_m_max": max(r["eowqs"][0] for r in rows),
+                     "owqs_one_array_width_mean": statistics.mean(r["owqs"][1] for r in rows),
+                     "eowqs_one_array_width_mean": statistics.mean(r["eowqs"][1] for r in rows)}
+    return out
 
 
 def recognition_leg(args, owqs, torch):
@@ -554,7 +592,11 @@ def run_owqs(args):
         barrier()
         return max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, "cuda")
 
-    run64 = lambda: h.run(None, dtype="c64", outcomes=wl.outcomes, out=out64)
+    # the workload as defined: every pass over one array of all live qubits
+    # (2^28 amplitudes once the greedy order has prepared 28 rows); the
+    # separate-sub-state layout, which a default run of this |+>-input
+    # pattern would take, is its own leg below
+    run64 = lambda: h.run(None, dtype="c64", outcomes=wl.outcomes, out=out64, layout="one_array")
     for _ in range(args.warmup):
         run64()
     gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if world > 1 else 0]
@@ -569,7 +611,7 @@ def run_owqs(args):
 
     def roofline(dtype):
         ms, by, kd, _ = h.profile(None, dtype=dtype, outcomes=wl.outcomes,
-                                  out=out64 if dtype == "c64" else None)
+                                  out=out64 if dtype == "c64" else None, layout="one_array")
         kinds = sorted(set(int(k) for k in kd))
         tot = {k: float(ms[kd == k].sum()) for k in kinds}
         dom = max(tot, key=tot.get)
@@ -645,7 +687,8 @@ def run_owqs(args):
             dev = []
 
             def run_s():
-                _, _, ps, _ = h.run(None, dtype="c64", mode=mode, policy="sampled", seed=next(seeds), out=out64)
+                _, _, ps, _ = h.run(None, dtype="c64", mode=mode, policy="sampled", seed=next(seeds), out=out64,
+                                    layout="one_array")
                 dev.append(float(np.max(np.abs(ps - 0.5))) if len(ps) else 0.0)
 
             run_s()
@@ -657,11 +700,11 @@ def run_owqs(args):
     if "c128" in legs:
         # FP64 (complex128) path on the same workload
         out128 = torch.empty(1 << nout, dtype=torch.complex128, device="cuda")
-        run128 = lambda: h.run(None, dtype="c128", outcomes=wl.outcomes, out=out128)
+        run128 = lambda: h.run(None, dtype="c128", outcomes=wl.outcomes, out=out128, layout="one_array")
         run128()
         t128 = timed(run128, args.fp64_steps)
         roof128, _ = roofline("c128")
-        _, _, p128, _ = h.run(None, dtype="c128", outcomes=wl.outcomes, out=out128)
+        _, _, p128, _ = run128()
         _, _, p64, _ = run64()
         a = out64.to(torch.complex128)
         ov = torch.vdot(a, out128)
@@ -672,6 +715,30 @@ def run_owqs(args):
                 "ms_per_step": 1e3 * t128 / args.fp64_steps, "roofline": roof128}
         accuracy = {"c64_vs_c128_max_abs_amp_err": amp_err, "c64_vs_c128_max_prob_err": prob_err, "bound": 2e-5}
 
+    subs = None
+    if "substates" in legs:
+        # the same pattern and branch with separate sub-states (Section 4.1):
+        # the |+> inputs are product factors, so a row joins the computation
+        # only when the order first touches it and rows stay apart until an E
+        # joins them
+        plan = h.plan_memory(wl.outcomes, dtype="c64")
+        out_s = torch.empty_like(out64)
+        run_s = lambda: h.run(None, dtype="c64", outcomes=wl.outcomes, out=out_s, layout="substates")
+        run_s()
+        ts = timed(run_s, args.steps)
+        _, _, p1, _ = run64()
+        _, _, p2, _ = run_s()
+        ov = torch.vdot(out64.to(torch.complex128), out_s.to(torch.complex128))
+        diff = torch.max(torch.abs(out_s.to(torch.complex128) * (ov / abs(ov)) - out64.to(torch.complex128))).item()
+        subs = {"ms_per_run": 1e3 * ts / args.steps, "one_array_ms_per_run": 1e3 * t64 / args.steps,
+                "peak_m": plan["peak_m"], "components": plan["components"], "joins": plan["joins"],
+                "arena_bytes": plan["substate_bytes"], "one_array_bytes": plan["one_array_bytes"],
+                "amplitudes_moved": plan["substate_work"], "one_array_amplitudes_moved_estimate": plan["one_array_work"],
+                "max_abs_diff_vs_one_array": diff, "max_prob_diff_vs_one_array": float(np.max(np.abs(p1 - p2))),
+                "launches_per_run": int(len(h.profile(None, dtype="c64", outcomes=wl.outcomes, out=out_s,
+                                                      layout="substates")[0]))}
+        del out_s
+    m_table = table3_leg(owqs) if "m" in legs else None
     rec = recognition_leg(args, owqs, torch) if "rec" in legs else None
     qft = qft_leg(args, owqs, torch) if "qft" in legs else None
     small = small_leg(args, owqs, torch) if "small" in legs else None
@@ -712,6 +779,8 @@ def run_owqs(args):
             "qft24": qft,
             "small": small,
             "learned_reorder": learned,
+            "substates": subs,
+            "peak_m_owqs_vs_eowqs": m_table,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": launches_per_step * args.steps,

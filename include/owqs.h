@@ -258,9 +258,19 @@ typedef struct {
                          the host, one device-to-host read per measurement.
                          OWQS_RUN_PER_PASS: one kernel per pass even when every array
                          of a forced or zero-outcome run fits 2^8 amplitudes (such
-                         runs otherwise execute in one single-block kernel)          */
+                         runs otherwise execute in one single-block kernel).
+                         Separate sub-states (Section 4.1): qubits that no E has
+                         joined yet live in separate arrays, each measure pass
+                         reads only its own component's array, and an E between
+                         two components joins their arrays (tensor product).
+                         Forced and zero-outcome runs with a single input vector
+                         use them when the components' arrays need at most half
+                         the memory of one array over all live qubits;
+                         OWQS_RUN_SUBSTATES: always (forced or zero outcomes);
+                         OWQS_RUN_ONE_ARRAY: never (one live array).           */
 } owqs_run_opts;
-enum { OWQS_RUN_HOST_SAMPLING = 1, OWQS_RUN_PER_PASS = 2, OWQS_RUN_SEQUENTIAL_SAMPLING = 4 };
+enum { OWQS_RUN_HOST_SAMPLING = 1, OWQS_RUN_PER_PASS = 2, OWQS_RUN_SEQUENTIAL_SAMPLING = 4,
+       OWQS_RUN_SUBSTATES = 8, OWQS_RUN_ONE_ARRAY = 16 };
 
 /* Simulate the pattern under its active order and return the output state.
  *   psi_in    2^|I| amplitudes (bit k = inputs[k]); NULL = |+> on every input
@@ -464,6 +474,39 @@ owqs_status owqs_run_static(owqs_pattern* p, const owqs_run_opts* opts, const vo
 owqs_status owqs_describe_launches(const owqs_pattern* p, uint32_t dtype, uint32_t mode, uint32_t real_input,
                                    const uint8_t* outcomes, uint32_t* kind, uint32_t* first_meas, uint32_t* nmeas,
                                    uint32_t cap, uint32_t* nlaunch);
+
+/* Memory of the two ways to hold the live qubits (host only, no GPU
+ * needed), for the active order: one array over every live qubit, or
+ * separate sub-states (Section 4.1: a component per set of qubits that E
+ * commands have joined; see OWQS_RUN_SUBSTATES).  Arguments as
+ * owqs_describe_launches. */
+typedef struct {
+  uint32_t peak_m;          /* widest sub-state at a measurement, the measured
+                               qubit and prepared ones included (Table I/III's m) */
+  uint32_t components;      /* sub-states over the run (inputs, prepared qubits)   */
+  uint32_t joins;           /* tensor products of two arrays                        */
+  uint32_t uses_substates;  /* 1 if a default owqs_run takes separate sub-states:
+                               they at least halve the amplitudes moved and need no
+                               more memory than one array                          */
+  uint64_t substate_bytes;  /* device arena that holds every live component array   */
+  uint64_t one_array_bytes; /* the two buffers of a one-array run                   */
+  double substate_work;     /* amplitudes read and written, separate sub-states     */
+  double one_array_work;    /* the same with one array (estimate)                   */
+} owqs_memory_plan;
+owqs_status owqs_plan_memory(const owqs_pattern* p, uint32_t dtype, uint32_t mode, uint32_t real_input,
+                            const uint8_t* outcomes, owqs_memory_plan* plan);
+
+/* The pass groups owqs_run would launch (host only, no GPU needed), in/* The pass groups owqs_run would launch (host only, no GPU needed), in
+ * launch order; for group i (i < *ngroups, at most cap): regs[i] the
+ * register qubits M, slots[i] its register-slot sequence (bits 24-27 the
+ * number of passes k, bits 2j and 2j+1 the slot that pass j measures),
+ * n_in[i] the live width it reads and specialised[i] 1 when a kernel
+ * compiled for exactly that sequence runs it (complex64 groups reading a
+ * materialised array), 0 when the slot-dispatching kernel does.  Arguments
+ * as owqs_describe_launches; any output pointer may be NULL. */
+owqs_status owqs_describe_groups(const owqs_pattern* p, uint32_t dtype, uint32_t mode, uint32_t real_input,
+                                const uint8_t* outcomes, uint32_t* regs, uint32_t* slots, uint32_t* n_in,
+                                uint32_t* specialised, uint32_t cap, uint32_t* ngroups);
 
 /* Per-kernel timing of one run (instrumentation).  Runs the same schedule
  * without a graph, with a CUDA event pair around every launch on opts->stream,

@@ -25,8 +25,10 @@
  *     OWQS keeps row s divided by sqrt(prob_s) (Eq. 7), EOWQS (Section 4.5)
  *     keeps row s times sqrt2; qubit v is dropped.  A scalar left when a
  *     whole sub-state is measured away is kept as a global factor.
- * Outcomes are forced (per qubit label) or all zero.  Sums over amplitudes
- * are FP64 OpenMP reductions.
+ * Outcomes are forced (per qubit label) or all zero.  The squared norms of a
+ * measurement are compensated (Kahan) FP64 sums per thread, added in thread
+ * order, so the probabilities stay exact to a few units in the last place
+ * at any array size.
  */
 #include <complex.h>
 #include <math.h>
@@ -49,6 +51,22 @@ typedef struct {
   int lab[OA_MAXQ];  /* ascending labels; bit k of an index is qubit lab[k] */
   cplx* t;           /* 2^n amplitudes */
 } Sub;
+
+/* compensated (Kahan) running sum */
+static void kahan(double* sum, double* comp, double x) {
+  const double y = x - *comp;
+  const double t = *sum + y;
+  *comp = (t - *sum) - y;
+  *sum = t;
+}
+
+static int omp_threads(void) {
+#ifdef _OPENMP
+  return omp_get_num_threads();
+#else
+  return 1;
+#endif
+}
 
 static int pos_of(const Sub* s, int q) {
   for (int k = 0; k < s->n; ++k)
@@ -270,15 +288,32 @@ int oa_run(int nqubits, const int32_t* inputs, int nin, const int32_t* outputs, 
       double n0 = 0.0, n1 = 0.0, nall = 0.0;
       Sub* nw = sub_new(s->n - 1);
       if (!nw) FAIL(OA_ERR_MEMORY);
-#pragma omp parallel for schedule(static) reduction(+ : n0, n1, nall)
-      for (int64_t j = 0; j < half; ++j) {
-        const uint64_t i0 = (((uint64_t)j & ~low) << 1) | ((uint64_t)j & low), i1 = i0 | (low + 1);
-        const cplx a0 = s->t[i0], a1 = s->t[i1];
-        const cplx h0 = (a0 + e * a1) * r2, h1 = (a0 - e * a1) * r2; /* rows of M_0 and M_1 */
-        n0 += creal(h0) * creal(h0) + cimag(h0) * cimag(h0);
-        n1 += creal(h1) * creal(h1) + cimag(h1) * cimag(h1);
-        nall += creal(a0) * creal(a0) + cimag(a0) * cimag(a0) + creal(a1) * creal(a1) + cimag(a1) * cimag(a1);
-        nw->t[j] = out ? h1 : h0;
+      /* squared norms: compensated (Kahan) sums per thread, then the
+         threads' sums in order, so that the oracle's probabilities stay
+         exact to a few units in the last place at any size */
+#pragma omp parallel
+      {
+        double s0 = 0.0, c0 = 0.0, s1 = 0.0, c1 = 0.0, sa = 0.0, ca = 0.0;
+#pragma omp for schedule(static)
+        for (int64_t j = 0; j < half; ++j) {
+          const uint64_t i0 = (((uint64_t)j & ~low) << 1) | ((uint64_t)j & low), i1 = i0 | (low + 1);
+          const cplx a0 = s->t[i0], a1 = s->t[i1];
+          const cplx h0 = (a0 + e * a1) * r2, h1 = (a0 - e * a1) * r2; /* rows of M_0 and M_1 */
+          kahan(&s0, &c0, creal(h0) * creal(h0) + cimag(h0) * cimag(h0));
+          kahan(&s1, &c1, creal(h1) * creal(h1) + cimag(h1) * cimag(h1));
+          kahan(&sa, &ca, creal(a0) * creal(a0) + cimag(a0) * cimag(a0) + creal(a1) * creal(a1) +
+                              cimag(a1) * cimag(a1));
+          nw->t[j] = out ? h1 : h0;
+        }
+#pragma omp for ordered schedule(static, 1)
+        for (int th = 0; th < omp_threads(); ++th) {
+#pragma omp ordered
+          {
+            n0 += s0;
+            n1 += s1;
+            nall += sa;
+          }
+        }
       }
       const double p = mode == 0 ? (out ? n1 : n0) / nall : 0.5;
       if (mode == 0 && !(p > 0.0)) {

@@ -15,6 +15,8 @@ available; these stand in for them with the same structure).
 """
 from __future__ import annotations
 
+import math
+
 from dataclasses import dataclass
 from typing import List, Optional
 
@@ -50,6 +52,31 @@ def brickwork(rows: int = 28, cols: int = 40, pattern_index: int = 0) -> Workloa
     rng = pattern_rng(1, pattern_index)
     gates, _ = brickwork_circuit(rows, cols, rng)
     p = circuit_to_pattern(rows, gates, f"brickwork{rows}x{cols}")
+    out = forced_outcomes(p, rng)
+    return Workload(p, None, out, p.name)
+
+
+def joined_bricks(rows: int, cols: int, copies: int = 2, pattern_index: int = 0) -> Workload:
+    """`copies` brickwork circuits of rows x cols on disjoint blocks of wires,
+    then one CZ joining the last wire of each block to the first wire of the
+    next and a J layer on those wires: |+> inputs, so the blocks stay
+    separate sub-states (Section 4.1) until the joining E.  Forced seeded
+    outcomes."""
+    rng = pattern_rng(5, pattern_index)
+    gates = []
+    for b in range(copies):
+        g, _ = brickwork_circuit(rows, cols, rng)
+        for gate in g:
+            if gate[0] == "CZ":
+                gates.append(("CZ", gate[1] + b * rows, gate[2] + b * rows))
+            else:
+                gates.append(("J", gate[1] + b * rows, gate[2]))
+    for b in range(copies - 1):
+        u, v = b * rows + rows - 1, (b + 1) * rows
+        gates.append(("CZ", u, v))
+        gates.append(("J", u, 2.0 * math.pi * rng.uniform()))
+        gates.append(("J", v, 2.0 * math.pi * rng.uniform()))
+    p = circuit_to_pattern(rows * copies, gates, f"joined_bricks{copies}x{rows}x{cols}")
     out = forced_outcomes(p, rng)
     return Workload(p, None, out, p.name)
 

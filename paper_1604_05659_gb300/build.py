@@ -27,6 +27,10 @@ LIB = os.path.join(HERE, "libowqs.so")
 BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(HERE, "libowqs_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# owqs_group_seq.cu is compiled once per slice of the sequence table
+# (kGroupSeqSlices in csrc/owqs_group_c64.cuh)
+SEQ_SOURCE = "owqs_group_seq.cu"
+SEQ_SLICES = 4
 
 
 def cuda_home() -> str:
@@ -65,16 +69,22 @@ def build(verbose: bool = False, ptxas_info: bool = False, bounds_check: bool = 
         obj = os.path.join(bdir, f[:-4] + ".o")
         jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function", *defs, *inc, "-c",
                      os.path.join(CSRC, f), "-o", obj])
+    cu_objs = []
     for f in cu:
-        obj = os.path.join(bdir, f[:-3] + ".o")
         extra = ["-Xptxas", "-v"] if ptxas_info else []
-        jobs.append([nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-                     "--expt-relaxed-constexpr", *defs, *extra, *inc, "-c", os.path.join(CSRC, f), "-o", obj])
+        # the sequence-specialised group kernels compile in SEQ_SLICES parallel parts
+        variants = [(f"_{k}", [f"-DOWQS_SEQ_SLICE={k}"]) for k in range(SEQ_SLICES)] if f == SEQ_SOURCE else [("", [])]
+        for suffix, vdefs in variants:
+            obj = os.path.join(bdir, f[:-3] + suffix + ".o")
+            cu_objs.append(obj)
+            jobs.append([nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+                         "--expt-relaxed-constexpr", *defs, *vdefs, *extra, *inc, "-c", os.path.join(CSRC, f),
+                         "-o", obj])
     logs = []
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(max(4, os.cpu_count() or 4), len(jobs))) as ex:
         for out in ex.map(_run, jobs):
             logs.append(out)
-    objs = [os.path.join(bdir, f[:-4] + ".o") for f in cpp] + [os.path.join(bdir, f[:-3] + ".o") for f in cu]
+    objs = [os.path.join(bdir, f[:-4] + ".o") for f in cpp] + cu_objs
     tmp = lib + ".tmp"
     logs.append(_run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread", "-ldl", "-lrt"]))
     os.replace(tmp, lib)
@@ -86,8 +96,7 @@ def build(verbose: bool = False, ptxas_info: bool = False, bounds_check: bool = 
 
 def ensure_built(bounds_check: bool = False) -> str:
     """Build if the library is missing or older than a source file."""
-    cpp, cu = sources()
-    srcs = [os.path.join(CSRC, f) for f in cpp + cu + os.listdir(CSRC) if f.endswith(".h")]
+    srcs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cpp", ".cu", ".h", ".cuh", ".inc"))]
     srcs.append(os.path.join(INCLUDE, "owqs.h"))
     lib = LIB_CHECKED if bounds_check else LIB
     if not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(s) for s in srcs):

@@ -294,6 +294,11 @@ struct GroupParams {
 int plan_group(const std::vector<PassDesc>& passes, size_t i, int dtype, GroupParams& G, LaunchPlan& L,
                bool virt_in = false);
 cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s);
+// the group's register-slot sequence (bits 28-29 m, 24-27 k, 2j and 2j+1 the
+// slot of pass j), and whether a kernel compiled for it exists (complex64,
+// materialised input)
+uint32_t group_sequence_code(const GroupParams& G);
+bool group_sequence_specialised(const GroupParams& G, int dtype, bool virt_in);
 int group_enabled();  // OWQS_GROUP=0 turns group fusion off
 
 
@@ -362,8 +367,42 @@ owqs_status compile_schedule(const Pattern& p, int mode, OutcomeSource& src,
                              std::vector<std::vector<int32_t>>* maps = nullptr,
                              const std::vector<std::vector<uint32_t>>* factors = nullptr);
 
-// Join of one input factor (product input): out[j] = s * in[j mod 2^n_in] *
-// phi[j >> n_in], s = 1/sqrt(norms[fnorm]) (the factor normalised) times
+// Separate sub-states (Section 4.1): the live qubits form components that
+// only an E joins; each component with prepared-and-touched qubits keeps its
+// own array.  The compiler walks the active order as compile_schedule does,
+// per component: a component's pending N/E/X/Z commands fold into its next
+// measure pass, which reads only that component's array; an E between two
+// components joins their arrays (a tensor product, the second component's
+// materialised qubits as the new high bits; a component with no array yet,
+// only |+> qubits, joins for free).  A component measured away entirely
+// leaves a one-amplitude array, a scalar factor.  At the end every
+// component is joined into one array, which the final pass (corrections and
+// the gather to output order) reads.  Ops of different components commute;
+// a component's ops are emitted together, just before its next join and at
+// the end, so that its consecutive measure passes can form pass groups.
+struct CompOp {
+  int kind = 0;        // 0 measure (d on component a), 1 join (b into a), 2 final (d on component a)
+  int a = -1, b = -1;
+  int n_a = 0, n_b = 0;  // join: the materialised widths of a and b (0: a one-amplitude array)
+  PassDesc d;          // measure and final ops
+};
+struct CompSchedule {
+  std::vector<CompOp> ops;   // in launch order
+  int ncomp = 0;             // component ids used by ops are < ncomp
+  int input_comp = -1;       // component whose first array is the caller's input vector (-1: none)
+  int peak_m = 0;            // widest component at a measurement, prepared qubits included (the paper's m)
+  uint64_t peak_amps = 0;    // most amplitudes held in component arrays at once (a pass's input and output both)
+  uint64_t single_amps = 0;  // the same for one array holding every live qubit (two ping-pong buffers)
+  double work = 0;           // amplitudes read and written by the passes and joins
+  double single_work = 0;    // the same for one array over every live qubit
+};
+// real_input: the caller passes an input vector (one component over the
+// inputs); otherwise every input qubit starts as its own |+> component.
+owqs_status compile_components(const Pattern& p, int mode, OutcomeSource& src, bool real_input, CompSchedule& cs);
+
+// Join of one input factor (product input) or of two components (separate
+// sub-states): out[j] = s * in[j mod 2^n_in] * phi[j >> n_in], s =
+// 1/sqrt(norms[fnorm]) if fnorm >= 0 (the factor normalised) times
 // 1/sqrt(norms[norm_in]) if norm_in >= 0; in == nullptr means the scalar 1.
 struct KronParams {
   const void* in;

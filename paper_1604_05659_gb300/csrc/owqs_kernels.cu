@@ -15,19 +15,9 @@
 #include <map>
 #include <mutex>
 
-#include "owqs_internal.h"
+#include "owqs_device.cuh"
 
 namespace owqs {
-
-template <typename T> struct Cplx;
-template <> struct Cplx<float> { using V = float2; };
-template <> struct Cplx<double> { using V = double2; };
-
-__device__ __forceinline__ uint32_t par64(uint64_t v) { return (uint32_t)__popcll(v) & 1u; }
-
-__device__ __forceinline__ uint64_t ins0(uint64_t j, int b) {
-  return ((j >> b) << (b + 1)) | (j & ((1ull << b) - 1));
-}
 
 // sign bit of x(k): c0 ^ parity(k & zmask) ^ XOR_e k_{qu[e]} parity(k & qa[e])
 __device__ __forceinline__ uint32_t qsign(const PassParams& P, uint64_t k) {
@@ -42,33 +32,6 @@ __device__ __forceinline__ double prev_scale(const PassParams& P) {
   const double nv = P.norms[P.norm_in];
   return (nv >= P.thresh && nv > 0.0) ? 1.0 / sqrt(nv) : 0.0;
 }
-
-// Compensated (Kahan) FP32 running sum: per-thread sums of squared norms
-// stay in FP32 across tiles and are promoted to FP64 once per kernel (FP64
-// issues at a small fraction of the FP32 rate on GB300)
-__device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
-  const float y = x - comp;
-  const float t = sum + y;
-  comp = (t - sum) - y;
-  sum = t;
-}
-
-// Bounds-checked builds (-DOWQS_BOUNDS_CHECK): a global access of the pass
-// kernels is first checked against the extent of the buffer it touches (cap
-// elements; 0: not checked); an access outside it is skipped and raises bit
-// 1 of the run's error flag, which the host reports.  Release builds compile
-// the checks away.
-#ifdef OWQS_BOUNDS_CHECK
-__device__ __forceinline__ bool in_extent(uint64_t first, uint64_t count, uint64_t cap, unsigned int* flag) {
-  if (cap == 0 || (first <= cap && count <= cap - first)) return true;
-  atomicOr(flag, 2u);
-  return false;
-}
-#define OWQS_IF_IN_EXTENT(first, count, cap, flag) if (in_extent((first), (count), (cap), (flag)))
-#else
-__device__ __forceinline__ bool in_extent(uint64_t, uint64_t, uint64_t, unsigned int*) { return true; }
-#define OWQS_IF_IN_EXTENT(first, count, cap, flag)
-#endif
 
 // Per-thread running sum of squared norms: compensated FP32 for complex64
 // passes, plain FP64 for complex128
@@ -92,74 +55,6 @@ struct NormAcc<double> {
 __device__ __forceinline__ double2 pass_w1(const PassParams& P) {
   if (P.w1dev) return make_double2(P.w1dev[0], P.w1dev[1]);
   return make_double2(P.w1re, P.w1im);
-}
-
-// ---------------------------------------------------------------------------
-// Block reduction of NV FP64 values into norms[slot .. slot+NV).  Each block
-// stores its partial; the last block to finish (counted with one atomic)
-// adds the partials, one warp per value: lane-strided Neumaier sums in block
-// order, then a fixed shuffle tree, so the result does not depend on block
-// scheduling.  The counter is reset for the next launch.  No thread ever
-// waits on another block.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void finish_slots(double* partials, unsigned int* counter, double* norms, int slot, int nv);
-template <int NV>
-__device__ __forceinline__ void reduce_to_slots(const double (&acc)[NV], double* partials,
-                                                unsigned int* counter, double* norms, int slot, int nv = NV) {
-  __shared__ double sh[NV][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double v = acc[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[i][warp] = v;
-  }
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      double v = lane < nwarp ? sh[i][lane] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) partials[(size_t)i * gridDim.x + blockIdx.x] = v;
-    }
-  }
-  finish_slots(partials, counter, norms, slot, nv);
-}
-
-// Second half of the slot reduction: every block's partials are stored (and
-// fenced by the threads that wrote them); the last block to finish adds them
-// into norms[slot ..).
-__device__ __forceinline__ void finish_slots(double* partials, unsigned int* counter, double* norms, int slot, int nv) {
-  __shared__ int am_last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned prev = atomicAdd(counter, 1u);
-    am_last = (prev == gridDim.x - 1) ? 1 : 0;
-  }
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  // one warp per slot: lane-strided Neumaier sums over the block partials,
-  // then a fixed shuffle tree (the order does not depend on scheduling)
-  for (int i = warp; i < nv; i += nwarp) {
-    double s = 0.0, c = 0.0;
-    for (unsigned blk = lane; blk < gridDim.x; blk += 32) {
-      const double x = __ldcg(&partials[(size_t)i * gridDim.x + blk]);
-      const double t = s + x;
-      c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
-      s = t;
-    }
-    s += c;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) norms[slot + i] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) *counter = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -505,59 +400,6 @@ __global__ void __launch_bounds__(kBlock) k_fast(const PassParams P) {
 // Every mbarrier wait is bounded (kWaitLimitCycles): on expiry the block
 // agrees to stop, records an error code and returns.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kWaitLimitCycles) return false;
-  return true;
-}
-// Test path of the bounded waits: thread 0 waits on a barrier that nothing
-// arrives at, gives up after `limit` cycles and raises the error flag; every
-// thread of the block then returns before any copy is issued.
-__device__ __forceinline__ void stall_and_give_up(long long limit, unsigned int* errflag) {
-  __shared__ uint64_t never;
-  if (threadIdx.x == 0) {
-    mbar_init(&never, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    bool done = mbar_try_wait(&never, 0u);
-    const long long t0 = clock64();
-    while (!done && clock64() - t0 <= limit) done = mbar_try_wait(&never, 0u);
-    if (!done) atomicOr(errflag, 1u);
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
 template <typename T>
 struct TmaShape {
   static constexpr int LTE = kTmaLogTileC64;
@@ -849,545 +691,6 @@ cudaError_t launch_pass(const PassParams& P, const LaunchPlan& L, int dtype, cud
   return dtype == OWQS_C64 ? launch_t<float>(P, L, s) : launch_t<double>(P, L, s);
 }
 
-// VIRT: the group reads the virtual |+> input (G.in == nullptr); a separate
-// instantiation keeps the array-reading kernel free of the test
-template <int M, bool VIRT>
-__global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G);
-
-template <int M, bool VIRT>
-__global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G);
-
-// a tile of 2^(TB-M) free indices x 2^M configurations: TB = 9 for complex64
-// (4 KB, one per warp), 11 for complex128 (32 KB, one per block); the kernel
-// pointer selects the precision
-template <int M, int TB, bool VIRT>
-static cudaError_t launch_group_t(void (*kern)(const GroupParams), const GroupParams& G, cudaStream_t s) {
-  constexpr int STAGE = 32768;  // one block-wide stage, or eight warps' 4 KB stages
-  // stages, barriers, the sign table and the abort flag
-  constexpr int SMEM = kTmaStages * STAGE + 1024;
-  static int grid_cap = 0;
-  static std::mutex mu;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    if (grid_cap == 0) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-      if (e != cudaSuccess) return e;
-      int per_sm = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, SMEM);
-      if (e != cudaSuccess) return e;
-      grid_cap = std::max(1, per_sm) * (max_grid() / 8);
-    }
-  }
-  const uint64_t tiles = 1ull << (G.nfree - (TB - M));
-  const uint64_t blocks = TB == 9 ? (tiles + kBlock / 32 - 1) / (kBlock / 32) : tiles;  // c64: one tile per warp
-  kern<<<capped_grid((int)std::min<uint64_t>(blocks, (uint64_t)grid_cap)), kBlock, SMEM, s>>>(G);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s) {
-  const bool v = G.in == nullptr;
-  if (dtype == OWQS_C64) {
-    switch (G.m) {
-      case 1: return v ? launch_group_t<1, 9, true>(k_group<1, true>, G, s)
-                       : launch_group_t<1, 9, false>(k_group<1, false>, G, s);
-      case 2: return v ? launch_group_t<2, 9, true>(k_group<2, true>, G, s)
-                       : launch_group_t<2, 9, false>(k_group<2, false>, G, s);
-      case 3: return v ? launch_group_t<3, 9, true>(k_group<3, true>, G, s)
-                       : launch_group_t<3, 9, false>(k_group<3, false>, G, s);
-      default: return cudaErrorInvalidValue;
-    }
-  }
-  switch (G.m) {
-    case 1: return v ? launch_group_t<1, 11, true>(k_group64<1, true>, G, s)
-                     : launch_group_t<1, 11, false>(k_group64<1, false>, G, s);
-    case 2: return v ? launch_group_t<2, 11, true>(k_group64<2, true>, G, s)
-                     : launch_group_t<2, 11, false>(k_group64<2, false>, G, s);
-    case 3: return v ? launch_group_t<3, 11, true>(k_group64<3, true>, G, s)
-                     : launch_group_t<3, 11, false>(k_group64<3, false>, G, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Group of up to kGroupMax measure passes in one HBM sweep (complex64): per
-// free index the group is arithmetic on an M-qubit register (the contract,
-// including how the signs and scales are carried, is in owqs_internal.h).
-// Pipelines are warp-private: a warp's tile is 2^(9-M) consecutive free
-// indices, whose 2^M input runs (one per configuration of the register's
-// input qubits) arrive by bulk copies into the warp's own 3-stage ring of
-// 4 KB stages.  The warp refills a stage as soon as its own lanes have read
-// it, so no warp ever waits for another (a block-wide ring, refilled once
-// every warp had released a stage, left the fastest warps waiting for the
-// slowest warp's release plus a DRAM round trip).
-// Each lane takes two consecutive elements at a time and holds their 2^M
-// amplitudes in registers.  Per pass and element: one sign bit XORed into w;
-// per butterfly: one complex product and, per output, two FP32 multiply-adds
-// for the amplitude and one packed FP32x2 multiply-add for its squared norm
-// (the tile's first product starts each pass's accumulator).  The element's
-// sign, the previous array's 1/sqrt(N) and the carried scales and register
-// signs are applied once, at the 16-byte stores.
-// Sign bits: the tile's part (two bits per pass) is evaluated by lanes
-// 0..k-1, one pass each, and OR-reduced across the warp; the element's
-// low-bit parities are fixed per lane (a lane always takes the same offsets
-// within a tile), so per tile one XOR gives every sign bit of an element.
-// Every wait is bounded; a warp that gives up raises the block's abort flag,
-// lets its issued copies land and returns.  Squared norms after every pass
-// are summed per thread in compensated FP32 and reduced once into k slots.
-// ---------------------------------------------------------------------------
-// Block stage of a complex64 group's slot sums (red: the threads'
-// compensated sums, slot-major).  Slot j is summed by warp j % 8 in FP32:
-// lane-strided Kahan sums, then a shuffle tree that carries each step's
-// rounding error (TwoSum); only the block's total goes to FP64, which on
-// GB300 runs at 1/64 of the FP32 rate (a per-thread FP64 tree over twelve
-// slots cost about 15 us per launch).  Out of line, so that the main loop's
-// code does not change with it.
-__device__ __noinline__ void group_slot_sums(const float* red, int k, double c2, const double* nscale,
-                                             double* partials, unsigned int* counter, double* norms, int slot) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int j = warp; j < k; j += nwarp) {
-    float s = 0.f, c = 0.f;
-    for (int t = lane; t < (int)blockDim.x; t += 32) kahan_add(s, c, red[j * blockDim.x + t]);
-    float e = -c;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float so = __shfl_xor_sync(0xffffffffu, s, o), eo = __shfl_xor_sync(0xffffffffu, e, o);
-      const float t = s + so, bp = t - s, err = (s - (t - bp)) + (so - bp);
-      s = t;
-      e = e + eo + err;
-    }
-    if (lane == 0) {
-      partials[(size_t)j * gridDim.x + blockIdx.x] = c2 * nscale[j] * ((double)s + (double)e);
-      __threadfence();
-    }
-  }
-  finish_slots(partials, counter, norms, slot, k);
-}
-
-template <int M, int S>
-__device__ __forceinline__ void group_butterfly(float2 (&x)[1 << M], const GroupPass& P, float wr, float wi,
-                                                float2& nacc, bool first) {
-#pragma unroll
-  for (int h = 0; h < (1 << (M - 1)); ++h) {
-    const int g0 = ((h >> S) << (S + 1)) | (h & ((1 << S) - 1));
-    const int g1 = g0 | (1 << S);
-    const float2 x0 = x[g0], x1 = x[g1];
-    const float2 v = make_float2(fmaf(wr, x1.x, -wi * x1.y), fmaf(wr, x1.y, wi * x1.x));
-    const float2 y0 = make_float2(fmaf(P.ct[g0], v.x, x0.x), fmaf(P.ct[g0], v.y, x0.y));
-    const float2 y1 = make_float2(fmaf(P.ct[g1], v.x, x0.x), fmaf(P.ct[g1], v.y, x0.y));
-    // the tile's first product starts the pass's accumulator (no zeroing)
-    nacc = (first && h == 0) ? __fmul2_rn(y0, y0) : __ffma2_rn(y0, y0, nacc);
-    nacc = __ffma2_rn(y1, y1, nacc);
-    x[g0] = y0;
-    x[g1] = y1;
-  }
-}
-
-// r0, r1: the two elements' sign bits for this pass, at bit 31 (one XOR
-// gives +-w)
-template <int M, int S>
-__device__ __forceinline__ void group_pass2(float2 (&x)[2][1 << M], const GroupPass& P, uint32_t r0, uint32_t r1,
-                                            float2& nacc, bool first) {
-  const uint32_t ur = __float_as_uint(P.fwr), ui = __float_as_uint(P.fwi);
-  group_butterfly<M, S>(x[0], P, __uint_as_float(ur ^ r0), __uint_as_float(ui ^ r0), nacc, first);
-  group_butterfly<M, S>(x[1], P, __uint_as_float(ur ^ r1), __uint_as_float(ui ^ r1), nacc, false);
-}
-
-template <int M, bool VIRT>
-__global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
-  if (G.stall_limit > 0) {
-    stall_and_give_up(G.stall_limit, G.errflag);
-    return;
-  }
-  constexpr int LT = 9 - M, TE = 1 << LT, NC = 1 << M, NS = kTmaStages;
-  constexpr int STAGE = NC * TE * 8;
-  constexpr int EPT = TE / 32;  // elements per lane per tile (even)
-  constexpr int NWARP = kBlock / 32;
-  static_assert(EPT >= 2 && EPT <= 8, "tile shape");
-  static_assert(2 * kGroupMax <= 32, "two sign bits per pass in one word");
-  extern __shared__ __align__(128) unsigned char smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* wsm = smem + warp * NS * STAGE;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NWARP * NS * STAGE) + warp * NS;
-  uint64_t* zf = reinterpret_cast<uint64_t*>(smem + NWARP * NS * STAGE + NWARP * NS * 8);
-  uint64_t* af = zf + kGroupMax;
-  uint32_t* cz = reinterpret_cast<uint32_t*>(af + kGroupMax);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(cz + kGroupMax);
-  const float2* __restrict__ in = reinterpret_cast<const float2*>(G.in);
-  float2* __restrict__ out = reinterpret_cast<float2*>(G.out);
-  double cprev = 1.0;
-  if (G.norm_in >= 0) {
-    const double nv = G.norms[G.norm_in];
-    cprev = (nv >= G.thresh && nv > 0.0) ? 1.0 / sqrt(nv) : 0.0;
-  }
-  const float fprev = (float)cprev;
-  // no input array: every input amplitude is vconst (the virtual |+> input);
-  // the ring then carries no data and only paces the loop
-  constexpr bool virt = VIRT;
-  const float vc = (float)G.vconst;
-  const uint64_t tiles = 1ull << (G.nfree - LT);
-  const uint64_t gw = (uint64_t)blockIdx.x * NWARP + warp;
-  const uint64_t step = (uint64_t)gridDim.x * NWARP;
-  const uint64_t mine = gw < tiles ? (tiles - gw + step - 1) / step : 0;
-  const int k = G.k;
-  uint32_t lowbits[EPT], spread[EPT];
-#pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const uint32_t e = (uint32_t)(lane * 2 + (q >> 1) * 64 + (q & 1));
-    uint32_t sp = e;
-    for (uint32_t lm = G.lowmask; lm; lm &= lm - 1) {
-      const int b = __ffs(lm) - 1;
-      sp = ((sp >> b) << (b + 1)) | (sp & ((1u << b) - 1u));
-    }
-    spread[q] = sp;
-    uint32_t w = 0;
-#pragma unroll
-    for (int j = 0; j < kGroupMax; ++j) {
-      w |= ((uint32_t)__popc(e & G.pass[j].zlo) & 1u) << (2 * j);
-      w |= ((uint32_t)__popc(e & G.pass[j].alo) & 1u) << (2 * j + 1);
-    }
-    lowbits[q] = w;
-  }
-  const uint32_t evenk = 0x55555555u & ((k >= 16) ? 0xffffffffu : ((1u << (2 * k)) - 1u));
-  const bool pair_contig = (G.lowmask & 1u) == 0u;
-
-  auto issue = [&](uint64_t i) {  // lane 0 of the warp
-    const int st = (int)(i % NS);
-    if (virt) {  // no input array: the stage only paces the loop
-      mbar_arrive(&full[st]);
-      return;
-    }
-    float2* buf = reinterpret_cast<float2*>(wsm + st * STAGE);
-    const uint64_t L0 = (gw + i * step) << LT;
-    uint64_t ib = L0;
-    int sorted[M];
-#pragma unroll
-    for (int q = 0; q < M; ++q) sorted[q] = G.B[q];
-#pragma unroll
-    for (int q = 0; q < M; ++q)
-#pragma unroll
-      for (int r = q + 1; r < M; ++r)
-        if (sorted[r] < sorted[q]) {
-          const int tmp = sorted[q];
-          sorted[q] = sorted[r];
-          sorted[r] = tmp;
-        }
-#pragma unroll
-    for (int q = 0; q < M; ++q) ib = ins0(ib, sorted[q]);
-#ifdef OWQS_BOUNDS_CHECK
-    bool ok = true;
-    for (int r = 0; r < G.nruns && ok; ++r) ok = in_extent(ib + G.runoff[r], G.runlen, G.in_cap, G.errflag);
-    if (!ok) {  // a run outside the input: no copy, the run reports the error
-      mbar_arrive(&full[st]);
-      return;
-    }
-#endif
-    mbar_expect_tx(&full[st], (unsigned)STAGE);
-    const unsigned rbytes = G.runlen * (unsigned)sizeof(float2);
-    for (int r = 0; r < G.nruns; ++r) bulk_g2s(buf + r * G.runlen, in + ib + G.runoff[r], rbytes, &full[st]);
-  };
-
-  if (threadIdx.x < kGroupMax) {
-    zf[threadIdx.x] = G.pass[threadIdx.x].zfree;
-    af[threadIdx.x] = G.pass[threadIdx.x].afree;
-    cz[threadIdx.x] = (G.pass[threadIdx.x].c0 & 1u) | ((G.pass[threadIdx.x].zb & 1u) << 1);
-  }
-  if (lane == 0)
-    for (int q = 0; q < NS; ++q) mbar_init(&full[q], 1);
-  if (threadIdx.x == 0) *abort_flag = 0;
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  __syncthreads();
-  if (lane == 0)
-    for (uint64_t q = 0; q < mine && q < (uint64_t)NS; ++q) issue(q);
-
-  float ks[kGroupMax], kc[kGroupMax];
-#pragma unroll
-  for (int j = 0; j < kGroupMax; ++j) ks[j] = kc[j] = 0.f;
-  uint64_t issued = mine < (uint64_t)NS ? mine : (uint64_t)NS;
-  for (uint64_t i = 0; i < mine; ++i) {
-    const int st = (int)(i % NS);
-    if (*abort_flag) break;
-    if (!mbar_wait_bounded(&full[st], (unsigned)((i / NS) & 1u))) {
-      *abort_flag = 1;
-      break;
-    }
-    const float2* buf = reinterpret_cast<const float2*>(wsm + st * STAGE);
-    const uint64_t L0 = (gw + i * step) << LT;
-    // the tile's sign word: lane j < k evaluates pass j's two tile parities
-    uint32_t mybits = 0;
-    if (lane < k)
-      mybits = (((cz[lane] & 1u) ^ par64(L0 & zf[lane])) << (2 * lane)) |
-               ((((cz[lane] >> 1) & 1u) ^ par64(L0 & af[lane])) << (2 * lane + 1));
-    const uint32_t sw = __reduce_or_sync(0xffffffffu, mybits);
-    float2 tacc[kGroupMax];
-#pragma unroll
-    for (int it = 0; it < EPT / 2; ++it) {
-      const int e = lane * 2 + it * 64;
-      float2 x[2][NC];
-      if (virt) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) x[0][c] = x[1][c] = make_float2(vc, 0.f);
-      } else if (pair_contig) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const float4 v = *reinterpret_cast<const float4*>(buf + G.cbase[c] + spread[2 * it]);
-          x[0][c] = make_float2(v.x, v.y);
-          x[1][c] = make_float2(v.z, v.w);
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          x[0][c] = buf[G.cbase[c] + spread[2 * it]];
-          x[1][c] = buf[G.cbase[c] + spread[2 * it + 1]];
-        }
-      }
-      const uint32_t b0 = sw ^ lowbits[2 * it], b1 = sw ^ lowbits[2 * it + 1];
-#pragma unroll
-      for (int j = 0; j < kGroupMax; ++j) {
-        if (j >= k) break;
-        const GroupPass& P = G.pass[j];
-        const uint32_t r0 = (b0 << (30 - 2 * j)) & 0x80000000u, r1 = (b1 << (30 - 2 * j)) & 0x80000000u;
-        if (M == 1 || P.slot == 0) group_pass2<M, 0>(x, P, r0, r1, tacc[j], it == 0);
-        else if (M == 2 || P.slot == 1) group_pass2<M, (M > 1 ? 1 : 0)>(x, P, r0, r1, tacc[j], it == 0);
-        else group_pass2<M, (M > 2 ? 2 : 0)>(x, P, r0, r1, tacc[j], it == 0);
-      }
-      const float f0 = (__popc(b0 & evenk) & 1) ? -fprev : fprev;
-      const float f1 = (__popc(b1 & evenk) & 1) ? -fprev : fprev;
-#pragma unroll
-      for (int g = 0; g < NC; ++g) {
-        const float s0 = f0 * G.fin[g], s1 = f1 * G.fin[g];
-        OWQS_IF_IN_EXTENT(L0 + G.outoff[g] + e, 2, G.out_cap, G.errflag)
-        *reinterpret_cast<float4*>(out + L0 + G.outoff[g] + e) =
-            make_float4(s0 * x[0][g].x, s0 * x[0][g].y, s1 * x[1][g].x, s1 * x[1][g].y);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < kGroupMax; ++j)
-      if (j < k) kahan_add(ks[j], kc[j], tacc[j].x + tacc[j].y);
-    // every lane has read the stage: refill it with this warp's tile i + NS
-    __syncwarp();
-    if (lane == 0 && issued < mine) issue(issued);
-    if (issued < mine) ++issued;
-  }
-  __syncthreads();
-  if (*abort_flag) {
-    if (lane == 0) {
-      if (threadIdx.x == 0) atomicOr(G.errflag, 1u);
-      // let every copy this warp issued land before the block's memory goes away
-      for (uint64_t j = issued > (uint64_t)NS ? issued - NS : 0; j < issued; ++j)
-        mbar_wait_bounded(&full[j % NS], (unsigned)((j / NS) & 1u));
-    }
-    __syncthreads();
-    return;
-  }
-  if (G.norm_out >= 0) {
-    // every copy has landed and been read: the stage memory now holds the
-    // threads' compensated sums, slot-major
-    float* red = reinterpret_cast<float*>(smem);
-#pragma unroll
-    for (int j = 0; j < kGroupMax; ++j) red[j * kBlock + threadIdx.x] = ks[j] - kc[j];
-    __syncthreads();
-    group_slot_sums(red, k, cprev * cprev, G.nscale, G.partials, G.counter, G.norms, G.norm_out);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Pass group in complex128: the same contract as k_group (the signs, scales
-// and register layout of owqs_internal.h), 2^(11-M) free indices per 32 KB
-// tile, one element per thread at a time (a complex128 amplitude is a
-// 16-byte vector), FP64 throughout.  Per butterfly: one complex product and,
-// per output, two FMAs for the amplitude and two for its squared norm: six
-// FP64 instructions per output and measurement, against eight for a single
-// measure pass (k_fast<double>), which is bound by the FP64 pipe on GB300.
-// ---------------------------------------------------------------------------
-template <int M, int S>
-__device__ __forceinline__ void group_butterfly64(double2 (&x)[1 << M], const GroupPass& P, double wr, double wi,
-                                                  double& nacc) {
-#pragma unroll
-  for (int h = 0; h < (1 << (M - 1)); ++h) {
-    const int g0 = ((h >> S) << (S + 1)) | (h & ((1 << S) - 1));
-    const int g1 = g0 | (1 << S);
-    const double2 x0 = x[g0], x1 = x[g1];
-    const double vx = fma(wr, x1.x, -wi * x1.y), vy = fma(wr, x1.y, wi * x1.x);
-    const double2 y0 = make_double2(fma(P.ctd[g0], vx, x0.x), fma(P.ctd[g0], vy, x0.y));
-    const double2 y1 = make_double2(fma(P.ctd[g1], vx, x0.x), fma(P.ctd[g1], vy, x0.y));
-    nacc = fma(y0.x, y0.x, fma(y0.y, y0.y, nacc));
-    nacc = fma(y1.x, y1.x, fma(y1.y, y1.y, nacc));
-    x[g0] = y0;
-    x[g1] = y1;
-  }
-}
-
-template <int M, bool VIRT>
-__global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G) {
-  if (G.stall_limit > 0) {
-    stall_and_give_up(G.stall_limit, G.errflag);
-    return;
-  }
-  constexpr int LT = 11 - M, TE = 1 << LT, NC = 1 << M, NS = kTmaStages;
-  constexpr int STAGE = NC * TE * 16;
-  constexpr int EPT = TE / kBlock;  // elements per thread per tile
-  constexpr int NWARP = kBlock / 32;
-  static_assert(EPT >= 1 && EPT <= 4, "tile shape");
-  extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * STAGE);
-  uint64_t* empty = full + NS;
-  uint32_t* signs = reinterpret_cast<uint32_t*>(smem + NS * STAGE + 2 * NS * 8);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(signs + NS);
-  const double2* __restrict__ in = reinterpret_cast<const double2*>(G.in);
-  double2* __restrict__ out = reinterpret_cast<double2*>(G.out);
-  double cprev = 1.0;
-  if (G.norm_in >= 0) {
-    const double nv = G.norms[G.norm_in];
-    cprev = (nv >= G.thresh && nv > 0.0) ? 1.0 / sqrt(nv) : 0.0;
-  }
-  constexpr bool virt = VIRT;  // virtual |+> input, as in k_group
-  const uint64_t tiles = 1ull << (G.nfree - LT);
-  const uint64_t step = gridDim.x;
-  const uint64_t mine = blockIdx.x < tiles ? (tiles - blockIdx.x + step - 1) / step : 0;
-  constexpr unsigned RUN = TE * sizeof(double2);
-  const int k = G.k;
-  uint32_t lowbits[EPT], spread[EPT];  // element q at offset threadIdx + q kBlock
-#pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const uint32_t e = (uint32_t)(threadIdx.x + q * kBlock);
-    uint32_t sp = e;
-    for (uint32_t lm = G.lowmask; lm; lm &= lm - 1) {
-      const int b = __ffs(lm) - 1;
-      sp = ((sp >> b) << (b + 1)) | (sp & ((1u << b) - 1u));
-    }
-    spread[q] = sp;
-    uint32_t w = 0;
-#pragma unroll
-    for (int j = 0; j < kGroupMax; ++j) {
-      w |= ((uint32_t)__popc(e & G.pass[j].zlo) & 1u) << (2 * j);
-      w |= ((uint32_t)__popc(e & G.pass[j].alo) & 1u) << (2 * j + 1);
-    }
-    lowbits[q] = w;
-  }
-  const uint32_t evenk = 0x55555555u & ((k >= 16) ? 0xffffffffu : ((1u << (2 * k)) - 1u));
-
-  auto issue = [&](uint64_t i) {  // thread 0 only
-    const int st = (int)(i % NS);
-    double2* buf = reinterpret_cast<double2*>(smem + st * STAGE);
-    const uint64_t L0 = (blockIdx.x + i * step) << LT;
-    uint64_t ib = L0;
-    int sorted[M];
-#pragma unroll
-    for (int q = 0; q < M; ++q) sorted[q] = G.B[q];
-#pragma unroll
-    for (int q = 0; q < M; ++q)
-#pragma unroll
-      for (int r = q + 1; r < M; ++r)
-        if (sorted[r] < sorted[q]) {
-          const int tmp = sorted[q];
-          sorted[q] = sorted[r];
-          sorted[r] = tmp;
-        }
-#pragma unroll
-    for (int q = 0; q < M; ++q) ib = ins0(ib, sorted[q]);
-    uint32_t w = 0;
-    for (int j = 0; j < k; ++j) {
-      w |= ((G.pass[j].c0 ^ par64(L0 & G.pass[j].zfree)) & 1u) << (2 * j);
-      w |= ((G.pass[j].zb ^ par64(L0 & G.pass[j].afree)) & 1u) << (2 * j + 1);
-    }
-    signs[st] = w;
-    if (virt) {  // as in k_group
-      mbar_arrive(&full[st]);
-      return;
-    }
-#ifdef OWQS_BOUNDS_CHECK
-    bool ok = true;
-    for (int r = 0; r < G.nruns && ok; ++r) ok = in_extent(ib + G.runoff[r], G.runlen, G.in_cap, G.errflag);
-    if (!ok) {
-      mbar_arrive(&full[st]);
-      return;
-    }
-#endif
-    mbar_expect_tx(&full[st], NC * RUN);
-    const unsigned rbytes = G.runlen * (unsigned)sizeof(double2);
-    for (int r = 0; r < G.nruns; ++r) bulk_g2s(buf + r * G.runlen, in + ib + G.runoff[r], rbytes, &full[st]);
-  };
-
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < NS; ++q) {
-      mbar_init(&full[q], 1);
-      mbar_init(&empty[q], NWARP);
-    }
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (uint64_t q = 0; q < mine && q < (uint64_t)NS; ++q) issue(q);
-
-  double acc[kGroupMax];
-#pragma unroll
-  for (int j = 0; j < kGroupMax; ++j) acc[j] = 0.0;
-  uint64_t issued = mine < (uint64_t)NS ? mine : (uint64_t)NS;
-  for (uint64_t i = 0; i < mine; ++i) {
-    const int st = (int)(i % NS);
-    if (*abort_flag) break;
-    if (!mbar_wait_bounded(&full[st], (unsigned)((i / NS) & 1u))) {
-      *abort_flag = 1;
-      break;
-    }
-    const double2* buf = reinterpret_cast<const double2*>(smem + st * STAGE);
-    const uint32_t sw = signs[st];
-    const uint64_t L0 = (blockIdx.x + i * step) << LT;
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const int e = threadIdx.x + q * kBlock;
-      double2 x[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) x[c] = virt ? make_double2(G.vconst, 0.0) : buf[G.cbase[c] + spread[q]];
-      const uint32_t b = sw ^ lowbits[q];
-#pragma unroll
-      for (int j = 0; j < kGroupMax; ++j) {
-        if (j >= k) break;
-        const GroupPass& P = G.pass[j];
-        const bool rho = (b >> (2 * j + 1)) & 1u;
-        const double wr = rho ? -P.wre : P.wre, wi = rho ? -P.wim : P.wim;
-        if (M == 1 || P.slot == 0) group_butterfly64<M, 0>(x, P, wr, wi, acc[j]);
-        else if (M == 2 || P.slot == 1) group_butterfly64<M, (M > 1 ? 1 : 0)>(x, P, wr, wi, acc[j]);
-        else group_butterfly64<M, (M > 2 ? 2 : 0)>(x, P, wr, wi, acc[j]);
-      }
-      const double f = (__popc(b & evenk) & 1) ? -cprev : cprev;
-#pragma unroll
-      for (int g = 0; g < NC; ++g) {
-        const double sc = f * G.find[g];
-        OWQS_IF_IN_EXTENT(L0 + G.outoff[g] + e, 1, G.out_cap, G.errflag)
-        out[L0 + G.outoff[g] + e] = make_double2(sc * x[g].x, sc * x[g].y);
-      }
-    }
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[st]);
-    if (threadIdx.x == 0 && issued < mine) {
-      if (!mbar_wait_bounded(&empty[st], (unsigned)((i / NS) & 1u))) {
-        *abort_flag = 1;
-        break;
-      }
-      issue(issued++);
-    }
-  }
-  __syncthreads();
-  if (*abort_flag) {
-    if (threadIdx.x == 0) {
-      atomicOr(G.errflag, 1u);
-      for (uint64_t j = issued > (uint64_t)NS ? issued - NS : 0; j < issued; ++j)
-        mbar_wait_bounded(&full[j % NS], (unsigned)((j / NS) & 1u));
-    }
-    __syncthreads();
-    return;
-  }
-  if (G.norm_out >= 0) {
-    const double c2 = cprev * cprev;
-    double a[kGroupMax];
-#pragma unroll
-    for (int j = 0; j < kGroupMax; ++j) a[j] = c2 * G.nscale[j] * acc[j];
-    reduce_to_slots<kGroupMax>(a, G.partials, G.counter, G.norms, G.norm_out, k);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Outcome of one measurement drawn on the device (sampled policy): u is
 // output number `draw` of the splitmix64 stream seeded with *seed (the
@@ -1445,8 +748,10 @@ __global__ void __launch_bounds__(kBlock) k_kron(const KronParams K) {
   const V* __restrict__ phi = reinterpret_cast<const V*>(K.phi);
   V* __restrict__ out = reinterpret_cast<V*>(K.out);
   double sc = 1.0;
-  const double nf = K.norms[K.fnorm];
-  sc = nf > 0.0 ? 1.0 / sqrt(nf) : 0.0;
+  if (K.fnorm >= 0) {  // -1: the factor is taken as normalised
+    const double nf = K.norms[K.fnorm];
+    sc = nf > 0.0 ? 1.0 / sqrt(nf) : 0.0;
+  }
   if (K.norm_in >= 0) {
     const double nv = K.norms[K.norm_in];
     sc = nv > 0.0 ? sc / sqrt(nv) : 0.0;

@@ -35,6 +35,10 @@ struct RunCache {
   std::vector<unsigned char> small_host;
   std::vector<double> h_norms;
   uint32_t last_launches = 0;
+  void* arena = nullptr;  // separate sub-states: every component array, at planned offsets
+  size_t arena_bytes = 0;
+  uint32_t last_components = 0;  // separate sub-states: components of the last run (0: one array)
+  uint64_t last_peak_bytes = 0;  // device bytes of the last run's live arrays at their peak
 
   ~RunCache() {
     int cur = -1;
@@ -43,7 +47,7 @@ struct RunCache {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (cap) cudaStreamDestroy(cap);
     for (void* p : {buf[0], buf[1], in_stage, out_stage, (void*)norms, (void*)partials, (void*)counter, samp,
-                    small_dev})
+                    small_dev, arena})
       if (p) cudaFree(p);
     if (device >= 0 && cur >= 0 && cur != device) cudaSetDevice(cur);
   }
@@ -223,6 +227,82 @@ class Runner {
     for (int j = 1; j < G.k; ++j) in_group.push_back(1);
     pass_i_ += G.k;
   }
+
+  // Explicit-array forms (separate sub-states): the caller supplies the
+  // arrays, their extents in amplitudes and the norm slots.
+  void measure_at(const PassDesc& d, const void* in, uint64_t in_cap, void* out, uint64_t out_cap, int norm_in,
+                  int norm_out) {
+    Item it;
+    plan_pass(d, dtype_, in == nullptr, it.P, it.L);
+    fill_common(it.P);
+    it.P.in = in;
+    it.P.out = out;
+    it.P.in_cap = in_cap;
+    it.P.out_cap = out_cap;
+    it.P.norm_in = norm_in;
+    it.P.norm_out = norm_out;
+    it.L.meas = 1;
+    issue(it);
+    in_group.push_back(0);
+    ++pass_i_;
+  }
+  void group_at(const GroupParams& G, const LaunchPlan& L, const void* in, uint64_t in_cap, void* out,
+                uint64_t out_cap, int norm_in, int norm_out) {
+    Item it;
+    it.type = 4;
+    it.G = G;
+    it.L = L;
+    it.L.meas = G.k;
+    it.G.norms = rc_.norms;
+    it.G.partials = rc_.partials;
+    it.G.counter = rc_.counter;
+    it.G.errflag = rc_.counter + 1;
+    it.G.thresh = thresh_;
+    it.G.in = in;
+    it.G.out = out;
+    it.G.in_cap = in_cap;
+    it.G.out_cap = out_cap;
+    it.G.norm_in = norm_in;
+    it.G.norm_out = norm_out;
+    issue(it);
+    in_group.push_back(0);
+    for (int j = 1; j < G.k; ++j) in_group.push_back(1);
+    pass_i_ += G.k;
+  }
+  // out = a (x) b, a's n_a qubits low: each factor divided by the square root
+  // of its norm slot (-1: taken as normalised)
+  void join_at(const void* a, int n_a, int norm_a, const void* b, int n_b, int norm_b, void* out, uint64_t out_cap) {
+    Item it;
+    it.type = 5;
+    it.Kp.in = a;
+    it.Kp.out = out;
+    it.Kp.phi = b;
+    it.Kp.norms = rc_.norms;
+    it.Kp.n_in = n_a;
+    it.Kp.q = n_b;
+    it.Kp.norm_in = norm_a;
+    it.Kp.fnorm = norm_b;
+    it.Kp.in_cap = 1ull << n_a;
+    it.Kp.out_cap = out_cap;
+    it.Kp.errflag = rc_.counter + 1;
+    it.L.kind = KK_KRON;
+    it.L.bytes = (std::ldexp(1.0, n_a) + std::ldexp(1.0, n_b) + std::ldexp(1.0, n_a + n_b)) *
+                 (dtype_ == OWQS_C64 ? 8.0 : 16.0);
+    issue(it);
+  }
+  void final_at(const PassDesc& d, const void* in, uint64_t in_cap, int norm_in) {
+    Item it;
+    plan_pass(d, dtype_, in == nullptr, it.P, it.L);
+    fill_common(it.P);
+    it.P.in = in;
+    it.P.out = out_final_;
+    it.P.in_cap = in_cap;
+    it.P.out_cap = out_cap_;
+    it.P.norm_in = norm_in;
+    it.P.norm_out = K_ + 1;
+    issue(it);
+  }
+  int pass_index() const { return pass_i_; }
 
   // join of an input factor (product input): its norm into slot fslot, then
   // the tensor product with the live array (normalised), the factor's qubits
@@ -525,6 +605,175 @@ static owqs_status prepare(Pattern& p, const owqs_run_opts* o, const void* psi_i
   return OWQS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// separate sub-states: launch records, arena plan, items
+// ---------------------------------------------------------------------------
+namespace {
+// First-fit plan of byte ranges in one arena (256-byte aligned).
+struct ArenaPlan {
+  std::vector<std::pair<size_t, size_t>> free_;  // (offset, length), sorted by offset
+  size_t end = 0;
+  size_t alloc(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    for (size_t i = 0; i < free_.size(); ++i)
+      if (free_[i].second >= bytes) {
+        const size_t off = free_[i].first;
+        free_[i].first += bytes;
+        free_[i].second -= bytes;
+        if (free_[i].second == 0) free_.erase(free_.begin() + i);
+        return off;
+      }
+    const size_t off = end;
+    end += bytes;
+    return off;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    auto it = std::lower_bound(free_.begin(), free_.end(), std::make_pair(off, (size_t)0));
+    it = free_.insert(it, {off, bytes});
+    const size_t i = (size_t)(it - free_.begin());
+    if (i + 1 < free_.size() && free_[i].first + free_[i].second == free_[i + 1].first) {
+      free_[i].second += free_[i + 1].second;
+      free_.erase(free_.begin() + i + 1);
+    }
+    if (i > 0 && free_[i - 1].first + free_[i - 1].second == free_[i].first) {
+      free_[i - 1].second += free_[i].second;
+      free_.erase(free_.begin() + i);
+    }
+  }
+};
+constexpr long long kUserInput = -2;  // the caller's input vector (not in the arena)
+struct CompLaunch {
+  int type = 0;  // 0 single measure pass, 1 pass group, 2 join, 3 final pass
+  PassDesc d;
+  GroupParams G;
+  LaunchPlan GL;
+  long long in_off = -1, in2_off = -1, out_off = -1;  // -1: no array (virtual |+> input) / the caller's output
+  uint64_t in_cap = 0, in2_cap = 0, out_cap = 0;
+  int n_a = 0, n_b = 0;
+  int comp = -1, comp2 = -1;
+};
+}  // namespace
+
+// A default run takes separate sub-states when they at least halve the
+// amplitudes the passes move and need no more memory than one array.
+static bool use_substates(const CompSchedule& cs) {
+  return 2.0 * cs.work <= cs.single_work && cs.peak_amps <= cs.single_amps;
+}
+
+// Walk a component schedule: measure passes of one component that follow
+// each other form pass groups as in a one-array run; every array gets an
+// arena range while it is live.  Fills `launches`, the arena size and the
+// measure passes in launch order (the order of the norm slots).
+static owqs_status plan_components(const CompSchedule& cs, int dtype, size_t amp, bool real_input, uint64_t in_elems,
+                                   std::vector<CompLaunch>& launches, size_t& arena_bytes,
+                                   std::vector<PassDesc>& order) {
+  ArenaPlan ap;
+  std::vector<long long> off(cs.ncomp, -1);  // arena offset of each component's array
+  std::vector<uint64_t> cap(cs.ncomp, 0);
+  if (cs.input_comp >= 0 && real_input) {
+    off[cs.input_comp] = kUserInput;
+    cap[cs.input_comp] = in_elems;
+  }
+  auto release = [&](int c) {
+    if (off[c] >= 0) ap.release((size_t)off[c], cap[c] * amp);
+    off[c] = -1;
+    cap[c] = 0;
+  };
+  order.clear();
+  for (size_t i = 0; i < cs.ops.size();) {
+    const CompOp& op = cs.ops[i];
+    if (op.kind == 0) {
+      std::vector<PassDesc> chain;
+      size_t j = i;
+      for (; j < cs.ops.size() && cs.ops[j].kind == 0 && cs.ops[j].a == op.a; ++j) chain.push_back(cs.ops[j].d);
+      for (size_t q = 0; q < chain.size();) {
+        CompLaunch L;
+        L.comp = op.a;
+        int k = 1;
+        const bool real = off[op.a] != -1;
+        if (real && group_enabled()) {
+          const int g = plan_group(chain, q, dtype, L.G, L.GL, false);
+          if (g >= 2) k = g;
+        } else if (!real && group_enabled()) {
+          const int g = plan_group(chain, q, dtype, L.G, L.GL, true);
+          if (g >= 2) k = g;
+        }
+        L.type = k >= 2 ? 1 : 0;
+        L.d = chain[q];
+        L.in_off = off[op.a];
+        L.in_cap = cap[op.a];
+        L.out_cap = 1ull << chain[q + k - 1].n_out;
+        L.out_off = (long long)ap.alloc(L.out_cap * amp);
+        release(op.a);
+        off[op.a] = L.out_off;
+        cap[op.a] = L.out_cap;
+        for (int t = 0; t < k; ++t) order.push_back(chain[q + t]);
+        launches.push_back(std::move(L));
+        q += (size_t)k;
+      }
+      i = j;
+    } else if (op.kind == 1) {
+      CompLaunch L;
+      L.type = 2;
+      L.comp = op.a;
+      L.comp2 = op.b;
+      L.n_a = op.n_a;
+      L.n_b = op.n_b;
+      L.in_off = off[op.a];
+      L.in_cap = cap[op.a];
+      L.in2_off = off[op.b];
+      L.in2_cap = cap[op.b];
+      L.out_cap = 1ull << (op.n_a + op.n_b);
+      L.out_off = (long long)ap.alloc(L.out_cap * amp);
+      release(op.a);
+      release(op.b);
+      off[op.a] = L.out_off;
+      cap[op.a] = L.out_cap;
+      launches.push_back(std::move(L));
+      ++i;
+    } else {
+      CompLaunch L;
+      L.type = 3;
+      L.comp = op.a;
+      L.d = op.d;
+      L.in_off = off[op.a];
+      L.in_cap = cap[op.a];
+      order.push_back(op.d);
+      launches.push_back(std::move(L));
+      ++i;
+    }
+  }
+  arena_bytes = std::max<size_t>(ap.end, 256);
+  return OWQS_OK;
+}
+
+// Issue the launch records as runner items: arena offsets become pointers,
+// every component keeps the norm slot that its next launch divides by.
+static void issue_components(const std::vector<CompLaunch>& launches, int ncomp, int input_comp, bool owqs,
+                             bool real_input, const void* in_dev, char* arena, Runner& R) {
+  std::vector<int> prev(ncomp, -1);
+  if (input_comp >= 0 && real_input && owqs) prev[input_comp] = 0;  // the input's norm (slot 0)
+  auto ptr = [&](long long off) -> const void* {
+    return off == kUserInput ? in_dev : (off >= 0 ? (const void*)(arena + off) : nullptr);
+  };
+  for (const CompLaunch& L : launches) {
+    if (L.type == 0 || L.type == 1) {
+      const int slot = owqs ? R.pass_index() + 1 : -1;
+      void* out = arena + L.out_off;
+      if (L.type == 0) R.measure_at(L.d, ptr(L.in_off), L.in_cap, out, L.out_cap, prev[L.comp], slot);
+      else R.group_at(L.G, L.GL, ptr(L.in_off), L.in_cap, out, L.out_cap, prev[L.comp], slot);
+      if (owqs) prev[L.comp] = R.pass_index();
+    } else if (L.type == 2) {
+      R.join_at(ptr(L.in_off), L.n_a, prev[L.comp], ptr(L.in2_off), L.n_b, prev[L.comp2], arena + L.out_off,
+                L.out_cap);
+      prev[L.comp] = -1;  // the tensor product of normalised factors
+    } else {
+      R.final_at(L.d, ptr(L.in_off), L.in_cap, owqs ? prev[L.comp] : -1);
+    }
+  }
+}
+
 static owqs_status ensure_pingpong(RunCache* rc, size_t elems, size_t amp) {
   const size_t need = std::max<size_t>(elems, 1) * amp;
   if (rc->buf_bytes >= need && rc->buf[0] && rc->buf[1]) return OWQS_OK;
@@ -815,18 +1064,57 @@ static owqs_status run_core(Pattern& p, const owqs_run_opts* o, const void* psi_
     for (const PassDesc& d : pr.passes)
       if (d.kind == 0) outcome_of_pass.push_back(d.outcome);
   } else {
-    size_t wmax = 1;
-    for (const PassDesc& d : pr.passes)
-      if (d.kind != 1) wmax = std::max<size_t>(wmax, (size_t)1 << d.n_out);
-    st = ensure_pingpong(rc, wmax, pr.amp);
-    if (st != OWQS_OK) return st;
+    // separate sub-states (Section 4.1) when the components' arrays need at
+    // most half the memory of one array over every live qubit, or when asked
+    CompSchedule cs;
+    bool comps = false;
+    if (!prod && vdiag == 0 && !(o->flags & OWQS_RUN_ONE_ARRAY)) {
+      FixedSource csrc(p, o->policy == OWQS_OUTCOME_ZERO ? nullptr : outcomes);
+      st = compile_components(p, o->mode, csrc, pr.in_dev != nullptr, cs);
+      if (st != OWQS_OK) {
+        if (o->flags & OWQS_RUN_SUBSTATES) return st;
+        clear_error();
+      } else {
+        comps = (o->flags & OWQS_RUN_SUBSTATES) || use_substates(cs);
+      }
+    } else if (o->flags & OWQS_RUN_SUBSTATES) {
+      return set_error(OWQS_ERR_UNSUPPORTED, "separate sub-states take one input vector (no product input, no unitary)");
+    }
+    std::vector<CompLaunch> claunch;
+    size_t arena_need = 0;
+    if (comps) {
+      st = plan_components(cs, o->dtype, pr.amp, pr.in_dev != nullptr, pr.in_elems, claunch, arena_need, pr.passes);
+      if (st != OWQS_OK) return st;
+      if (rc->arena_bytes < arena_need || !rc->arena) {
+        if (rc->gexec) {  // graphs hold the old addresses
+          cudaGraphExecDestroy(rc->gexec);
+          rc->gexec = nullptr;
+          rc->gkey.clear();
+        }
+        st = ensure_buf(rc->arena, rc->arena_bytes, arena_need, "sub-state arena");
+        if (st != OWQS_OK) return st;
+      }
+      rc->last_components = (uint32_t)cs.ncomp;
+      rc->last_peak_bytes = (uint64_t)arena_need;
+    } else {
+      size_t wmax = 1;
+      for (const PassDesc& d : pr.passes)
+        if (d.kind != 1) wmax = std::max<size_t>(wmax, (size_t)1 << d.n_out);
+      st = ensure_pingpong(rc, wmax, pr.amp);
+      if (st != OWQS_OK) return st;
+      rc->last_components = 0;
+      rc->last_peak_bytes = (uint64_t)rc->buf_bytes * 2;
+    }
     for (const PassDesc& d : pr.passes)
       if (d.kind == 0) outcome_of_pass.push_back(d.outcome);
     Runner R(p, *rc, o->dtype, o->mode, s);
     R.vdiag = vdiag;
     R.begin(pr.in_dev, pr.in_elems, pr.out_dev, pr.out_elems);
-    const bool small = !prod && !(o->flags & OWQS_RUN_PER_PASS) && small_run_ok(pr.passes);
-    for (size_t i = 0; i < pr.passes.size(); ++i) {
+    const bool small = !comps && !prod && !(o->flags & OWQS_RUN_PER_PASS) && small_run_ok(pr.passes);
+    if (comps)
+      issue_components(claunch, cs.ncomp, cs.input_comp, o->mode == OWQS_MODE_OWQS, pr.in_dev != nullptr, pr.in_dev,
+                       static_cast<char*>(rc->arena), R);
+    for (size_t i = 0; !comps && i < pr.passes.size(); ++i) {
       const PassDesc& d = pr.passes[i];
       if (small) {  // planned one pass at a time, run in one kernel below
         if (d.kind == 1) R.final_pass(d);
@@ -956,6 +1244,10 @@ static owqs_status run_core(Pattern& p, const owqs_run_opts* o, const void* psi_
         st = replay(rc, R, std::string(), false, s);
       } else {
         std::string key = graph_key(p, o, pr.in_dev, pr.out_dev, outcomes);
+        if (comps) {  // a component run: its arena (the items hold pointers into it)
+          key.push_back('C');
+          key.append(reinterpret_cast<const char*>(&rc->arena), sizeof(rc->arena));
+        }
         if (prod)
           for (const void* v : prod->vecs) key.append(reinterpret_cast<const char*>(&v), sizeof(v));
         st = replay(rc, R, key, o->use_graph != 0, s);
@@ -1205,6 +1497,69 @@ owqs_status owqs_profile_run(owqs_pattern* h, const owqs_run_opts* o, const void
   if (outcomes) oc.assign(outcomes, outcomes + h->p.meas_qubit.size());
   return run_impl(h->p, o, psi_in, psi_out, oc.empty() ? nullptr : oc.data(), nullptr, ms, bytes, kind, cap,
                   nlaunch, 0, nullptr, nullptr, nmeas);
+}
+
+owqs_status owqs_plan_memory(const owqs_pattern* h, uint32_t dtype, uint32_t mode, uint32_t real_input,
+                            const uint8_t* outcomes, owqs_memory_plan* plan) {
+  clear_error();
+  if (!h || !plan) return set_error(OWQS_ERR_ARG, "NULL argument");
+  if (dtype > OWQS_C128 || mode > OWQS_MODE_EOWQS) return set_error(OWQS_ERR_ARG, "bad option value");
+  FixedSource src(h->p, outcomes);
+  CompSchedule cs;
+  owqs_status st = compile_components(h->p, (int)mode, src, real_input != 0, cs);
+  if (st != OWQS_OK) return st;
+  const size_t amp = dtype == OWQS_C64 ? 8 : 16;
+  std::vector<CompLaunch> launches;
+  std::vector<PassDesc> order;
+  size_t arena = 0;
+  st = plan_components(cs, (int)dtype, amp, real_input != 0, 1ull << h->p.inputs.size(), launches, arena, order);
+  if (st != OWQS_OK) return st;
+  std::memset(plan, 0, sizeof(*plan));
+  plan->peak_m = (uint32_t)cs.peak_m;
+  plan->components = (uint32_t)cs.ncomp;
+  plan->substate_bytes = (uint64_t)arena;
+  plan->one_array_bytes = (uint64_t)cs.single_amps * amp;
+  for (const CompLaunch& L : launches) plan->joins += L.type == 2 ? 1u : 0u;
+  plan->uses_substates = use_substates(cs) ? 1u : 0u;
+  plan->substate_work = cs.work;
+  plan->one_array_work = cs.single_work;
+  return OWQS_OK;
+}
+
+owqs_status owqs_describe_groups(const owqs_pattern* h, uint32_t dtype, uint32_t mode, uint32_t real_input,
+                                const uint8_t* outcomes, uint32_t* regs, uint32_t* slots, uint32_t* n_in,
+                                uint32_t* specialised, uint32_t cap, uint32_t* ngroups) {
+  clear_error();
+  if (!h || !ngroups) return set_error(OWQS_ERR_ARG, "NULL argument");
+  if (dtype > OWQS_C128 || mode > OWQS_MODE_EOWQS) return set_error(OWQS_ERR_ARG, "bad option value");
+  FixedSource src(h->p, outcomes);
+  std::vector<PassDesc> passes;
+  owqs_status st = compile_schedule(h->p, (int)mode, src, passes);
+  if (st != OWQS_OK) return st;
+  uint32_t n = 0;
+  bool real = real_input != 0;
+  if (!small_run_ok(passes)) {
+    for (size_t i = 0; i < passes.size(); ++i) {
+      GroupParams G;
+      LaunchPlan GL;
+      int k = 0;
+      const int kind = decide_launch(passes, i, (int)dtype, real, false, G, GL, k);
+      if (kind == LAUNCH_GROUP) {
+        if (n < cap) {
+          if (regs) regs[n] = (uint32_t)G.m;
+          if (slots) slots[n] = group_sequence_code(G) & 0x0fffffffu;
+          if (n_in) n_in[n] = (uint32_t)passes[i].n_in;
+          // the launch reads the virtual |+> input only while no array exists
+          if (specialised) specialised[n] = group_sequence_specialised(G, (int)dtype, !real) ? 1u : 0u;
+        }
+        ++n;
+      }
+      if (kind == LAUNCH_GROUP || kind == LAUNCH_SINGLE) real = true;
+      if (kind == LAUNCH_GROUP) i += (size_t)k - 1;
+    }
+  }
+  *ngroups = n;
+  return OWQS_OK;
 }
 
 owqs_status owqs_describe_launches(const owqs_pattern* h, uint32_t dtype, uint32_t mode, uint32_t real_input,

@@ -223,6 +223,257 @@ owqs_status compile_schedule(const Pattern& p, int mode, OutcomeSource& src,
 }
 
 // ---------------------------------------------------------------------------
+// separate sub-states (Section 4.1)
+// ---------------------------------------------------------------------------
+namespace {
+struct Comp {
+  std::vector<uint32_t> bits;  // qubit at each bit: [0, nmat) in the array, then prepared (|+>) ones
+  int nmat = 0;
+  bool arr = false;            // an array exists (nmat qubits; nmat = 0: one amplitude)
+  bool alive = true;
+  uint64_t adj[64] = {0};      // pending segment, over the bit positions
+  uint64_t z = 0, x = 0;
+  uint32_t c0 = 0;
+  std::vector<CompOp> queue;   // ops not emitted yet
+};
+}  // namespace
+
+owqs_status compile_components(const Pattern& p, int mode, OutcomeSource& src, bool real_input, CompSchedule& cs) {
+  cs = CompSchedule();
+  const uint32_t n = p.n;
+  std::vector<int8_t> outcome(n, 0);
+  if (!src.known_upfront(outcome)) return set_error(OWQS_ERR_UNSUPPORTED, "separate sub-states need outcomes known before the run");
+  std::vector<Comp> comps;
+  std::vector<int32_t> owner(n, -1);
+  auto pos_of = [&](const Comp& c, uint32_t q) -> int {
+    for (size_t i = 0; i < c.bits.size(); ++i)
+      if (c.bits[i] == q) return (int)i;
+    return -1;
+  };
+  auto new_comp = [&](uint32_t q) -> int {
+    comps.emplace_back();
+    comps.back().bits.push_back(q);
+    owner[q] = (int)comps.size() - 1;
+    return owner[q];
+  };
+  if (real_input) {
+    comps.emplace_back();
+    Comp& c = comps.back();
+    c.bits = p.inputs;
+    c.nmat = (int)p.inputs.size();
+    c.arr = true;
+    for (uint32_t q : p.inputs) owner[q] = 0;
+    cs.input_comp = 0;
+    if (c.nmat > kMaxLive) return set_error(OWQS_ERR_OOM, "more than 62 input qubits");
+  } else {
+    for (uint32_t q : p.inputs) new_comp(q);
+  }
+  // live amplitudes: arrays alive now, and the peak over the run
+  uint64_t live = real_input ? (1ull << p.inputs.size()) : 0, peak = live;
+  uint64_t single_live_max = 0;  // widest single-array pass (the one-array plan)
+  int single_w = (int)p.inputs.size();
+  auto flush = [&](int id) {
+    for (CompOp& op : comps[id].queue) cs.ops.push_back(std::move(op));
+    comps[id].queue.clear();
+  };
+  auto arr_amps = [&](const Comp& c) -> uint64_t { return c.arr ? (1ull << c.nmat) : 0; };
+  // join component b into a; returns the merged id (the one holding an
+  // array, so that its array keeps its id)
+  auto merge = [&](int a, int b) -> int {
+    if (comps[b].arr && !comps[a].arr) std::swap(a, b);
+    Comp& A = comps[a];
+    Comp& B = comps[b];
+    flush(a);
+    flush(b);
+    std::vector<uint32_t> nb;
+    nb.insert(nb.end(), A.bits.begin(), A.bits.begin() + A.nmat);
+    nb.insert(nb.end(), B.bits.begin(), B.bits.begin() + B.nmat);
+    nb.insert(nb.end(), A.bits.begin() + A.nmat, A.bits.end());
+    nb.insert(nb.end(), B.bits.begin() + B.nmat, B.bits.end());
+    if ((int)nb.size() > kMaxLive) return -1;
+    std::vector<int> posA(A.bits.size()), posB(B.bits.size());
+    for (size_t i = 0; i < A.bits.size(); ++i) posA[i] = (int)i < A.nmat ? (int)i : B.nmat + (int)i;
+    for (size_t i = 0; i < B.bits.size(); ++i)
+      posB[i] = (int)i < B.nmat ? A.nmat + (int)i : (int)A.bits.size() + (int)i;
+    uint64_t adj[64] = {0}, z = 0, x = 0;
+    auto remap = [&](const Comp& C, const std::vector<int>& pos) {
+      for (size_t u = 0; u < C.bits.size(); ++u) {
+        for (uint64_t m = C.adj[u]; m; m &= m - 1) adj[pos[u]] |= 1ull << pos[__builtin_ctzll(m)];
+        if ((C.z >> u) & 1u) z |= 1ull << pos[u];
+        if ((C.x >> u) & 1u) x |= 1ull << pos[u];
+      }
+    };
+    remap(A, posA);
+    remap(B, posB);
+    if (A.arr && B.arr) {  // tensor product of the two arrays
+      CompOp op;
+      op.kind = 1;
+      op.a = a;
+      op.b = b;
+      op.n_a = A.nmat;
+      op.n_b = B.nmat;
+      cs.ops.push_back(op);
+      cs.work += std::ldexp(1.0, A.nmat) + std::ldexp(1.0, B.nmat) + std::ldexp(1.0, A.nmat + B.nmat);
+      const uint64_t before = live;
+      live += 1ull << (A.nmat + B.nmat);
+      peak = std::max<uint64_t>(peak, live);
+      live = before - arr_amps(A) - arr_amps(B) + (1ull << (A.nmat + B.nmat));
+    }
+    A.c0 ^= B.c0;
+    A.nmat += B.nmat;
+    A.arr = A.arr || B.arr;
+    A.bits = nb;
+    std::memcpy(A.adj, adj, sizeof(adj));
+    A.z = z;
+    A.x = x;
+    for (uint32_t q : B.bits) owner[q] = a;
+    B.alive = false;
+    B.bits.clear();
+    return a;
+  };
+  auto touch = [&](uint32_t q) -> int {
+    if (owner[q] < 0) {
+      new_comp(q);
+      ++single_w;
+    }
+    return owner[q];
+  };
+  for (size_t ai = 0; ai < p.active.size(); ++ai) {
+    const Cmd& c = p.cmds[p.active[ai]];
+    switch (c.kind) {
+      case OWQS_CMD_N:
+        break;  // prepared at first touch
+      case OWQS_CMD_E: {
+        int a = touch(c.q0), b = touch(c.q1);
+        if (a != b) {
+          a = merge(a, b);
+          if (a < 0) return set_error(OWQS_ERR_OOM, "a sub-state wider than 62 qubits; reorder the pattern");
+        }
+        Comp& C = comps[a];
+        const int u = pos_of(C, c.q0), v = pos_of(C, c.q1);
+        C.adj[u] ^= 1ull << v;
+        C.adj[v] ^= 1ull << u;
+        break;
+      }
+      case OWQS_CMD_Z: {
+        Comp& C = comps[touch(c.q0)];
+        const int u = pos_of(C, c.q0);
+        if (parity_of(outcome, c.sdom)) C.z ^= 1ull << u;
+        break;
+      }
+      case OWQS_CMD_X: {
+        Comp& C = comps[touch(c.q0)];
+        const int u = pos_of(C, c.q0);
+        if (parity_of(outcome, c.sdom)) {  // as in compile_schedule
+          C.c0 ^= (uint32_t)((C.z >> u) & 1u);
+          C.z ^= C.adj[u];
+          C.x ^= 1ull << u;
+        }
+        break;
+      }
+      case OWQS_CMD_M: {
+        const int id = touch(c.q0);
+        Comp& C = comps[id];
+        const int b = pos_of(C, c.q0);
+        const int width = (int)C.bits.size();
+        cs.peak_m = std::max(cs.peak_m, width);
+        single_live_max = std::max<uint64_t>(single_live_max, 1ull << std::min(single_w, 62));
+        cs.work += (C.arr ? std::ldexp(1.0, C.nmat) : 0.0) + std::ldexp(1.0, width - 1);
+        cs.single_work += std::ldexp(1.0, single_w);  // read and write about 2^(w-1) each
+        PassDesc d;
+        d.kind = 0;
+        d.n_in = C.nmat;
+        d.r = width - C.nmat;
+        d.b = b;
+        d.n_out = width - 1;
+        d.meas_k = (uint32_t)p.k_of_qubit[c.q0];
+        d.xmask = C.nmat ? (C.x & ((1ull << C.nmat) - 1)) : 0;  // X on a |+> qubit is dropped
+        d.zmask = C.z;
+        d.c0 = C.c0;
+        for (int u = 0; u < width; ++u)
+          for (uint64_t m = C.adj[u] & ~((2ull << u) - 1); m; m &= m - 1) d.edges.emplace_back(u, __builtin_ctzll(m));
+        const int s = parity_of(outcome, c.sdom), t = parity_of(outcome, c.tdom);
+        double er = std::cos(c.angle), ei = s ? std::sin(c.angle) : -std::sin(c.angle);
+        if (t) er = -er, ei = -ei;
+        d.ere = er;
+        d.eim = ei;
+        d.scale = mode == OWQS_MODE_OWQS ? pow2_half(d.r + 1) : pow2_half(d.r);
+        const int o = src.decide(d);
+        if (o < 0) return OWQS_ERR_CUDA;
+        d.outcome = o & 1;
+        d.w1re = d.outcome ? -er : er;
+        d.w1im = d.outcome ? -ei : ei;
+        outcome[c.q0] = (int8_t)d.outcome;
+        CompOp op;
+        op.kind = 0;
+        op.a = id;
+        op.d = std::move(d);
+        C.queue.push_back(std::move(op));
+        // input and output arrays both live during the pass
+        peak = std::max<uint64_t>(peak, live + (1ull << (width - 1)));
+        live = live - arr_amps(C) + (1ull << (width - 1));
+        C.bits.erase(C.bits.begin() + b);
+        C.nmat = (int)C.bits.size();
+        C.arr = true;
+        std::memset(C.adj, 0, sizeof(C.adj));
+        C.z = C.x = 0;
+        C.c0 = 0;
+        owner[c.q0] = -1;
+        --single_w;
+        break;
+      }
+      default:
+        return set_error(OWQS_ERR_ARG, "unknown command kind");
+    }
+  }
+  for (uint32_t q : p.outputs) touch(q);
+  // join every component (arrays, scalars, |+> outputs) into one
+  int last = -1;
+  for (int id = 0; id < (int)comps.size(); ++id) {
+    if (!comps[id].alive || (!comps[id].arr && comps[id].bits.empty())) continue;
+    if (last < 0) {
+      last = id;
+      continue;
+    }
+    last = merge(last, id);
+    if (last < 0) return set_error(OWQS_ERR_OOM, "live width above 62 qubits at the end");
+  }
+  if (last < 0) {  // nothing at all: no input, output or measurement
+    comps.emplace_back();
+    last = (int)comps.size() - 1;
+  }
+  flush(last);
+  Comp& C = comps[last];
+  if (C.bits.size() != p.outputs.size())
+    return set_error(OWQS_ERR_PATTERN, "live qubits at the end are not the outputs");
+  PassDesc f;
+  f.kind = 1;
+  f.n_in = C.arr ? C.nmat : 0;
+  f.r = (int)C.bits.size() - f.n_in;
+  f.b = -1;
+  f.n_out = (int)C.bits.size();
+  f.xmask = f.n_in ? (C.x & ((1ull << f.n_in) - 1)) : 0;
+  f.zmask = C.z;
+  f.c0 = C.c0;
+  for (int u = 0; u < f.n_out; ++u)
+    for (uint64_t m = C.adj[u] & ~((2ull << u) - 1); m; m &= m - 1) f.edges.emplace_back(u, __builtin_ctzll(m));
+  f.scale = pow2_half(f.r);
+  f.perm.resize(p.outputs.size());
+  for (size_t k = 0; k < p.outputs.size(); ++k) f.perm[k] = pos_of(C, p.outputs[k]);
+  CompOp op;
+  op.kind = 2;
+  op.a = last;
+  op.d = std::move(f);
+  cs.ops.push_back(std::move(op));
+  peak = std::max<uint64_t>(peak, live + (1ull << p.outputs.size()));
+  single_live_max = std::max<uint64_t>(single_live_max, 1ull << std::min<size_t>(p.outputs.size(), 62));
+  cs.ncomp = (int)comps.size();
+  cs.peak_amps = peak;
+  cs.single_amps = 2 * single_live_max;
+  return OWQS_OK;
+}
+
+// ---------------------------------------------------------------------------
 // launch planning
 // ---------------------------------------------------------------------------
 static int g_max_grid = 0;

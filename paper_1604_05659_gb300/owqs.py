@@ -26,6 +26,8 @@ FLOW_CAUSAL, FLOW_GFLOW = 0, 1
 RUN_HOST_SAMPLING = 1
 RUN_PER_PASS = 2
 RUN_SEQUENTIAL_SAMPLING = 4
+RUN_SUBSTATES = 8
+RUN_ONE_ARRAY = 16
 DTYPE = {"c64": 0, "c128": 1}
 POLICY = {"forced": 0, "sampled": 1, "zero": 2}
 KERNEL_KIND = {0: "fast_pass", 1: "generic_pass", 2: "final", 3: "norm", 4: "prob", 5: "tma_pass", 10: "small_run",
@@ -65,6 +67,12 @@ class owqs_reorder_info(C.Structure):
 class owqs_run_opts(C.Structure):
     _fields_ = [("dtype", C.c_uint32), ("mode", C.c_uint32), ("policy", C.c_uint32), ("io", C.c_uint32),
                 ("seed", C.c_uint64), ("stream", C.c_void_p), ("use_graph", C.c_uint32), ("flags", C.c_uint32)]
+
+
+class owqs_memory_plan(C.Structure):
+    _fields_ = [("peak_m", C.c_uint32), ("components", C.c_uint32), ("joins", C.c_uint32),
+                ("uses_substates", C.c_uint32), ("substate_bytes", C.c_uint64), ("one_array_bytes", C.c_uint64),
+                ("substate_work", C.c_double), ("one_array_work", C.c_double)]
 
 
 class owqs_batch_item(C.Structure):
@@ -112,6 +120,11 @@ EXPORTS = {
                                    C.POINTER(C.c_uint8), C.POINTER(C.c_float), C.POINTER(C.c_double),
                                    C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32)]),
     "owqs_get_index_map": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_int32)]),
+    "owqs_plan_memory": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.POINTER(C.c_uint8),
+                                   C.c_void_p]),
+    "owqs_describe_groups": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.POINTER(C.c_uint8),
+                                       C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                       C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32)]),
     "owqs_describe_passes": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_uint8), C.POINTER(owqs_pass_desc),
                                        C.c_uint32, C.POINTER(C.c_uint32)]),
     "owqs_reorder_features": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32), C.c_uint32,
@@ -329,6 +342,32 @@ class Handle:
                                                 cap, C.byref(n)))
         return [(KERNEL_KIND[kd[i]], fm[i], nm[i]) for i in range(min(n.value, cap))]
 
+    def plan_memory(self, outcomes=None, *, dtype: str = "c64", mode: str = "owqs", real_input: bool = False):
+        """One live array against separate sub-states for the active order
+        (host only): the paper's m, components, joins, arena and one-array
+        bytes, and which a default run takes."""
+        plan = owqs_memory_plan()
+        oc = _outcome_buf(outcomes, self.K) if outcomes is not None else None
+        _check(library().owqs_plan_memory(self._h, DTYPE[dtype], MODE[mode], int(real_input), oc, C.byref(plan)))
+        return {f: getattr(plan, f) for f, _ in owqs_memory_plan._fields_}
+
+    def describe_groups(self, outcomes=None, *, dtype: str = "c64", mode: str = "owqs", real_input: bool = False):
+        """The pass groups a run would launch (host only): list of dicts with
+        the register qubits m, the slot sequence, the input width n_in and
+        whether a kernel compiled for that sequence runs it."""
+        cap = self.K + 16
+        regs, slots, nin, spec = ((C.c_uint32 * cap)() for _ in range(4))
+        n = C.c_uint32()
+        oc = _outcome_buf(outcomes, self.K) if outcomes is not None else None
+        _check(library().owqs_describe_groups(self._h, DTYPE[dtype], MODE[mode], int(real_input), oc, regs, slots,
+                                              nin, spec, cap, C.byref(n)))
+        out = []
+        for i in range(min(n.value, cap)):
+            k = (slots[i] >> 24) & 15
+            out.append({"m": regs[i], "slots": tuple((slots[i] >> (2 * j)) & 3 for j in range(k)),
+                        "n_in": nin[i], "specialised": bool(spec[i])})
+        return out
+
     def index_map(self, pass_index: int):
         out = (C.c_int32 * self.pattern.nqubits)()
         _check(library().owqs_get_index_map(self._h, pass_index, out))
@@ -346,7 +385,7 @@ class Handle:
     def run(self, psi_in=None, *, dtype: str = "c128", mode: str = "owqs", policy: str = "forced",
             outcomes=None, seed: int = 0, stream=None, use_graph: bool = True, out=None,
             check: bool = True, host_sampling: bool = False, per_pass: bool = False,
-            sequential_sampling: bool = False):
+            sequential_sampling: bool = False, layout: str = "auto"):
         """Run on the GPU.  psi_in: torch tensor on the GPU (complex64 for
         c64, complex128 for c128) or None for |+> inputs; returns
         (psi_out tensor, outcomes array, probs array, status).
@@ -355,7 +394,9 @@ class Handle:
         even for a run that fits the single-block kernel.
         sequential_sampling: draw sampled OWQS outcomes one measurement at a
         time from the start, instead of first checking the guess u > 1/2 with
-        one forced run."""
+        one forced run.
+        layout: "auto" (separate sub-states when they need at most half the
+        memory of one array), "substates" or "one_array"."""
         import torch
         tdt = torch.complex64 if dtype == "c64" else torch.complex128
         _check_vectors(psi_in, out, tdt, self.nin, self.nout)
@@ -370,7 +411,8 @@ class Handle:
         opts = owqs_run_opts(DTYPE[dtype], MODE[mode], POLICY[policy], 0, seed, C.c_void_p(s.cuda_stream),
                              int(use_graph), (RUN_HOST_SAMPLING if host_sampling else 0) |
                              (RUN_PER_PASS if per_pass else 0) |
-                             (RUN_SEQUENTIAL_SAMPLING if sequential_sampling else 0))
+                             (RUN_SEQUENTIAL_SAMPLING if sequential_sampling else 0) |
+                             {"auto": 0, "substates": RUN_SUBSTATES, "one_array": RUN_ONE_ARRAY}[layout])
         st = library().owqs_run(self._h, C.byref(opts), C.c_void_p(psi_in.data_ptr() if psi_in is not None else 0),
                                 C.c_void_p(out.data_ptr()), oc.ctypes.data_as(C.POINTER(C.c_uint8)),
                                 probs.ctypes.data_as(C.POINTER(C.c_double)))
@@ -472,7 +514,7 @@ class Handle:
         return oc[: self.K].copy(), probs[: self.K].copy()
 
     def profile(self, psi_in=None, *, dtype: str = "c64", mode: str = "owqs", policy: str = "forced",
-                outcomes=None, stream=None, out=None):
+                outcomes=None, stream=None, out=None, layout: str = "auto"):
         """Per-launch CUDA-event durations of one run (no graph)."""
         import torch
         tdt = torch.complex64 if dtype == "c64" else torch.complex128
@@ -487,7 +529,8 @@ class Handle:
         nm = (C.c_uint32 * cap)()
         n = C.c_uint32()
         s = stream if stream is not None else torch.cuda.current_stream(dev)
-        opts = owqs_run_opts(DTYPE[dtype], MODE[mode], POLICY[policy], 0, 0, C.c_void_p(s.cuda_stream), 0, 0)
+        opts = owqs_run_opts(DTYPE[dtype], MODE[mode], POLICY[policy], 0, 0, C.c_void_p(s.cuda_stream), 0,
+                             {"auto": 0, "substates": RUN_SUBSTATES, "one_array": RUN_ONE_ARRAY}[layout])
         oc = _outcome_buf(outcomes, self.K)
         _check(library().owqs_profile_run(self._h, C.byref(opts),
                                           C.c_void_p(psi_in.data_ptr() if psi_in is not None else 0),

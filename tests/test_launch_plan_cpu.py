@@ -122,3 +122,47 @@ def test_small_run_boundary(owqs):
     h = owqs.load(wl.pattern)
     h.reorder()
     assert h.describe_launches(wl.outcomes, dtype="c128")[0][0] != "small_run"
+
+
+def test_group_slot_sequences_and_compiled_kernels(owqs):
+    """owqs_describe_groups lists the same groups as owqs_describe_launches,
+    with valid register-slot sequences (k <= 12 passes, slots below m, the
+    first pass on slot 0, a new slot only after every lower one); the
+    brickwork's groups that read an array all run on kernels compiled for
+    their sequence, complex128 and virtual-input groups never do."""
+    wl = workloads.brickwork(28, 40)
+    h = owqs.load(wl.pattern)
+    h.reorder()
+    for real in (False, True):
+        lv = [x for x in h.describe_launches(wl.outcomes, real_input=real) if x[0] == "group_pass"]
+        gs = h.describe_groups(wl.outcomes, real_input=real)
+        assert [len(g["slots"]) for g in gs] == [x[2] for x in lv]
+        for i, g in enumerate(gs):
+            sl = g["slots"]
+            assert 2 <= len(sl) <= 12 and 1 <= g["m"] <= 3 and sl[0] == 0
+            assert all(s < g["m"] for s in sl) and max(sl) == g["m"] - 1
+            for j, s in enumerate(sl):
+                assert s <= max(sl[:j], default=-1) + 1
+            assert g["specialised"] == (real or i > 0), (i, g)
+        assert not any(g["specialised"] for g in h.describe_groups(wl.outcomes, dtype="c128", real_input=real))
+
+
+def test_memory_plan_separate_substates(owqs):
+    """owqs_plan_memory: two brickwork blocks with |+> inputs stay separate
+    sub-states until the joining E (joins, less memory and at most half the
+    work of one array, so a default run takes them); with an input vector
+    the inputs are one sub-state and the blocks share it from the start; the
+    paper's m of the order is the widest sub-state at a measurement."""
+    wl = workloads.joined_bricks(12, 8, 2)
+    h = owqs.load(wl.pattern)
+    order, info = h.reorder()
+    plan = h.plan_memory(wl.outcomes)
+    assert plan["joins"] >= 1 and plan["components"] >= 2 and plan["uses_substates"] == 1, plan
+    assert plan["substate_bytes"] < plan["one_array_bytes"], plan
+    assert 2 * plan["substate_work"] <= plan["one_array_work"], plan
+    assert plan["peak_m"] <= info["peak_m"]
+    one = h.plan_memory(wl.outcomes, real_input=True)
+    assert one["joins"] == 0 and one["uses_substates"] == 0, one
+    for dtype, amp in (("c64", 8), ("c128", 16)):
+        p2 = h.plan_memory(wl.outcomes, dtype=dtype)
+        assert p2["one_array_bytes"] % amp == 0 and p2["substate_bytes"] >= amp
