@@ -72,7 +72,7 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["owqs", "reference"], default="owqs")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end calls timed (0: --steps)")
-    ap.add_argument("--cpu-meas", type=int, default=3,
+    ap.add_argument("--cpu-meas", type=int, default=10,
                     help="measurements of the workload in each CPU-oracle sample (all host cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rows", type=int, default=ROWS)
@@ -81,7 +81,7 @@ def parse_args(argv=None):
                     help="comma list of c64 (always run), c128, e2e, sampled, cpu, rec, learned, qft, small, "
                          "substates, m; fewer legs for profiler runs")
     ap.add_argument("--sampled-steps", type=int, default=3, help="sampled-outcome runs per mode")
-    ap.add_argument("--learned-count", type=int, default=24, help="held-out patterns in the learned leg")
+    ap.add_argument("--learned-count", type=int, default=200, help="held-out patterns in the learned leg")
     ap.add_argument("--rec-branches", type=int, default=64, help="outcome branches per pattern in the recognition leg")
     ap.add_argument("--rec-count", type=int, default=256, help="patterns in the recognition leg")
     return ap.parse_args(argv)
@@ -495,14 +495,17 @@ def small_leg(args, owqs, torch):
 
 
 def learned_leg(args, owqs, torch, hbm_gbs):
-    """Held-out random J/CZ patterns (16..30 qubits, depth 20..60) reordered
-    in EOWQS mode by the greedy Eq. 18 order alone and with the committed
-    learned proposal (greedy judges).  Reports peak live widths, amplitude
-    updates, acceptance, whether the greedy order's widest array would fit
-    in device memory at all, the GPU time of simulating each kept order
-    (complex64, EOWQS, all-zero branch) up to 26 live qubits, and for the
-    greedy order the time its amplitude updates need at the measured HBM
-    bandwidth (about 2.3 bytes per update)."""
+    """The committed learned proposal against the best greedy order on the
+    held-out random J/CZ patterns (16..30 qubits, depth 20..60; the first
+    --learned-count of the 200 held out from training).  Per pattern, host
+    side: the greedy EOWQS order (every qubit ready) and the greedy OWQS
+    sweep order (which waits for every domain, so it is valid with
+    preselected outcomes too), each with the paper's m and the one-array
+    width; then owqs_reorder with the proposal, which keeps it only if it is
+    no worse than the better greedy order by (peak live width, amplitude
+    updates).  GPU side, wherever the order fits: complex64, EOWQS, all-zero
+    branch, one array, CUDA-event time of the kept order and of the best
+    greedy order (one warm-up and one timed run each)."""
     import numpy as np
     from owqs_inputs import workloads
     path = os.path.join(ROOT, "paper_1604_05659_gb300", "reorder_mlp.json")
@@ -511,44 +514,84 @@ def learned_leg(args, owqs, torch, hbm_gbs):
     meta = json.load(open(path))
     model = owqs.Model(weights=np.array(meta["params"], dtype=np.float32))
     free = torch.cuda.mem_get_info()[0]
+
+    def gpu_seconds(h):
+        width = h.info()["peak_live"]
+        if (1 << min(width, 62)) * 8 * 2.2 > 0.8 * free:
+            return None
+        out = torch.empty(1 << h.nout, dtype=torch.complex64, device="cuda")
+        run = lambda: h.run(None, dtype="c64", mode="eowqs", policy="zero", out=out, check=False, layout="one_array")
+        run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        del out
+        return e0.elapsed_time(e1) / 1e3
+
+    def m_of_active(h):
+        """The paper's m of the active order (its widest sub-state at a
+        measurement); None when a sub-state exceeds 62 qubits."""
+        try:
+            return h.plan_memory(real_input=True)["peak_m"]
+        except owqs.OwqsError:
+            return None
+
     rows = []
     for i in range(1_000_000, 1_000_000 + args.learned_count):
         wl = workloads.random_pattern(i, 16, 30, 20, 60, 4, with_input=False)
         h = owqs.load(wl.pattern)
         k = float(max(1, h.nout))
         w = (k, k, 0.5, k)
+        oe, ie = h.reorder(mode="eowqs", sweep=False, weights=w)
+        me = ie["peak_m"]  # PROA's own MS bookkeeping (the order is too wide to plan)
+        oo, io = h.reorder(mode="owqs", sweep=True)
+        mo = m_of_active(h)
+        t_owqs = gpu_seconds(h)
         t0 = time.perf_counter()
-        _, info = h.reorder(mode="eowqs", sweep=False, weights=w, model=model)
+        _, il = h.reorder(mode="eowqs", sweep=False, weights=w, model=model)
         t_reorder = time.perf_counter() - t0
-        row = {"n": h.nin, "K": h.K, "greedy_peak_live": info["greedy_peak_live"],
-               "learned_peak_live": info["learned_peak_live"], "accepted": info["learned_accepted"],
-               "greedy_amp_updates": info["greedy_amp_updates"], "learned_amp_updates": info["learned_amp_updates"],
+        sat = lambda v: None if v >= (1 << 64) - 1 else v   # the count saturates past 2^64
+        row = {"n": h.nin, "K": h.K,
+               "eowqs_greedy": {"m": me, "peak_live": ie["peak_live"], "amp_updates": sat(ie["amp_updates"])},
+               "owqs_greedy": {"m": mo, "peak_live": io["peak_live"], "amp_updates": io["amp_updates"]},
+               "best_greedy": "owqs" if il["greedy_judge_owqs"] else "eowqs",
+               "learned": {"peak_live": il["learned_peak_live"], "amp_updates": il["learned_amp_updates"]},
+               "accepted": il["learned_accepted"],
+               "kept": {"m": m_of_active(h), "peak_live": il["peak_live"], "amp_updates": il["amp_updates"]},
                "reorder_seconds": t_reorder}
-        # a pass moves about 16 bytes per amplitude update of width w (read + write, complex64)
-        row["greedy_hbm_seconds_estimate"] = (2.3 * info["greedy_amp_updates"] / (hbm_gbs * 1e9)
-                                              if info["greedy_amp_updates"] < (1 << 64) - 1 else None)
-        width = info["peak_live"]
-        row["greedy_fits_in_hbm"] = bool((1 << min(info["greedy_peak_live"], 62)) * 8 * 2.5 < free * 0.8)
-        if width <= 26 and (1 << width) * 8 * 2.5 < free * 0.8:
-            out = torch.empty(1 << h.nout, dtype=torch.complex64, device="cuda")
-            h.run(None, dtype="c64", mode="eowqs", policy="zero", out=out, check=False)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            h.run(None, dtype="c64", mode="eowqs", policy="zero", out=out, check=False)
-            torch.cuda.synchronize()
-            row["kept_order_gpu_seconds"] = time.perf_counter() - t0
-            del out
+        best = (il["greedy_peak_live"], il["greedy_amp_updates"])
+        row["kept_not_worse"] = (il["peak_live"], il["amp_updates"]) <= best
+        if il["learned_accepted"]:
+            row["kept_gpu_seconds"] = gpu_seconds(h)
+        elif il["greedy_judge_owqs"]:
+            row["kept_gpu_seconds"] = t_owqs
+        row["best_greedy_gpu_seconds"] = t_owqs if il["greedy_judge_owqs"] else None
         h.close()
         rows.append(row)
-    acc = sum(r["accepted"] for r in rows)
-    return {"patterns": len(rows), "accepted": acc,
-            "mean_greedy_peak_live": float(np.mean([r["greedy_peak_live"] for r in rows])),
-            "mean_learned_peak_live": float(np.mean([r["learned_peak_live"] for r in rows])),
-            "learned_peak_equals_n_plus_1": sum(r["learned_peak_live"] == r["n"] + 1 for r in rows),
-            "greedy_updates_saturated": sum(r["greedy_amp_updates"] == (1 << 64) - 1 for r in rows),
-            "greedy_orders_fitting_hbm": sum(r["greedy_fits_in_hbm"] for r in rows),
-            "kept_order_gpu_seconds_total": float(sum(r.get("kept_order_gpu_seconds", 0.0) for r in rows)),
-            "trained": {k: v for k, v in meta.items() if k != "params"}, "rows": rows}
+    timed = [r for r in rows if r.get("kept_gpu_seconds") and r.get("best_greedy_gpu_seconds")]
+    acc = [r for r in rows if r["accepted"]]
+    return {"patterns": len(rows), "accepted": len(acc),
+            "kept_never_worse_than_best_greedy": all(r["kept_not_worse"] for r in rows),
+            "best_greedy_is_owqs_sweep": sum(r["best_greedy"] == "owqs" for r in rows),
+            "mean_m": {"eowqs_greedy": float(np.mean([r["eowqs_greedy"]["m"] for r in rows])),
+                       "owqs_greedy": float(np.mean([r["owqs_greedy"]["m"] for r in rows if r["owqs_greedy"]["m"]])),
+                       "kept": float(np.mean([r["kept"]["m"] for r in rows if r["kept"]["m"]]))},
+            "mean_peak_live": {"eowqs_greedy": float(np.mean([r["eowqs_greedy"]["peak_live"] for r in rows])),
+                               "owqs_greedy": float(np.mean([r["owqs_greedy"]["peak_live"] for r in rows])),
+                               "learned": float(np.mean([r["learned"]["peak_live"] for r in rows])),
+                               "kept": float(np.mean([r["kept"]["peak_live"] for r in rows]))},
+            "geomean_update_ratio_best_greedy_over_kept": float(np.exp(np.mean(
+                [np.log(max(1, min(r["owqs_greedy"]["amp_updates"], r["eowqs_greedy"]["amp_updates"] or 2**64)) /
+                        max(1, r["kept"]["amp_updates"])) for r in rows]))),
+            "gpu_timed_patterns": len(timed),
+            "geomean_gpu_time_best_greedy_over_kept": float(np.exp(np.mean(
+                [np.log(r["best_greedy_gpu_seconds"] / r["kept_gpu_seconds"]) for r in timed]))) if timed else None,
+            "gpu_seconds_total": {"kept": float(sum(r["kept_gpu_seconds"] for r in timed)),
+                                  "best_greedy": float(sum(r["best_greedy_gpu_seconds"] for r in timed))},
+            "trained": {k: v for k, v in meta.items() if k not in ("params", "heldout")},
+            "rows_shown": f"first 8 of {len(rows)}", "rows": rows[:8]}
 
 
 def run_owqs(args):
@@ -710,9 +753,23 @@ def run_owqs(args):
         ov = torch.vdot(a, out128)
         amp_err = torch.max(torch.abs(a * (ov / abs(ov)) - out128)).item()
         prob_err = float(np.max(np.abs(p64 - p128)))
-        del a, out128
+        del a
         fp64 = {"dtype": "c128", "value": replica_throughput(upd, args.fp64_steps, world, t128),
                 "ms_per_step": 1e3 * t128 / args.fp64_steps, "roofline": roof128}
+        # the same complex128 arrays with the pass groups in double-float
+        # arithmetic on the FP32 pipes (GB300's FP64 rate is 1/64 of FP32)
+        outdf = torch.empty(1 << nout, dtype=torch.complex128, device="cuda")
+        rundf = lambda: h.run(None, dtype="c128", outcomes=wl.outcomes, out=outdf, layout="one_array",
+                              double_float=True)
+        rundf()
+        tdf = timed(rundf, args.fp64_steps)
+        _, _, pdf, _ = rundf()
+        fp64["double_float"] = {"value": replica_throughput(upd, args.fp64_steps, world, tdf),
+                                "ms_per_step": 1e3 * tdf / args.fp64_steps,
+                                "max_abs_amp_diff_vs_fp64": torch.max(torch.abs(outdf - out128)).item(),
+                                "max_prob_diff_vs_fp64": float(np.max(np.abs(pdf - p128))),
+                                "bound": 1e-12}
+        del outdf, out128
         accuracy = {"c64_vs_c128_max_abs_amp_err": amp_err, "c64_vs_c128_max_prob_err": prob_err, "bound": 2e-5}
 
     subs = None

@@ -131,7 +131,11 @@ typedef struct {
                               g = 0.5; 0: one run with the weights below        */
   uint32_t use_learned;    /* 1: also build the learned proposal with `model`;
                               it is kept only if its (peak live width, amplitude
-                              updates) is no worse than the greedy order's     */
+                              updates) is no worse than the best greedy order:
+                              the greedy order of `mode` and, in EOWQS mode, the
+                              greedy OWQS sweep order too (an order that waits
+                              for every domain is valid with preselected
+                              outcomes), whichever is better                    */
   double alpha, beta, gamma, delta;  /* Eq. 18 weights when sweep == 0 (> 0)   */
   const owqs_model* model; /* use_learned: the scoring network (runs on the
                               current device)                                   */
@@ -147,7 +151,8 @@ typedef struct {
   uint32_t greedy_peak_live;   /* the greedy order's figures (use_learned)      */
   uint64_t greedy_amp_updates;
   uint32_t learned_peak_live;  /* the proposal's figures (use_learned)          */
-  uint32_t pad_;
+  uint32_t greedy_judge_owqs;  /* use_learned in EOWQS mode: 1 if the greedy OWQS
+                                  sweep order was the better greedy order       */
   uint64_t learned_amp_updates;
 } owqs_reorder_info;
 
@@ -267,10 +272,15 @@ typedef struct {
                          use them when the components' arrays need at most half
                          the memory of one array over all live qubits;
                          OWQS_RUN_SUBSTATES: always (forced or zero outcomes);
-                         OWQS_RUN_ONE_ARRAY: never (one live array).           */
+                         OWQS_RUN_ONE_ARRAY: never (one live array).
+                         OWQS_RUN_DOUBLE_FLOAT (OWQS_C128 only): pass groups
+                         compute in double-float arithmetic (a value as the sum
+                         of two floats, about 48 significant bits) on the FP32
+                         pipes instead of FP64; arrays between two such groups
+                         hold double-float pairs, every other array complex128. */
 } owqs_run_opts;
 enum { OWQS_RUN_HOST_SAMPLING = 1, OWQS_RUN_PER_PASS = 2, OWQS_RUN_SEQUENTIAL_SAMPLING = 4,
-       OWQS_RUN_SUBSTATES = 8, OWQS_RUN_ONE_ARRAY = 16 };
+       OWQS_RUN_SUBSTATES = 8, OWQS_RUN_ONE_ARRAY = 16, OWQS_RUN_DOUBLE_FLOAT = 32 };
 
 /* Simulate the pattern under its active order and return the output state.
  *   psi_in    2^|I| amplitudes (bit k = inputs[k]); NULL = |+> on every input
@@ -432,7 +442,11 @@ typedef struct {
   uint32_t tasks;           /* (item, column block) tasks of the persistent launch  */
   uint32_t smem_bytes_per_cta;
   uint32_t launches;        /* kernel launches of this call                         */
-  uint32_t pad_;
+  uint32_t global_items;    /* items too wide for shared memory run by the second
+                               persistent launch, whose state buffers are in
+                               global memory (up to 2^18 amplitudes per array);
+                               hbm_items counts the items wider still, which
+                               run through the pass kernels of owqs_run         */
 } owqs_batch_info;
 
 owqs_status owqs_run_batch(const owqs_batch_item* items, uint32_t n, const owqs_batch_opts* opts,

@@ -30,6 +30,10 @@ namespace owqs {
 // host threads (each with its own stream) that run the wide items of
 // different patterns side by side
 constexpr size_t kWideWorkers = 8;
+// items up to 2^kBatchGlobalLog amplitudes that do not fit shared memory run
+// in the persistent global-memory launch (state buffers of 2 x 2 MiB per CTA
+// in complex64)
+constexpr int kBatchGlobalLog = 18;
 
 struct BPass {
   int32_t n_in, r, b, n_out;  // b < 0: final pass
@@ -74,14 +78,18 @@ __device__ __forceinline__ uint32_t b_sign(const BPass& ps, const BQ* __restrict
   return s & 1u;
 }
 
-template <typename T>
+// GLOBAL: the two state buffers of a task live in this CTA's slice of a
+// global-memory scratch (2 cap amplitudes per CTA) instead of shared memory,
+// for items too wide for a shared-memory column block; the pass interpreter
+// is the same (the CTA's threads share the buffers through __syncthreads).
+template <typename T, bool GLOBAL>
 __global__ void __launch_bounds__(kBlock) k_batch(const BItem* __restrict__ items, const BPass* __restrict__ passes,
                                                   const BQ* __restrict__ qs, const int32_t* __restrict__ perms,
                                                   const BTask* __restrict__ tasks, uint32_t ntasks,
-                                                  unsigned int* next_task, uint32_t cap) {
+                                                  unsigned int* next_task, uint32_t cap, void* gscratch) {
   using V = typename BCplx<T>::V;
   extern __shared__ __align__(16) unsigned char bsm[];
-  V* const base = reinterpret_cast<V*>(bsm);
+  V* const base = GLOBAL ? reinterpret_cast<V*>(gscratch) + (size_t)blockIdx.x * 2 * cap : reinterpret_cast<V*>(bsm);
   __shared__ uint32_t task_id;
   for (;;) {
     if (threadIdx.x == 0) task_id = atomicAdd(next_task, 1u);
@@ -118,7 +126,7 @@ __global__ void __launch_bounds__(kBlock) k_batch(const BItem* __restrict__ item
       const uint32_t n_out = (uint32_t)ps.n_out;
       const uint32_t total = B << n_out;
       if (ps.b >= 0 && ps.star) {
-        // star form, no X mask, every index below 2^16: 32-bit index math and
+        // star form, no X mask, every index below 2^24: 32-bit index math and
         // both signs from two parities
         const uint32_t b = (uint32_t)ps.b, z = (uint32_t)ps.zmask;
         const uint32_t lowm = (1u << b) - 1u, nmask = (1u << n_out) - 1u, inm = (1u << ps.n_in) - 1u;
@@ -222,6 +230,11 @@ struct BatchCache {
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t cap = nullptr;
   std::map<std::string, int> tuned;  // signature -> shared-memory budget (bytes per CTA)
+  // items too wide for shared memory: global-memory state buffers and the
+  // tasks of their persistent launch, also replayed from a graph
+  DevBuf gtasks, gscratch;
+  std::string gkey2;
+  cudaGraphExec_t gexec2 = nullptr;
 };
 
 std::mutex g_batch_mu;
@@ -284,7 +297,7 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
   std::vector<BPass> bpasses;
   std::vector<BQ> bqs;
   std::vector<int32_t> bperms;
-  std::vector<char> on_chip(n, 0);
+  std::vector<char> on_chip(n, 0), in_global(n, 0);
   std::string sig = std::to_string(dtype) + ":";
   for (uint32_t i = 0; i < n; ++i) {
     const owqs_batch_item& it = items[i];
@@ -320,7 +333,7 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
       // quadratic terms: one lower endpoint per edge
       for (auto& ed : d.edges) bqs.push_back(BQ{1ull << ed.second, ed.first, 0});
       bp.nq = (uint32_t)(bqs.size() - bp.q_off);
-      if (d.kind == 0 && d.xmask == 0 && d.n_in + d.r <= 16) {
+      if (d.kind == 0 && d.xmask == 0 && d.n_in + d.r <= 24) {
         uint32_t a = 0;
         bool star = true;
         for (auto& ed : d.edges) {
@@ -343,6 +356,7 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
     }
     b.wmax = wmax;
     on_chip[i] = wmax <= 16 && 2 * ((size_t)1 << wmax) * amp <= smem_limit && b.nin <= 20;
+    in_global[i] = !on_chip[i] && wmax <= kBatchGlobalLog && b.nin <= 20;
     sig += std::to_string(wmax) + "/" + std::to_string(b.nin) + "/" + std::to_string(it.psi_in ? 1 : 0) + ",";
   }
 
@@ -377,7 +391,7 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
     for (auto& t : tmp) tasks.push_back(t.second);
   };
 
-  auto kernel = dtype == OWQS_C64 ? (const void*)k_batch<float> : (const void*)k_batch<double>;
+  auto kernel = dtype == OWQS_C64 ? (const void*)k_batch<float, false> : (const void*)k_batch<double, false>;
   auto launch_batch = [&](size_t budget, const std::vector<BTask>& tasks, uint32_t cap,
                           bool graph) -> owqs_status {
     if (tasks.empty()) return OWQS_OK;
@@ -411,9 +425,9 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
       cudaError_t e3 = cudaMemsetAsync(cp, 0, sizeof(unsigned int), st);
       if (e3 != cudaSuccess) return e3;
       if (dtype == OWQS_C64)
-        k_batch<float><<<grid, kBlock, smem, st>>>(ip, pp, qp, mp, tp, nt, cp, cap);
+        k_batch<float, false><<<grid, kBlock, smem, st>>>(ip, pp, qp, mp, tp, nt, cp, cap, nullptr);
       else
-        k_batch<double><<<grid, kBlock, smem, st>>>(ip, pp, qp, mp, tp, nt, cp, cap);
+        k_batch<double, false><<<grid, kBlock, smem, st>>>(ip, pp, qp, mp, tp, nt, cp, cap, nullptr);
       return cudaGetLastError();
     };
     (void)budget;
@@ -510,6 +524,117 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
     ++launches;
   }
 
+  // items too wide for shared memory (up to 2^kBatchGlobalLog amplitudes):
+  // one persistent launch over (item, column) tasks with global-memory
+  // state buffers, largest item first
+  uint32_t global_items = 0;
+  {
+    std::vector<std::pair<double, BTask>> tmp;
+    uint32_t gcap = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+      if (!in_global[i]) continue;
+      ++global_items;
+      BItem& b = bitems[i];
+      b.cb = 1;
+      gcap = std::max<uint32_t>(gcap, 1u << b.wmax);
+      double cost = 0;
+      for (uint32_t q = 0; q < b.npass; ++q) cost += std::ldexp(1.0, bpasses[b.pass_off + q].n_out);
+      for (uint32_t c0 = 0; c0 < b.cols; ++c0) tmp.push_back({cost, BTask{i, c0}});
+    }
+    if (!tmp.empty()) {
+      std::stable_sort(tmp.begin(), tmp.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+      std::vector<BTask> gt;
+      gt.reserve(tmp.size());
+      for (auto& t : tmp) gt.push_back(t.second);
+      auto gkern = dtype == OWQS_C64 ? (const void*)k_batch<float, true> : (const void*)k_batch<double, true>;
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gkern, kBlock, 0);
+      if (e != cudaSuccess) return bfail(e, "batch occupancy");
+      const int grid = std::max(1, std::min<int>(std::max(1, per_sm) * (max_grid() / 8), (int)gt.size()));
+      // items (the column blocks changed), tasks, scratch
+      owqs_status st = upload(bc.items, bitems.data(), bitems.size() * sizeof(BItem), s, "batch items");
+      if (st == OWQS_OK) st = upload(bc.passes, bpasses.data(), bpasses.size() * sizeof(BPass), s, "batch passes");
+      if (st == OWQS_OK && !bqs.empty()) st = upload(bc.qs, bqs.data(), bqs.size() * sizeof(BQ), s, "batch terms");
+      if (st == OWQS_OK && !bperms.empty())
+        st = upload(bc.perms, bperms.data(), bperms.size() * sizeof(int32_t), s, "batch perms");
+      if (st == OWQS_OK) st = upload(bc.gtasks, gt.data(), gt.size() * sizeof(BTask), s, "batch tasks");
+      if (st != OWQS_OK) return st;
+      const size_t scratch = (size_t)grid * 2 * gcap * amp;
+      if (bc.gscratch.bytes < scratch) {
+        if (bc.gscratch.p) cudaFree(bc.gscratch.p);
+        bc.gscratch.p = nullptr;
+        bc.gscratch.bytes = 0;
+        e = cudaMalloc(&bc.gscratch.p, scratch);
+        if (e != cudaSuccess) return bfail(e, "batch scratch");
+        bc.gscratch.bytes = scratch;
+      }
+      if (!bc.counter.p) {
+        e = cudaMalloc(&bc.counter.p, 256);
+        if (e != cudaSuccess) return bfail(e, "batch counter");
+        bc.counter.bytes = 256;
+      }
+      auto* ip = static_cast<const BItem*>(bc.items.p);
+      auto* pp = static_cast<const BPass*>(bc.passes.p);
+      auto* qp = static_cast<const BQ*>(bc.qs.p);
+      auto* mp = static_cast<const int32_t*>(bc.perms.p);
+      auto* tp = static_cast<const BTask*>(bc.gtasks.p);
+      auto* cp = static_cast<unsigned int*>(bc.counter.p) + 1;  // the shared-memory launch uses [0]
+      void* sp = bc.gscratch.p;
+      const uint32_t nt = (uint32_t)gt.size();
+      auto enqueue = [&](cudaStream_t st2) -> cudaError_t {
+        cudaError_t e3 = cudaMemsetAsync(cp, 0, sizeof(unsigned int), st2);
+        if (e3 != cudaSuccess) return e3;
+        if (dtype == OWQS_C64)
+          k_batch<float, true><<<grid, kBlock, 0, st2>>>(ip, pp, qp, mp, tp, nt, cp, gcap, sp);
+        else
+          k_batch<double, true><<<grid, kBlock, 0, st2>>>(ip, pp, qp, mp, tp, nt, cp, gcap, sp);
+        return cudaGetLastError();
+      };
+      if (!o->use_graph) {
+        e = enqueue(s);
+        if (e != cudaSuccess) return bfail(e, "batch kernel launch");
+      } else {
+        std::string key;
+        auto add = [&](const void* v, size_t nb) { key.append(reinterpret_cast<const char*>(v), nb); };
+        const void* ptrs[7] = {ip, pp, qp, mp, tp, cp, sp};
+        add(&dtype, sizeof(dtype));
+        add(&grid, sizeof(grid));
+        add(&nt, sizeof(nt));
+        add(&gcap, sizeof(gcap));
+        add(ptrs, sizeof(ptrs));
+        if (!bc.gexec2 || key != bc.gkey2) {
+          if (bc.gexec2) {
+            cudaGraphExecDestroy(bc.gexec2);
+            bc.gexec2 = nullptr;
+          }
+          if (!bc.cap) {
+            e = cudaStreamCreateWithFlags(&bc.cap, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return bfail(e, "batch capture stream");
+          }
+          e = cudaStreamBeginCapture(bc.cap, cudaStreamCaptureModeThreadLocal);
+          if (e != cudaSuccess) return bfail(e, "batch begin capture");
+          const cudaError_t el = enqueue(bc.cap);
+          cudaGraph_t g = nullptr;
+          e = cudaStreamEndCapture(bc.cap, &g);
+          if (el != cudaSuccess || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return bfail(el != cudaSuccess ? el : e, "batch capture");
+          }
+          e = cudaGraphInstantiate(&bc.gexec2, g, 0);
+          cudaGraphDestroy(g);
+          if (e != cudaSuccess) {
+            bc.gexec2 = nullptr;
+            return bfail(e, "batch graph instantiate");
+          }
+          bc.gkey2 = key;
+        }
+        e = cudaGraphLaunch(bc.gexec2, s);
+        if (e != cudaSuccess) return bfail(e, "batch graph launch");
+      }
+      ++launches;
+    }
+  }
+
   // wide items: the pass kernels.  Items of different patterns are
   // independent (each pattern has its own workspace), so they run on up to
   // kWideWorkers host threads, each with its own stream: the many small
@@ -520,7 +645,7 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
   {
     std::map<const owqs_pattern*, size_t> slot;
     for (uint32_t i = 0; i < n; ++i) {
-      if (on_chip[i]) continue;
+      if (on_chip[i] || in_global[i]) continue;
       ++hbm;
       auto it = slot.find(items[i].pattern);
       if (it == slot.end()) {
@@ -671,6 +796,7 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
     info->tasks = (uint32_t)tasks.size();
     info->smem_bytes_per_cta = (uint32_t)(2 * (size_t)cap * amp);
     info->launches = launches;
+    info->global_items = global_items;
   }
   return OWQS_OK;
 }

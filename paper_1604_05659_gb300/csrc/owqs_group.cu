@@ -49,6 +49,7 @@ cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s) {
       default: return cudaErrorInvalidValue;
     }
   }
+  if (G.df) return launch_group_df(G, G.df_in != 0, G.df_out != 0, s);
   switch (G.m) {
     case 1: return v ? launch_group_t<1, 11>(k_group64<1, true>, G, s) : launch_group_t<1, 11>(k_group64<1, false>, G, s);
     case 2: return v ? launch_group_t<2, 11>(k_group64<2, true>, G, s) : launch_group_t<2, 11>(k_group64<2, false>, G, s);

@@ -286,6 +286,10 @@ struct GroupParams {
   double thresh;
   double vconst;            // in == nullptr: the value of every input amplitude (virtual |+> input)
   long long stall_limit;    // > 0 (tests only): as PassParams::stall_limit
+  // complex128 in double-float arithmetic (OWQS_RUN_DOUBLE_FLOAT): df = 1;
+  // df_in / df_out: the input / output array holds double-float pairs (the
+  // previous / next launch is such a group on the same array), else complex128
+  int df, df_in, df_out;
   GroupPass pass[kGroupMax];
   uint64_t in_cap, out_cap;  // as PassParams
 };
@@ -294,6 +298,8 @@ struct GroupParams {
 int plan_group(const std::vector<PassDesc>& passes, size_t i, int dtype, GroupParams& G, LaunchPlan& L,
                bool virt_in = false);
 cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s);
+// complex128 group in double-float arithmetic (owqs_group_df.cu)
+cudaError_t launch_group_df(const GroupParams& G, bool in_df, bool out_df, cudaStream_t s);
 // the group's register-slot sequence (bits 28-29 m, 24-27 k, 2j and 2j+1 the
 // slot of pass j), and whether a kernel compiled for it exists (complex64,
 // materialised input)

@@ -552,17 +552,46 @@ __global__ void __launch_bounds__(kBlock, 2) k_tma(const PassParams P) {
 }
 
 
-// squared norm of an input vector (OWQS divides by it)
+// squared norm of an input vector (OWQS divides by it).  complex64: 16-byte
+// loads of two amplitudes, squared norms summed in FP32 (packed FP32x2) over
+// chunks of at most 16 amplitudes and the chunks in FP64 (GB300's FP64 pipe
+// runs at 1/64 of the FP32 rate: per-amplitude FP64 products made this
+// kernel FP64-bound, 2.5 ms for 2^28 amplitudes); complex128, and a
+// complex64 vector that is not 16-byte aligned: FP64 per amplitude.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_norm(const void* vin, uint64_t n, double* norms, int slot,
                                                  double* partials, unsigned int* counter) {
   using V = typename Cplx<T>::V;
-  const V* __restrict__ in = reinterpret_cast<const V*>(vin);
   double acc = 0.0;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const V x = in[i];
-    acc += (double)x.x * (double)x.x + (double)x.y * (double)x.y;
+  if (sizeof(T) == 4 && ((uintptr_t)vin & 15u) == 0) {
+    constexpr int kChunk = 8;  // float4 loads per FP32 partial
+    const float4* __restrict__ in4 = reinterpret_cast<const float4*>(vin);
+    const uint64_t npairs = n / 2;
+    for (uint64_t i = tid; i < npairs;) {
+      float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < kChunk; ++c) {
+        if (i < npairs) {
+          const float4 v = in4[i];
+          s2 = __ffma2_rn(make_float2(v.x, v.y), make_float2(v.x, v.y), s2);
+          s2 = __ffma2_rn(make_float2(v.z, v.w), make_float2(v.z, v.w), s2);
+          i += stride;
+        }
+      }
+      acc += (double)s2.x + (double)s2.y;
+    }
+    if ((n & 1u) && tid == 0) {
+      const float2 x = reinterpret_cast<const float2*>(vin)[n - 1];
+      acc += (double)x.x * (double)x.x + (double)x.y * (double)x.y;
+    }
+  } else {  // complex128, or a complex64 vector that is not 16-byte aligned
+    const V* __restrict__ in = reinterpret_cast<const V*>(vin);
+    for (uint64_t i = tid; i < n; i += stride) {
+      const V x = in[i];
+      acc += (double)x.x * (double)x.x + (double)x.y * (double)x.y;
+    }
   }
   const double a1[1] = {acc};
   reduce_to_slots<1>(a1, partials, counter, norms, slot);

@@ -454,11 +454,53 @@ owqs_status owqs_reorder(owqs_pattern* h, const owqs_reorder_opts* o, owqs_reord
   uint32_t g_peak = 0, l_peak = 0;
   uint64_t g_upd = 0, l_upd = 0;
   order_stats(p, &g_peak, &g_upd);
-  bool accepted = false;
+  bool accepted = false, judge_owqs = false;
   std::vector<uint32_t> lorder;
+  if (o->use_learned && eowqs) {
+    // with preselected outcomes an order that waits for every domain is
+    // valid too: the greedy OWQS sweep order joins the judges
+    ReorderGraph g2 = build_reorder_graph(p, false);
+    GreedyResult b2;
+    uint32_t b2_peak = 0;
+    unsigned __int128 b2_sum = 0;
+    bool have2 = false;
+    for (int a = std::max<int>(1, (int)p.outputs.size()); a >= 1; --a) {
+      GreedyResult r = greedy(g2, p.inputs, o->product_input != 0, (double)a, k, 0.5, k);
+      if (r.order.size() != g2.measured.size()) break;  // a dependency cycle: no OWQS order
+      uint32_t pk = 0;
+      unsigned __int128 sum = 0;
+      for (uint32_t m : r.ms) {
+        pk = std::max(pk, m);
+        sum += (unsigned __int128)1 << std::min<uint32_t>(m, 126);
+      }
+      if (!have2 || pk < b2_peak || (pk == b2_peak && sum < b2_sum)) {
+        have2 = true;
+        b2 = std::move(r);
+        b2_peak = pk;
+        b2_sum = sum;
+      }
+    }
+    if (have2) {
+      st = build_active_order(p, b2.order, true);
+      if (st != OWQS_OK) return st;
+      uint32_t o_peak = 0;
+      uint64_t o_upd = 0;
+      order_stats(p, &o_peak, &o_upd);
+      if (o_peak < g_peak || (o_peak == g_peak && o_upd < g_upd)) {
+        judge_owqs = true;
+        best = std::move(b2);
+        best_peak = b2_peak;
+        g_peak = o_peak;
+        g_upd = o_upd;
+      } else {
+        st = build_active_order(p, best.order, !eowqs);
+        if (st != OWQS_OK) return st;
+      }
+    }
+  }
   if (o->use_learned) {
-    // the proposal is judged by the greedy order: kept only if its peak live
-    // width and amplitude updates are no worse
+    // the proposal is judged by the best greedy order: kept only if its peak
+    // live width and amplitude updates are no worse
     st = learned_order(p, o->model, eowqs, o->product_input != 0, lorder);
     if (st != OWQS_OK) return st;
     st = build_active_order(p, lorder, !eowqs);
@@ -482,6 +524,7 @@ owqs_status owqs_reorder(owqs_pattern* h, const owqs_reorder_opts* o, owqs_reord
     info->greedy_amp_updates = g_upd;
     info->learned_peak_live = l_peak;
     info->learned_amp_updates = l_upd;
+    info->greedy_judge_owqs = judge_owqs ? 1u : 0u;
   }
   return OWQS_OK;
 }

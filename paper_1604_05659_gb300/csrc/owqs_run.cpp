@@ -502,6 +502,7 @@ static std::string graph_key(const Pattern& p, const owqs_run_opts* o, const voi
   for (uint32_t i : p.active) h = (h ^ i) * 1099511628211ull;
   add(&h, 8);
   if (o->policy == OWQS_OUTCOME_FORCED && outcomes) add(outcomes, p.meas_qubit.size());
+  add(&o->flags, 4);
   const int cap = test_grid_cap();
   add(&cap, sizeof(cap));
   return k;
@@ -1140,6 +1141,19 @@ static owqs_status run_core(Pattern& p, const owqs_run_opts* o, const void* psi_
       }
     }
     in_group = R.in_group;
+    if (o->dtype == OWQS_C128 && (o->flags & OWQS_RUN_DOUBLE_FLOAT)) {
+      // pass groups in double-float; between two such groups on the same
+      // array the array stays in double-float pairs
+      for (size_t i = 0; i < R.items.size(); ++i) {
+        Item& it = R.items[i];
+        if (it.type != 4) continue;
+        it.G.df = 1;
+        const Item* prev = i > 0 ? &R.items[i - 1] : nullptr;
+        const Item* next = i + 1 < R.items.size() ? &R.items[i + 1] : nullptr;
+        it.G.df_in = prev && prev->type == 4 && prev->G.df_out && prev->G.out == it.G.in ? 1 : 0;
+        it.G.df_out = next && next->type == 4 && next->G.in == it.G.out ? 1 : 0;
+      }
+    }
     if (o->io == OWQS_IO_HOST && psi_in) {
       cudaError_t e = cudaMemcpyAsync(rc->in_stage, psi_in, pr.in_elems * pr.amp, cudaMemcpyHostToDevice, s);
       if (e != cudaSuccess) return cuda_fail(e, "input copy");

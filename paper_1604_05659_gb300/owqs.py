@@ -28,6 +28,7 @@ RUN_PER_PASS = 2
 RUN_SEQUENTIAL_SAMPLING = 4
 RUN_SUBSTATES = 8
 RUN_ONE_ARRAY = 16
+RUN_DOUBLE_FLOAT = 32
 DTYPE = {"c64": 0, "c128": 1}
 POLICY = {"forced": 0, "sampled": 1, "zero": 2}
 KERNEL_KIND = {0: "fast_pass", 1: "generic_pass", 2: "final", 3: "norm", 4: "prob", 5: "tma_pass", 10: "small_run",
@@ -60,8 +61,8 @@ class owqs_reorder_opts(C.Structure):
 class owqs_reorder_info(C.Structure):
     _fields_ = [("peak_m", C.c_uint32), ("peak_live", C.c_uint32), ("amp_updates", C.c_uint64),
                 ("alpha_used", C.c_double), ("learned_accepted", C.c_uint32), ("greedy_peak_live", C.c_uint32),
-                ("greedy_amp_updates", C.c_uint64), ("learned_peak_live", C.c_uint32), ("pad_", C.c_uint32),
-                ("learned_amp_updates", C.c_uint64)]
+                ("greedy_amp_updates", C.c_uint64), ("learned_peak_live", C.c_uint32),
+                ("greedy_judge_owqs", C.c_uint32), ("learned_amp_updates", C.c_uint64)]
 
 
 class owqs_run_opts(C.Structure):
@@ -87,7 +88,7 @@ class owqs_batch_opts(C.Structure):
 
 class owqs_batch_info(C.Structure):
     _fields_ = [("smem_items", C.c_uint32), ("hbm_items", C.c_uint32), ("tasks", C.c_uint32),
-                ("smem_bytes_per_cta", C.c_uint32), ("launches", C.c_uint32), ("pad_", C.c_uint32)]
+                ("smem_bytes_per_cta", C.c_uint32), ("launches", C.c_uint32), ("global_items", C.c_uint32)]
 
 
 class owqs_pass_desc(C.Structure):
@@ -385,7 +386,7 @@ class Handle:
     def run(self, psi_in=None, *, dtype: str = "c128", mode: str = "owqs", policy: str = "forced",
             outcomes=None, seed: int = 0, stream=None, use_graph: bool = True, out=None,
             check: bool = True, host_sampling: bool = False, per_pass: bool = False,
-            sequential_sampling: bool = False, layout: str = "auto"):
+            sequential_sampling: bool = False, layout: str = "auto", double_float: bool = False):
         """Run on the GPU.  psi_in: torch tensor on the GPU (complex64 for
         c64, complex128 for c128) or None for |+> inputs; returns
         (psi_out tensor, outcomes array, probs array, status).
@@ -396,7 +397,9 @@ class Handle:
         time from the start, instead of first checking the guess u > 1/2 with
         one forced run.
         layout: "auto" (separate sub-states when they need at most half the
-        memory of one array), "substates" or "one_array"."""
+        memory of one array), "substates" or "one_array".
+        double_float: complex128 pass groups in double-float arithmetic on the
+        FP32 pipes."""
         import torch
         tdt = torch.complex64 if dtype == "c64" else torch.complex128
         _check_vectors(psi_in, out, tdt, self.nin, self.nout)
@@ -412,7 +415,8 @@ class Handle:
                              int(use_graph), (RUN_HOST_SAMPLING if host_sampling else 0) |
                              (RUN_PER_PASS if per_pass else 0) |
                              (RUN_SEQUENTIAL_SAMPLING if sequential_sampling else 0) |
-                             {"auto": 0, "substates": RUN_SUBSTATES, "one_array": RUN_ONE_ARRAY}[layout])
+                             {"auto": 0, "substates": RUN_SUBSTATES, "one_array": RUN_ONE_ARRAY}[layout] |
+                             (RUN_DOUBLE_FLOAT if double_float else 0))
         st = library().owqs_run(self._h, C.byref(opts), C.c_void_p(psi_in.data_ptr() if psi_in is not None else 0),
                                 C.c_void_p(out.data_ptr()), oc.ctypes.data_as(C.POINTER(C.c_uint8)),
                                 probs.ctypes.data_as(C.POINTER(C.c_double)))
@@ -514,7 +518,7 @@ class Handle:
         return oc[: self.K].copy(), probs[: self.K].copy()
 
     def profile(self, psi_in=None, *, dtype: str = "c64", mode: str = "owqs", policy: str = "forced",
-                outcomes=None, stream=None, out=None, layout: str = "auto"):
+                outcomes=None, stream=None, out=None, layout: str = "auto", double_float: bool = False):
         """Per-launch CUDA-event durations of one run (no graph)."""
         import torch
         tdt = torch.complex64 if dtype == "c64" else torch.complex128
@@ -530,7 +534,8 @@ class Handle:
         n = C.c_uint32()
         s = stream if stream is not None else torch.cuda.current_stream(dev)
         opts = owqs_run_opts(DTYPE[dtype], MODE[mode], POLICY[policy], 0, 0, C.c_void_p(s.cuda_stream), 0,
-                             {"auto": 0, "substates": RUN_SUBSTATES, "one_array": RUN_ONE_ARRAY}[layout])
+                             {"auto": 0, "substates": RUN_SUBSTATES, "one_array": RUN_ONE_ARRAY}[layout] |
+                             (RUN_DOUBLE_FLOAT if double_float else 0))
         oc = _outcome_buf(outcomes, self.K)
         _check(library().owqs_profile_run(self._h, C.byref(opts),
                                           C.c_void_p(psi_in.data_ptr() if psi_in is not None else 0),

@@ -45,15 +45,15 @@ def target_order(h):
 
 def gpu_seconds(h, reps: int = 3) -> float:
     """Median CUDA-event time of one EOWQS run (complex64, all-zero branch,
-    graph replay) under the handle's active order."""
+    one array, graph replay) under the handle's active order."""
     import torch
     out = torch.empty(1 << h.nout, dtype=torch.complex64, device="cuda")
-    h.run(None, dtype="c64", mode="eowqs", policy="zero", out=out)
+    h.run(None, dtype="c64", mode="eowqs", policy="zero", out=out, layout="one_array")
     ts = []
     for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        h.run(None, dtype="c64", mode="eowqs", policy="zero", out=out)
+        h.run(None, dtype="c64", mode="eowqs", policy="zero", out=out, layout="one_array")
         e1.record()
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1) / 1e3)
@@ -119,34 +119,34 @@ def build_dataset(handles, cands, seed, timed: int = 0, timed_width: int = 22):
     return X if timed == 0 else (X, stats)
 
 
-def evaluate(handles, model, sweep, timed: int = 0, timed_width: int = 22):
-    """EOWQS reordering of each pattern, greedy alone and with the proposal
-    (without the sweep the Eq. 18 weights are Section 5's first run,
-    a = b = d = |O|, g = 0.5).  For the first `timed` patterns of at most
-    timed_width inputs, the kept order's GPU time is measured against the
-    fastest greedy order that fits the device (greedy EOWQS, else the greedy
-    OWQS sweep; EOWQS runs, complex64, all-zero branch)."""
+def evaluate(handles, model, sweep, timed: int = 0, timed_width: int = 30):
+    """EOWQS reordering of each held-out pattern with the proposal, judged by
+    the best greedy order: the greedy EOWQS order (without the sweep the
+    Eq. 18 weights are Section 5's first run, a = b = d = |O|, g = 0.5) and
+    the greedy OWQS sweep order, which waits for every domain and so is
+    valid with preselected outcomes too; the library keeps the proposal only
+    if it is no worse by (peak live width, amplitude updates).  For the first
+    `timed` patterns of at most timed_width inputs, the kept order and the
+    best greedy order are simulated on the GPU (EOWQS, complex64, all-zero
+    branch) when they fit the device."""
     rows = []
     ntimed = 0
     for h in handles:
         k = float(max(1, h.nout))
         w = (k, k, 0.5, k)
-        _, g = h.reorder(mode="eowqs", sweep=sweep, weights=w)
+        _, e = h.reorder(mode="eowqs", sweep=sweep, weights=w)
+        _, o = h.reorder(mode="owqs", sweep=True)
+        greedy_seconds = gpu_seconds(h) if ntimed < timed and h.nin <= timed_width and o["peak_live"] <= 31 else None
         _, l = h.reorder(mode="eowqs", sweep=sweep, weights=w, model=model)
-        row = {"n": h.nin, "K": h.K, "greedy_peak": l["greedy_peak_live"],
-               "greedy_updates": l["greedy_amp_updates"], "learned_peak": l["learned_peak_live"],
-               "learned_updates": l["learned_amp_updates"], "accepted": l["learned_accepted"]}
-        if ntimed < timed and h.nin <= timed_width and l["peak_live"] <= 24:
-            row["kept_seconds"] = gpu_seconds(h)
-            best = None
-            for mode, sw in (("eowqs", sweep), ("owqs", True)):
-                _, gi = h.reorder(mode=mode, sweep=sw, weights=w)
-                if gi["peak_live"] <= 24:
-                    t = gpu_seconds(h)
-                    if best is None or t < best[0]:
-                        best = (t, mode, gi["peak_live"])
-            if best is not None:
-                row["greedy_seconds"], row["greedy_timed_mode"], row["greedy_timed_peak"] = best
+        row = {"n": h.nin, "K": h.K, "eowqs_greedy_peak": e["peak_live"], "owqs_greedy_peak": o["peak_live"],
+               "greedy_peak": l["greedy_peak_live"], "greedy_updates": l["greedy_amp_updates"],
+               "greedy_judge": "owqs" if l["greedy_judge_owqs"] else "eowqs",
+               "learned_peak": l["learned_peak_live"], "learned_updates": l["learned_amp_updates"],
+               "accepted": l["learned_accepted"], "kept_peak": l["peak_live"], "kept_updates": l["amp_updates"]}
+        if greedy_seconds is not None and l["peak_live"] <= 31:
+            row["kept_seconds"] = gpu_seconds(h) if l["learned_accepted"] else greedy_seconds
+            if l["greedy_judge_owqs"]:
+                row["greedy_seconds"] = greedy_seconds
             ntimed += 1
         rows.append(row)
     return rows
@@ -156,29 +156,32 @@ SATURATED = (1 << 64) - 1  # the library's update count saturates here (64+ live
 
 
 def summary(rows):
-    """Held-out comparison.  The update ratio is a geometric mean over the
-    patterns whose greedy count did not saturate; the others are counted."""
+    """Held-out comparison against the best greedy order.  The update ratio is
+    a geometric mean over the patterns whose greedy count did not saturate."""
     acc = sum(r["accepted"] for r in rows)
-    gp = float(np.mean([r["greedy_peak"] for r in rows]))
-    lp = float(np.mean([r["learned_peak"] for r in rows]))
     exact = [r for r in rows if r["greedy_updates"] < SATURATED]
-    ratio = (float(np.exp(np.mean([np.log(r["greedy_updates"] / r["learned_updates"]) for r in exact])))
+    ratio = (float(np.exp(np.mean([np.log(r["greedy_updates"] / r["kept_updates"]) for r in exact])))
              if exact else None)
-    tr = [r for r in rows if "greedy_seconds" in r]
+    tr = [r for r in rows if "greedy_seconds" in r and "kept_seconds" in r]
     timing = None
     if tr:
         timing = {"patterns": len(tr),
-                  "geomean_greedy_over_kept_seconds": float(np.exp(np.mean(
+                  "geomean_best_greedy_over_kept_seconds": float(np.exp(np.mean(
                       [np.log(r["greedy_seconds"] / r["kept_seconds"]) for r in tr]))),
                   "kept_seconds_total": float(sum(r["kept_seconds"] for r in tr)),
-                  "greedy_seconds_total": float(sum(r["greedy_seconds"] for r in tr)),
-                  "greedy_modes": {m: sum(r["greedy_timed_mode"] == m for r in tr) for m in ("eowqs", "owqs")}}
-    return {"patterns": len(rows), "accepted": acc, "mean_greedy_peak_live": gp, "mean_learned_peak_live": lp,
+                  "best_greedy_seconds_total": float(sum(r["greedy_seconds"] for r in tr))}
+    return {"patterns": len(rows), "accepted": acc,
+            "judge": "best of the greedy EOWQS order and the greedy OWQS sweep order",
+            "best_greedy_is_owqs_sweep": sum(r["greedy_judge"] == "owqs" for r in rows),
+            "kept_never_worse": all((r["kept_peak"], r["kept_updates"]) <= (r["greedy_peak"], r["greedy_updates"])
+                                    for r in rows),
+            "mean_peak_live": {"eowqs_greedy": float(np.mean([r["eowqs_greedy_peak"] for r in rows])),
+                               "owqs_greedy": float(np.mean([r["owqs_greedy_peak"] for r in rows])),
+                               "best_greedy": float(np.mean([r["greedy_peak"] for r in rows])),
+                               "learned": float(np.mean([r["learned_peak"] for r in rows])),
+                               "kept": float(np.mean([r["kept_peak"] for r in rows]))},
             "gpu_time": timing,
-            "max_greedy_peak_live": max(r["greedy_peak"] for r in rows),
-            "max_learned_peak_live": max(r["learned_peak"] for r in rows),
-            "greedy_updates_saturated": len(rows) - len(exact),
-            "geomean_update_ratio_greedy_over_learned": ratio,
+            "geomean_update_ratio_best_greedy_over_kept": ratio,
             "learned_peak_equals_n_plus_1": sum(r["learned_peak"] == r["n"] + 1 for r in rows)}
 
 
@@ -201,7 +204,7 @@ def main(argv=None):
     ap.add_argument("--eval-sweep", action="store_true", help="judge with the full Section 5 sweep")
     ap.add_argument("--out", default=DEFAULT_OUT)
     ap.add_argument("--timed", type=int, default=64, help="training patterns labelled by GPU timings")
-    ap.add_argument("--timed-eval", type=int, default=48, help="held-out patterns whose kept order is GPU-timed")
+    ap.add_argument("--timed-eval", type=int, default=200, help="held-out patterns whose orders are GPU-timed")
     ap.add_argument("--eval-only", action="store_true",
                     help="re-evaluate the weights already in --out on the held-out set and rewrite its summary")
     a = ap.parse_args(argv)

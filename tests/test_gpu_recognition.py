@@ -89,13 +89,15 @@ def test_unitary_qft_is_dft(env):
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_batch_unitaries_mixed_widths(env, dtype):
-    """One call: many small patterns in the persistent shared-memory launch
-    and wider ones through the pass kernels; each matrix against the single
-    call and, for n <= 8, every column against the oracle."""
+    """One call: many small patterns in the persistent shared-memory launch,
+    a wider one in the persistent launch with global-memory state buffers,
+    and a still wider input-vector item through the pass kernels; each
+    result against the single call and, for n <= 8, every column against the
+    oracle."""
     torch, owqs = env
     tdt = torch.complex64 if dtype == "c64" else torch.complex128
     # widest arrays: 2^12 fits a block's shared memory in both dtypes; 2^13
-    # (c128) and 2^14 (c64) do not and go through the pass kernels
+    # (c128) and 2^14 (c64) do not and run with global-memory buffers
     wide = (13, 1) if dtype == "c128" else (14, 1)
     specs = [(1 + (i % 8), 3 + (i % 5)) for i in range(20)] + [(11, 3), (12, 2), wide]
     items, meta = [], []
@@ -107,8 +109,18 @@ def test_batch_unitaries_mixed_widths(env, dtype):
         out = torch.empty(1 << (2 * n), dtype=tdt, device="cuda")
         items.append({"handle": h, "outcomes": bits, "psi_in": None, "out": out, "ref": -1})
         meta.append((p, order, bits, n))
-    info, _ = owqs.run_batch(items, dtype=dtype)
-    assert info["smem_items"] == len(specs) - 1 and info["hbm_items"] == 1, info
+    # an input-vector item whose arrays exceed 2^18 amplitudes: pass kernels
+    pw, rngw = _circ(199, 19, 1)
+    hw = owqs.load(pw)
+    hw.reorder()
+    bw = rngw.bits(pw.K)
+    psi_w = torch.from_numpy(random_state(rngw, 19)).to(tdt).cuda()
+    out_w = torch.empty(1 << 19, dtype=tdt, device="cuda")
+    info, _ = owqs.run_batch(items + [{"handle": hw, "outcomes": bw, "psi_in": psi_w, "out": out_w, "ref": -1}],
+                             dtype=dtype)
+    assert info["smem_items"] == len(specs) - 1 and info["global_items"] == 1 and info["hbm_items"] == 1, info
+    single_w, _, _, _ = hw.run(psi_w, dtype=dtype, mode="eowqs", outcomes=bw, check=False)
+    assert torch.max(torch.abs(out_w - single_w)).item() <= TOL[dtype]
     for it, (p, order, bits, n) in zip(items, meta):
         single, _ = it["handle"].unitary(dtype=dtype, outcomes=bits)
         assert torch.max(torch.abs(it["out"] - single)).item() <= TOL[dtype], p.name

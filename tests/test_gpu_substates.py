@@ -8,7 +8,7 @@ inside each component."""
 import numpy as np
 import pytest
 
-from oracle import proa, substate
+from oracle import proa, substate, substate_c
 from owqs_inputs import workloads
 from owqs_inputs.patterns import E, M, N, Pattern
 from owqs_inputs.rng import SplitMix64, random_state
@@ -45,9 +45,11 @@ def _compare(env, wl, psi, dtype, mode, expect_joins=None):
     torch, owqs = env
     p = wl.pattern
     h = owqs.load(p)
-    h.reorder(mode=mode)
+    h.reorder()  # an order that measures every domain first, valid in both modes
     op = proa.reorder_commands(p, h.order())
-    ref = substate.run(op, psi, outcomes=outcomes_by_label(p, wl.outcomes), mode=mode)
+    # the C build of O-A: compensated probability sums, exact enough at the
+    # 2^25-amplitude sub-states of the larger cases for the complex128 bound
+    ref = substate_c.run(op, psi, outcomes=outcomes_by_label(p, wl.outcomes), mode=mode)
     got, probs = _run(env, h, psi, dtype, mode, wl.outcomes, "substates")
     one, probs1 = _run(env, h, psi, dtype, mode, wl.outcomes, "one_array")
     for x in (got, one):
