@@ -45,14 +45,14 @@ def workload_name(rows: int, cols: int) -> str:
             f"forced seeded outcomes, greedy reordering (a reduced size of the 28x40 workload)")
 FALLBACK_HBM_GBS = 6800.0
 # ncu DRAM bytes (read + write) per launch of the dominant kernel, keyed by the
-# sha256 prefix of the kernel source they were measured on (a changed kernel
-# reports null).  Both are pass groups on the full brickwork workload, mean of
-# three launches: c64 k_group<3> (2^28 complex64 amplitudes in and out;
-# 2147.9 MB read + 2095.4 MB written) and c128 k_group64<3> (2^28 complex128;
-# 4298.5 MB read + 4246.7 MB written).  profiles/k_group_c64_brickwork28x40_dram.md,
-# profiles/k_group64_c128_brickwork26x8.md.
-NCU_TRAFFIC = {("68309cd2b9084767", "c64"): (2147674880 + 2097199360 + 2148430080 + 2094572032 + 2147639552 + 2094421504) / 3.0,
-               ("68309cd2b9084767", "c128"): (4299186432 + 4248895232 + 4298526720 + 4245655808 + 4297742336 + 4245464320) / 3.0}
+# sha256 prefix of the pass-group sources they were measured on (a changed
+# kernel reports null).  Both are pass groups on the full brickwork workload,
+# mean of three launches: c64 k_group<3, 0, SEQ> (2^28 complex64 amplitudes in
+# and out; 2147.7 MB read + 2103.8 MB written) and c128 k_group64<3, 0> (2^28
+# complex128; 4299.3 MB read + 4247.1 MB written).
+# profiles/k_group_c64_brickwork28x40_dram.md.
+NCU_TRAFFIC = {("faafb09b1344fb89", "c64"): (2147718144 + 2105868288 + 2147657728 + 2102733056 + 2147620352 + 2102921216) / 3.0,
+               ("faafb09b1344fb89", "c128"): (4299367168 + 4249121792 + 4299737600 + 4246787072 + 4298777600 + 4245467136) / 3.0}
 # nominal GB300 FP64 rate (no measured FP64 peak exists for this machine)
 FP64_PEAK_TFLOPS = 1.25
 # FP64 flops per output amplitude of the complex128 pass: complex multiply-add
@@ -169,7 +169,8 @@ class ClockSampler:
 def kernel_source_hash():
     """sha256 prefix of the pass-group sources (the dominant kernels)."""
     h = hashlib.sha256()
-    for name in ("owqs_group.cu", "owqs_device.cuh", "owqs_group_sequences.inc"):
+    for name in ("owqs_group.cu", "owqs_group_c64.cuh", "owqs_group_seq.cu", "owqs_device.cuh",
+                 "owqs_group_sequences.inc"):
         with open(os.path.join(ROOT, "paper_1604_05659_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -267,6 +268,57 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def readout_leg(args, owqs, torch, timed):
+    """Sampled OWQS on patterns without a gflow: the brickwork rows x cols
+    with all of its outputs, or half of them, measured as well at seeded
+    random angles (these last measurements have probabilities other than
+    1/2).  Complex64, one array.  Times, per run: the forced run of one
+    outcome vector, the sampled run by checked launches (a new seed every
+    run; relaunches and host checks reported) and the one-measurement-at-a-
+    time draw (one run)."""
+    import numpy as np
+    from owqs_inputs import workloads
+    res = {}
+    for kept in (0, args.rows // 2):
+        wl = workloads.brickwork_readout(args.rows, args.cols, kept=kept)
+        h = owqs.load(wl.pattern)
+        _, info = h.reorder()
+        out = torch.empty(1 << h.nout, dtype=torch.complex64, device="cuda")
+        steps = args.sampled_steps
+        forced = lambda: h.run(None, dtype="c64", outcomes=wl.outcomes, out=out, layout="one_array", check=False)
+        forced()
+        tf = timed(forced, steps)
+        seeds = iter(range(3000, 4000))
+        infos, devs = [], []
+
+        def sampled():
+            _, _, ps, _ = h.run(None, dtype="c64", policy="sampled", seed=next(seeds), out=out, layout="one_array")
+            infos.append(h.last_sample_info())
+            devs.append(float(np.max(np.abs(ps - 0.5))))
+
+        sampled()
+        infos.clear()
+        ts = timed(sampled, steps)
+        one = lambda: h.run(None, dtype="c64", policy="sampled", seed=3999, out=out, layout="one_array",
+                            sequential_sampling=True)
+        t1 = timed(one, 1)
+        res[f"outputs_kept_{kept}"] = {
+            "workload": f"brickwork {args.rows}x{args.cols} with {args.rows - kept} of its {args.rows} outputs measured "
+                        f"at seeded random angles (no gflow), |+> inputs, {wl.pattern.K} measurements, peak live "
+                        f"{info['peak_live']}, {info['amp_updates']} amplitude updates",
+            "forced_ms_per_run": 1e3 * tf / steps,
+            "checked_launches_ms_per_run": 1e3 * ts / steps,
+            "one_at_a_time_ms_per_run": 1e3 * t1,
+            "checked_over_forced": ts / tf,
+            "paths": sorted({i["path"] for i in infos}),
+            "relaunches_per_run": [i["relaunches"] for i in infos],
+            "checks_per_run": [i["checks"] for i in infos],
+            "max_abs_prob_minus_half": max(devs)}
+        del out
+        h.close()
+    return res
 
 
 def table3_leg(owqs):
@@ -738,6 +790,7 @@ def run_owqs(args):
             ts = timed(run_s, args.sampled_steps)
             sampled[mode] = {"value": replica_throughput(upd, args.sampled_steps, world, ts), "unit": UNIT,
                              "ms_per_run": 1e3 * ts / args.sampled_steps, "max_abs_prob_minus_half": max(dev)}
+        sampled["no_gflow"] = readout_leg(args, owqs, torch, timed)
 
     fp64, accuracy = None, None
     if "c128" in legs:

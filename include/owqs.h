@@ -246,15 +246,29 @@ typedef struct {
   uint64_t seed;      /* sampled policy only                                          */
   void* stream;       /* cudaStream_t to run on; NULL = the legacy default stream    */
   uint32_t use_graph; /* 1: replay the pass sequence as a CUDA graph                */
-  uint32_t flags;     /* Sampled OWQS runs first guess every outcome as u > 1/2 (the
-                         probability of a gflow pattern, Section 4.5), run the
-                         guesses as forced outcomes, and keep that run iff every
-                         draw u_k <= prob_0 it computed reproduces its guess and
-                         lies more than a tie margin (1e-6 for OWQS_C64, 1e-12
-                         for OWQS_C128) from that prob_0 (then the one-at-a-time
-                         draw, whose prob_0 differs only by rounding, takes the
-                         same branch); otherwise they draw one measurement at a
-                         time:
+  uint32_t flags;     /* Sampled OWQS runs on a pattern with a gflow first guess
+                         every outcome as u > 1/2 (the probability of a gflow
+                         pattern, Section 4.5), run the guesses as forced
+                         outcomes, and keep that run iff every draw u_k <= prob_0
+                         it computed reproduces its guess and lies more than a tie
+                         margin (1e-6 for OWQS_C64, 1e-12 for OWQS_C128) from that
+                         prob_0 (then the one-at-a-time draw, whose prob_0 differs
+                         only by rounding, takes the same branch).  Otherwise, and
+                         on patterns without a gflow, they take checked launches
+                         when no X or Z with a signal comes before the last
+                         measurement: the forced run of the current outcome
+                         vector (initially those guesses), one kernel at a time;
+                         after each launch that measures, the host checks its
+                         measurements' draws against the probabilities it
+                         computed, in execution order, and at the first draw that
+                         decides the other outcome corrects that outcome and runs
+                         the same launch again on its untouched input.  The
+                         outcomes are those of a one-at-a-time draw (a draw
+                         within rounding of prob_0 follows the launch's own
+                         prob_0).  Patterns with such an X or Z draw one
+                         measurement at a time.  owqs_last_sample_info says which
+                         of these ran.
+                         Flags:
                          OWQS_RUN_SEQUENTIAL_SAMPLING: draw one measurement at a
                          time from the start, on the device whenever no X or Z with
                          a signal comes before the last measurement (e.g. standard
@@ -281,6 +295,26 @@ typedef struct {
 } owqs_run_opts;
 enum { OWQS_RUN_HOST_SAMPLING = 1, OWQS_RUN_PER_PASS = 2, OWQS_RUN_SEQUENTIAL_SAMPLING = 4,
        OWQS_RUN_SUBSTATES = 8, OWQS_RUN_ONE_ARRAY = 16, OWQS_RUN_DOUBLE_FLOAT = 32 };
+
+/* How the pattern's last run with sampled outcomes (owqs_run, policy
+ * OWQS_OUTCOME_SAMPLED) was carried out. */
+enum {
+  OWQS_SAMPLE_NONE = 0,              /* no sampled run yet                                */
+  OWQS_SAMPLE_DRAWN_FIRST = 1,       /* EOWQS: every outcome drawn, then a forced run     */
+  OWQS_SAMPLE_GUESS_KEPT = 2,        /* OWQS: the whole-run guess held                     */
+  OWQS_SAMPLE_CHECKED_LAUNCHES = 3,  /* OWQS: checked launches                              */
+  OWQS_SAMPLE_ONE_AT_A_TIME = 4,     /* OWQS: one measurement at a time, drawn on the device */
+  OWQS_SAMPLE_HOST = 5               /* OWQS: one measurement at a time, drawn on the host   */
+};
+typedef struct {
+  uint32_t path;        /* OWQS_SAMPLE_*                                                   */
+  uint32_t guessed;     /* 1: a whole-run guess ran first (kept or not)                     */
+  uint32_t checks;      /* checked launches: host checks, one per launch that measures      */
+  uint32_t relaunches;  /* checked launches: launches run again after a corrected outcome   */
+} owqs_sample_info;
+/* Fills *info for the pattern's last sampled run (zeros before the first).
+ * OWQS_ERR_ARG on a NULL argument. */
+owqs_status owqs_last_sample_info(const owqs_pattern* p, owqs_sample_info* info);
 
 /* Simulate the pattern under its active order and return the output state.
  *   psi_in    2^|I| amplitudes (bit k = inputs[k]); NULL = |+> on every input

@@ -12,6 +12,9 @@ available; these stand in for them with the same structure).
                     size), random normalised input.  Stands in for the QFT
                     rows of Table II.
   random_batch      uneven random J/CZ patterns for batched recognition.
+  brickwork_readout the brickwork with (some of) its outputs measured in
+                    seeded random bases: no gflow, sampled-outcome workloads.
+  measured_inputs   a random product input measured qubit by qubit.
 """
 from __future__ import annotations
 
@@ -22,7 +25,7 @@ from typing import List, Optional
 
 import numpy as np
 
-from .patterns import (Pattern, brickwork_circuit, circuit_to_pattern, qft_circuit,
+from .patterns import (M, Pattern, brickwork_circuit, circuit_to_pattern, qft_circuit,
                        random_jcz_circuit)
 from .rng import SplitMix64, pattern_rng, random_state
 
@@ -79,6 +82,52 @@ def joined_bricks(rows: int, cols: int, copies: int = 2, pattern_index: int = 0)
     p = circuit_to_pattern(rows * copies, gates, f"joined_bricks{copies}x{rows}x{cols}")
     out = forced_outcomes(p, rng)
     return Workload(p, None, out, p.name)
+
+
+def brickwork_readout(rows: int, cols: int, kept: int = 0, pattern_index: int = 0,
+                      with_input: bool = False) -> Workload:
+    """The brickwork rows x cols with its output wires kept..rows-1 measured
+    as well, each at a seeded random angle in [0, 2 pi): the corrections X^s
+    Z^t the flow pattern puts on such an output become that measurement's s-
+    and t-domains (X^s before M_a gives the angle (-1)^s a, Z^t gives a + t pi,
+    Eq. 2), and the measurements follow all the others.  Outputs: wires
+    0..kept-1.  With fewer outputs than inputs the open graph has no gflow,
+    so these last measurements' probabilities are not 1/2 (Section 4.5); the
+    rest of the pattern is the flow pattern, whose probabilities are 1/2.
+    |+> inputs unless with_input (a random normalised state)."""
+    if not 0 <= kept <= rows:
+        raise ValueError("kept must lie in [0, rows]")
+    rng = pattern_rng(6, pattern_index)
+    gates, _ = brickwork_circuit(rows, cols, rng)
+    base = circuit_to_pattern(rows, gates, "")
+    measured_out = set(base.outputs[kept:])
+    xdom = {c.q0: c.sdom for c in base.cmds if c.kind == "X"}
+    zdom = {c.q0: c.sdom for c in base.cmds if c.kind == "Z"}
+    cmds = [c for c in base.cmds if c.kind in ("N", "E", "M")]
+    for q in base.outputs[kept:]:
+        cmds.append(M(q, 2.0 * math.pi * rng.uniform(), xdom.get(q, ()), zdom.get(q, ())))
+    cmds += [c for c in base.cmds if c.kind in ("X", "Z") and c.q0 not in measured_out]
+    p = Pattern(base.nqubits, list(base.inputs), base.outputs[:kept], cmds, f"brickwork_readout{rows}x{cols}k{kept}",
+                list(gates), rows)
+    psi = random_state(rng, rows) if with_input else None
+    out = forced_outcomes(p, rng)
+    return Workload(p, psi, out, p.name)
+
+
+def measured_inputs(n: int, kept: int = 2, pattern_index: int = 0) -> Workload:
+    """n input qubits, every one but the last `kept` measured directly at a
+    seeded random angle (no E, no N): with a random product input, each
+    probability is |<+_a|psi_q>|^2, far from 1/2 in general.  Outputs: the
+    last `kept` inputs."""
+    rng = pattern_rng(7, pattern_index)
+    cmds = [M(q, 2.0 * math.pi * rng.uniform()) for q in range(n - kept)]
+    p = Pattern(n, list(range(n)), list(range(n - kept, n)), cmds, f"measured_inputs{n}k{kept}")
+    psi = np.ones(1, dtype=np.complex128)
+    for q in range(n):   # bit q of the index is qubit q: kron puts the last factor lowest
+        v = random_state(rng, 1)
+        psi = np.kron(v, psi)
+    out = forced_outcomes(p, rng)
+    return Workload(p, psi, out, p.name)
 
 
 def qft(n: int = 24, pattern_index: int = 0, with_input: bool = True) -> Workload:

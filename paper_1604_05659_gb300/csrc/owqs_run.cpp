@@ -35,6 +35,10 @@ struct RunCache {
   std::vector<unsigned char> small_host;
   std::vector<double> h_norms;
   uint32_t last_launches = 0;
+  uint32_t last_sample_path = 0;   // OWQS_SAMPLE_* of the last sampled run
+  uint32_t last_guessed = 0;       // a whole-run guess ran first
+  uint32_t last_relaunches = 0;    // checked launches: launches run again after a corrected outcome
+  uint32_t last_checks = 0;        // checked launches: host checks (one per launch that measures)
   void* arena = nullptr;  // separate sub-states: every component array, at planned offsets
   size_t arena_bytes = 0;
   uint32_t last_components = 0;  // separate sub-states: components of the last run (0: one array)
@@ -1008,6 +1012,20 @@ static owqs_status sample_on_device(Pattern& p, const owqs_run_opts* o, RunCache
   return OWQS_OK;
 }
 
+// Pass groups in double-float (complex128, OWQS_RUN_DOUBLE_FLOAT): between
+// two such groups on the same array the array stays in double-float pairs.
+static void mark_double_float(std::vector<Item>& items) {
+  for (size_t i = 0; i < items.size(); ++i) {
+    Item& it = items[i];
+    if (it.type != 4) continue;
+    it.G.df = 1;
+    const Item* prev = i > 0 ? &items[i - 1] : nullptr;
+    const Item* next = i + 1 < items.size() ? &items[i + 1] : nullptr;
+    it.G.df_in = prev && prev->type == 4 && prev->G.df_out && prev->G.out == it.G.in ? 1 : 0;
+    it.G.df_out = next && next->type == 4 && next->G.in == it.G.out ? 1 : 0;
+  }
+}
+
 static owqs_status run_core(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
                             uint8_t* outcomes, double* probs, float* prof_ms, double* prof_bytes,
                             uint32_t* prof_kind, uint32_t prof_cap, uint32_t* prof_n, int vdiag,
@@ -1141,19 +1159,7 @@ static owqs_status run_core(Pattern& p, const owqs_run_opts* o, const void* psi_
       }
     }
     in_group = R.in_group;
-    if (o->dtype == OWQS_C128 && (o->flags & OWQS_RUN_DOUBLE_FLOAT)) {
-      // pass groups in double-float; between two such groups on the same
-      // array the array stays in double-float pairs
-      for (size_t i = 0; i < R.items.size(); ++i) {
-        Item& it = R.items[i];
-        if (it.type != 4) continue;
-        it.G.df = 1;
-        const Item* prev = i > 0 ? &R.items[i - 1] : nullptr;
-        const Item* next = i + 1 < R.items.size() ? &R.items[i + 1] : nullptr;
-        it.G.df_in = prev && prev->type == 4 && prev->G.df_out && prev->G.out == it.G.in ? 1 : 0;
-        it.G.df_out = next && next->type == 4 && next->G.in == it.G.out ? 1 : 0;
-      }
-    }
+    if (o->dtype == OWQS_C128 && (o->flags & OWQS_RUN_DOUBLE_FLOAT)) mark_double_float(R.items);
     if (o->io == OWQS_IO_HOST && psi_in) {
       cudaError_t e = cudaMemcpyAsync(rc->in_stage, psi_in, pr.in_elems * pr.amp, cudaMemcpyHostToDevice, s);
       if (e != cudaSuccess) return cuda_fail(e, "input copy");
@@ -1278,6 +1284,152 @@ static owqs_status run_core(Pattern& p, const owqs_run_opts* o, const void* psi_
                 in_group);
 }
 
+// Sampled OWQS by checked launches (the draw of Fig. 6, one launch at a
+// time instead of one measurement at a time).
+//
+// The outcome vector starts as the guesses u_k > 1/2 and the run is the
+// forced run of the current vector, launched one kernel at a time.  After
+// each launch that measures, the host reads the probabilities it computed
+// and takes its measurements in execution order.  One whose draw u_k <=
+// prob_0 reproduces its outcome is decided.  At the first one that does not,
+// the draw has decided the other outcome: its prob_0 was computed on the
+// branch of the decided outcomes before it, so this is the draw a
+// one-measurement-at-a-time run makes.  The outcome vector is corrected,
+// the schedule recompiled, and the same launch runs again on its input,
+// which no later launch has touched.  A launch thus runs once, plus once per
+// corrected outcome among its measurements; where every probability is 1/2
+// (a gflow, Section 4.5) the guesses hold and this is the forced run with one
+// host check per launch.  A draw within rounding of prob_0 follows this
+// run's prob_0.  Requires measure passes whose sign forms and X masks do not
+// depend on outcomes (masks_outcome_free), so that every recompiled schedule
+// has the same launches on the same buffers; returns OWQS_ERR_UNSUPPORTED
+// before any launch otherwise.
+static bool same_launches(const std::vector<Item>& a, const std::vector<Item>& b) {
+  if (a.size() != b.size()) return false;
+  for (size_t i = 0; i < a.size(); ++i) {
+    const Item& x = a[i];
+    const Item& y = b[i];
+    if (x.type != y.type || x.L.meas != y.L.meas || x.L.kind != y.L.kind) return false;
+    if (x.type == 4 && (x.G.in != y.G.in || x.G.out != y.G.out || x.G.k != y.G.k)) return false;
+    if (x.type == 0 && (x.P.in != y.P.in || x.P.out != y.P.out)) return false;
+  }
+  return true;
+}
+
+static owqs_status sample_checked(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
+                                  uint8_t* outcomes, double* probs, const std::vector<double>& u,
+                                  std::vector<uint8_t>& oc) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(o->stream);
+  owqs_run_opts fo = *o;
+  fo.policy = OWQS_OUTCOME_FORCED;
+  RunCache* rc = nullptr;
+  Prepared pr;
+  owqs_status st = prepare(p, &fo, psi_in, psi_out, oc.data(), rc, pr, false);
+  if (st != OWQS_OK) return st;
+  size_t wmax = 1;
+  for (const PassDesc& d : pr.passes)
+    if (d.kind != 1) wmax = std::max<size_t>(wmax, (size_t)1 << d.n_out);
+  st = ensure_pingpong(rc, wmax, pr.amp);
+  if (st != OWQS_OK) return st;
+  auto build = [&](Runner& R) {
+    R.begin(pr.in_dev, pr.in_elems, pr.out_dev, pr.out_elems);
+    for (size_t i = 0; i < pr.passes.size(); ++i) {
+      GroupParams G;
+      LaunchPlan GL;
+      int gk = 0;
+      switch (decide_launch(pr.passes, i, o->dtype, R.real_input(), false, G, GL, gk)) {
+        case LAUNCH_JOIN:
+          return false;
+        case LAUNCH_FINAL:
+          R.final_pass(pr.passes[i]);
+          break;
+        case LAUNCH_GROUP:
+          R.measure_group(G, GL);
+          i += (size_t)gk - 1;
+          break;
+        default:
+          R.measure(pr.passes[i]);
+      }
+    }
+    if (o->dtype == OWQS_C128 && (o->flags & OWQS_RUN_DOUBLE_FLOAT)) mark_double_float(R.items);
+    return R.err == OWQS_OK;
+  };
+  Runner R(p, *rc, o->dtype, o->mode, s);
+  if (!build(R)) return set_error(OWQS_ERR_UNSUPPORTED, "checked launches: a run without factor joins");
+  if (o->io == OWQS_IO_HOST && psi_in) {
+    cudaError_t e = cudaMemcpyAsync(rc->in_stage, psi_in, pr.in_elems * pr.amp, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "input copy");
+  }
+  const size_t K = p.meas_qubit.size();
+  std::vector<uint32_t> kpos;  // execution position -> K-index
+  for (const PassDesc& d : pr.passes)
+    if (d.kind == 0) kpos.push_back(d.meas_k);
+  std::vector<char> decided(std::max<size_t>(K, 1), 0);
+  std::vector<double> slot(K + 2, 0.0);
+  uint32_t relaunches = 0, checks = 0;
+  size_t mi0 = 0;  // execution position of the next launch's first measurement
+  for (size_t pos = 0; pos < R.items.size();) {
+    st = R.launch(R.items[pos], s);
+    if (st != OWQS_OK) return st;
+    const size_t cnt = (size_t)R.items[pos].L.meas;
+    if (cnt == 0) {
+      ++pos;
+      continue;
+    }
+    // slots mi0 (the value before this launch) .. mi0 + cnt
+    cudaError_t e = cudaMemcpyAsync(slot.data() + mi0, rc->norms + mi0, sizeof(double) * (cnt + 1),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "reading probabilities");
+    ++checks;
+    bool corrected = false;
+    for (size_t j = 0; j < cnt; ++j) {
+      const size_t mi = mi0 + j;
+      const uint32_t k = kpos[mi];
+      if (decided[k]) continue;
+      // later measurements of a group hold the running product of its probabilities
+      double pv = slot[mi + 1];
+      if (j > 0) pv = slot[mi] > 0.0 ? pv / slot[mi] : 0.0;
+      const double p0 = oc[k] ? 1.0 - pv : pv;
+      const uint8_t drawn = u[k] <= p0 ? 0 : 1;
+      decided[k] = 1;
+      if (drawn != oc[k]) {
+        oc[k] = drawn;
+        corrected = true;
+        break;
+      }
+    }
+    if (!corrected) {
+      mi0 += cnt;
+      ++pos;
+      continue;
+    }
+    // recompile under the corrected outcomes; the launches are the same, on
+    // the same buffers, with other signs and phases
+    ++relaunches;
+    pr.passes.clear();
+    FixedSource src(p, oc.data());
+    st = compile_schedule(p, o->mode, src, pr.passes);
+    if (st != OWQS_OK) return st;
+    Runner R2(p, *rc, o->dtype, o->mode, s);
+    if (!build(R2) || !same_launches(R.items, R2.items))
+      return set_error(OWQS_ERR_UNSUPPORTED, "checked launches: the recompiled schedule has other launches");
+    R.items.swap(R2.items);
+    R.in_group.swap(R2.in_group);
+  }
+  rc->last_launches = (uint32_t)R.items.size();
+  rc->last_relaunches = relaunches;
+  rc->last_checks = checks;
+  if (o->io == OWQS_IO_HOST) {
+    cudaError_t e = cudaMemcpyAsync(psi_out, rc->out_stage, pr.out_elems * pr.amp, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "output copy");
+  }
+  std::vector<int> outcome_of_pass;
+  for (const PassDesc& d : pr.passes)
+    if (d.kind == 0) outcome_of_pass.push_back(d.outcome);
+  return finish(p, o, rc, pr, s, outcomes, probs, outcome_of_pass, pr.in_dev != nullptr, 0, nullptr, R.in_group);
+}
+
 // Sampled outcomes as a forced run.
 //
 // EOWQS (Section 4.5): a pattern with a gflow is strongly deterministic, so
@@ -1294,9 +1446,11 @@ static owqs_status run_core(Pattern& p, const owqs_run_opts* o, const void* psi_
 // have taken the same branch, so the result is that draw's.  On a pattern
 // with a gflow every prob_0 is 1/2 (Section 4.5) and the guess holds unless
 // a draw lies within a tie margin of 1/2 (1e-6 for complex64, 1e-12 for
-// complex128: the two ways of computing prob_0 differ by rounding); otherwise
-// (or on a guessed branch of probability 0) the run is repeated one
-// measurement at a time.
+// complex128: the two ways of computing prob_0 differ by rounding).  A
+// pattern without a gflow skips this whole-run guess.  Otherwise (and on a
+// guessed branch of probability 0) the run takes checked launches
+// (sample_checked) where the measure passes allow it, else one measurement
+// at a time.
 //
 // Any other policy or mode, and sampling with OWQS_RUN_HOST_SAMPLING or
 // OWQS_RUN_SEQUENTIAL_SAMPLING, goes straight to run_core.
@@ -1306,10 +1460,20 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
                             double* frob2 = nullptr, const ProductInput* prod = nullptr,
                             uint32_t* prof_meas = nullptr) {
   const bool eowqs = o && o->mode == OWQS_MODE_EOWQS;
+  // the path of a one-at-a-time draw (run_core's sampled branch)
+  const uint32_t one_at_a_time = o && !(o->flags & OWQS_RUN_HOST_SAMPLING) && masks_outcome_free(p)
+                                     ? OWQS_SAMPLE_ONE_AT_A_TIME
+                                     : OWQS_SAMPLE_HOST;
   if (!o || o->policy != OWQS_OUTCOME_SAMPLED || prod || vdiag ||
-      (!eowqs && (prof_ms || !p.deps_ok || (o->flags & (OWQS_RUN_HOST_SAMPLING | OWQS_RUN_SEQUENTIAL_SAMPLING)))))
+      (!eowqs && (prof_ms || !p.deps_ok || (o->flags & (OWQS_RUN_HOST_SAMPLING | OWQS_RUN_SEQUENTIAL_SAMPLING))))) {
+    RunCache* rc0 = nullptr;
+    if (o && o->policy == OWQS_OUTCOME_SAMPLED && !prod && !vdiag && !prof_ms && get_cache(p, rc0) == OWQS_OK) {
+      rc0->last_sample_path = one_at_a_time;
+      rc0->last_guessed = rc0->last_relaunches = rc0->last_checks = 0;
+    }
     return run_core(p, o, psi_in, psi_out, outcomes, probs, prof_ms, prof_bytes, prof_kind, prof_cap, prof_n,
                     vdiag, frob2, prod, prof_meas);
+  }
   const size_t K = p.meas_qubit.size();
   std::vector<uint8_t> drawn(std::max<size_t>(K, 1), 0);
   std::vector<double> u(std::max<size_t>(K, 1), 0.0);
@@ -1324,8 +1488,30 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
   owqs_run_opts fo = *o;
   fo.policy = OWQS_OUTCOME_FORCED;
   std::vector<double> pk(std::max<size_t>(K, 1), 0.0);
-  owqs_status st = run_core(p, &fo, psi_in, psi_out, drawn.data(), pk.data(), prof_ms, prof_bytes, prof_kind,
-                            prof_cap, prof_n, vdiag, frob2, prod, prof_meas);
+  const bool checkable = !eowqs && masks_outcome_free(p);
+  RunCache* rc = nullptr;
+  owqs_status st = get_cache(p, rc);
+  if (st != OWQS_OK) return st;
+  auto checked = [&]() {
+    std::vector<uint8_t> oc(std::max<size_t>(K, 1), 0);
+    for (size_t k = 0; k < K; ++k) oc[k] = u[k] <= 0.5 ? 0 : 1;
+    owqs_status cs = sample_checked(p, o, psi_in, psi_out, outcomes, probs, u, oc);
+    if (cs == OWQS_ERR_UNSUPPORTED) {  // one measurement at a time
+      clear_error();
+      cs = run_core(p, o, psi_in, psi_out, outcomes, probs, prof_ms, prof_bytes, prof_kind, prof_cap, prof_n, vdiag,
+                    frob2, prod, prof_meas);
+      rc->last_sample_path = one_at_a_time;
+    } else {
+      rc->last_sample_path = OWQS_SAMPLE_CHECKED_LAUNCHES;
+    }
+    return cs;
+  };
+  rc->last_guessed = rc->last_relaunches = rc->last_checks = 0;
+  if (checkable && !has_gflow(p)) return checked();
+  rc->last_sample_path = eowqs ? OWQS_SAMPLE_DRAWN_FIRST : OWQS_SAMPLE_GUESS_KEPT;
+  rc->last_guessed = eowqs ? 0 : 1;
+  st = run_core(p, &fo, psi_in, psi_out, drawn.data(), pk.data(), prof_ms, prof_bytes, prof_kind, prof_cap, prof_n,
+                vdiag, frob2, prod, prof_meas);
   bool kept = st == OWQS_OK;
   if (!eowqs) {
     // The guessed run computes prob_0 as 1 - prob_1 where it guessed 1, and
@@ -1339,6 +1525,8 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
     }
     if (!kept && (st == OWQS_OK || st == OWQS_ERR_IMPOSSIBLE_BRANCH)) {
       clear_error();
+      if (checkable) return checked();
+      rc->last_sample_path = one_at_a_time;
       return run_core(p, o, psi_in, psi_out, outcomes, probs, prof_ms, prof_bytes, prof_kind, prof_cap, prof_n,
                       vdiag, frob2, prod, prof_meas);
     }
@@ -1415,6 +1603,20 @@ owqs_status owqs_run_product(owqs_pattern* h, const owqs_run_opts* o, uint32_t n
     return set_error(OWQS_ERR_NOT_DETERMINISTIC, "EOWQS: the open graph has no gflow (Section 4.5)");
   return run_impl(h->p, o, nullptr, psi_out, outcomes, probs, nullptr, nullptr, nullptr, 0, nullptr, 0, nullptr,
                   &prod);
+}
+
+owqs_status owqs_last_sample_info(const owqs_pattern* h, owqs_sample_info* info) {
+  clear_error();
+  if (!h || !info) return set_error(OWQS_ERR_ARG, "NULL argument");
+  std::memset(info, 0, sizeof(*info));
+  const RunCache* rc = h->p.cache.get();
+  if (rc) {
+    info->path = rc->last_sample_path;
+    info->guessed = rc->last_guessed;
+    info->checks = rc->last_checks;
+    info->relaunches = rc->last_relaunches;
+  }
+  return OWQS_OK;
 }
 
 owqs_status owqs_test_grid_cap(uint32_t blocks) {

@@ -76,6 +76,14 @@ class owqs_memory_plan(C.Structure):
                 ("substate_work", C.c_double), ("one_array_work", C.c_double)]
 
 
+class owqs_sample_info(C.Structure):
+    _fields_ = [("path", C.c_uint32), ("guessed", C.c_uint32), ("checks", C.c_uint32), ("relaunches", C.c_uint32)]
+
+
+SAMPLE_PATH = {0: "none", 1: "drawn_first", 2: "guess_kept", 3: "checked_launches", 4: "one_at_a_time",
+               5: "host"}
+
+
 class owqs_batch_item(C.Structure):
     _fields_ = [("pattern", C.c_void_p), ("outcomes", C.POINTER(C.c_uint8)), ("psi_in", C.c_void_p),
                 ("out", C.c_void_p), ("ref", C.c_int32), ("pad_", C.c_uint32)]
@@ -123,6 +131,7 @@ EXPORTS = {
     "owqs_get_index_map": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_int32)]),
     "owqs_plan_memory": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.POINTER(C.c_uint8),
                                    C.c_void_p]),
+    "owqs_last_sample_info": (C.c_int, [C.c_void_p, C.POINTER(owqs_sample_info)]),
     "owqs_describe_groups": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.POINTER(C.c_uint8),
                                        C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                        C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32)]),
@@ -352,6 +361,15 @@ class Handle:
         _check(library().owqs_plan_memory(self._h, DTYPE[dtype], MODE[mode], int(real_input), oc, C.byref(plan)))
         return {f: getattr(plan, f) for f, _ in owqs_memory_plan._fields_}
 
+    def last_sample_info(self):
+        """How the last sampled run was carried out: path ("guess_kept",
+        "checked_launches", "one_at_a_time", ...), whether a whole-run guess
+        ran first, host checks and relaunches of checked launches."""
+        info = owqs_sample_info()
+        _check(library().owqs_last_sample_info(self._h, C.byref(info)))
+        return {"path": SAMPLE_PATH.get(info.path, str(info.path)), "guessed": bool(info.guessed),
+                "checks": info.checks, "relaunches": info.relaunches}
+
     def describe_groups(self, outcomes=None, *, dtype: str = "c64", mode: str = "owqs", real_input: bool = False):
         """The pass groups a run would launch (host only): list of dicts with
         the register qubits m, the slot sequence, the input width n_in and
@@ -499,7 +517,7 @@ class Handle:
         return out, oc[: self.K].copy(), probs[: self.K].copy(), st
 
     def run_host(self, psi_in: Optional[np.ndarray], out: np.ndarray, *, dtype: str = "c64",
-                 mode: str = "owqs", policy: str = "forced", outcomes=None, stream=None,
+                 mode: str = "owqs", policy: str = "forced", outcomes=None, seed: int = 0, stream=None,
                  use_graph: bool = True):
         """Run with host vectors; the library copies them in and out."""
         import torch
@@ -509,7 +527,7 @@ class Handle:
             oc[: self.K] = np.asarray(outcomes, dtype=np.uint8)[: self.K]
         probs = np.zeros(max(1, self.K), dtype=np.float64)
         s = stream if stream is not None else torch.cuda.current_stream()
-        opts = owqs_run_opts(DTYPE[dtype], MODE[mode], POLICY[policy], 1, 0, C.c_void_p(s.cuda_stream),
+        opts = owqs_run_opts(DTYPE[dtype], MODE[mode], POLICY[policy], 1, seed, C.c_void_p(s.cuda_stream),
                              int(use_graph), 0)
         pin = 0 if psi_in is None else _host_ptr(psi_in)
         _check(library().owqs_run(self._h, C.byref(opts), C.c_void_p(pin), C.c_void_p(_host_ptr(out)),

@@ -68,3 +68,59 @@ def test_checked_guess_reproduces_the_one_at_a_time_draw(owqs):
         if p.name.startswith("flow"):
             assert all(abs(v - 0.5) < 1e-12 for v in probs)
     assert kept_n >= 60 and failed_n >= 5, (kept_n, failed_n)
+
+
+def test_checked_launches_reproduce_the_one_at_a_time_draw(owqs):
+    """Checked launches (patterns without a gflow): run the forced schedule
+    of the current outcome vector, take the measurements in execution order,
+    and at the first draw u_k <= prob_0 that decides the other outcome
+    correct it and run again from that measurement (its input is the same,
+    since every earlier outcome is unchanged).  The outcomes end equal to the
+    oracle's one-at-a-time draw, and the corrections are exactly the
+    measurements whose drawn outcome differs from its guess u_k > 1/2, each
+    corrected once."""
+    from owqs_inputs import workloads
+    pats = [(w.pattern, w.psi_in) for w in (workloads.measured_inputs(6), workloads.brickwork_readout(3, 4, kept=1,
+                                                                                                  with_input=True))]
+    pats += [(p, None) for p in _patterns()[-2:]]
+    corrected_total = 0
+    for p, psi in pats:
+        h = owqs.load(p)
+        if p.is_standard():
+            h.reorder()
+        order = h.order()
+        load = p.measured()
+        if psi is None:
+            psi = random_state(SplitMix64(4300 + p.nqubits), len(p.inputs))
+        op_cmds = p
+        if p.is_standard():
+            from oracle import proa
+            op_cmds = proa.reorder_commands(p, order)
+        for seed in range(12):
+            stream = SplitMix64(seed)
+            u = {q: stream.uniform() for q in order}
+            oc = {q: 0 if u[q] <= 0.5 else 1 for q in order}
+            guess = dict(oc)
+            decided = set()
+            corrections = 0
+            while True:
+                _, probs = pass_emulator.emulate(h.describe_passes([oc[q] for q in load]), psi)
+                bad = None
+                for q, pv in zip(order, probs):
+                    if q in decided:
+                        continue
+                    decided.add(q)
+                    p0 = pv if oc[q] == 0 else 1.0 - pv
+                    drawn = 0 if u[q] <= p0 else 1
+                    if drawn != oc[q]:
+                        bad = q
+                        oc[q] = drawn
+                        break
+                if bad is None:
+                    break
+                corrections += 1
+            ref = substate.run(op_cmds, psi, policy="sampled", seed=seed)
+            assert all(ref.outcomes[q] == oc[q] for q in order), (p.name, seed)
+            assert corrections == sum(ref.outcomes[q] != guess[q] for q in order), (p.name, seed)
+            corrected_total += corrections
+    assert corrected_total >= 10
