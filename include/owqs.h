@@ -481,6 +481,9 @@ typedef struct {
                                global memory (up to 2^18 amplitudes per array);
                                hbm_items counts the items wider still, which
                                run through the pass kernels of owqs_run         */
+  float compile_ms;         /* host time compiling the items' pass lists (on
+                               up to 32 host threads) and building the tables   */
+  float call_ms;            /* host time of the whole call, device work included */
 } owqs_batch_info;
 
 owqs_status owqs_run_batch(const owqs_batch_item* items, uint32_t n, const owqs_batch_opts* opts,
@@ -544,10 +547,13 @@ typedef struct {
 owqs_status owqs_plan_memory(const owqs_pattern* p, uint32_t dtype, uint32_t mode, uint32_t real_input,
                             const uint8_t* outcomes, owqs_memory_plan* plan);
 
-/* The pass groups owqs_run would launch (host only, no GPU needed), in/* The pass groups owqs_run would launch (host only, no GPU needed), in
+/* The pass groups owqs_run would launch (host only, no GPU needed), in
  * launch order; for group i (i < *ngroups, at most cap): regs[i] the
  * register qubits M, slots[i] its register-slot sequence (bits 24-27 the
- * number of passes k, bits 2j and 2j+1 the slot that pass j measures),
+ * number of passes k, bits 2j and 2j+1 the slot that pass j measures, bit
+ * 30 set when every pass measures a qubit joined by E to the qubit that
+ * pass prepares, so that each probability is exactly 1/2 and the group sums
+ * no norms),
  * n_in[i] the live width it reads and specialised[i] 1 when a kernel
  * compiled for exactly that sequence runs it (complex64 groups reading a
  * materialised array), 0 when the slot-dispatching kernel does.  Arguments

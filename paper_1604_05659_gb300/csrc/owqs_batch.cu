@@ -278,6 +278,7 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
                              owqs_batch_info* info) {
   if (!o || (n && !items)) return set_error(OWQS_ERR_ARG, "NULL argument");
   if (o->dtype > OWQS_C128) return set_error(OWQS_ERR_ARG, "bad dtype");
+  const auto t_call = std::chrono::steady_clock::now();
   const int dtype = (int)o->dtype;
   const size_t amp = dtype == OWQS_C64 ? 8 : 16;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(o->stream);
@@ -292,25 +293,36 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const size_t smem_limit = (size_t)std::max(0, max_smem - 1024);
 
-  // compile every item
+  const auto t_compile = std::chrono::steady_clock::now();
+  // compile every item: items in contiguous slices on host threads, each
+  // into its own tables, then concatenated in item order (offsets shifted)
   std::vector<BItem> bitems(n);
   std::vector<BPass> bpasses;
   std::vector<BQ> bqs;
   std::vector<int32_t> bperms;
   std::vector<char> on_chip(n, 0), in_global(n, 0);
-  std::string sig = std::to_string(dtype) + ":";
   for (uint32_t i = 0; i < n; ++i) {
     const owqs_batch_item& it = items[i];
     if (!it.pattern || !it.out) return set_error(OWQS_ERR_ARG, "batch item " + std::to_string(i) + ": NULL");
     if (((uintptr_t)it.out % 16) || ((uintptr_t)it.psi_in % 16))
       return set_error(OWQS_ERR_ARG, "batch item " + std::to_string(i) + ": vectors must be 16-byte aligned");
+  }
+  struct Slice {
+    std::vector<BPass> passes;
+    std::vector<BQ> qs;
+    std::vector<int32_t> perms;
+    owqs_status st = OWQS_OK;
+    std::string msg;
+  };
+  auto compile_item = [&](uint32_t i, Slice& sl) -> owqs_status {
+    const owqs_batch_item& it = items[i];
     const Pattern& p = it.pattern->p;
     ZeroOrBits src(p, it.outcomes);
     std::vector<PassDesc> pd;
     owqs_status st = compile_schedule(p, OWQS_MODE_EOWQS, src, pd);
     if (st != OWQS_OK) return st;
     BItem& b = bitems[i];
-    b.pass_off = (uint32_t)bpasses.size();
+    b.pass_off = (uint32_t)sl.passes.size();
     b.npass = (uint32_t)pd.size();
     b.nin = (int32_t)p.inputs.size();
     b.nout = (int32_t)p.outputs.size();
@@ -329,10 +341,10 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
       bp.xmask = d.xmask;
       bp.zmask = d.zmask;
       bp.c0 = d.c0;
-      bp.q_off = (uint32_t)bqs.size();
+      bp.q_off = (uint32_t)sl.qs.size();
       // quadratic terms: one lower endpoint per edge
-      for (auto& ed : d.edges) bqs.push_back(BQ{1ull << ed.second, ed.first, 0});
-      bp.nq = (uint32_t)(bqs.size() - bp.q_off);
+      for (auto& ed : d.edges) sl.qs.push_back(BQ{1ull << ed.second, ed.first, 0});
+      bp.nq = (uint32_t)(sl.qs.size() - bp.q_off);
       if (d.kind == 0 && d.xmask == 0 && d.n_in + d.r <= 24) {
         uint32_t a = 0;
         bool star = true;
@@ -347,18 +359,69 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
           bp.zb = (uint32_t)((d.zmask >> d.b) & 1u);
         }
       }
-      bp.perm_off = (uint32_t)bperms.size();
-      for (int q : d.perm) bperms.push_back(q);
+      bp.perm_off = (uint32_t)sl.perms.size();
+      for (int q : d.perm) sl.perms.push_back(q);
       bp.w1re = d.w1re;
       bp.w1im = d.w1im;
       bp.scale = d.scale;
-      bpasses.push_back(bp);
+      sl.passes.push_back(bp);
     }
     b.wmax = wmax;
     on_chip[i] = wmax <= 16 && 2 * ((size_t)1 << wmax) * amp <= smem_limit && b.nin <= 20;
     in_global[i] = !on_chip[i] && wmax <= kBatchGlobalLog && b.nin <= 20;
-    sig += std::to_string(wmax) + "/" + std::to_string(b.nin) + "/" + std::to_string(it.psi_in ? 1 : 0) + ",";
+    return OWQS_OK;
+  };
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const uint32_t nslices = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>({hw, 32u, (n + 255) / 256}));
+  std::vector<Slice> slices(nslices);
+  std::vector<uint32_t> first(nslices + 1);
+  for (uint32_t t = 0; t <= nslices; ++t) first[t] = (uint32_t)((uint64_t)n * t / nslices);
+  auto run_slice = [&](uint32_t t) {
+    Slice& sl = slices[t];
+    for (uint32_t i = first[t]; i < first[t + 1]; ++i) {
+      sl.st = compile_item(i, sl);
+      if (sl.st != OWQS_OK) {
+        sl.msg = owqs_last_error();
+        return;
+      }
+    }
+  };
+  if (nslices == 1) {
+    run_slice(0);
+  } else {
+    std::vector<std::thread> pool;
+    for (uint32_t t = 0; t < nslices; ++t) pool.emplace_back(run_slice, t);
+    for (auto& th : pool) th.join();
   }
+  size_t np = 0, nq = 0, nm = 0;
+  for (const Slice& sl : slices) {
+    if (sl.st != OWQS_OK) return set_error(sl.st, sl.msg);
+    np += sl.passes.size();
+    nq += sl.qs.size();
+    nm += sl.perms.size();
+  }
+  bpasses.reserve(np);
+  bqs.reserve(nq);
+  bperms.reserve(nm);
+  for (uint32_t t = 0; t < nslices; ++t) {
+    Slice& sl = slices[t];
+    const uint32_t po = (uint32_t)bpasses.size(), qo = (uint32_t)bqs.size(), mo = (uint32_t)bperms.size();
+    for (uint32_t i = first[t]; i < first[t + 1]; ++i) bitems[i].pass_off += po;
+    for (BPass& bp : sl.passes) {
+      bp.q_off += qo;
+      bp.perm_off += mo;
+    }
+    bpasses.insert(bpasses.end(), sl.passes.begin(), sl.passes.end());
+    bqs.insert(bqs.end(), sl.qs.begin(), sl.qs.end());
+    bperms.insert(bperms.end(), sl.perms.begin(), sl.perms.end());
+    std::vector<BPass>().swap(sl.passes);
+  }
+  std::string sig = std::to_string(dtype) + ":";
+  for (uint32_t i = 0; i < n; ++i)
+    sig += std::to_string(bitems[i].wmax) + "/" + std::to_string(bitems[i].nin) + "/" +
+           std::to_string(items[i].psi_in ? 1 : 0) + ",";
+  const float compile_ms =
+      std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t_compile).count();
 
   // shared-memory budget per CTA: tuned once per batch signature by timing
   // the candidates, unless the caller fixes the column block
@@ -797,6 +860,8 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
     info->smem_bytes_per_cta = (uint32_t)(2 * (size_t)cap * amp);
     info->launches = launches;
     info->global_items = global_items;
+    info->compile_ms = compile_ms;
+    info->call_ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t_call).count();
   }
   return OWQS_OK;
 }

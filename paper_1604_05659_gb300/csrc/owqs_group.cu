@@ -9,7 +9,7 @@ namespace owqs {
 static_assert(kGroupSeqSlices == 4, "launch_group dispatches four slices");
 
 uint32_t group_sequence_code(const GroupParams& G) {
-  uint32_t c = ((uint32_t)G.m << 28) | ((uint32_t)G.k << 24);
+  uint32_t c = ((uint32_t)(G.half ? 1 : 0) << 30) | ((uint32_t)G.m << 28) | ((uint32_t)G.k << 24);
   for (int j = 0; j < G.k; ++j) c |= ((uint32_t)G.pass[j].slot & 3u) << (2 * j);
   return c;
 }
@@ -50,10 +50,26 @@ cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s) {
     }
   }
   if (G.df) return launch_group_df(G, G.df_in != 0, G.df_out != 0, s);
+  // the last pass's squared norm only where every probability is exactly 1/2
+  // or none is needed (EOWQS)
+  if (G.half || G.norm_out < 0) {
+    switch (G.m) {
+      case 1: return v ? launch_group_t<1, 11>(k_group64<1, true, false>, G, s)
+                       : launch_group_t<1, 11>(k_group64<1, false, false>, G, s);
+      case 2: return v ? launch_group_t<2, 11>(k_group64<2, true, false>, G, s)
+                       : launch_group_t<2, 11>(k_group64<2, false, false>, G, s);
+      case 3: return v ? launch_group_t<3, 11>(k_group64<3, true, false>, G, s)
+                       : launch_group_t<3, 11>(k_group64<3, false, false>, G, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (G.m) {
-    case 1: return v ? launch_group_t<1, 11>(k_group64<1, true>, G, s) : launch_group_t<1, 11>(k_group64<1, false>, G, s);
-    case 2: return v ? launch_group_t<2, 11>(k_group64<2, true>, G, s) : launch_group_t<2, 11>(k_group64<2, false>, G, s);
-    case 3: return v ? launch_group_t<3, 11>(k_group64<3, true>, G, s) : launch_group_t<3, 11>(k_group64<3, false>, G, s);
+    case 1: return v ? launch_group_t<1, 11>(k_group64<1, true, true>, G, s)
+                     : launch_group_t<1, 11>(k_group64<1, false, true>, G, s);
+    case 2: return v ? launch_group_t<2, 11>(k_group64<2, true, true>, G, s)
+                     : launch_group_t<2, 11>(k_group64<2, false, true>, G, s);
+    case 3: return v ? launch_group_t<3, 11>(k_group64<3, true, true>, G, s)
+                     : launch_group_t<3, 11>(k_group64<3, false, true>, G, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -67,7 +83,7 @@ cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s) {
 // FP64 instructions per output and measurement, against eight for a single
 // measure pass (k_fast<double>), which is bound by the FP64 pipe on GB300.
 // ---------------------------------------------------------------------------
-template <int M, int S>
+template <int M, int S, bool NORM>
 __device__ __forceinline__ void group_butterfly64(double2 (&x)[1 << M], const GroupPass& P, double wr, double wi,
                                                   double& nacc) {
 #pragma unroll
@@ -78,14 +94,20 @@ __device__ __forceinline__ void group_butterfly64(double2 (&x)[1 << M], const Gr
     const double vx = fma(wr, x1.x, -wi * x1.y), vy = fma(wr, x1.y, wi * x1.x);
     const double2 y0 = make_double2(fma(P.ctd[g0], vx, x0.x), fma(P.ctd[g0], vy, x0.y));
     const double2 y1 = make_double2(fma(P.ctd[g1], vx, x0.x), fma(P.ctd[g1], vy, x0.y));
-    nacc = fma(y0.x, y0.x, fma(y0.y, y0.y, nacc));
-    nacc = fma(y1.x, y1.x, fma(y1.y, y1.y, nacc));
+    if (NORM) {
+      nacc = fma(y0.x, y0.x, fma(y0.y, y0.y, nacc));
+      nacc = fma(y1.x, y1.x, fma(y1.y, y1.y, nacc));
+    }
     x[g0] = y0;
     x[g1] = y1;
   }
 }
 
-template <int M, bool VIRT>
+// NORM = false: every probability of the group is exactly 1/2
+// (GroupParams::half) or the run needs none: only the last pass's squared
+// norm is summed (the next launch divides by it); the other slots get the
+// exact products 2^-(j+1)
+template <int M, bool VIRT, bool NORM>
 __global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G) {
   if (G.stall_limit > 0) {
     stall_and_give_up(G.stall_limit, G.errflag);
@@ -209,15 +231,26 @@ __global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) x[c] = virt ? make_double2(G.vconst, 0.0) : buf[G.cbase[c] + spread[q]];
       const uint32_t b = sw ^ lowbits[q];
+      // NORM = false: the passes before the last sum no norm; the last one
+      // sums its output's squared norm into acc[0]
+      const int kl = NORM ? k : k - 1;
 #pragma unroll
       for (int j = 0; j < kGroupMax; ++j) {
-        if (j >= k) break;
+        if (j >= kl) break;
         const GroupPass& P = G.pass[j];
         const bool rho = (b >> (2 * j + 1)) & 1u;
         const double wr = rho ? -P.wre : P.wre, wi = rho ? -P.wim : P.wim;
-        if (M == 1 || P.slot == 0) group_butterfly64<M, 0>(x, P, wr, wi, acc[j]);
-        else if (M == 2 || P.slot == 1) group_butterfly64<M, (M > 1 ? 1 : 0)>(x, P, wr, wi, acc[j]);
-        else group_butterfly64<M, (M > 2 ? 2 : 0)>(x, P, wr, wi, acc[j]);
+        if (M == 1 || P.slot == 0) group_butterfly64<M, 0, NORM>(x, P, wr, wi, acc[j]);
+        else if (M == 2 || P.slot == 1) group_butterfly64<M, (M > 1 ? 1 : 0), NORM>(x, P, wr, wi, acc[j]);
+        else group_butterfly64<M, (M > 2 ? 2 : 0), NORM>(x, P, wr, wi, acc[j]);
+      }
+      if (!NORM) {
+        const GroupPass& P = G.pass[k - 1];
+        const bool rho = (b >> (2 * (k - 1) + 1)) & 1u;
+        const double wr = rho ? -P.wre : P.wre, wi = rho ? -P.wim : P.wim;
+        if (M == 1 || P.slot == 0) group_butterfly64<M, 0, true>(x, P, wr, wi, acc[0]);
+        else if (M == 2 || P.slot == 1) group_butterfly64<M, (M > 1 ? 1 : 0), true>(x, P, wr, wi, acc[0]);
+        else group_butterfly64<M, (M > 2 ? 2 : 0), true>(x, P, wr, wi, acc[0]);
       }
       const double f = (__popc(b & evenk) & 1) ? -cprev : cprev;
 #pragma unroll
@@ -245,6 +278,16 @@ __global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G) {
         mbar_wait_bounded(&full[j % NS], (unsigned)((j / NS) & 1u));
     }
     __syncthreads();
+    return;
+  }
+  if (!NORM) {
+    if (G.norm_out >= 0) {
+      // slot j < k - 1: 2^-(j+1); slot k - 1: the output's summed squared norm
+      if (blockIdx.x == 0 && threadIdx.x < k - 1)
+        G.norms[G.norm_out + threadIdx.x] = ldexp(1.0, -(int)(threadIdx.x + 1));
+      const double a1[1] = {cprev * cprev * G.nscale[k - 1] * acc[0]};
+      reduce_to_slots<1>(a1, G.partials, G.counter, G.norms, G.norm_out + k - 1, 1);
+    }
     return;
   }
   if (G.norm_out >= 0) {

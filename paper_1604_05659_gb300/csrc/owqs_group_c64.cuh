@@ -17,12 +17,13 @@ namespace owqs {
 // VIRT: the group reads the virtual |+> input (G.in == nullptr); a separate
 // instantiation keeps the array-reading kernel free of the test.  SEQ != 0:
 // the group's register-slot sequence fixed at compile time (bits 24-27 the
-// number of passes k, bits 2j and 2j+1 the slot pass j measures); SEQ = 0
-// reads the slots from the parameter block and dispatches on them per pass.
+// number of passes k, bits 2j and 2j+1 the slot pass j measures, bit 30:
+// every probability is exactly 1/2 and no norm is summed); SEQ = 0 reads the
+// slots from the parameter block and dispatches on them per pass.
 template <int M, bool VIRT, uint32_t SEQ = 0>
 __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G);
 
-template <int M, bool VIRT>
+template <int M, bool VIRT, bool NORM>
 __global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G);
 
 // a tile of 2^(TB-M) free indices x 2^M configurations: TB = 9 for complex64
@@ -161,7 +162,7 @@ __device__ __forceinline__ void group_flush_norms(float (&s)[kGroupMax], double 
   for (int j = 0; j < kGroupMax; ++j) s[j] = 0.f;
 }
 
-template <int M, int S>
+template <int M, int S, bool NORM>
 __device__ __forceinline__ void group_butterfly(float2 (&x)[1 << M], const GroupPass& P, float wr, float wi,
                                                 float2& nacc, bool first) {
 #pragma unroll
@@ -173,8 +174,10 @@ __device__ __forceinline__ void group_butterfly(float2 (&x)[1 << M], const Group
     const float2 y0 = make_float2(fmaf(P.ct[g0], v.x, x0.x), fmaf(P.ct[g0], v.y, x0.y));
     const float2 y1 = make_float2(fmaf(P.ct[g1], v.x, x0.x), fmaf(P.ct[g1], v.y, x0.y));
     // the pass's first product starts its accumulator (no zeroing)
-    nacc = (first && h == 0) ? __fmul2_rn(y0, y0) : __ffma2_rn(y0, y0, nacc);
-    nacc = __ffma2_rn(y1, y1, nacc);
+    if (NORM) {
+      nacc = (first && h == 0) ? __fmul2_rn(y0, y0) : __ffma2_rn(y0, y0, nacc);
+      nacc = __ffma2_rn(y1, y1, nacc);
+    }
     x[g0] = y0;
     x[g1] = y1;
   }
@@ -182,12 +185,12 @@ __device__ __forceinline__ void group_butterfly(float2 (&x)[1 << M], const Group
 
 // r0, r1: the two elements' sign bits for this pass, at bit 31 (one XOR
 // gives +-w)
-template <int M, int S>
+template <int M, int S, bool NORM>
 __device__ __forceinline__ void group_pass2(float2 (&x)[2][1 << M], const GroupPass& P, uint32_t r0, uint32_t r1,
                                             float2& nacc) {
   const uint32_t ur = __float_as_uint(P.fwr), ui = __float_as_uint(P.fwi);
-  group_butterfly<M, S>(x[0], P, __uint_as_float(ur ^ r0), __uint_as_float(ui ^ r0), nacc, true);
-  group_butterfly<M, S>(x[1], P, __uint_as_float(ur ^ r1), __uint_as_float(ui ^ r1), nacc, false);
+  group_butterfly<M, S, NORM>(x[0], P, __uint_as_float(ur ^ r0), __uint_as_float(ui ^ r0), nacc, true);
+  group_butterfly<M, S, NORM>(x[1], P, __uint_as_float(ur ^ r1), __uint_as_float(ui ^ r1), nacc, false);
 }
 
 template <int M, bool VIRT, uint32_t SEQ>
@@ -227,6 +230,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
   const uint64_t step = (uint64_t)gridDim.x * NWARP;
   const uint64_t mine = gw < tiles ? (tiles - gw + step - 1) / step : 0;
   const int k = SEQ ? (int)((SEQ >> 24) & 15u) : G.k;
+  // a sequence kernel with bit 30: every probability of the group is exactly
+  // 1/2 (GroupParams::half), so only the last pass's squared norm is summed:
+  // the next launch divides by it, so that the rounding in the array's norm
+  // does not build up from group to group
+  constexpr bool NORM = !(SEQ != 0 && ((SEQ >> 30) & 1u));
   uint32_t lowbits[EPT], spread[EPT];
 #pragma unroll
   for (int q = 0; q < EPT; ++q) {
@@ -296,6 +304,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
 #pragma unroll
   for (int j = 0; j < kGroupMax; ++j) s[j] = 0.f;
   double dacc[3] = {0.0, 0.0, 0.0};
+  float hs = 0.f;    // half groups: the last pass's squared norm over kNormTiles tiles
+  double hd = 0.0;   // and its FP64 sum
   uint64_t issued = mine < (uint64_t)NS ? mine : (uint64_t)NS;
   for (uint64_t i = 0; i < mine; ++i) {
     const int st = (int)(i % NS);
@@ -341,11 +351,18 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
         const uint32_t r0 = (b0 << (31 - j)) & 0x80000000u, r1 = (b1 << (31 - j)) & 0x80000000u;
         // a compile-time slot leaves one code variant per pass
         const int slot = SEQ ? (int)((SEQ >> (2 * j)) & 3u) : P.slot;
-        float2 acc;
-        if (M == 1 || slot == 0) group_pass2<M, 0>(x, P, r0, r1, acc);
-        else if (M == 2 || slot == 1) group_pass2<M, (M > 1 ? 1 : 0)>(x, P, r0, r1, acc);
-        else group_pass2<M, (M > 2 ? 2 : 0)>(x, P, r0, r1, acc);
-        s[j] += acc.x + acc.y;
+        float2 acc = make_float2(0.f, 0.f);
+        if (NORM || j == k - 1) {
+          if (M == 1 || slot == 0) group_pass2<M, 0, true>(x, P, r0, r1, acc);
+          else if (M == 2 || slot == 1) group_pass2<M, (M > 1 ? 1 : 0), true>(x, P, r0, r1, acc);
+          else group_pass2<M, (M > 2 ? 2 : 0), true>(x, P, r0, r1, acc);
+        } else {
+          if (M == 1 || slot == 0) group_pass2<M, 0, false>(x, P, r0, r1, acc);
+          else if (M == 2 || slot == 1) group_pass2<M, (M > 1 ? 1 : 0), false>(x, P, r0, r1, acc);
+          else group_pass2<M, (M > 2 ? 2 : 0), false>(x, P, r0, r1, acc);
+        }
+        if (NORM) s[j] += acc.x + acc.y;
+        else if (j == k - 1) hs += acc.x + acc.y;
       }
       const float f0 = __uint_as_float(__float_as_uint(fprev) ^ (b0 & 0x80000000u));
       const float f1 = __uint_as_float(__float_as_uint(fprev) ^ (b1 & 0x80000000u));
@@ -357,7 +374,14 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
             make_float4(s0 * x[0][g].x, s0 * x[0][g].y, s1 * x[1][g].x, s1 * x[1][g].y);
       }
     }
-    if ((i % kNormTiles) == kNormTiles - 1) group_flush_norms(s, dacc, lane);
+    if ((i % kNormTiles) == kNormTiles - 1) {
+      if (NORM) {
+        group_flush_norms(s, dacc, lane);
+      } else {
+        hd += (double)hs;
+        hs = 0.f;
+      }
+    }
     // every lane has read the stage: refill it with this warp's tile i + NS
     __syncwarp();
     if (lane == 0 && issued < mine) issue(issued);
@@ -372,6 +396,17 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
         mbar_wait_bounded(&full[j % NS], (unsigned)((j / NS) & 1u));
     }
     __syncthreads();
+    return;
+  }
+  if (!NORM) {
+    if (G.norm_out >= 0) {
+      // slot j < k - 1: the product of the group's first j + 1 probabilities,
+      // 2^-(j+1); slot k - 1: the summed squared norm of the output
+      if (blockIdx.x == 0 && threadIdx.x < k - 1)
+        G.norms[G.norm_out + threadIdx.x] = ldexp(1.0, -(int)(threadIdx.x + 1));
+      const double a1[1] = {cprev * cprev * G.nscale[k - 1] * (hd + (double)hs)};
+      reduce_to_slots<1>(a1, G.partials, G.counter, G.norms, G.norm_out + k - 1, 1);
+    }
     return;
   }
   if (G.norm_out >= 0) {

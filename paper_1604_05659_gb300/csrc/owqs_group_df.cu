@@ -78,7 +78,7 @@ struct CDF {
 // one pass on register slot S: y[g0] = x[g0] + ct[g0] v, y[g1] = x[g0] +
 // ct[g1] v, v = w x[g1] (w already carries the element's sign); the squared
 // norms of the outputs are added to acc
-template <int M, int S>
+template <int M, int S, bool NORM>
 __device__ __forceinline__ void df_pass(CDF (&x)[1 << M], const float (&ct)[1 << M], DF wr, DF wi, DF& acc) {
 #pragma unroll
   for (int h = 0; h < (1 << (M - 1)); ++h) {
@@ -91,10 +91,12 @@ __device__ __forceinline__ void df_pass(CDF (&x)[1 << M], const float (&ct)[1 <<
     const DF c1r = ct[g1] < 0.f ? df_neg(vr) : vr, c1i = ct[g1] < 0.f ? df_neg(vi) : vi;
     const CDF y0{df_add(x0.re, c0r), df_add(x0.im, c0i)};
     const CDF y1{df_add(x0.re, c1r), df_add(x0.im, c1i)};
-    df_acc_sq(acc, y0.re);
-    df_acc_sq(acc, y0.im);
-    df_acc_sq(acc, y1.re);
-    df_acc_sq(acc, y1.im);
+    if (NORM) {
+      df_acc_sq(acc, y0.re);
+      df_acc_sq(acc, y0.im);
+      df_acc_sq(acc, y1.re);
+      df_acc_sq(acc, y1.im);
+    }
     x[g0] = y0;
     x[g1] = y1;
   }
@@ -133,6 +135,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_group_df(const GroupParams G) {
   float4* pw = reinterpret_cast<float4*>(smem + NS * STAGE + 256);
   float* pct = reinterpret_cast<float*>(pw + kGroupMax);
   float2* accs = reinterpret_cast<float2*>(pct + kGroupMax * 8);  // [pass][thread]: double-float sums
+  // every pass's squared norm unless every probability is exactly 1/2
+  // (GroupParams::half) or the run needs none; then only the last pass's (the
+  // next launch divides by it) and the other slots get 2^-(j+1)
+  const bool norm = !G.half && G.norm_out >= 0;
   const double cprev = [&] {
     if (G.norm_in < 0) return 1.0;
     const double nv = G.norms[G.norm_in];
@@ -259,13 +265,20 @@ __global__ void __launch_bounds__(kBlock, 2) k_group_df(const GroupParams G) {
         float ct[NC];
 #pragma unroll
         for (int g = 0; g < NC; ++g) ct[g] = pct[j * 8 + g];
-        const float2 a2 = accs[j * kBlock + threadIdx.x];
-        DF acc{a2.x, a2.y};
         const int slot = (int)((slots >> (2 * j)) & 3u);
-        if (M == 1 || slot == 0) df_pass<M, 0>(x, ct, wr, wi, acc);
-        else if (M == 2 || slot == 1) df_pass<M, (M > 1 ? 1 : 0)>(x, ct, wr, wi, acc);
-        else df_pass<M, (M > 2 ? 2 : 0)>(x, ct, wr, wi, acc);
-        accs[j * kBlock + threadIdx.x] = make_float2(acc.hi, acc.lo);
+        if (norm || j == k - 1) {  // half groups: the last pass's squared norm only
+          const float2 a2 = accs[j * kBlock + threadIdx.x];
+          DF acc{a2.x, a2.y};
+          if (M == 1 || slot == 0) df_pass<M, 0, true>(x, ct, wr, wi, acc);
+          else if (M == 2 || slot == 1) df_pass<M, (M > 1 ? 1 : 0), true>(x, ct, wr, wi, acc);
+          else df_pass<M, (M > 2 ? 2 : 0), true>(x, ct, wr, wi, acc);
+          accs[j * kBlock + threadIdx.x] = make_float2(acc.hi, acc.lo);
+        } else {
+          DF acc{0.f, 0.f};
+          if (M == 1 || slot == 0) df_pass<M, 0, false>(x, ct, wr, wi, acc);
+          else if (M == 2 || slot == 1) df_pass<M, (M > 1 ? 1 : 0), false>(x, ct, wr, wi, acc);
+          else df_pass<M, (M > 2 ? 2 : 0), false>(x, ct, wr, wi, acc);
+        }
       }
       // the element's sign, the previous array's 1/sqrt(N) and the carried
       // scales: exact powers of two and signs times cprev, applied in FP64
@@ -305,6 +318,16 @@ __global__ void __launch_bounds__(kBlock, 2) k_group_df(const GroupParams G) {
         mbar_wait_bounded(&full[j % NS], (unsigned)((j / NS) & 1u));
     }
     __syncthreads();
+    return;
+  }
+  if (!norm) {
+    if (G.norm_out >= 0) {
+      if (blockIdx.x == 0 && threadIdx.x < k - 1)
+        G.norms[G.norm_out + threadIdx.x] = ldexp(1.0, -(int)(threadIdx.x + 1));
+      const float2 sl = accs[(k - 1) * kBlock + threadIdx.x];
+      const double a1[1] = {cprev * cprev * G.nscale[k - 1] * ((double)sl.x + (double)sl.y)};
+      reduce_to_slots<1>(a1, G.partials, G.counter, G.norms, G.norm_out + k - 1, 1);
+    }
     return;
   }
   if (G.norm_out >= 0) {

@@ -290,6 +290,11 @@ struct GroupParams {
   // df_in / df_out: the input / output array holds double-float pairs (the
   // previous / next launch is such a group on the same array), else complex128
   int df, df_in, df_out;
+  // every pass measures a qubit joined by an odd number of E to the qubit the
+  // pass prepares (a fresh |+>): then each probability is exactly 1/2 on any
+  // state (the projection leaves |+>phi0 +- e^{-i a}|->phi1, half of phi's
+  // squared norm), so no norm is summed and the slots get the exact products
+  int half;
   GroupPass pass[kGroupMax];
   uint64_t in_cap, out_cap;  // as PassParams
 };
@@ -300,9 +305,9 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i, int dtype, GroupPa
 cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s);
 // complex128 group in double-float arithmetic (owqs_group_df.cu)
 cudaError_t launch_group_df(const GroupParams& G, bool in_df, bool out_df, cudaStream_t s);
-// the group's register-slot sequence (bits 28-29 m, 24-27 k, 2j and 2j+1 the
-// slot of pass j), and whether a kernel compiled for it exists (complex64,
-// materialised input)
+// the group's register-slot sequence (bit 30 half, bits 28-29 m, 24-27 k, 2j
+// and 2j+1 the slot of pass j), and whether a kernel compiled for it exists
+// (complex64, materialised input)
 uint32_t group_sequence_code(const GroupParams& G);
 bool group_sequence_specialised(const GroupParams& G, int dtype, bool virt_in);
 int group_enabled();  // OWQS_GROUP=0 turns group fusion off

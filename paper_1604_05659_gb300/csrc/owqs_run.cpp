@@ -1763,7 +1763,7 @@ owqs_status owqs_describe_groups(const owqs_pattern* h, uint32_t dtype, uint32_t
       if (kind == LAUNCH_GROUP) {
         if (n < cap) {
           if (regs) regs[n] = (uint32_t)G.m;
-          if (slots) slots[n] = group_sequence_code(G) & 0x0fffffffu;
+          if (slots) slots[n] = group_sequence_code(G) & 0x4fffffffu;
           if (n_in) n_in[n] = (uint32_t)passes[i].n_in;
           // the launch reads the virtual |+> input only while no array exists
           if (specialised) specialised[n] = group_sequence_specialised(G, (int)dtype, !real) ? 1u : 0u;

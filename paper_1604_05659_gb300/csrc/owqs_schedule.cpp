@@ -642,10 +642,13 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupP
   const uint32_t lomask = (1u << G.lt) - 1u;
   uint32_t pend = 0;  // register-diagonal sign mask carried by the scaled register
   double prod = 1.0;
+  G.half = 1;
   for (int j = 0; j < best_k; ++j) {
     const PassDesc& d = passes[i0 + j];
     uint64_t A = 0;
     star_mask(d, &A);
+    // bit n_in of the output index is the qubit this pass prepares
+    if (!((A >> d.n_in) & 1u)) G.half = 0;
     GroupPass& P = G.pass[j];
     const int s = -lv[d.b] - 1;
     P.slot = s;

@@ -38,7 +38,7 @@ def workload_families():
 
 
 def sequence_work(families):
-    """Share of each (m, slots) in the group work of each family (work =
+    """Share of each (m, slots, half) in the group work of each family (work =
     passes x 2^(input width)), summed over the families."""
     from paper_1604_05659_gb300 import owqs
     owqs.library()
@@ -50,15 +50,15 @@ def sequence_work(families):
             h.reorder()
             for real in (False, True):
                 for g in h.describe_groups(wl.outcomes, dtype="c64", real_input=real):
-                    work[(g["m"], g["slots"])] += len(g["slots"]) * 2.0 ** g["n_in"]
+                    work[(g["m"], g["slots"], g["half"])] += len(g["slots"]) * 2.0 ** g["n_in"]
         total = sum(work.values())
         for key, w in work.items():
             share[key] += w / total
     return share
 
 
-def code(m: int, slots) -> int:
-    c = (m << 28) | (len(slots) << 24)
+def code(m: int, slots, half: bool) -> int:
+    c = (int(half) << 30) | (m << 28) | (len(slots) << 24)
     for j, s in enumerate(slots):
         c |= s << (2 * j)
     return c
@@ -72,10 +72,11 @@ def main(argv=None):
     work = sequence_work(workload_families())
     total = sum(work.values())
     rows, acc = [], 0.0
-    for (m, slots), w in work.most_common():
+    for (m, slots, half), w in work.most_common():
         if len(rows) >= a.limit or acc >= a.coverage * total:
             break
-        rows.append(f"    0x{code(m, slots):08x}u,  // M={m} {' '.join(str(s) for s in slots)}")
+        rows.append(f"    0x{code(m, slots, half):08x}u,  // M={m} {' '.join(str(s) for s in slots)}"
+                    f"{' (every probability 1/2)' if half else ''}")
         acc += w
     with open(OUT, "w") as f:
         f.write("// generated by gen_group_sequences.py: register-slot sequences of the complex64\n")

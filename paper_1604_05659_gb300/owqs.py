@@ -89,6 +89,11 @@ class owqs_batch_item(C.Structure):
                 ("out", C.c_void_p), ("ref", C.c_int32), ("pad_", C.c_uint32)]
 
 
+_BATCH_ITEM_DTYPE = np.dtype([("pattern", np.uint64), ("outcomes", np.uint64), ("psi_in", np.uint64),
+                              ("out", np.uint64), ("ref", np.int32), ("pad_", np.uint32)])
+assert _BATCH_ITEM_DTYPE.itemsize == C.sizeof(owqs_batch_item)
+
+
 class owqs_batch_opts(C.Structure):
     _fields_ = [("dtype", C.c_uint32), ("column_block", C.c_uint32), ("stream", C.c_void_p),
                 ("use_graph", C.c_uint32), ("pad_", C.c_uint32), ("overlaps", C.POINTER(C.c_double))]
@@ -96,7 +101,8 @@ class owqs_batch_opts(C.Structure):
 
 class owqs_batch_info(C.Structure):
     _fields_ = [("smem_items", C.c_uint32), ("hbm_items", C.c_uint32), ("tasks", C.c_uint32),
-                ("smem_bytes_per_cta", C.c_uint32), ("launches", C.c_uint32), ("global_items", C.c_uint32)]
+                ("smem_bytes_per_cta", C.c_uint32), ("launches", C.c_uint32), ("global_items", C.c_uint32),
+                ("compile_ms", C.c_float), ("call_ms", C.c_float)]
 
 
 class owqs_pass_desc(C.Structure):
@@ -372,8 +378,9 @@ class Handle:
 
     def describe_groups(self, outcomes=None, *, dtype: str = "c64", mode: str = "owqs", real_input: bool = False):
         """The pass groups a run would launch (host only): list of dicts with
-        the register qubits m, the slot sequence, the input width n_in and
-        whether a kernel compiled for that sequence runs it."""
+        the register qubits m, the slot sequence, whether every probability
+        of the group is exactly 1/2 (half), the input width n_in and whether
+        a kernel compiled for that sequence runs it."""
         cap = self.K + 16
         regs, slots, nin, spec = ((C.c_uint32 * cap)() for _ in range(4))
         n = C.c_uint32()
@@ -384,7 +391,7 @@ class Handle:
         for i in range(min(n.value, cap)):
             k = (slots[i] >> 24) & 15
             out.append({"m": regs[i], "slots": tuple((slots[i] >> (2 * j)) & 3 for j in range(k)),
-                        "n_in": nin[i], "specialised": bool(spec[i])})
+                        "half": bool((slots[i] >> 30) & 1), "n_in": nin[i], "specialised": bool(spec[i])})
         return out
 
     def index_map(self, pass_index: int):
@@ -593,19 +600,34 @@ def run_batch(items, *, dtype: str = "c128", column_block: int = 0, stream=None,
     Returns (info dict, overlaps array of shape (n, 4) or None)."""
     import torch
     n = len(items)
-    arr = (owqs_batch_item * max(1, n))()
-    keep = []
+    # the item structs as one numpy record array (the layout of
+    # owqs_batch_item) and every item's outcomes in one byte buffer
+    rec = np.zeros(max(1, n), dtype=_BATCH_ITEM_DTYPE)
+    ks = np.array([max(1, it["handle"].K) for it in items], dtype=np.int64)
+    offs = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(ks, out=offs[1:])
+    ocbuf = np.zeros(max(1, int(offs[-1])), dtype=np.uint8)
+    base = ocbuf.ctypes.data
+    pat, ocp, pin, pout, ref = (np.zeros(n, dtype=np.uint64), np.zeros(n, dtype=np.uint64),
+                                np.zeros(n, dtype=np.uint64), np.zeros(n, dtype=np.uint64),
+                                np.zeros(n, dtype=np.int32))
     for i, it in enumerate(items):
         h = it["handle"]
-        oc = None
-        if it.get("outcomes") is not None:
-            oc = _outcome_buf(it["outcomes"], h.K)
-            keep.append(oc)
-        arr[i].pattern = h._h
-        arr[i].outcomes = C.cast(oc, C.POINTER(C.c_uint8)) if oc is not None else None
-        arr[i].psi_in = it["psi_in"].data_ptr() if it.get("psi_in") is not None else None
-        arr[i].out = it["out"].data_ptr()
-        arr[i].ref = int(it.get("ref", -1))
+        oc = it.get("outcomes")
+        if oc is not None:
+            a = np.asarray(oc).ravel()[: h.K]
+            ocbuf[offs[i]: offs[i] + a.size] = a.astype(np.uint8) & 1
+            ocp[i] = base + int(offs[i])
+        pat[i] = h._h.value
+        x = it.get("psi_in")
+        if x is not None:
+            pin[i] = x.data_ptr()
+        pout[i] = it["out"].data_ptr()
+        ref[i] = int(it.get("ref", -1))
+    if n:
+        rec["pattern"][:n], rec["outcomes"][:n], rec["psi_in"][:n], rec["out"][:n] = pat, ocp, pin, pout
+        rec["ref"][:n] = ref
+    arr = rec.ctypes.data_as(C.POINTER(owqs_batch_item))
     ov = np.zeros(4 * max(1, n), dtype=np.float64) if overlaps else None
     s = stream if stream is not None else torch.cuda.current_stream()
     opts = owqs_batch_opts(DTYPE[dtype], column_block, C.c_void_p(s.cuda_stream), int(use_graph), 0,
