@@ -48,11 +48,11 @@ FALLBACK_HBM_GBS = 6800.0
 # sha256 prefix of the pass-group sources they were measured on (a changed
 # kernel reports null).  Both are pass groups on the full brickwork workload,
 # mean of three launches: c64 k_group<3, 0, SEQ> (2^28 complex64 amplitudes in
-# and out; 2147.7 MB read + 2103.8 MB written) and c128 k_group64<3, 0> (2^28
-# complex128; 4299.3 MB read + 4247.1 MB written).
+# and out; 2147.6 MB read + 2095.6 MB written) and c128 k_group64<3, 0, 0>
+# (2^28 complex128; 4299.2 MB read + 4247.2 MB written).
 # profiles/k_group_c64_brickwork28x40_dram.md.
-NCU_TRAFFIC = {("faafb09b1344fb89", "c64"): (2147718144 + 2105868288 + 2147657728 + 2102733056 + 2147620352 + 2102921216) / 3.0,
-               ("faafb09b1344fb89", "c128"): (4299367168 + 4249121792 + 4299737600 + 4246787072 + 4298777600 + 4245467136) / 3.0}
+NCU_TRAFFIC = {("33986a87fed490c9", "c64"): (2147601408 + 2097735936 + 2147583232 + 2094633728 + 2147595008 + 2094318080) / 3.0,
+               ("33986a87fed490c9", "c128"): (4298327808 + 4248759296 + 4302077952 + 4247692032 + 4297135872 + 4245162752) / 3.0}
 # nominal GB300 FP64 rate (no measured FP64 peak exists for this machine)
 FP64_PEAK_TFLOPS = 1.25
 # FP64 flops per output amplitude of the complex128 pass: complex multiply-add

@@ -15,6 +15,9 @@ available; these stand in for them with the same structure).
   brickwork_readout the brickwork with (some of) its outputs measured in
                     seeded random bases: no gflow, sampled-outcome workloads.
   measured_inputs   a random product input measured qubit by qubit.
+  chain_measurements inputs measured one by one, each pass preparing a qubit
+                    that is (mostly) not joined to the measured one: pass
+                    groups whose probabilities are not 1/2.
 """
 from __future__ import annotations
 
@@ -25,7 +28,7 @@ from typing import List, Optional
 
 import numpy as np
 
-from .patterns import (M, Pattern, brickwork_circuit, circuit_to_pattern, qft_circuit,
+from .patterns import (E, M, N, Pattern, brickwork_circuit, circuit_to_pattern, qft_circuit,
                        random_jcz_circuit)
 from .rng import SplitMix64, pattern_rng, random_state
 
@@ -126,6 +129,32 @@ def measured_inputs(n: int, kept: int = 2, pattern_index: int = 0) -> Workload:
     for q in range(n):   # bit q of the index is qubit q: kron puts the last factor lowest
         v = random_state(rng, 1)
         psi = np.kron(v, psi)
+    out = forced_outcomes(p, rng)
+    return Workload(p, psi, out, p.name)
+
+
+def chain_measurements(n: int, k: int, joined_every: int = 0, pattern_index: int = 0) -> Workload:
+    """n input qubits in a random normalised state; k passes, pass j measuring
+    input j (at a seeded random angle) after E(j, j+1) and preparing qubit
+    n + j.  The prepared qubit gets E(j, n + j) once where joined_every > 0
+    and j % joined_every == 0, and twice (the identity: an E is its own
+    inverse) elsewhere, so most passes prepare a qubit that stays unentangled
+    and their probabilities are not 1/2 (Section 4.5 does not apply).
+    Outputs: inputs k..n-1 and the prepared qubits."""
+    if not 1 <= k < n:
+        raise ValueError("need 1 <= k < n")
+    rng = pattern_rng(8, pattern_index)
+    cmds = []
+    for j in range(k):
+        cmds.append(N(n + j))
+        cmds.append(E(j, j + 1))
+        cmds.append(E(j, n + j))
+        if not (joined_every and j % joined_every == 0):
+            cmds.append(E(j, n + j))
+        cmds.append(M(j, 2.0 * math.pi * rng.uniform()))
+    p = Pattern(n + k, list(range(n)), list(range(k, n)) + [n + j for j in range(k)], cmds,
+                f"chain{n}x{k}j{joined_every}")
+    psi = random_state(rng, n)
     out = forced_outcomes(p, rng)
     return Workload(p, psi, out, p.name)
 

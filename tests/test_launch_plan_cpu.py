@@ -147,6 +147,27 @@ def test_group_slot_sequences_and_compiled_kernels(owqs):
         assert not any(g["specialised"] for g in h.describe_groups(wl.outcomes, dtype="c128", real_input=real))
 
 
+def test_exact_half_groups(owqs):
+    """A pass group sums no per-pass norms (bit 30, "half") exactly when every
+    pass measures a qubit joined by an odd number of E to the qubit it
+    prepares: all groups of the J/CZ families, none of a chain whose
+    prepared qubits get E twice (the identity), and all of the same chain
+    with one E each."""
+    for wl in (workloads.brickwork(12, 8), workloads.qft(12, with_input=False),
+               workloads.random_batch(2, 12, 14, 10, 20)[0]):
+        h = owqs.load(wl.pattern)
+        h.reorder()
+        for real in (False, True):
+            gs = h.describe_groups(wl.outcomes, real_input=real)
+            assert gs and all(g["half"] for g in gs), wl.name
+    for joined, half in ((0, False), (1, True)):
+        wl = workloads.chain_measurements(14, 9, joined_every=joined)
+        h = owqs.load(wl.pattern)
+        for dtype in ("c64", "c128"):
+            gs = h.describe_groups(wl.outcomes, dtype=dtype, real_input=True)
+            assert len(gs) == 3 and all(g["half"] == half for g in gs), (joined, dtype, gs)
+
+
 def test_memory_plan_separate_substates(owqs):
     """owqs_plan_memory: two brickwork blocks with |+> inputs stay separate
     sub-states until the joining E (joins, less memory and at most half the
