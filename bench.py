@@ -776,9 +776,36 @@ def run_owqs(args):
             nbytes = (1 << nin) * 8 if name == "h2d" else (1 << nout) * 8
             link[name] = {"GBps": nbytes / tl / 1e9, "ms": 1e3 * tl}
         del dev_in
-        e2e = {"value": replica_throughput(upd, e2e_steps, world, te), "unit": UNIT,
-               "h2d_bytes_per_step": (1 << nin) * 8, "d2h_bytes_per_step": (1 << nout) * 8 + 8 * (p.K + 2),
-               "ms_per_step": 1e3 * te / e2e_steps, "steps": e2e_steps, "clocks": clocks_e2e,
+        # the same steps through owqs_run_async / owqs_wait with two runs in
+        # flight: every step still copies its own input in and its output out
+        # (two pinned output buffers in turn), but a step's input copy
+        # overlaps the previous step's launches and its output copy the next
+        # step's
+        host_out2 = torch.empty(1 << nout, dtype=torch.complex64).pin_memory()
+        outs = (host_out, host_out2)
+
+        def run_pipe(n):
+            h.run_async(host_in, outs[0], dtype="c64", outcomes=wl.outcomes)
+            for i in range(1, n):
+                h.run_async(host_in, outs[i % 2], dtype="c64", outcomes=wl.outcomes)
+                h.wait()
+            h.wait()
+
+        run_pipe(2)
+        sampler_p = ClockSampler(gpu_id)
+        sampler_p.start()
+        tp = timed(lambda: run_pipe(e2e_steps), 1)
+        clocks_p = sampler_p.stop()
+        pipe_ok = bool(torch.equal(host_out2, host_out))  # both hold the same step's result
+        del host_out2, outs
+        e2e = {"value": replica_throughput(upd, e2e_steps, world, tp), "unit": UNIT,
+               "h2d_bytes_per_step": (1 << nin) * 8, "d2h_bytes_per_step": (1 << nout) * 8 + 8 * (p.K + 3),
+               "ms_per_step": 1e3 * tp / e2e_steps, "steps": e2e_steps, "clocks": clocks_p,
+               "api": "owqs_run_async + owqs_wait, two runs in flight, pinned host vectors",
+               "outputs_equal": pipe_ok,
+               "sync": {"value": replica_throughput(upd, e2e_steps, world, te), "unit": UNIT,
+                        "api": "owqs_run with OWQS_IO_HOST, one call per step",
+                        "ms_per_step": 1e3 * te / e2e_steps, "clocks": clocks_e2e},
                "host_link": link,
                "device_step_plus_copies_ms": 1e3 * t64 / args.steps + link["h2d"]["ms"] + link["d2h"]["ms"]}
 

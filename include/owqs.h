@@ -339,6 +339,29 @@ owqs_status owqs_last_sample_info(const owqs_pattern* p, owqs_sample_info* info)
 owqs_status owqs_run(owqs_pattern* p, const owqs_run_opts* opts, const void* psi_in,
                      void* psi_out, uint8_t* outcomes, double* probs);
 
+/* Asynchronous runs of the same simulation as owqs_run (forced or zero
+ * outcomes, one live array, one launch per pass or pass group, no CUDA
+ * graph).  owqs_run_async compiles the schedule, enqueues the run on
+ * opts->stream and returns; owqs_wait blocks until the oldest run in flight
+ * on the pattern has finished and returns its status, its outcomes (zero
+ * policy) and probabilities (as owqs_run's).  At most two runs are in
+ * flight per pattern handle (a third returns OWQS_ERR_ARG, as does owqs_wait
+ * with none).  With OWQS_IO_HOST, the input copy runs on a copy stream as
+ * soon as the previous run's launches that read the input staging buffer
+ * are done, and the output copy on another copy stream after the final pass:
+ * the copies of consecutive runs overlap each other's launches.
+ *   psi_in, psi_out  as owqs_run; they must stay valid, and psi_out unread,
+ *                    until owqs_wait has returned for this run (host
+ *                    vectors: pinned memory)
+ *   outcomes         forced policy: read during the call (may be reused after
+ *                    it returns)
+ * owqs_run and the other synchronous runs of a pattern return OWQS_ERR_ARG
+ * while it has asynchronous runs in flight.  Errors of the device work
+ * (OWQS_ERR_TIMEOUT, ...) are reported by owqs_wait. */
+owqs_status owqs_run_async(owqs_pattern* p, const owqs_run_opts* opts, const void* psi_in, void* psi_out,
+                           const uint8_t* outcomes);
+owqs_status owqs_wait(owqs_pattern* p, uint8_t* outcomes, double* probs);
+
 /* Product input (Section 4.1 and Fig. 8a: the input as separate sub-states).
  * The inputs are given as nfactors factors: factor f holds sizes[f] input
  * qubits (1 .. 30), listed in qubits[] (all factors concatenated, each in its

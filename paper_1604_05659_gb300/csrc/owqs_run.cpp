@@ -35,6 +35,24 @@ struct RunCache {
   std::vector<unsigned char> small_host;
   std::vector<double> h_norms;
   uint32_t last_launches = 0;
+  // asynchronous runs (owqs_run_async / owqs_wait), at most two in flight,
+  // completed in order
+  struct Pending {
+    cudaEvent_t done = nullptr;  // the run's output copy and slot read-back have finished
+    double* host = nullptr;      // pinned: the K + 2 norm slots, then the error flag
+    double* snap = nullptr;      // device: the same, copied right after the final pass
+    size_t cap = 0;              // doubles in host and snap
+    owqs_run_opts opts{};
+    std::vector<PassDesc> passes;
+    std::vector<char> in_group;
+    std::vector<int> outcome_of_pass;
+    bool has_input = false;
+  } pend[2];
+  int pend_head = 0, pend_count = 0, last_slot = -1;
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  cudaEvent_t in_free = nullptr;  // the last asynchronous run's launches that read in_stage are done
+  cudaEvent_t h2d_done = nullptr, ready = nullptr;
+  bool in_free_set = false;
   uint32_t last_sample_path = 0;   // OWQS_SAMPLE_* of the last sampled run
   uint32_t last_guessed = 0;       // a whole-run guess ran first
   uint32_t last_relaunches = 0;    // checked launches: launches run again after a corrected outcome
@@ -48,6 +66,18 @@ struct RunCache {
     int cur = -1;
     cudaGetDevice(&cur);
     if (device >= 0 && cur != device) cudaSetDevice(device);
+    for (Pending& q : pend) {
+      if (q.done) {
+        cudaEventSynchronize(q.done);
+        cudaEventDestroy(q.done);
+      }
+      if (q.host) cudaFreeHost(q.host);
+      if (q.snap) cudaFree(q.snap);
+    }
+    for (cudaEvent_t ev : {in_free, h2d_done, ready})
+      if (ev) cudaEventDestroy(ev);
+    for (cudaStream_t cs : {copy_in, copy_out})
+      if (cs) cudaStreamDestroy(cs);
     if (gexec) cudaGraphExecDestroy(gexec);
     if (cap) cudaStreamDestroy(cap);
     for (void* p : {buf[0], buf[1], in_stage, out_stage, (void*)norms, (void*)partials, (void*)counter, samp,
@@ -795,19 +825,15 @@ static owqs_status ensure_pingpong(RunCache* rc, size_t elems, size_t amp) {
   return OWQS_OK;
 }
 
-static owqs_status finish(Pattern& p, const owqs_run_opts* o, RunCache* rc, const Prepared& pr,
-                          cudaStream_t s, uint8_t* outcomes, double* probs, const std::vector<int>& outcome_of_pass,
-                          bool has_input, int vdiag, double* frob2, const std::vector<char>& in_group) {
+// The run's result from its norm slots (h_norms: K + 2 values read back from
+// the device) and its error flag: probabilities, outcomes of a sampled run,
+// the impossible-branch and EOWQS checks.
+static owqs_status interpret_run(Pattern& p, const owqs_run_opts* o, const std::vector<double>& h_norms,
+                                 unsigned int flag, const std::vector<PassDesc>& passes, uint8_t* outcomes,
+                                 double* probs, const std::vector<int>& outcome_of_pass, bool has_input, int vdiag,
+                                 double* frob2, const std::vector<char>& in_group) {
   const int K = (int)p.meas_qubit.size();
-  rc->h_norms.assign((size_t)K + 2, 0.0);
-  unsigned int flag = 0;
-  cudaError_t e = cudaMemcpyAsync(rc->h_norms.data(), rc->norms, sizeof(double) * (K + 2), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, rc->counter + 1, sizeof(flag), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(e, "run");
   if (flag) {  // a device-side wait gave up (bit 0; blocks skipped the reduction) or a bounds check failed (bit 1)
-    cudaMemsetAsync(rc->counter, 0, 2 * sizeof(unsigned int), s);
-    cudaStreamSynchronize(s);
     if (flag & 2u)
       return set_error(OWQS_ERR_CUDA, "a kernel access fell outside its buffer (bounds-checked build); results are invalid");
     return set_error(OWQS_ERR_TIMEOUT, "a device-side wait in a pass kernel gave up; results are invalid");
@@ -815,12 +841,12 @@ static owqs_status finish(Pattern& p, const owqs_run_opts* o, RunCache* rc, cons
   const double thresh = o->dtype == OWQS_C128 ? 1e-24 : 1e-12;
   owqs_status st = OWQS_OK;
   int mi = 0;
-  for (const PassDesc& d : pr.passes) {
+  for (const PassDesc& d : passes) {
     if (d.kind != 0) continue;
-    double pv = o->mode == OWQS_MODE_OWQS ? rc->h_norms[mi + 1] : 0.5;
+    double pv = o->mode == OWQS_MODE_OWQS ? h_norms[mi + 1] : 0.5;
     if (o->mode == OWQS_MODE_OWQS && (size_t)mi < in_group.size() && in_group[mi]) {
       // later measurement of a pass group: its slot holds the running product of the group's probabilities
-      const double first = rc->h_norms[mi];
+      const double first = h_norms[mi];
       pv = first > 0.0 ? pv / first : 0.0;
     }
     if (probs) probs[d.meas_k] = pv;
@@ -831,18 +857,36 @@ static owqs_status finish(Pattern& p, const owqs_run_opts* o, RunCache* rc, cons
     ++mi;
   }
   if (vdiag > 0) {  // recognition: |U|_F^2 / 2^|I| is 1 for an isometry; reported, not judged
-    if (frob2) *frob2 = rc->h_norms[K + 1] / std::ldexp(1.0, vdiag);
+    if (frob2) *frob2 = h_norms[K + 1] / std::ldexp(1.0, vdiag);
     return st;
   }
   if (o->mode == OWQS_MODE_EOWQS) {
-    const double nin = has_input ? rc->h_norms[0] : 1.0;
-    const double nout = rc->h_norms[K + 1];
+    const double nin = has_input ? h_norms[0] : 1.0;
+    const double nout = h_norms[K + 1];
     const double tol = o->dtype == OWQS_C128 ? 1e-10 : 1e-4;
     if (!(std::fabs(nout - nin) <= tol * std::max(nin, 1e-300)))
       st = set_error(OWQS_ERR_NOT_DETERMINISTIC,
                      "EOWQS output norm " + std::to_string(nout) + " differs from the input norm " + std::to_string(nin));
   }
   return st;
+}
+
+static owqs_status finish(Pattern& p, const owqs_run_opts* o, RunCache* rc, const Prepared& pr,
+                          cudaStream_t s, uint8_t* outcomes, double* probs, const std::vector<int>& outcome_of_pass,
+                          bool has_input, int vdiag, double* frob2, const std::vector<char>& in_group) {
+  const int K = (int)p.meas_qubit.size();
+  rc->h_norms.assign((size_t)K + 2, 0.0);
+  unsigned int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(rc->h_norms.data(), rc->norms, sizeof(double) * (K + 2), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, rc->counter + 1, sizeof(flag), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "run");
+  if (flag) {
+    cudaMemsetAsync(rc->counter, 0, 2 * sizeof(unsigned int), s);
+    cudaStreamSynchronize(s);
+  }
+  return interpret_run(p, o, rc->h_norms, flag, pr.passes, outcomes, probs, outcome_of_pass, has_input, vdiag, frob2,
+                       in_group);
 }
 
 // Launch a runner's item list: from a CUDA graph cached under `key` (captured
@@ -1316,6 +1360,32 @@ static bool same_launches(const std::vector<Item>& a, const std::vector<Item>& b
   return true;
 }
 
+// The launch list of a one-array run of pr.passes, one launch per pass or
+// pass group, nothing launched (no factor joins: false if the passes have one).
+static bool build_one_array(Runner& R, const Prepared& pr, const owqs_run_opts* o) {
+  R.begin(pr.in_dev, pr.in_elems, pr.out_dev, pr.out_elems);
+  for (size_t i = 0; i < pr.passes.size(); ++i) {
+    GroupParams G;
+    LaunchPlan GL;
+    int gk = 0;
+    switch (decide_launch(pr.passes, i, o->dtype, R.real_input(), false, G, GL, gk)) {
+      case LAUNCH_JOIN:
+        return false;
+      case LAUNCH_FINAL:
+        R.final_pass(pr.passes[i]);
+        break;
+      case LAUNCH_GROUP:
+        R.measure_group(G, GL);
+        i += (size_t)gk - 1;
+        break;
+      default:
+        R.measure(pr.passes[i]);
+    }
+  }
+  if (o->dtype == OWQS_C128 && (o->flags & OWQS_RUN_DOUBLE_FLOAT)) mark_double_float(R.items);
+  return R.err == OWQS_OK;
+}
+
 static owqs_status sample_checked(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
                                   uint8_t* outcomes, double* probs, const std::vector<double>& u,
                                   std::vector<uint8_t>& oc) {
@@ -1331,29 +1401,7 @@ static owqs_status sample_checked(Pattern& p, const owqs_run_opts* o, const void
     if (d.kind != 1) wmax = std::max<size_t>(wmax, (size_t)1 << d.n_out);
   st = ensure_pingpong(rc, wmax, pr.amp);
   if (st != OWQS_OK) return st;
-  auto build = [&](Runner& R) {
-    R.begin(pr.in_dev, pr.in_elems, pr.out_dev, pr.out_elems);
-    for (size_t i = 0; i < pr.passes.size(); ++i) {
-      GroupParams G;
-      LaunchPlan GL;
-      int gk = 0;
-      switch (decide_launch(pr.passes, i, o->dtype, R.real_input(), false, G, GL, gk)) {
-        case LAUNCH_JOIN:
-          return false;
-        case LAUNCH_FINAL:
-          R.final_pass(pr.passes[i]);
-          break;
-        case LAUNCH_GROUP:
-          R.measure_group(G, GL);
-          i += (size_t)gk - 1;
-          break;
-        default:
-          R.measure(pr.passes[i]);
-      }
-    }
-    if (o->dtype == OWQS_C128 && (o->flags & OWQS_RUN_DOUBLE_FLOAT)) mark_double_float(R.items);
-    return R.err == OWQS_OK;
-  };
+  auto build = [&](Runner& R) { return build_one_array(R, pr, o); };
   Runner R(p, *rc, o->dtype, o->mode, s);
   if (!build(R)) return set_error(OWQS_ERR_UNSUPPORTED, "checked launches: a run without factor joins");
   if (o->io == OWQS_IO_HOST && psi_in) {
@@ -1430,6 +1478,134 @@ static owqs_status sample_checked(Pattern& p, const owqs_run_opts* o, const void
   return finish(p, o, rc, pr, s, outcomes, probs, outcome_of_pass, pr.in_dev != nullptr, 0, nullptr, R.in_group);
 }
 
+// Asynchronous runs: the call compiles the schedule, enqueues the run and
+// returns; owqs_wait completes the oldest run in flight.  With host vectors,
+// the input copy goes on a copy stream once the previous asynchronous run's
+// launches that read the input staging buffer are done, the output copy on a
+// second copy stream once the final pass has written the output staging
+// buffer; a run's final pass waits for the previous run's output copy.  So a
+// run's input copy overlaps the previous run's launches and its output copy
+// the next run's.  The norm slots and the error flag are copied on the
+// compute stream right after the final pass (the next run's launches follow
+// on the same stream), then read back on the copy stream.  One array, one
+// launch per pass or pass group, forced or zero outcomes.
+static owqs_status ensure_async(RunCache* rc, RunCache::Pending& q, size_t doubles) {
+  cudaError_t e = cudaSuccess;
+  if (!rc->copy_in) e = cudaStreamCreateWithFlags(&rc->copy_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !rc->copy_out) e = cudaStreamCreateWithFlags(&rc->copy_out, cudaStreamNonBlocking);
+  for (cudaEvent_t* ev : {&rc->in_free, &rc->h2d_done, &rc->ready, &q.done})
+    if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  if (e == cudaSuccess && q.cap < doubles) {
+    if (q.host) cudaFreeHost(q.host);
+    if (q.snap) cudaFree(q.snap);
+    q.host = nullptr;
+    q.snap = nullptr;
+    q.cap = 0;
+    e = cudaMallocHost(reinterpret_cast<void**>(&q.host), doubles * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&q.snap), doubles * sizeof(double));
+    if (e == cudaSuccess) q.cap = doubles;
+  }
+  return e == cudaSuccess ? OWQS_OK : cuda_fail(e, "asynchronous run resources");
+}
+
+static owqs_status run_async_enqueue(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
+                                     const uint8_t* outcomes) {
+  if (!o || !psi_out) return set_error(OWQS_ERR_ARG, "NULL argument");
+  if (o->policy == OWQS_OUTCOME_SAMPLED)
+    return set_error(OWQS_ERR_UNSUPPORTED, "asynchronous runs take forced or zero outcomes");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(o->stream);
+  RunCache* rc = nullptr;
+  owqs_status st = get_cache(p, rc);
+  if (st != OWQS_OK) return st;
+  if (rc->pend_count == 2) return set_error(OWQS_ERR_ARG, "two asynchronous runs in flight: call owqs_wait first");
+  Prepared pr;
+  st = prepare(p, o, psi_in, psi_out, outcomes, rc, pr, false);
+  if (st != OWQS_OK) return st;
+  size_t wmax = 1;
+  for (const PassDesc& d : pr.passes)
+    if (d.kind != 1) wmax = std::max<size_t>(wmax, (size_t)1 << d.n_out);
+  st = ensure_pingpong(rc, wmax, pr.amp);
+  if (st != OWQS_OK) return st;
+  Runner R(p, *rc, o->dtype, o->mode, s);
+  if (!build_one_array(R, pr, o)) return set_error(OWQS_ERR_UNSUPPORTED, "asynchronous runs take one input vector");
+  const int slot = (rc->pend_head + rc->pend_count) % 2;
+  RunCache::Pending& q = rc->pend[slot];
+  const size_t K = p.meas_qubit.size();
+  st = ensure_async(rc, q, K + 3);
+  if (st != OWQS_OK) return st;
+  const bool host_io = o->io == OWQS_IO_HOST;
+  // the last launch that reads the input staging buffer
+  size_t last_in = SIZE_MAX;
+  for (size_t i = 0; i < R.items.size(); ++i) {
+    const Item& it = R.items[i];
+    const void* in = it.type == 1 ? it.norm_in : it.type == 4 ? it.G.in : it.type == 0 ? it.P.in : nullptr;
+    if (pr.in_dev && in == pr.in_dev) last_in = i;
+  }
+  cudaError_t e = cudaSuccess;
+  if (host_io && psi_in) {
+    if (rc->in_free_set) e = cudaStreamWaitEvent(rc->copy_in, rc->in_free, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(rc->in_stage, psi_in, pr.in_elems * pr.amp, cudaMemcpyHostToDevice, rc->copy_in);
+    if (e == cudaSuccess) e = cudaEventRecord(rc->h2d_done, rc->copy_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, rc->h2d_done, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "asynchronous input copy");
+  }
+  for (size_t i = 0; i < R.items.size(); ++i) {
+    if (host_io && i + 1 == R.items.size() && rc->last_slot >= 0) {
+      // the final pass writes the output staging buffer: the previous run's output copy must be done
+      e = cudaStreamWaitEvent(s, rc->pend[rc->last_slot].done, 0);
+      if (e != cudaSuccess) return cuda_fail(e, "asynchronous run order");
+    }
+    st = R.launch(R.items[i], s);
+    if (st != OWQS_OK) return st;
+    if (host_io && i == last_in) {
+      e = cudaEventRecord(rc->in_free, s);
+      if (e != cudaSuccess) return cuda_fail(e, "asynchronous run order");
+      rc->in_free_set = true;
+    }
+  }
+  e = cudaMemcpyAsync(q.snap, rc->norms, sizeof(double) * (K + 2), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(q.snap + K + 2, 0, sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(q.snap + K + 2, rc->counter + 1, sizeof(unsigned int),
+                                            cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(rc->counter + 1, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = cudaEventRecord(rc->ready, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(rc->copy_out, rc->ready, 0);
+  if (e == cudaSuccess && host_io)
+    e = cudaMemcpyAsync(psi_out, rc->out_stage, pr.out_elems * pr.amp, cudaMemcpyDeviceToHost, rc->copy_out);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(q.host, q.snap, sizeof(double) * (K + 3), cudaMemcpyDeviceToHost, rc->copy_out);
+  if (e == cudaSuccess) e = cudaEventRecord(q.done, rc->copy_out);
+  if (e != cudaSuccess) return cuda_fail(e, "asynchronous run");
+  q.opts = *o;
+  q.passes = pr.passes;
+  q.in_group = R.in_group;
+  q.outcome_of_pass.clear();
+  for (const PassDesc& d : pr.passes)
+    if (d.kind == 0) q.outcome_of_pass.push_back(d.outcome);
+  q.has_input = pr.in_dev != nullptr;
+  rc->last_slot = slot;
+  ++rc->pend_count;
+  rc->last_launches = (uint32_t)R.items.size();
+  return OWQS_OK;
+}
+
+static owqs_status run_async_wait(Pattern& p, uint8_t* outcomes, double* probs) {
+  RunCache* rc = p.cache.get();
+  if (!rc || rc->pend_count == 0) return set_error(OWQS_ERR_ARG, "no asynchronous run in flight");
+  RunCache::Pending& q = rc->pend[rc->pend_head];
+  const cudaError_t e = cudaEventSynchronize(q.done);
+  rc->pend_head = (rc->pend_head + 1) % 2;
+  --rc->pend_count;
+  if (e != cudaSuccess) return cuda_fail(e, "asynchronous run");
+  const size_t K = p.meas_qubit.size();
+  const std::vector<double> h(q.host, q.host + K + 2);
+  unsigned int flag = 0;
+  std::memcpy(&flag, q.host + K + 2, sizeof(flag));
+  return interpret_run(p, &q.opts, h, flag, q.passes, outcomes, probs, q.outcome_of_pass, q.has_input, 0, nullptr,
+                       q.in_group);
+}
+
 // Sampled outcomes as a forced run.
 //
 // EOWQS (Section 4.5): a pattern with a gflow is strongly deterministic, so
@@ -1459,6 +1635,8 @@ static owqs_status run_impl(Pattern& p, const owqs_run_opts* o, const void* psi_
                             uint32_t* prof_kind, uint32_t prof_cap, uint32_t* prof_n, int vdiag = 0,
                             double* frob2 = nullptr, const ProductInput* prod = nullptr,
                             uint32_t* prof_meas = nullptr) {
+  if (p.cache && p.cache->pend_count)
+    return set_error(OWQS_ERR_ARG, "asynchronous runs in flight on this pattern: call owqs_wait first");
   const bool eowqs = o && o->mode == OWQS_MODE_EOWQS;
   // the path of a one-at-a-time draw (run_core's sampled branch)
   const uint32_t one_at_a_time = o && !(o->flags & OWQS_RUN_HOST_SAMPLING) && masks_outcome_free(p)
@@ -1649,6 +1827,21 @@ owqs_status owqs_run(owqs_pattern* h, const owqs_run_opts* o, const void* psi_in
   if (o && o->mode == OWQS_MODE_EOWQS && !has_gflow(h->p))
     return set_error(OWQS_ERR_NOT_DETERMINISTIC, "EOWQS: the open graph has no gflow (Section 4.5)");
   return run_impl(h->p, o, psi_in, psi_out, outcomes, probs, nullptr, nullptr, nullptr, 0, nullptr);
+}
+
+owqs_status owqs_run_async(owqs_pattern* h, const owqs_run_opts* o, const void* psi_in, void* psi_out,
+                           const uint8_t* outcomes) {
+  clear_error();
+  if (!h) return set_error(OWQS_ERR_ARG, "NULL pattern");
+  if (o && o->mode == OWQS_MODE_EOWQS && !has_gflow(h->p))
+    return set_error(OWQS_ERR_NOT_DETERMINISTIC, "EOWQS: the open graph has no gflow (Section 4.5)");
+  return run_async_enqueue(h->p, o, psi_in, psi_out, outcomes);
+}
+
+owqs_status owqs_wait(owqs_pattern* h, uint8_t* outcomes, double* probs) {
+  clear_error();
+  if (!h) return set_error(OWQS_ERR_ARG, "NULL pattern");
+  return run_async_wait(h->p, outcomes, probs);
 }
 
 // recognition (Section 1: which unitary a pattern implements): the pattern

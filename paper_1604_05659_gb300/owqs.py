@@ -125,6 +125,9 @@ EXPORTS = {
     "owqs_get_order": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32)]),
     "owqs_run": (C.c_int, [C.c_void_p, C.POINTER(owqs_run_opts), C.c_void_p, C.c_void_p,
                            C.POINTER(C.c_uint8), C.POINTER(C.c_double)]),
+    "owqs_run_async": (C.c_int, [C.c_void_p, C.POINTER(owqs_run_opts), C.c_void_p, C.c_void_p,
+                                 C.POINTER(C.c_uint8)]),
+    "owqs_wait": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_double)]),
     "owqs_unitary": (C.c_int, [C.c_void_p, C.POINTER(owqs_run_opts), C.POINTER(C.c_uint8), C.c_void_p,
                                C.POINTER(C.c_double)]),
     "owqs_run_batch": (C.c_int, [C.POINTER(owqs_batch_item), C.c_uint32, C.POINTER(owqs_batch_opts),
@@ -448,6 +451,45 @@ class Handle:
         if check and st not in (OK,):
             _check(st)
         return out, oc[: self.K].copy(), probs[: self.K].copy(), st
+
+    def run_async(self, psi_in, out, *, dtype: str = "c64", mode: str = "owqs", policy: str = "forced",
+                  outcomes=None, stream=None, double_float: bool = False):
+        """owqs_run_async: enqueue a run and return.  psi_in (or None for |+>)
+        and out: CUDA tensors, or pinned CPU tensors / numpy arrays (host
+        vectors, copied on the library's copy streams).  They must stay alive
+        and out unread until wait() has returned for this run."""
+        import torch
+        host = not (isinstance(out, torch.Tensor) and out.is_cuda)
+        if host:
+            _check_host_vectors(psi_in, out, dtype, self.nin, self.nout)
+            pin = 0 if psi_in is None else _host_ptr(psi_in)
+            pout = _host_ptr(out)
+            dev = torch.device("cuda", torch.cuda.current_device())
+        else:
+            tdt = torch.complex64 if dtype == "c64" else torch.complex128
+            _check_vectors(psi_in, out, tdt, self.nin, self.nout)
+            pin = 0 if psi_in is None else psi_in.data_ptr()
+            pout = out.data_ptr()
+            dev = out.device
+        oc = np.zeros(max(1, self.K), dtype=np.uint8)
+        if outcomes is not None:
+            oc[: self.K] = np.asarray(outcomes, dtype=np.uint8)[: self.K]
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        opts = owqs_run_opts(DTYPE[dtype], MODE[mode], POLICY[policy], 1 if host else 0, 0,
+                             C.c_void_p(s.cuda_stream), 0, RUN_DOUBLE_FLOAT if double_float else 0)
+        _check(library().owqs_run_async(self._h, C.byref(opts), C.c_void_p(pin), C.c_void_p(pout),
+                                        oc.ctypes.data_as(C.POINTER(C.c_uint8))))
+
+    def wait(self, check: bool = True):
+        """owqs_wait: finish the oldest run in flight; returns (outcomes,
+        probs, status)."""
+        oc = np.zeros(max(1, self.K), dtype=np.uint8)
+        probs = np.zeros(max(1, self.K), dtype=np.float64)
+        st = library().owqs_wait(self._h, oc.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                 probs.ctypes.data_as(C.POINTER(C.c_double)))
+        if check and st != OK:
+            _check(st)
+        return oc[: self.K].copy(), probs[: self.K].copy(), st
 
     def run_product(self, factors, *, dtype: str = "c128", mode: str = "owqs", policy: str = "forced",
                     outcomes=None, stream=None, use_graph: bool = True, out=None, check: bool = True):
