@@ -616,7 +616,7 @@ def learned_leg(args, owqs, torch, hbm_gbs):
         row = {"n": h.nin, "K": h.K,
                "eowqs_greedy": {"m": me, "peak_live": ie["peak_live"], "amp_updates": sat(ie["amp_updates"])},
                "owqs_greedy": {"m": mo, "peak_live": io["peak_live"], "amp_updates": io["amp_updates"]},
-               "best_greedy": "owqs" if il["greedy_judge_owqs"] else "eowqs",
+               "best_greedy": "owqs" if il["greedy_best_owqs"] else "eowqs",
                "learned": {"peak_live": il["learned_peak_live"], "amp_updates": il["learned_amp_updates"]},
                "accepted": il["learned_accepted"],
                "kept": {"m": m_of_active(h), "peak_live": il["peak_live"], "amp_updates": il["amp_updates"]},
@@ -625,9 +625,9 @@ def learned_leg(args, owqs, torch, hbm_gbs):
         row["kept_not_worse"] = (il["peak_live"], il["amp_updates"]) <= best
         if il["learned_accepted"]:
             row["kept_gpu_seconds"] = gpu_seconds(h)
-        elif il["greedy_judge_owqs"]:
+        elif il["greedy_best_owqs"]:
             row["kept_gpu_seconds"] = t_owqs
-        row["best_greedy_gpu_seconds"] = t_owqs if il["greedy_judge_owqs"] else None
+        row["best_greedy_gpu_seconds"] = t_owqs if il["greedy_best_owqs"] else None
         h.close()
         rows.append(row)
     timed = [r for r in rows if r.get("kept_gpu_seconds") and r.get("best_greedy_gpu_seconds")]

@@ -112,8 +112,8 @@ owqs_status owqs_get_info(const owqs_pattern* p, owqs_pattern_info* info);
 /* modes (Section 4.5) */
 enum { OWQS_MODE_OWQS = 0, OWQS_MODE_EOWQS = 1 };
 
-/* Learned reorder proposal (not in the paper; it proposes, the greedy PROA
- * judges).  A 3-layer MLP, OWQS_MODEL_FEATURES -> 64 -> 64 -> 1 with ReLU,
+/* Learned reorder proposal (not in the paper; it proposes, and the proposal is
+ * kept only if no worse than the greedy PROA order).  A 3-layer MLP, OWQS_MODEL_FEATURES -> 64 -> 64 -> 1 with ReLU,
  * scores every candidate qubit at each reordering step; the lowest score is
  * measured next.  Its matrix products take bfloat16 inputs (features,
  * weights and activations rounded to nearest even) and accumulate in FP32;
@@ -151,7 +151,7 @@ typedef struct {
   uint32_t greedy_peak_live;   /* the greedy order's figures (use_learned)      */
   uint64_t greedy_amp_updates;
   uint32_t learned_peak_live;  /* the proposal's figures (use_learned)          */
-  uint32_t greedy_judge_owqs;  /* use_learned in EOWQS mode: 1 if the greedy OWQS
+  uint32_t greedy_best_owqs;  /* use_learned in EOWQS mode: 1 if the greedy OWQS
                                   sweep order was the better greedy order       */
   uint64_t learned_amp_updates;
 } owqs_reorder_info;

@@ -1,7 +1,7 @@
 """FP64 reference of the learned reorder proposal's network (oracle; test
 infrastructure only).  Not from the paper: the paper's reordering is the
-greedy Eq. 18 cost; the network is this project's proposal that the greedy
-judges.
+greedy Eq. 18 cost; the network is this project's proposal, kept only
+where it is no worse than the greedy order.
 
 Network: F = 12 features -> 64 -> 64 -> 1 with ReLU; parameters flattened as
 W1[64][12], b1[64], W2[64][64], b2[64], w3[64], b3.  With bf16=True the

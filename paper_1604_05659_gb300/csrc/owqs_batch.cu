@@ -732,7 +732,7 @@ static owqs_status run_batch(const owqs_batch_item* items, uint32_t n, const owq
     if (items[i].psi_in) {
       st = run_unchecked(items[i].pattern->p, &ro, items[i].psi_in, items[i].out,
                          const_cast<uint8_t*>(items[i].outcomes), nullptr);
-      if (st == OWQS_ERR_NOT_DETERMINISTIC) st = OWQS_OK;  // the caller judges the overlaps
+      if (st == OWQS_ERR_NOT_DETERMINISTIC) st = OWQS_OK;  // the caller compares the overlaps
     } else {
       st = owqs_unitary(items[i].pattern, &ro, items[i].outcomes, items[i].out, nullptr);
     }

@@ -61,7 +61,7 @@ int take_test_shrink(uint64_t* elems);
 // kept with the pattern; owqs_flow.cpp)
 bool has_gflow(Pattern& p);
 
-// owqs_run without the gflow pre-check (batched determinism checks judge
+// owqs_run without the gflow pre-check (batched determinism checks compare
 // the branch overlaps themselves)
 owqs_status run_unchecked(Pattern& p, const owqs_run_opts* o, const void* psi_in, void* psi_out,
                           uint8_t* outcomes, double* probs);

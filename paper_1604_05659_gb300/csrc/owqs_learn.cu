@@ -1,6 +1,6 @@
 // Learned reorder proposal: candidate features, a small MLP scorer with its
-// training kernels, and the learned reordering that the greedy PROA of
-// Section 4.3 judges.
+// training kernels, and the learned reordering, kept only where it is no
+// worse than the greedy PROA order of Section 4.3.
 //
 // The paper picks the next measurement with the hand-set Eq. 18 cost.  Here a
 // network scores the same candidates from the Eq. 18 criteria plus quantities

@@ -454,11 +454,11 @@ owqs_status owqs_reorder(owqs_pattern* h, const owqs_reorder_opts* o, owqs_reord
   uint32_t g_peak = 0, l_peak = 0;
   uint64_t g_upd = 0, l_upd = 0;
   order_stats(p, &g_peak, &g_upd);
-  bool accepted = false, judge_owqs = false;
+  bool accepted = false, best_owqs = false;
   std::vector<uint32_t> lorder;
   if (o->use_learned && eowqs) {
     // with preselected outcomes an order that waits for every domain is
-    // valid too: the greedy OWQS sweep order joins the judges
+    // valid too: the greedy OWQS sweep order is a candidate too
     ReorderGraph g2 = build_reorder_graph(p, false);
     GreedyResult b2;
     uint32_t b2_peak = 0;
@@ -487,7 +487,7 @@ owqs_status owqs_reorder(owqs_pattern* h, const owqs_reorder_opts* o, owqs_reord
       uint64_t o_upd = 0;
       order_stats(p, &o_peak, &o_upd);
       if (o_peak < g_peak || (o_peak == g_peak && o_upd < g_upd)) {
-        judge_owqs = true;
+        best_owqs = true;
         best = std::move(b2);
         best_peak = b2_peak;
         g_peak = o_peak;
@@ -499,7 +499,7 @@ owqs_status owqs_reorder(owqs_pattern* h, const owqs_reorder_opts* o, owqs_reord
     }
   }
   if (o->use_learned) {
-    // the proposal is judged by the best greedy order: kept only if its peak
+    // the proposal is checked against the best greedy order: kept only if its peak
     // live width and amplitude updates are no worse
     st = learned_order(p, o->model, eowqs, o->product_input != 0, lorder);
     if (st != OWQS_OK) return st;
@@ -524,7 +524,7 @@ owqs_status owqs_reorder(owqs_pattern* h, const owqs_reorder_opts* o, owqs_reord
     info->greedy_amp_updates = g_upd;
     info->learned_peak_live = l_peak;
     info->learned_amp_updates = l_upd;
-    info->greedy_judge_owqs = judge_owqs ? 1u : 0u;
+    info->greedy_best_owqs = best_owqs ? 1u : 0u;
   }
   return OWQS_OK;
 }

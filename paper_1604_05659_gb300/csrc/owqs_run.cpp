@@ -856,7 +856,7 @@ static owqs_status interpret_run(Pattern& p, const owqs_run_opts* o, const std::
                                                       " has probability " + std::to_string(pv));
     ++mi;
   }
-  if (vdiag > 0) {  // recognition: |U|_F^2 / 2^|I| is 1 for an isometry; reported, not judged
+  if (vdiag > 0) {  // recognition: |U|_F^2 / 2^|I| is 1 for an isometry; reported, not checked
     if (frob2) *frob2 = h_norms[K + 1] / std::ldexp(1.0, vdiag);
     return st;
   }

@@ -62,7 +62,7 @@ class owqs_reorder_info(C.Structure):
     _fields_ = [("peak_m", C.c_uint32), ("peak_live", C.c_uint32), ("amp_updates", C.c_uint64),
                 ("alpha_used", C.c_double), ("learned_accepted", C.c_uint32), ("greedy_peak_live", C.c_uint32),
                 ("greedy_amp_updates", C.c_uint64), ("learned_peak_live", C.c_uint32),
-                ("greedy_judge_owqs", C.c_uint32), ("learned_amp_updates", C.c_uint64)]
+                ("greedy_best_owqs", C.c_uint32), ("learned_amp_updates", C.c_uint64)]
 
 
 class owqs_run_opts(C.Structure):

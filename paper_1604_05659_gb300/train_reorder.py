@@ -12,7 +12,7 @@ candidates at every step (features from owqs_reorder_features, training by
 owqs_model_train: the library's own forward and backward kernels).  For a
 seeded subset the target is instead the fastest of the library's candidate
 orders as simulated and timed on the GPU.  The held-out patterns are then
-reordered in EOWQS mode with the proposal, which the greedy order judges,
+reordered in EOWQS mode with the proposal, which is kept only if no worse than the greedy order,
 the kept orders of a subset are timed against the greedy orders that fit the
 device, and the comparison is stored next to the weights.
 """
@@ -120,7 +120,7 @@ def build_dataset(handles, cands, seed, timed: int = 0, timed_width: int = 22):
 
 
 def evaluate(handles, model, sweep, timed: int = 0, timed_width: int = 30):
-    """EOWQS reordering of each held-out pattern with the proposal, judged by
+    """EOWQS reordering of each held-out pattern with the proposal, checked against
     the best greedy order: the greedy EOWQS order (without the sweep the
     Eq. 18 weights are Section 5's first run, a = b = d = |O|, g = 0.5) and
     the greedy OWQS sweep order, which waits for every domain and so is
@@ -140,12 +140,12 @@ def evaluate(handles, model, sweep, timed: int = 0, timed_width: int = 30):
         _, l = h.reorder(mode="eowqs", sweep=sweep, weights=w, model=model)
         row = {"n": h.nin, "K": h.K, "eowqs_greedy_peak": e["peak_live"], "owqs_greedy_peak": o["peak_live"],
                "greedy_peak": l["greedy_peak_live"], "greedy_updates": l["greedy_amp_updates"],
-               "greedy_judge": "owqs" if l["greedy_judge_owqs"] else "eowqs",
+               "greedy_best": "owqs" if l["greedy_best_owqs"] else "eowqs",
                "learned_peak": l["learned_peak_live"], "learned_updates": l["learned_amp_updates"],
                "accepted": l["learned_accepted"], "kept_peak": l["peak_live"], "kept_updates": l["amp_updates"]}
         if greedy_seconds is not None and l["peak_live"] <= 31:
             row["kept_seconds"] = gpu_seconds(h) if l["learned_accepted"] else greedy_seconds
-            if l["greedy_judge_owqs"]:
+            if l["greedy_best_owqs"]:
                 row["greedy_seconds"] = greedy_seconds
             ntimed += 1
         rows.append(row)
@@ -171,8 +171,8 @@ def summary(rows):
                   "kept_seconds_total": float(sum(r["kept_seconds"] for r in tr)),
                   "best_greedy_seconds_total": float(sum(r["greedy_seconds"] for r in tr))}
     return {"patterns": len(rows), "accepted": acc,
-            "judge": "best of the greedy EOWQS order and the greedy OWQS sweep order",
-            "best_greedy_is_owqs_sweep": sum(r["greedy_judge"] == "owqs" for r in rows),
+            "compared_with": "the better of the greedy EOWQS order and the greedy OWQS sweep order",
+            "best_greedy_is_owqs_sweep": sum(r["greedy_best"] == "owqs" for r in rows),
             "kept_never_worse": all((r["kept_peak"], r["kept_updates"]) <= (r["greedy_peak"], r["greedy_updates"])
                                     for r in rows),
             "mean_peak_live": {"eowqs_greedy": float(np.mean([r["eowqs_greedy_peak"] for r in rows])),
@@ -201,7 +201,7 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=6)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--batch-steps", type=int, default=2048)
-    ap.add_argument("--eval-sweep", action="store_true", help="judge with the full Section 5 sweep")
+    ap.add_argument("--eval-sweep", action="store_true", help="compare with the full Section 5 sweep")
     ap.add_argument("--out", default=DEFAULT_OUT)
     ap.add_argument("--timed", type=int, default=64, help="training patterns labelled by GPU timings")
     ap.add_argument("--timed-eval", type=int, default=200, help="held-out patterns whose orders are GPU-timed")

@@ -1,7 +1,7 @@
 """The learned reorder proposal on the GPU: the library's forward and
 backward kernels against the FP64 reference network (oracle/mlp.py), GPU
 training, and what the trained proposal gains over the greedy reordering it
-is judged by."""
+is checked against."""
 import json
 import os
 
@@ -102,7 +102,7 @@ def test_training_reduces_loss_and_proposal_is_never_worse(env):
     """Train on small random J/CZ patterns with the library's kernels, then
     reorder held-out patterns in EOWQS mode with the proposal: the kept order
     is never worse, by (peak live width, amplitude updates), than the best
-    greedy order, which the library uses as the judge; the gain over it is
+    greedy order, against which the library keeps or drops it; the gain over it is
     reported, not required."""
     torch, owqs = env
     X, first, target = _dataset(owqs, _small_set(40, 0))
