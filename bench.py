@@ -481,7 +481,7 @@ def recognition_leg(args, owqs, torch):
 def qft_leg(args, owqs, torch):
     """QFT-shaped pattern on 24 logical qubits (2784 measurements, peak 25
     live qubits), random normalised input, forced seeded outcomes, complex64
-    and complex128.  The pattern has no final swaps, so the exact output is
+    and complex128 (FP64 groups, and double-float groups).  The pattern has no final swaps, so the exact output is
     the inverse DFT (numpy FFT) of the bit-reversed input times 2^(n/2); per
     output the max-abs error after global-phase alignment and the fidelity
     |<ref|out>|^2 are reported for both precisions."""
@@ -499,10 +499,12 @@ def qft_leg(args, owqs, torch):
     ref = np.fft.ifft(wl.psi_in[rev]) * math.sqrt(1 << n)
     res = {"workload": "QFT-shaped J/CZ pattern, 24 logical qubits, random normalised input",
            "measurements": wl.pattern.K, "peak_m": rinfo["peak_m"], "amp_updates_per_run": upd}
-    for dtype, tdt in (("c64", torch.complex64), ("c128", torch.complex128)):
+    for key, dtype, tdt in (("c64", "c64", torch.complex64), ("c128", "c128", torch.complex128),
+                            ("c128_double_float", "c128", torch.complex128)):
         psi = torch.from_numpy(wl.psi_in.astype(np.complex64 if dtype == "c64" else np.complex128)).cuda()
         out = torch.empty(1 << n, dtype=tdt, device="cuda")
-        run = lambda: h.run(psi, dtype=dtype, outcomes=wl.outcomes, out=out)
+        run = lambda: h.run(psi, dtype=dtype, outcomes=wl.outcomes, out=out,
+                            double_float=key.endswith("double_float"))
         run()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -516,7 +518,7 @@ def qft_leg(args, owqs, torch):
         got = out.cpu().numpy().astype(np.complex128)
         ov = np.vdot(got, ref)
         aligned = got * (ov / abs(ov))
-        res[dtype] = {"ms_per_run": 1e3 * t, "amp_updates_per_s": upd / t,
+        res[key] = {"ms_per_run": 1e3 * t, "amp_updates_per_s": upd / t,
                       "max_abs_err_vs_exact": float(np.max(np.abs(aligned - ref))),
                       "fidelity": float(abs(ov) ** 2 / (np.vdot(got, got).real * np.vdot(ref, ref).real))}
         del out, psi

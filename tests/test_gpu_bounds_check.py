@@ -3,11 +3,13 @@ OWQS_BOUNDS_CHECK): every global access of the pass kernels is first checked
 against the extent of the buffer it touches.
 
 - Runs that take every launch kind (pass groups from a materialised and from
-  the virtual input, bulk-copy and register-tiled single passes, generic and
-  final passes, the input norm, factor joins, unitaries, sampled outcomes
-  by a checked guess and one measurement at a time on the device, EOWQS, the
-  allocation-free entry point) finish with no failed
-  check and give the release library's results.
+  the virtual input, exact-half and norm-summing groups, complex128 groups in
+  FP64 and in double-float, bulk-copy and register-tiled single passes,
+  generic and final passes, the input norm, factor joins and separate
+  sub-states, unitaries, sampled outcomes by a whole-run guess, by checked
+  launches and one measurement at a time on the device, EOWQS, asynchronous
+  runs, the allocation-free entry point) finish with no failed check and
+  give the release library's results.
 - With every extent shortened through the test hook, the checked build
   reports the accesses beyond them (skipping them, so nothing outside a
   buffer is touched) and the run fails with OWQS_ERR_CUDA.
@@ -75,6 +77,32 @@ def run_cases(out_path):
         res[f"{{dtype}}:static"] = (st, out.cpu().numpy(), probs)
         u, _ = h.unitary(dtype=dtype, outcomes=bits)
         res[f"{{dtype}}:unitary"] = (owqs.OK, u.cpu().numpy(), np.zeros(1))
+        # separate sub-states (arena), double-float groups, groups that sum
+        # every pass's norm, checked launches, an asynchronous run
+        wl = workloads.brickwork(10, 6)
+        h = owqs.load(wl.pattern)
+        h.reorder()
+        out, _, probs, st = h.run(None, dtype=dtype, outcomes=wl.outcomes, layout="substates", check=False)
+        res[f"{{dtype}}:substates"] = (st, out.cpu().numpy(), probs)
+        o = torch.empty(1 << 10, dtype=tdt, device="cuda")
+        h.run_async(None, o, dtype=dtype, outcomes=wl.outcomes)
+        _, probs, st = h.wait(check=False)
+        res[f"{{dtype}}:async"] = (st, o.cpu().numpy(), probs)
+        wl = workloads.brickwork(14, 8)
+        h = owqs.load(wl.pattern)
+        h.reorder()
+        psi = dev(random_state(SplitMix64(1305), 14))
+        out, _, probs, st = h.run(psi, dtype=dtype, outcomes=wl.outcomes, double_float=True, check=False)
+        res[f"{{dtype}}:df"] = (st, out.cpu().numpy(), probs)
+        wl = workloads.chain_measurements(14, 9, joined_every=0)
+        h = owqs.load(wl.pattern)
+        out, _, probs, st = h.run(dev(wl.psi_in), dtype=dtype, outcomes=wl.outcomes, layout="one_array", check=False)
+        res[f"{{dtype}}:chain"] = (st, out.cpu().numpy(), probs)
+        wl = workloads.brickwork_readout(7, 8, kept=2, with_input=True)
+        h = owqs.load(wl.pattern)
+        h.reorder()
+        out, _, probs, st = h.run(dev(wl.psi_in), dtype=dtype, policy="sampled", seed=3, check=False)
+        res[f"{{dtype}}:checked"] = (st, out.cpu().numpy(), probs)
     np.savez(out_path, **{{k + "|st": np.array(v[0]) for k, v in res.items()}},
              **{{k + "|out": v[1] for k, v in res.items()}}, **{{k + "|p": v[2] for k, v in res.items()}})
 
@@ -122,7 +150,7 @@ def test_every_launch_kind_passes_the_checks_and_matches_release(libs):
     rel = _child(script, build.LIB, "cases", d / "release.npz")
     chk = _child(script, checked, "cases", d / "checked.npz")
     keys = sorted(k[:-3] for k in rel.files if k.endswith("|st"))
-    assert len(keys) == 2 * (7 * 2 + 5)
+    assert len(keys) == 2 * (7 * 2 + 5 + 5)
     for k in keys:
         assert int(chk[k + "|st"]) == 0, (k, int(chk[k + "|st"]))
         assert int(rel[k + "|st"]) == int(chk[k + "|st"]), k
