@@ -62,6 +62,14 @@ __device__ __forceinline__ DF df_dot2(DF a, DF b, DF c, DF d) {
   e = fmaf(c.lo, d.hi, e);
   return fast_two_sum(s.hi, e);
 }
+// a * b (the product of the high parts exact, the cross terms rounded once)
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
 // acc += x^2 (x's square formed exactly in its high part)
 __device__ __forceinline__ void df_acc_sq(DF& acc, DF x) {
   const float p = x.hi * x.hi;
@@ -135,6 +143,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_group_df(const GroupParams G) {
   float4* pw = reinterpret_cast<float4*>(smem + NS * STAGE + 256);
   float* pct = reinterpret_cast<float*>(pw + kGroupMax);
   float2* accs = reinterpret_cast<float2*>(pct + kGroupMax * 8);  // [pass][thread]: double-float sums
+  // the output scales +-cprev * fin[g] as double-float, [sign][g]: converted
+  // once per block, so that the stores of a double-float output need no FP64
+  // instruction (GB300's FP64 pipe runs at 1/64 of the FP32 rate)
+  float2* scs = accs + kGroupMax * kBlock;
   // every pass's squared norm unless every probability is exactly 1/2
   // (GroupParams::half) or the run needs none; then only the last pass's (the
   // next launch divides by it) and the other slots get 2^-(j+1)
@@ -215,6 +227,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_group_df(const GroupParams G) {
   }
   for (int t = threadIdx.x; t < kGroupMax * 8; t += kBlock) pct[t] = G.pass[t / 8].ct[t % 8];
   for (int t = threadIdx.x; t < kGroupMax * kBlock; t += kBlock) accs[t] = make_float2(0.f, 0.f);
+  if (threadIdx.x < 2 * NC) {
+    const int g = threadIdx.x % NC;
+    const DF d = df_from((threadIdx.x >= NC ? -cprev : cprev) * G.find[g]);
+    scs[threadIdx.x] = make_float2(d.hi, d.lo);
+  }
   if (threadIdx.x == 0) {
     for (int q = 0; q < NS; ++q) {
       mbar_init(&full[q], 1);
@@ -281,19 +298,19 @@ __global__ void __launch_bounds__(kBlock, 2) k_group_df(const GroupParams G) {
         }
       }
       // the element's sign, the previous array's 1/sqrt(N) and the carried
-      // scales: exact powers of two and signs times cprev, applied in FP64
-      // (OUT_DF: scaled in double-float by the float pair of that factor)
-      const double f = ((b >> 31) & 1u) ? -cprev : cprev;
+      // scales: applied in FP64 to a complex128 output, in double-float (the
+      // block's converted table) to a double-float one
+      const uint32_t neg = (b >> 31) & 1u;
 #pragma unroll
       for (int g = 0; g < NC; ++g) {
-        const double sc = f * G.find[g];
         OWQS_IF_IN_EXTENT(L0 + G.outoff[g] + e, 1, G.out_cap, G.errflag) {
           if (OUT_DF) {
-            const DF s = df_from(sc);
-            const DF yr = df_dot2(s, x[g].re, DF{0.f, 0.f}, DF{0.f, 0.f});
-            const DF yi = df_dot2(s, x[g].im, DF{0.f, 0.f}, DF{0.f, 0.f});
+            const float2 s2 = scs[neg * NC + g];
+            const DF s{s2.x, s2.y};
+            const DF yr = df_mul(s, x[g].re), yi = df_mul(s, x[g].im);
             reinterpret_cast<float4*>(G.out)[L0 + G.outoff[g] + e] = make_float4(yr.hi, yr.lo, yi.hi, yi.lo);
           } else {
+            const double sc = (neg ? -cprev : cprev) * G.find[g];
             reinterpret_cast<double2*>(G.out)[L0 + G.outoff[g] + e] =
                 make_double2(sc * df_to(x[g].re), sc * df_to(x[g].im));
           }
@@ -345,7 +362,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_group_df(const GroupParams G) {
 template <int M, bool VIRT, bool IN_DF, bool OUT_DF>
 static cudaError_t launch_df_t(const GroupParams& G, cudaStream_t s) {
   constexpr int STAGE = 32768;
-  constexpr int SMEM = kDfStages * STAGE + 256 + kGroupMax * 16 + kGroupMax * 8 * 4 + kGroupMax * kBlock * 8;
+  constexpr int SMEM =
+      kDfStages * STAGE + 256 + kGroupMax * 16 + kGroupMax * 8 * 4 + kGroupMax * kBlock * 8 + 2 * 8 * 8;
   auto kern = k_group_df<M, VIRT, IN_DF, OUT_DF>;
   static int grid_cap = 0;
   static std::mutex mu;
