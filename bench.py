@@ -762,22 +762,35 @@ def run_owqs(args):
         run_e2e = lambda: h.run_host(host_in, host_out, dtype="c64", outcomes=wl.outcomes)
         run_e2e()
         e2e_steps = args.e2e_steps or args.steps
+        # the host link of this machine on the same pinned buffers: one plain copy
+        # each way (the end-to-end call moves these bytes before its first
+        # launch and after its last), before and after the end-to-end loops,
+        # and the copies alone for as many steps as the loops (the host link
+        # is shared with other work on the machine and can be slower while
+        # the loops run than in a single copy)
+        dev_in = torch.empty(1 << nin, dtype=torch.complex64, device="cuda")
+
+        def link_now():
+            res = {}
+            for name, fn in (("h2d", lambda: dev_in.copy_(host_in, non_blocking=True)),
+                             ("d2h", lambda: host_out.copy_(out64, non_blocking=True))):
+                fn()
+                tl = timed(fn, 3) / 3
+                nbytes = (1 << nin) * 8 if name == "h2d" else (1 << nout) * 8
+                res[name] = {"GBps": nbytes / tl / 1e9, "ms": 1e3 * tl}
+            return res
+
+        def copies_only():
+            dev_in.copy_(host_in, non_blocking=True)
+            host_out.copy_(out64, non_blocking=True)
+
+        link_before = link_now()
         sampler_e = ClockSampler(gpu_id)
         sampler_e.start()
         te = timed(run_e2e, e2e_steps)
         clocks_e2e = sampler_e.stop()
-        # the host link of this machine, measured on the same pinned buffers: one
-        # plain copy each way (the end-to-end call moves these bytes before
-        # its first launch and after its last)
-        dev_in = torch.empty(1 << nin, dtype=torch.complex64, device="cuda")
-        link = {}
-        for name, fn in (("h2d", lambda: dev_in.copy_(host_in, non_blocking=True)),
-                         ("d2h", lambda: host_out.copy_(out64, non_blocking=True))):
-            fn()
-            tl = timed(fn, 3) / 3
-            nbytes = (1 << nin) * 8 if name == "h2d" else (1 << nout) * 8
-            link[name] = {"GBps": nbytes / tl / 1e9, "ms": 1e3 * tl}
-        del dev_in
+        tc = timed(copies_only, e2e_steps)
+        link = link_now()
         # the same steps through owqs_run_async / owqs_wait with two runs in
         # flight: every step still copies its own input in and its output out
         # (two pinned output buffers in turn), but a step's input copy
@@ -799,7 +812,7 @@ def run_owqs(args):
         tp = timed(lambda: run_pipe(e2e_steps), 1)
         clocks_p = sampler_p.stop()
         pipe_ok = bool(torch.equal(host_out2, host_out))  # both hold the same step's result
-        del host_out2, outs
+        del host_out2, outs, dev_in
         e2e = {"value": replica_throughput(upd, e2e_steps, world, tp), "unit": UNIT,
                "h2d_bytes_per_step": (1 << nin) * 8, "d2h_bytes_per_step": (1 << nout) * 8 + 8 * (p.K + 3),
                "ms_per_step": 1e3 * tp / e2e_steps, "steps": e2e_steps, "clocks": clocks_p,
@@ -808,7 +821,8 @@ def run_owqs(args):
                "sync": {"value": replica_throughput(upd, e2e_steps, world, te), "unit": UNIT,
                         "api": "owqs_run with OWQS_IO_HOST, one call per step",
                         "ms_per_step": 1e3 * te / e2e_steps, "clocks": clocks_e2e},
-               "host_link": link,
+               "host_link": link, "host_link_before": link_before,
+               "copies_only_ms_per_step": 1e3 * tc / e2e_steps,
                "device_step_plus_copies_ms": 1e3 * t64 / args.steps + link["h2d"]["ms"] + link["d2h"]["ms"]}
 
     roof64, launches_per_step = roofline("c64")

@@ -41,13 +41,15 @@ __device__ __forceinline__ DF two_sum(float a, float b) {
   const float bb = s - a;
   return DF{s, (a - (s - bb)) + (b - bb)};
 }
-// a + b with the error of the low parts folded in: absolute error about
-// 2^-48 times the larger operand (enough here: the bounds checked are
-// absolute on amplitudes of at most 1, and the squared norms only add
-// positive terms)
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-  const DF s = two_sum(a.hi, b.hi);
-  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+// a + sg * b, sg = +-1, with the error of the low parts folded in: absolute
+// error about 2^-48 times the larger operand (enough here: the bounds checked
+// are absolute on amplitudes of at most 1).  The sign enters as an FMA by
+// +-1, which is exact, so no separate negation is needed.
+__device__ __forceinline__ DF df_add_signed(DF a, DF b, float sg) {
+  const float s = fmaf(sg, b.hi, a.hi);
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + fmaf(sg, b.hi, -bb);
+  return fast_two_sum(s, e + fmaf(sg, b.lo, a.lo));
 }
 __device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
 // a * b + c * d (one rounding of the cross terms), for the complex product
@@ -95,10 +97,8 @@ __device__ __forceinline__ void df_pass(CDF (&x)[1 << M], const float (&ct)[1 <<
     const CDF x0 = x[g0], x1 = x[g1];
     const DF vr = df_dot2(wr, x1.re, df_neg(wi), x1.im);
     const DF vi = df_dot2(wr, x1.im, wi, x1.re);
-    const DF c0r = ct[g0] < 0.f ? df_neg(vr) : vr, c0i = ct[g0] < 0.f ? df_neg(vi) : vi;
-    const DF c1r = ct[g1] < 0.f ? df_neg(vr) : vr, c1i = ct[g1] < 0.f ? df_neg(vi) : vi;
-    const CDF y0{df_add(x0.re, c0r), df_add(x0.im, c0i)};
-    const CDF y1{df_add(x0.re, c1r), df_add(x0.im, c1i)};
+    const CDF y0{df_add_signed(x0.re, vr, ct[g0]), df_add_signed(x0.im, vi, ct[g0])};
+    const CDF y1{df_add_signed(x0.re, vr, ct[g1]), df_add_signed(x0.im, vi, ct[g1])};
     if (NORM) {
       df_acc_sq(acc, y0.re);
       df_acc_sq(acc, y0.im);
