@@ -48,11 +48,11 @@ FALLBACK_HBM_GBS = 6800.0
 # sha256 prefix of the pass-group sources they were measured on (a changed
 # kernel reports null).  Both are pass groups on the full brickwork workload,
 # mean of three launches: c64 k_group<3, 0, SEQ> (2^28 complex64 amplitudes in
-# and out; 2147.6 MB read + 2095.6 MB written) and c128 k_group64<3, 0, 0>
-# (2^28 complex128; 4299.2 MB read + 4247.2 MB written).
+# and out; 2147.6 MB read + 2095.4 MB written) and c128 k_group64<3, 0, 0>
+# (2^28 complex128; 4298.7 MB read + 4247.0 MB written).
 # profiles/k_group_c64_brickwork28x40_dram.md.
-NCU_TRAFFIC = {("33986a87fed490c9", "c64"): (2147601408 + 2097735936 + 2147583232 + 2094633728 + 2147595008 + 2094318080) / 3.0,
-               ("33986a87fed490c9", "c128"): (4298327808 + 4248759296 + 4302077952 + 4247692032 + 4297135872 + 4245162752) / 3.0}
+NCU_TRAFFIC = {("fefe82cddcc8a760", "c64"): (2147667968 + 2097627904 + 2147591424 + 2094440960 + 2147593472 + 2094274304) / 3.0,
+               ("fefe82cddcc8a760", "c128"): (4299533056 + 4248800512 + 4298402560 + 4246980864 + 4298248192 + 4245296128) / 3.0}
 # nominal GB300 FP64 rate (no measured FP64 peak exists for this machine)
 FP64_PEAK_TFLOPS = 1.25
 # FP64 flops per output amplitude of the complex128 pass: complex multiply-add

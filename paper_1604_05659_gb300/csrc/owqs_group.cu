@@ -42,6 +42,19 @@ cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s) {
         break;
       }
     }
+    // slots read at run time; exact-half groups sum only the last pass's norm
+    constexpr uint32_t H = 1u << 30;
+    if (G.half) {
+      switch (G.m) {
+        case 1: return v ? launch_group_t<1, 9>(k_group<1, true, H>, G, s)
+                         : launch_group_t<1, 9>(k_group<1, false, H>, G, s);
+        case 2: return v ? launch_group_t<2, 9>(k_group<2, true, H>, G, s)
+                         : launch_group_t<2, 9>(k_group<2, false, H>, G, s);
+        case 3: return v ? launch_group_t<3, 9>(k_group<3, true, H>, G, s)
+                         : launch_group_t<3, 9>(k_group<3, false, H>, G, s);
+        default: return cudaErrorInvalidValue;
+      }
+    }
     switch (G.m) {
       case 1: return v ? launch_group_t<1, 9>(k_group<1, true>, G, s) : launch_group_t<1, 9>(k_group<1, false>, G, s);
       case 2: return v ? launch_group_t<2, 9>(k_group<2, true>, G, s) : launch_group_t<2, 9>(k_group<2, false>, G, s);

@@ -15,11 +15,12 @@
 namespace owqs {
 
 // VIRT: the group reads the virtual |+> input (G.in == nullptr); a separate
-// instantiation keeps the array-reading kernel free of the test.  SEQ != 0:
-// the group's register-slot sequence fixed at compile time (bits 24-27 the
-// number of passes k, bits 2j and 2j+1 the slot pass j measures, bit 30:
-// every probability is exactly 1/2 and no norm is summed); SEQ = 0 reads the
-// slots from the parameter block and dispatches on them per pass.
+// instantiation keeps the array-reading kernel free of the test.  SEQ bits
+// 24-27 nonzero: the group's register-slot sequence fixed at compile time
+// (bits 24-27 the number of passes k, bits 2j and 2j+1 the slot pass j
+// measures); zero: the kernel reads the slots from the parameter block and
+// dispatches on them per pass.  Bit 30: every probability of the group is
+// exactly 1/2 and only the last pass's norm is summed.
 template <int M, bool VIRT, uint32_t SEQ = 0>
 __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G);
 
@@ -229,12 +230,14 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
   const uint64_t gw = (uint64_t)blockIdx.x * NWARP + warp;
   const uint64_t step = (uint64_t)gridDim.x * NWARP;
   const uint64_t mine = gw < tiles ? (tiles - gw + step - 1) / step : 0;
-  const int k = SEQ ? (int)((SEQ >> 24) & 15u) : G.k;
-  // a sequence kernel with bit 30: every probability of the group is exactly
-  // 1/2 (GroupParams::half), so only the last pass's squared norm is summed:
-  // the next launch divides by it, so that the rounding in the array's norm
-  // does not build up from group to group
-  constexpr bool NORM = !(SEQ != 0 && ((SEQ >> 30) & 1u));
+  // bits 24-27 of SEQ nonzero: the pass count and the slots are compile-time
+  constexpr bool STATIC = ((SEQ >> 24) & 15u) != 0;
+  const int k = STATIC ? (int)((SEQ >> 24) & 15u) : G.k;
+  // bit 30 of SEQ: every probability of the group is exactly 1/2
+  // (GroupParams::half), so only the last pass's squared norm is summed: the
+  // next launch divides by it, so that the rounding in the array's norm does
+  // not build up from group to group
+  constexpr bool NORM = !((SEQ >> 30) & 1u);
   uint32_t lowbits[EPT], spread[EPT];
 #pragma unroll
   for (int q = 0; q < EPT; ++q) {
@@ -350,7 +353,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
         const GroupPass& P = G.pass[j];
         const uint32_t r0 = (b0 << (31 - j)) & 0x80000000u, r1 = (b1 << (31 - j)) & 0x80000000u;
         // a compile-time slot leaves one code variant per pass
-        const int slot = SEQ ? (int)((SEQ >> (2 * j)) & 3u) : P.slot;
+        const int slot = STATIC ? (int)((SEQ >> (2 * j)) & 3u) : P.slot;
         float2 acc = make_float2(0.f, 0.f);
         if (NORM || j == k - 1) {
           if (M == 1 || slot == 0) group_pass2<M, 0, true>(x, P, r0, r1, acc);
