@@ -109,3 +109,33 @@ def test_refusals(env):
     out, _, _, st = h.run(None, dtype="c64", outcomes=wl.outcomes, out=o[2])
     assert st == owqs.OK and torch.equal(o[0], o[1])
     h.close()
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_eowqs_and_zero_policy(env, dtype):
+    """EOWQS (every probability reported as 1/2, the output norm checked) and
+    the zero policy (all outcomes 0, reported by owqs_wait) give the
+    synchronous one-array run's results."""
+    torch, owqs = env
+    t = torch.complex64 if dtype == "c64" else torch.complex128
+    wl = workloads.qft(10)
+    p = wl.pattern
+    h = owqs.load(p)
+    h.reorder()
+    psi = torch.from_numpy(wl.psi_in).to(t).cuda()
+    for mode, policy in (("eowqs", "forced"), ("owqs", "zero"), ("eowqs", "zero")):
+        bits = wl.outcomes if policy == "forced" else None
+        ref, ref_oc, ref_p, st = h.run(psi, dtype=dtype, mode=mode, policy=policy, outcomes=bits,
+                                       layout="one_array", per_pass=True)
+        assert st == owqs.OK
+        o = torch.empty(1 << len(p.outputs), dtype=t, device="cuda")
+        h.run_async(psi, o, dtype=dtype, mode=mode, policy=policy, outcomes=bits)
+        oc, probs, st = h.wait()
+        assert st == owqs.OK, (mode, policy)
+        assert torch.equal(o, ref), (mode, policy)
+        assert np.array_equal(probs, ref_p), (mode, policy)
+        if policy == "zero":
+            assert not np.any(oc) and np.array_equal(oc, ref_oc)
+        if mode == "eowqs":
+            assert np.all(probs == 0.5)
+    h.close()
