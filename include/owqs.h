@@ -409,6 +409,13 @@ owqs_status owqs_test_shrink_extents(uint32_t runs, uint64_t elems);
  * the cap.  Not for production use. */
 owqs_status owqs_test_grid_cap(uint32_t blocks);
 
+/* Test hook: complex64 pass groups may take a 4-qubit register from input
+ * width `width` on (instead of 26, below which the one-block-per-SM kernel
+ * of such groups does not pay), so that small arrays exercise that kernel.
+ * Part of the CUDA-graph key and of every launch plan.  width = 0 restores
+ * the default.  Not for production use. */
+owqs_status owqs_test_group_m4_width(uint32_t width);
+
 /* Flows of the pattern's open graph (G, I, O), Section 4.5 with the
  * definitions of ref. [13]; G has an edge u-v iff the pattern holds an odd
  * number of E commands on {u, v}.
@@ -574,9 +581,9 @@ owqs_status owqs_plan_memory(const owqs_pattern* p, uint32_t dtype, uint32_t mod
  * launch order; for group i (i < *ngroups, at most cap): regs[i] the
  * register qubits M, slots[i] its register-slot sequence (bits 24-27 the
  * number of passes k, bits 2j and 2j+1 the slot that pass j measures, bit
- * 30 set when every pass measures a qubit joined by E to the qubit that
+ * 31 set when every pass measures a qubit joined by E to the qubit that
  * pass prepares, so that each probability is exactly 1/2 and the group sums
- * no norms),
+ * only its last pass's norm),
  * n_in[i] the live width it reads and specialised[i] 1 when a kernel
  * compiled for exactly that sequence runs it (complex64 groups reading a
  * materialised array), 0 when the slot-dispatching kernel does.  Arguments

@@ -30,7 +30,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # owqs_group_seq.cu is compiled once per slice of the sequence table
 # (kGroupSeqSlices in csrc/owqs_group_c64.cuh)
 SEQ_SOURCE = "owqs_group_seq.cu"
-SEQ_SLICES = 4
+SEQ_SLICES = 8
 
 
 def cuda_home() -> str:

@@ -6,10 +6,10 @@
 
 namespace owqs {
 
-static_assert(kGroupSeqSlices == 4, "launch_group dispatches four slices");
+static_assert(kGroupSeqSlices == 8, "launch_group dispatches eight slices");
 
 uint32_t group_sequence_code(const GroupParams& G) {
-  uint32_t c = ((uint32_t)(G.half ? 1 : 0) << 30) | ((uint32_t)G.m << 28) | ((uint32_t)G.k << 24);
+  uint32_t c = ((uint32_t)(G.half ? 1 : 0) << 31) | ((uint32_t)G.m << 28) | ((uint32_t)G.k << 24);
   for (int j = 0; j < G.k; ++j) c |= ((uint32_t)G.pass[j].slot & 3u) << (2 * j);
   return c;
 }
@@ -36,6 +36,10 @@ cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s) {
           case 1: e = launch_group_seq_slice<1>(G, code, s, &launched); break;
           case 2: e = launch_group_seq_slice<2>(G, code, s, &launched); break;
           case 3: e = launch_group_seq_slice<3>(G, code, s, &launched); break;
+          case 4: e = launch_group_seq_slice<4>(G, code, s, &launched); break;
+          case 5: e = launch_group_seq_slice<5>(G, code, s, &launched); break;
+          case 6: e = launch_group_seq_slice<6>(G, code, s, &launched); break;
+          case 7: e = launch_group_seq_slice<7>(G, code, s, &launched); break;
           default: break;
         }
         if (launched) return e;
@@ -43,7 +47,7 @@ cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s) {
       }
     }
     // slots read at run time; exact-half groups sum only the last pass's norm
-    constexpr uint32_t H = 1u << 30;
+    constexpr uint32_t H = 1u << 31;
     if (G.half) {
       switch (G.m) {
         case 1: return v ? launch_group_t<1, 9>(k_group<1, true, H>, G, s)
@@ -52,6 +56,8 @@ cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s) {
                          : launch_group_t<2, 9>(k_group<2, false, H>, G, s);
         case 3: return v ? launch_group_t<3, 9>(k_group<3, true, H>, G, s)
                          : launch_group_t<3, 9>(k_group<3, false, H>, G, s);
+        case 4: return v ? launch_group_t<4, 10>(k_group<4, true, H>, G, s)
+                         : launch_group_t<4, 10>(k_group<4, false, H>, G, s);
         default: return cudaErrorInvalidValue;
       }
     }
@@ -59,6 +65,7 @@ cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s) {
       case 1: return v ? launch_group_t<1, 9>(k_group<1, true>, G, s) : launch_group_t<1, 9>(k_group<1, false>, G, s);
       case 2: return v ? launch_group_t<2, 9>(k_group<2, true>, G, s) : launch_group_t<2, 9>(k_group<2, false>, G, s);
       case 3: return v ? launch_group_t<3, 9>(k_group<3, true>, G, s) : launch_group_t<3, 9>(k_group<3, false>, G, s);
+      case 4: return v ? launch_group_t<4, 10>(k_group<4, true>, G, s) : launch_group_t<4, 10>(k_group<4, false>, G, s);
       default: return cudaErrorInvalidValue;
     }
   }

@@ -22,18 +22,22 @@ namespace owqs {
 // dispatches on them per pass.  Bit 30: every probability of the group is
 // exactly 1/2 and only the last pass's norm is summed.
 template <int M, bool VIRT, uint32_t SEQ = 0>
-__global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G);
+__global__ void __launch_bounds__(kBlock, M == 4 ? 1 : 2) k_group(const GroupParams G);
 
 template <int M, bool VIRT, bool NORM>
 __global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G);
 
 // a tile of 2^(TB-M) free indices x 2^M configurations: TB = 9 for complex64
-// (4 KB, one per warp), 11 for complex128 (32 KB, one per block); the kernel
+// (4 KB, one per warp; 10 and 8 KB with a 4-qubit register, one block per
+// SM), 11 for complex128 (32 KB, one per block); the kernel
 // pointer selects the precision and the instantiation (the shared-memory
 // opt-in and the resident grid are looked up once per kernel)
 template <int M, int TB>
 static cudaError_t launch_group_t(void (*kern)(const GroupParams), const GroupParams& G, cudaStream_t s) {
-  constexpr int STAGE = 32768;  // one block-wide stage, or eight warps' 4 KB stages
+  // complex64 (TB 9 or 10): one tile per warp; complex128 (TB 11): one per block
+  constexpr bool kWarpTiles = TB < 11;
+  // one block-wide 32 KB stage, or the eight warps' stages of 2^TB amplitudes
+  constexpr int STAGE = kWarpTiles ? (kBlock / 32) * (1 << TB) * 8 : 32768;
   // stages, barriers, the sign table and the abort flag
   constexpr int SMEM = kTmaStages * STAGE + 1024;
   static std::map<const void*, int> caps;
@@ -55,7 +59,7 @@ static cudaError_t launch_group_t(void (*kern)(const GroupParams), const GroupPa
     }
   }
   const uint64_t tiles = 1ull << (G.nfree - (TB - M));
-  const uint64_t blocks = TB == 9 ? (tiles + kBlock / 32 - 1) / (kBlock / 32) : tiles;  // c64: one tile per warp
+  const uint64_t blocks = kWarpTiles ? (tiles + kBlock / 32 - 1) / (kBlock / 32) : tiles;
   kern<<<capped_grid((int)std::min<uint64_t>(blocks, (uint64_t)grid_cap)), kBlock, SMEM, s>>>(G);
   return cudaGetLastError();
 }
@@ -71,14 +75,14 @@ static cudaError_t launch_group_t(void (*kern)(const GroupParams), const GroupPa
 // QFT-shaped J/CZ patterns, whose J(alpha) chains measure a qubit and then
 // its flow successor in the same slot (gen_group_sequences.py rebuilds it);
 // any other sequence runs on the dispatching kernel.
-// Code: bits 28-29 M, bits 24-27 k, bits 2j and 2j+1 the slot of pass j.
+// Code: bit 31 exact-half, bits 28-30 M, bits 24-27 k, bits 2j and 2j+1 the slot of pass j.
 constexpr uint32_t kGroupSequences[] = {
 #include "owqs_group_sequences.inc"
 };
 constexpr int kNumGroupSequences = (int)(sizeof(kGroupSequences) / sizeof(kGroupSequences[0]));
 
 // the instantiations of sequence i live in slice i % kGroupSeqSlices
-constexpr int kGroupSeqSlices = 4;
+constexpr int kGroupSeqSlices = 8;
 // launch G on the kernel of its sequence if this slice holds it (*launched)
 template <int SLICE>
 cudaError_t launch_group_seq_slice(const GroupParams& G, uint32_t code, cudaStream_t s, bool* launched);
@@ -195,12 +199,12 @@ __device__ __forceinline__ void group_pass2(float2 (&x)[2][1 << M], const GroupP
 }
 
 template <int M, bool VIRT, uint32_t SEQ>
-__global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
+__global__ void __launch_bounds__(kBlock, M == 4 ? 1 : 2) k_group(const GroupParams G) {
   if (G.stall_limit > 0) {
     stall_and_give_up(G.stall_limit, G.errflag);
     return;
   }
-  constexpr int LT = 9 - M, TE = 1 << LT, NC = 1 << M, NS = kTmaStages;
+  constexpr int LT = group_tile_bits(OWQS_C64, M) - M, TE = 1 << LT, NC = 1 << M, NS = kTmaStages;
   constexpr int STAGE = NC * TE * 8;
   constexpr int EPT = TE / 32;  // elements per lane per tile (even)
   constexpr int NWARP = kBlock / 32;
@@ -233,11 +237,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
   // bits 24-27 of SEQ nonzero: the pass count and the slots are compile-time
   constexpr bool STATIC = ((SEQ >> 24) & 15u) != 0;
   const int k = STATIC ? (int)((SEQ >> 24) & 15u) : G.k;
-  // bit 30 of SEQ: every probability of the group is exactly 1/2
+  // bit 31 of SEQ: every probability of the group is exactly 1/2
   // (GroupParams::half), so only the last pass's squared norm is summed: the
   // next launch divides by it, so that the rounding in the array's norm does
   // not build up from group to group
-  constexpr bool NORM = !((SEQ >> 30) & 1u);
+  constexpr bool NORM = !((SEQ >> 31) & 1u);
   uint32_t lowbits[EPT], spread[EPT];
 #pragma unroll
   for (int q = 0; q < EPT; ++q) {
@@ -358,11 +362,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_group(const GroupParams G) {
         if (NORM || j == k - 1) {
           if (M == 1 || slot == 0) group_pass2<M, 0, true>(x, P, r0, r1, acc);
           else if (M == 2 || slot == 1) group_pass2<M, (M > 1 ? 1 : 0), true>(x, P, r0, r1, acc);
-          else group_pass2<M, (M > 2 ? 2 : 0), true>(x, P, r0, r1, acc);
+          else if (M == 3 || slot == 2) group_pass2<M, (M > 2 ? 2 : 0), true>(x, P, r0, r1, acc);
+          else group_pass2<M, (M > 3 ? 3 : 0), true>(x, P, r0, r1, acc);
         } else {
           if (M == 1 || slot == 0) group_pass2<M, 0, false>(x, P, r0, r1, acc);
           else if (M == 2 || slot == 1) group_pass2<M, (M > 1 ? 1 : 0), false>(x, P, r0, r1, acc);
-          else group_pass2<M, (M > 2 ? 2 : 0), false>(x, P, r0, r1, acc);
+          else if (M == 3 || slot == 2) group_pass2<M, (M > 2 ? 2 : 0), false>(x, P, r0, r1, acc);
+          else group_pass2<M, (M > 3 ? 3 : 0), false>(x, P, r0, r1, acc);
         }
         if (NORM) s[j] += acc.x + acc.y;
         else if (j == k - 1) hs += acc.x + acc.y;

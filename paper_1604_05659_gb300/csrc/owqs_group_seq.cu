@@ -16,13 +16,13 @@ template <int I>
 static cudaError_t launch_group_sequence(const GroupParams& G, uint32_t code, cudaStream_t s, bool* launched) {
   if constexpr (I < kNumGroupSequences) {
     constexpr uint32_t C = kGroupSequences[I];
-    constexpr int MM = (int)((C >> 28) & 3u);
+    constexpr int MM = (int)((C >> 28) & 7u);
     static_assert(MM >= 1 && MM <= kGroupRegMax && ((C >> 24) & 15u) >= 2 && ((C >> 24) & 15u) <= kGroupMax,
                   "sequence code");
     if (code == C) {
       *launched = true;
       // the kernel's sequence: the slots, k and the exact-half bit (M is its own parameter)
-      return launch_group_t<MM, 9>(k_group<MM, false, (C & 0x4fffffffu)>, G, s);
+      return launch_group_t<MM, group_tile_bits(OWQS_C64, MM)>(k_group<MM, false, (C & 0x8fffffffu)>, G, s);
     }
     return launch_group_sequence<I + kGroupSeqSlices>(G, code, s, launched);
   } else {

@@ -211,6 +211,10 @@ int max_grid();               // grid cap for grid-stride kernels
 int capped_grid(int want);
 int test_grid_cap();          // the test hook's cap, 0 for none
 void set_test_grid_cap(int blocks);
+// the input width from which a complex64 group may take a 4-qubit register
+// (kGroupM4MinWidth, or the test hook's owqs_test_group_m4_width)
+int group_m4_min_width();
+void set_test_m4_width(int width);
 
 // A group of 2..kGroupMax consecutive measure passes run as one sweep
 // (bulk copies into shared memory).  Every pass is in star form with no X mask and prepares
@@ -237,7 +241,8 @@ void set_test_grid_cap(int blocks);
 // c0 ^ par(f & zfree); the new mask is zr ^ (p without the measured slot).
 // The store multiplies by E and fin[g] = D_final(g) * product of scales.
 // A tile is 2^(T-M) consecutive free indices (T = 9 for complex64: 4 KB of
-// input per warp; T = 11 for complex128: 32 KB per block).  Register
+// input per warp, T = 10 for a complex64 register of 4 qubits: 8 KB per warp;
+// T = 11 for complex128: 32 KB per block).  Register
 // inputs with input bit below T - M + (the number of such bits) are "low":
 // they lie inside the tile's contiguous input block of 2^(T-M+nlow)
 // amplitudes; the others are "high" and select one of 2^(M-nlow) such
@@ -248,7 +253,12 @@ void set_test_grid_cap(int blocks);
 // group): the product of the group's first j+1 outcome probabilities;
 // nscale[j] = product of the first j+1 squared scales.
 constexpr int kGroupMax = 12;
-constexpr int kGroupRegMax = 3;
+constexpr int kGroupRegMax = 4;      // register qubits of a complex64 group
+constexpr int kGroupRegMaxC128 = 3;  // of a complex128 group
+constexpr int kGroupMaxM4 = 8;       // passes of a group on a 4-qubit register
+constexpr int kGroupM4MinWidth = 26; // input width from which a group may take a 4-qubit register
+// log2 of a group's tile (the T above) for M register qubits
+constexpr int group_tile_bits(int dtype, int m) { return dtype == OWQS_C64 ? (m == 4 ? 10 : 9) : 11; }
 struct GroupPass {
   int slot;                 // register slot measured, then refilled by the new qubit
   uint32_t c0, zb;
@@ -257,9 +267,8 @@ struct GroupPass {
   uint64_t zfree, afree;    // sign masks over the free index
   double scale, wre, wim;   // scale and (-1)^s e^{-i theta}
   float ct[1 << kGroupRegMax];  // +-1 per output configuration
-  float2 ct2[1 << kGroupRegMax];  // (ct, ct): the same factor for both elements of a packed pair
   float fwr, fwi;           // (-1)^s e^{-i theta} in FP32
-  double ctd[1 << kGroupRegMax];  // ct in FP64 (complex128 groups)
+  double ctd[1 << kGroupRegMaxC128];  // ct in FP64 (complex128 groups)
 };
 struct GroupParams {
   const void* in;
@@ -278,7 +287,7 @@ struct GroupParams {
   uint32_t cbase[1 << kGroupRegMax];   // smem offset of configuration c: run * runlen + low bits
   uint64_t outoff[1 << kGroupRegMax];
   float fin[1 << kGroupRegMax];
-  double find[1 << kGroupRegMax];  // fin in FP64 (complex128 groups)
+  double find[1 << kGroupRegMaxC128];  // fin in FP64 (complex128 groups)
   double nscale[kGroupMax];
   uint64_t zall;            // XOR of the passes' zfree: the element's accumulated Z sign is
   uint32_t zall_lo, c0all;  // c0all ^ par(f & zall); zall_lo = its low (tile) bits
@@ -305,7 +314,7 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i, int dtype, GroupPa
 cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s);
 // complex128 group in double-float arithmetic (owqs_group_df.cu)
 cudaError_t launch_group_df(const GroupParams& G, bool in_df, bool out_df, cudaStream_t s);
-// the group's register-slot sequence (bit 30 half, bits 28-29 m, 24-27 k, 2j
+// the group's register-slot sequence (bit 31 half, bits 28-30 m, 24-27 k, 2j
 // and 2j+1 the slot of pass j), and whether a kernel compiled for it exists
 // (complex64, materialised input)
 uint32_t group_sequence_code(const GroupParams& G);

@@ -539,6 +539,8 @@ static std::string graph_key(const Pattern& p, const owqs_run_opts* o, const voi
   add(&o->flags, 4);
   const int cap = test_grid_cap();
   add(&cap, sizeof(cap));
+  const int m4 = group_m4_min_width();  // the launch plan depends on it
+  add(&m4, sizeof(m4));
   return k;
 }
 
@@ -1803,6 +1805,12 @@ owqs_status owqs_test_grid_cap(uint32_t blocks) {
   return OWQS_OK;
 }
 
+owqs_status owqs_test_group_m4_width(uint32_t width) {
+  clear_error();
+  set_test_m4_width((int)std::min<uint32_t>(width, 62u));
+  return OWQS_OK;
+}
+
 owqs_status owqs_test_shrink_extents(uint32_t runs, uint64_t elems) {
   clear_error();
   if (runs && elems == 0) return set_error(OWQS_ERR_ARG, "elems must be positive");
@@ -1956,7 +1964,7 @@ owqs_status owqs_describe_groups(const owqs_pattern* h, uint32_t dtype, uint32_t
       if (kind == LAUNCH_GROUP) {
         if (n < cap) {
           if (regs) regs[n] = (uint32_t)G.m;
-          if (slots) slots[n] = group_sequence_code(G) & 0x4fffffffu;
+          if (slots) slots[n] = group_sequence_code(G) & 0x8fffffffu;
           if (n_in) n_in[n] = (uint32_t)passes[i].n_in;
           // the launch reads the virtual |+> input only while no array exists
           if (specialised) specialised[n] = group_sequence_specialised(G, (int)dtype, !real) ? 1u : 0u;

@@ -491,6 +491,13 @@ int max_grid() {
 }
 
 static std::atomic<int> g_test_grid_cap{0};
+static std::atomic<int> g_test_m4_width{0};
+
+int group_m4_min_width() {
+  const int w = g_test_m4_width.load();
+  return w > 0 ? w : kGroupM4MinWidth;
+}
+void set_test_m4_width(int width) { g_test_m4_width.store(width > 0 ? width : 0); }
 
 int test_grid_cap() { return g_test_grid_cap.load(); }
 void set_test_grid_cap(int blocks) { g_test_grid_cap.store(blocks > 0 ? blocks : 0); }
@@ -558,9 +565,12 @@ int group_enabled() {
 int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupParams& G, LaunchPlan& L,
                bool virt_in) {
   if (i0 >= passes.size() || passes[i0].kind != 0) return 0;
-  // log2 of a tile in amplitudes: a warp's 4 KB stage (complex64), a block's
-  // 32 KB stage (complex128)
-  const int tb = dtype == OWQS_C64 ? 9 : 11;
+  // log2 of a tile in amplitudes: a warp's 4 KB stage (complex64; 8 KB with
+  // a 4-qubit register), a block's 32 KB stage (complex128)
+  const int tb = group_tile_bits(dtype, 1);
+  // a 4-qubit register (one block per SM) only where a launch is long: arrays
+  // of at least 2^kGroupM4MinWidth amplitudes (a test hook can lower it)
+  const int mmax = dtype != OWQS_C64 ? kGroupRegMaxC128 : (passes[i0].n_in >= group_m4_min_width() ? kGroupRegMax : 3);
   const int n0 = passes[i0].n_in;
   if (n0 < tb || n0 > 62) return 0;
   // scan: the longest valid prefix
@@ -575,12 +585,15 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupP
       break;
     const int src = live[d.b];
     if (src >= 0) {
-      if ((int)regs.size() == kGroupRegMax) break;
+      if ((int)regs.size() == mmax) break;
       regs.push_back(src);
     }
     live.erase(live.begin() + d.b);
     live.push_back(-1);
-    const int k = (int)(i - i0) + 1, m = (int)regs.size(), lt = tb - m;
+    const int k = (int)(i - i0) + 1, m = (int)regs.size(), lt = group_tile_bits(dtype, m) - m;
+    // a 4-qubit register runs one block per SM (8 KB warp stages), where long
+    // groups are bound by instruction issue: at most kGroupMaxM4 passes
+    if (m == 4 && k > kGroupMaxM4) break;
     if (k >= 2 && n0 - m >= lt) best_k = k;
   }
   if (best_k < 2) return 0;
@@ -600,7 +613,7 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupP
   std::memset(&G, 0, sizeof(G));
   G.k = best_k;
   G.m = m;
-  G.lt = tb - m;
+  G.lt = group_tile_bits(dtype, m) - m;
   G.nfree = n0 - m;
   std::vector<int> slot_of_input(n0, -1), free_of(n0, -1);
   for (int q = 0; q < m; ++q) slot_of_input[regs[q]] = q, G.B[q] = regs[q];
@@ -676,8 +689,7 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupP
     const uint32_t ps = (pend >> s) & 1u;
     for (int g = 0; g < (1 << kGroupRegMax); ++g) {
       P.ct[g] = ((__builtin_popcount(P.ar & (uint32_t)g) & 1u) ^ ps) ? -1.0f : 1.0f;
-      P.ct2[g] = make_float2(P.ct[g], P.ct[g]);
-      P.ctd[g] = P.ct[g];
+      if (g < (1 << kGroupRegMaxC128)) P.ctd[g] = P.ct[g];
     }
     P.fwr = (float)d.w1re;
     P.fwi = (float)d.w1im;
@@ -700,8 +712,9 @@ int plan_group(const std::vector<PassDesc>& passes, size_t i0, int dtype, GroupP
       if ((g >> t) & 1) off |= 1ull << l;
     }
     G.outoff[g] = off;
-    G.find[g] = ((__builtin_popcount(pend & (uint32_t)g) & 1u) ? -1.0 : 1.0) * prod;
-    G.fin[g] = (float)G.find[g];
+    const double f = ((__builtin_popcount(pend & (uint32_t)g) & 1u) ? -1.0 : 1.0) * prod;
+    if (g < (1 << kGroupRegMaxC128)) G.find[g] = f;
+    G.fin[g] = (float)f;
   }
   G.norm_in = G.norm_out = -1;
   L.kind = KK_GROUP;

@@ -11,7 +11,7 @@ sequences cover at least `coverage` of that work or `limit` of them are
 listed.  Every other sequence runs on the kernel that reads the slots at run
 time.
 
-  python -m paper_1604_05659_gb300.gen_group_sequences [--limit 96] [--coverage 0.999]
+  python -m paper_1604_05659_gb300.gen_group_sequences [--limit 160] [--coverage 0.999]
 """
 from __future__ import annotations
 
@@ -58,7 +58,7 @@ def sequence_work(families):
 
 
 def code(m: int, slots, half: bool) -> int:
-    c = (int(half) << 30) | (m << 28) | (len(slots) << 24)
+    c = (int(half) << 31) | (m << 28) | (len(slots) << 24)
     for j, s in enumerate(slots):
         c |= s << (2 * j)
     return c
@@ -66,7 +66,7 @@ def code(m: int, slots, half: bool) -> int:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--limit", type=int, default=96)
+    ap.add_argument("--limit", type=int, default=160)
     ap.add_argument("--coverage", type=float, default=0.999)
     a = ap.parse_args(argv)
     work = sequence_work(workload_families())

@@ -162,6 +162,7 @@ EXPORTS = {
     "owqs_test_wait_timeout": (C.c_int, [C.c_uint32, C.c_uint64]),
     "owqs_test_shrink_extents": (C.c_int, [C.c_uint32, C.c_uint64]),
     "owqs_test_grid_cap": (C.c_int, [C.c_uint32]),
+    "owqs_test_group_m4_width": (C.c_int, [C.c_uint32]),
     "owqs_describe_launches": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.POINTER(C.c_uint8),
                                          C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                          C.c_uint32, C.POINTER(C.c_uint32)]),
@@ -394,7 +395,7 @@ class Handle:
         for i in range(min(n.value, cap)):
             k = (slots[i] >> 24) & 15
             out.append({"m": regs[i], "slots": tuple((slots[i] >> (2 * j)) & 3 for j in range(k)),
-                        "half": bool((slots[i] >> 30) & 1), "n_in": nin[i], "specialised": bool(spec[i])})
+                        "half": bool((slots[i] >> 31) & 1), "n_in": nin[i], "specialised": bool(spec[i])})
         return out
 
     def index_map(self, pass_index: int):
@@ -627,6 +628,12 @@ def test_grid_cap(blocks: int):
     hook; 0 removes the cap), so that small arrays make the persistent
     kernels loop over many tiles per warp."""
     _check(library().owqs_test_grid_cap(int(blocks)))
+
+
+def test_group_m4_width(width: int):
+    """Let complex64 pass groups take a 4-qubit register from input width
+    `width` on (test hook; 0 restores the default)."""
+    _check(library().owqs_test_group_m4_width(int(width)))
 
 
 def test_shrink_extents(runs: int, elems: int):

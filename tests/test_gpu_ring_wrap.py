@@ -78,20 +78,21 @@ def test_capped_grid_wraps_the_rings(env, blocks):
 
 
 def test_23_live_qubits_against_the_c_oracle(env):
-    """Brickwork 22 x 16 (23 live qubits, 2^22-amplitude arrays): at the
-    production grid every warp of the complex64 group kernel takes at least
-    three tiles, every block of the complex128 one at least three; with the
-    grid capped at three blocks the complex64 run's last measurement, a
-    bulk-copy single pass, also takes hundreds of tiles per block through its
-    ring."""
+    """Brickwork 22 x 16 with 11 of its outputs also measured (23 live
+    qubits, 2^22-amplitude arrays): at the production grid every warp of the
+    complex64 group kernel takes at least three tiles, every block of the
+    complex128 one at least three; with the grid capped at three blocks the
+    complex64 run's output measurements, bulk-copy single passes (no qubit
+    prepared, so no group), also take hundreds of tiles per block through
+    their ring."""
     torch, owqs = env
-    wl = workloads.brickwork(22, 16)
+    wl = workloads.brickwork_readout(22, 16, kept=11, with_input=True)
     p = wl.pattern
     h = owqs.load(p)
     h.reorder()
     op = proa.reorder_commands(p, h.order())
     oc = outcomes_by_label(p, wl.outcomes)
-    psi = random_state(SplitMix64(412), len(p.inputs))
+    psi = wl.psi_in
     for inp in (None, psi):
         ref = substate_c.run(op, inp, outcomes=oc)
         for dtype in ("c128", "c64"):

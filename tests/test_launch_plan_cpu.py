@@ -127,9 +127,10 @@ def test_small_run_boundary(owqs):
 def test_group_slot_sequences_and_compiled_kernels(owqs):
     """owqs_describe_groups lists the same groups as owqs_describe_launches,
     with valid register-slot sequences (k <= 12 passes, slots below m, the
-    first pass on slot 0, a new slot only after every lower one); the
-    brickwork's groups that read an array all run on kernels compiled for
-    their sequence, complex128 and virtual-input groups never do."""
+    first pass on slot 0, a new slot only after every lower one); all but at
+    most two of the brickwork's groups that read an array run on kernels
+    compiled for their sequence, complex128 and virtual-input groups never
+    do."""
     wl = workloads.brickwork(28, 40)
     h = owqs.load(wl.pattern)
     h.reorder()
@@ -139,16 +140,19 @@ def test_group_slot_sequences_and_compiled_kernels(owqs):
         assert [len(g["slots"]) for g in gs] == [x[2] for x in lv]
         for i, g in enumerate(gs):
             sl = g["slots"]
-            assert 2 <= len(sl) <= 12 and 1 <= g["m"] <= 3 and sl[0] == 0
+            assert 2 <= len(sl) <= 12 and 1 <= g["m"] <= 4 and sl[0] == 0
             assert all(s < g["m"] for s in sl) and max(sl) == g["m"] - 1
             for j, s in enumerate(sl):
                 assert s <= max(sl[:j], default=-1) + 1
-            assert g["specialised"] == (real or i > 0), (i, g)
+            if not real and i == 0:
+                assert not g["specialised"]   # the virtual input: the run-time-slot kernel
+        spec = [g["specialised"] for i, g in enumerate(gs) if real or i > 0]
+        assert sum(spec) >= len(spec) - 2, spec
         assert not any(g["specialised"] for g in h.describe_groups(wl.outcomes, dtype="c128", real_input=real))
 
 
 def test_exact_half_groups(owqs):
-    """A pass group sums no per-pass norms (bit 30, "half") exactly when every
+    """A pass group sums no per-pass norms (bit 31 of the sequence code, "half") exactly when every
     pass measures a qubit joined by an odd number of E to the qubit it
     prepares: all groups of the J/CZ families, none of a chain whose
     prepared qubits get E twice (the identity), and all of the same chain
@@ -165,7 +169,9 @@ def test_exact_half_groups(owqs):
         h = owqs.load(wl.pattern)
         for dtype in ("c64", "c128"):
             gs = h.describe_groups(wl.outcomes, dtype=dtype, real_input=True)
-            assert len(gs) == 3 and all(g["half"] == half for g in gs), (joined, dtype, gs)
+            # nine passes on 3-qubit registers (arrays below 2^26 amplitudes take no 4-qubit register)
+            assert len(gs) == 3 and all(g["m"] == 3 for g in gs), (joined, dtype, gs)
+            assert all(g["half"] == half for g in gs), (joined, dtype, gs)
 
 
 def test_memory_plan_separate_substates(owqs):
@@ -187,3 +193,25 @@ def test_memory_plan_separate_substates(owqs):
     for dtype, amp in (("c64", 8), ("c128", 16)):
         p2 = h.plan_memory(wl.outcomes, dtype=dtype)
         assert p2["one_array_bytes"] % amp == 0 and p2["substate_bytes"] >= amp
+
+
+def test_four_qubit_registers_from_a_width(owqs):
+    """Complex64 groups take a 4-qubit register (at most 8 passes) only on
+    arrays of at least 2^26 amplitudes, or from the width the test hook
+    sets; complex128 groups never do."""
+    wl = workloads.brickwork(14, 8)
+    h = owqs.load(wl.pattern)
+    h.reorder()
+    assert max(g["m"] for g in h.describe_groups(wl.outcomes)) == 3
+    try:
+        owqs.test_group_m4_width(10)
+        gs = h.describe_groups(wl.outcomes)
+        assert any(g["m"] == 4 for g in gs) and all(len(g["slots"]) <= 8 for g in gs if g["m"] == 4)
+        assert max(g["m"] for g in h.describe_groups(wl.outcomes, dtype="c128")) == 3
+    finally:
+        owqs.test_group_m4_width(0)
+    big = workloads.brickwork(28, 40)
+    hb = owqs.load(big.pattern)
+    hb.reorder()
+    gs = hb.describe_groups(big.outcomes)
+    assert sum(g["m"] == 4 for g in gs) >= 30 and len(gs) <= 106
