@@ -46,13 +46,14 @@ def workload_name(rows: int, cols: int) -> str:
 FALLBACK_HBM_GBS = 6800.0
 # ncu DRAM bytes (read + write) per launch of the dominant kernel, keyed by the
 # sha256 prefix of the pass-group sources they were measured on (a changed
-# kernel reports null).  Both are pass groups on the full brickwork workload,
-# mean of three launches: c64 k_group<3, 0, SEQ> (2^28 complex64 amplitudes in
-# and out; 2147.6 MB read + 2095.4 MB written) and c128 k_group64<3, 0, 0>
-# (2^28 complex128; 4298.7 MB read + 4247.0 MB written).
-# profiles/k_group_c64_brickwork28x40_dram.md.
-NCU_TRAFFIC = {("fefe82cddcc8a760", "c64"): (2147667968 + 2097627904 + 2147591424 + 2094440960 + 2147593472 + 2094274304) / 3.0,
-               ("fefe82cddcc8a760", "c128"): (4299533056 + 4248800512 + 4298402560 + 4246980864 + 4298248192 + 4245296128) / 3.0}
+# kernel reports null).  Both are pass groups on the full brickwork workload:
+# c64, the mean over all 105 group launches of one run (k_group on 2-, 3- and
+# 4-qubit registers, 2^28 complex64 amplitudes in and out, the first one
+# reading the virtual input; 2127.2 MB read + 2094.7 MB written), and c128,
+# the mean of three k_group64<3, 0, 0> launches (2^28 complex128; 4299.4 MB
+# read + 4247.3 MB written).  profiles/k_group_c64_brickwork28x40_dram.md.
+NCU_TRAFFIC = {("320ca87b93aac192", "c64"): (223356237312 + 219946280192) / 105.0,
+               ("320ca87b93aac192", "c128"): (12898334720 + 12741801728) / 3.0}
 # nominal GB300 FP64 rate (no measured FP64 peak exists for this machine)
 FP64_PEAK_TFLOPS = 1.25
 # FP64 flops per output amplitude of the complex128 pass: complex multiply-add
