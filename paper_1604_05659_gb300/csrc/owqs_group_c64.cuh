@@ -259,6 +259,49 @@ __global__ void __launch_bounds__(kBlock, M == 4 ? 1 : 2) k_group(const GroupPar
   }
   const bool pair_contig = (G.lowmask & 1u) == 0u;
 
+  // Copies of a tile: its 2^M configurations arrive as nruns contiguous runs.
+  // Sequence kernels of 11 or more passes on at most 3 register qubits are
+  // bound by instruction issue: lane r < nruns copies run r, so that the
+  // warp spends one instruction on all of them.  The others (closer to the
+  // memory bound, where this measured slower) issue every run from lane 0.
+  constexpr bool WARP_ISSUE = M <= 3 && ((SEQ >> 24) & 15u) >= 11;
+  int wsorted[M];  // WARP_ISSUE: the register's input bits, ascending
+#pragma unroll
+  for (int q = 0; q < M; ++q) wsorted[q] = G.B[q];
+#pragma unroll
+  for (int q = 0; q < M; ++q)
+#pragma unroll
+    for (int r = q + 1; r < M; ++r)
+      if (wsorted[r] < wsorted[q]) {
+        const int tmp = wsorted[q];
+        wsorted[q] = wsorted[r];
+        wsorted[r] = tmp;
+      }
+  uint64_t my_runoff = 0;  // WARP_ISSUE: this lane's run
+#pragma unroll
+  for (int r = 0; r < NC; ++r)
+    if (lane == r) my_runoff = G.runoff[r];
+  const bool my_run = lane < G.nruns;
+
+  auto issue_warp = [&](uint64_t i) {  // WARP_ISSUE: the whole warp, converged
+    const int st = (int)(i % NS);
+    float2* buf = reinterpret_cast<float2*>(wsm + st * STAGE);
+    uint64_t ib = (gw + i * step) << LT;
+#pragma unroll
+    for (int q = 0; q < M; ++q) ib = ins0(ib, wsorted[q]);
+#ifdef OWQS_BOUNDS_CHECK
+    const bool ok = !my_run || in_extent(ib + my_runoff, G.runlen, G.in_cap, G.errflag);
+    if (!__all_sync(0xffffffffu, ok)) {  // a run outside the input: no copy, the run reports the error
+      if (lane == 0) mbar_arrive(&full[st]);
+      return;
+    }
+#endif
+    // the stage's byte count is armed before any of its copies is issued
+    if (lane == 0) mbar_expect_tx(&full[st], (unsigned)STAGE);
+    __syncwarp();
+    if (my_run) bulk_g2s(buf + lane * G.runlen, in + ib + my_runoff, G.runlen * (unsigned)sizeof(float2), &full[st]);
+  };
+
   auto issue = [&](uint64_t i) {  // lane 0 of the warp
     const int st = (int)(i % NS);
     if (virt) {  // no input array: the stage only paces the loop
@@ -304,8 +347,11 @@ __global__ void __launch_bounds__(kBlock, M == 4 ? 1 : 2) k_group(const GroupPar
   if (threadIdx.x == 0) *abort_flag = 0;
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
-  if (lane == 0)
+  if (WARP_ISSUE && !virt) {
+    for (uint64_t q = 0; q < mine && q < (uint64_t)NS; ++q) issue_warp(q);
+  } else if (lane == 0) {
     for (uint64_t q = 0; q < mine && q < (uint64_t)NS; ++q) issue(q);
+  }
 
   float s[kGroupMax];
 #pragma unroll
@@ -393,7 +439,11 @@ __global__ void __launch_bounds__(kBlock, M == 4 ? 1 : 2) k_group(const GroupPar
     }
     // every lane has read the stage: refill it with this warp's tile i + NS
     __syncwarp();
-    if (lane == 0 && issued < mine) issue(issued);
+    if (WARP_ISSUE && !virt) {
+      if (issued < mine) issue_warp(issued);
+    } else if (lane == 0 && issued < mine) {
+      issue(issued);
+    }
     if (issued < mine) ++issued;
   }
   __syncthreads();

@@ -162,6 +162,62 @@ __global__ void __launch_bounds__(kBlock) k_generic(const PassParams P) {
   }
 }
 
+// Final pass (corrections and output order, MODE 2 above) from an input
+// array: four outputs per thread and iteration, whose four loads are issued
+// before any of them is used.  With one 8-byte load in flight per thread the
+// resident grid keeps about 2.5 MB in flight, too little to cover HBM
+// latency at full bandwidth; four loads keep about four times that.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_final(const PassParams P) {
+  using V = typename Cplx<T>::V;
+  constexpr int U = 4;
+  const V* __restrict__ in = reinterpret_cast<const V*>(P.in);
+  V* __restrict__ out = reinterpret_cast<V*>(P.out);
+  const T sc = (T)(P.scale * prev_scale(P));
+  const uint64_t nout = 1ull << P.n_out;
+  const uint64_t inmask = (1ull << P.n_in) - 1ull;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nout; j += U * stride) {
+    V x[U];
+    uint32_t neg[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t jj = j + u * stride;
+      x[u].x = x[u].y = (T)0;
+      neg[u] = 0;
+      if (jj < nout) {
+        uint64_t k = jj;
+        if (!P.identity_perm) {
+          k = 0;
+          for (int i = 0; i < P.n_out; ++i) k |= ((jj >> i) & 1ull) << P.perm[i];
+        }
+        const uint64_t i = (k ^ P.xmask) & inmask;
+        if (in_extent(i, 1, P.in_cap, P.errflag)) x[u] = in[i];
+        neg[u] = qsign(P, k);
+      }
+    }
+    T part = (T)0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t jj = j + u * stride;
+      if (jj < nout) {
+        const T f = neg[u] ? -sc : sc;
+        V y;
+        y.x = f * x[u].x;
+        y.y = f * x[u].y;
+        if (in_extent(jj, 1, P.out_cap, P.errflag)) out[jj] = y;
+        part += y.x * y.x + y.y * y.y;
+      }
+    }
+    acc += (double)part;
+  }
+  if (P.norm_out >= 0) {
+    const double a1[1] = {acc};
+    reduce_to_slots<1>(a1, P.partials, P.counter, P.norms, P.norm_out);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // A whole run of a small pattern in one warp (every array of the run at most
 // 2^kSmallLog amplitudes and at most kSmallMaxPasses passes, where one launch
@@ -706,7 +762,7 @@ static cudaError_t launch_t(const PassParams& P, const LaunchPlan& L, cudaStream
       else go(k_generic<T, 1, 0>, P, L.grid, s);
       break;
     case KK_FINAL:
-      if (!virt) go(k_generic<T, 2, 0>, P, L.grid, s);
+      if (!virt) go(k_final<T>, P, L.grid, s);
       else if (P.vdiag) go(k_generic<T, 2, 2>, P, L.grid, s);
       else go(k_generic<T, 2, 1>, P, L.grid, s);
       break;
