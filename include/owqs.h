@@ -585,8 +585,9 @@ owqs_status owqs_plan_memory(const owqs_pattern* p, uint32_t dtype, uint32_t mod
  * pass prepares, so that each probability is exactly 1/2 and the group sums
  * only its last pass's norm),
  * n_in[i] the live width it reads and specialised[i] 1 when a kernel
- * compiled for exactly that sequence runs it (complex64 groups reading a
- * materialised array), 0 when the slot-dispatching kernel does.  Arguments
+ * compiled for exactly that sequence runs it (complex64 groups reading an
+ * array, or reading the virtual |+> input on a register of at most 2
+ * qubits), 0 when the slot-dispatching kernel does.  Arguments
  * as owqs_describe_launches; any output pointer may be NULL. */
 owqs_status owqs_describe_groups(const owqs_pattern* p, uint32_t dtype, uint32_t mode, uint32_t real_input,
                                 const uint8_t* outcomes, uint32_t* regs, uint32_t* slots, uint32_t* n_in,

@@ -15,7 +15,8 @@ uint32_t group_sequence_code(const GroupParams& G) {
 }
 
 bool group_sequence_specialised(const GroupParams& G, int dtype, bool virt_in) {
-  if (dtype != OWQS_C64 || virt_in) return false;
+  // from the virtual |+> input: the sequence kernels of registers of at most 2 qubits
+  if (dtype != OWQS_C64 || (virt_in && G.m > 2)) return false;
   const uint32_t c = group_sequence_code(G);
   for (int i = 0; i < kNumGroupSequences; ++i)
     if (kGroupSequences[i] == c) return true;
@@ -25,7 +26,7 @@ bool group_sequence_specialised(const GroupParams& G, int dtype, bool virt_in) {
 cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s) {
   const bool v = G.in == nullptr;
   if (dtype == OWQS_C64) {
-    if (!v) {
+    if (!v || G.m <= 2) {
       const uint32_t code = group_sequence_code(G);
       for (int i = 0; i < kNumGroupSequences; ++i) {
         if (kGroupSequences[i] != code) continue;

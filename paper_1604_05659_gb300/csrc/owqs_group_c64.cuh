@@ -227,8 +227,11 @@ __global__ void __launch_bounds__(kBlock, M == 4 ? 1 : 2) k_group(const GroupPar
   }
   const float fprev = (float)cprev;
   // no input array: every input amplitude is vconst (the virtual |+> input);
-  // the ring then carries no data and only paces the loop
-  constexpr bool virt = VIRT;
+  // the ring then carries no data and only paces the loop.  Sequence kernels
+  // on at most 2 register qubits (VIRT = false) also see it at run time, for
+  // the first group of a run from |+> inputs (on larger registers the run-
+  // time test measured slower for the groups that read an array).
+  const bool virt = VIRT || (M <= 2 && ((SEQ >> 24) & 15u) != 0 && G.in == nullptr);
   const float vc = (float)G.vconst;
   const uint64_t tiles = 1ull << (G.nfree - LT);
   const uint64_t gw = (uint64_t)blockIdx.x * NWARP + warp;

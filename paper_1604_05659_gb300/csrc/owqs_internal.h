@@ -315,8 +315,8 @@ cudaError_t launch_group(const GroupParams& G, int dtype, cudaStream_t s);
 // complex128 group in double-float arithmetic (owqs_group_df.cu)
 cudaError_t launch_group_df(const GroupParams& G, bool in_df, bool out_df, cudaStream_t s);
 // the group's register-slot sequence (bit 31 half, bits 28-30 m, 24-27 k, 2j
-// and 2j+1 the slot of pass j), and whether a kernel compiled for it exists
-// (complex64, materialised input)
+// and 2j+1 the slot of pass j), and whether a kernel compiled for it runs it
+// (complex64; from the virtual |+> input only on registers of at most 2 qubits)
 uint32_t group_sequence_code(const GroupParams& G);
 bool group_sequence_specialised(const GroupParams& G, int dtype, bool virt_in);
 int group_enabled();  // OWQS_GROUP=0 turns group fusion off

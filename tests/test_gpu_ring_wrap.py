@@ -7,7 +7,8 @@ once its data has been read, with mbarrier phases that flip on each round.
 At full size every warp loops; in small parity cases the grid covers every
 tile at once and no stage is reused.  Here the grid is capped (a test hook)
 to one to three blocks, so that a brickwork or QFT pattern of 13-16 live
-qubits makes every warp take 4-32 tiles through its ring; and a brickwork of
+qubits makes every warp take 4-32 tiles through its ring (from |+>, the
+first group's sequence kernel paces its ring without copies); and a brickwork of
 23 live qubits runs with the full grid (at least three tiles per warp at the
 production grid), checked against the C build of the oracle.  Both
 precisions, |+> and random inputs, OWQS probabilities."""
@@ -70,6 +71,9 @@ def test_capped_grid_wraps_the_rings(env, blocks):
             for psi in (None, random_state(rng, len(p.inputs))):
                 if psi is None and p.name.startswith("qft"):
                     continue
+                if psi is None:   # the first group paces its ring without copies, on its sequence kernel
+                    g0 = h.describe_groups(wl.outcomes, real_input=False)[0]
+                    assert g0["m"] == 2 and g0["specialised"], (p.name, g0)
                 ref = substate.run(op, psi, outcomes=outcomes_by_label(p, wl.outcomes))
                 for dtype in ("c128", "c64"):
                     _check(env, wl, psi, dtype, ref, {"group_pass"})

@@ -128,9 +128,9 @@ def test_group_slot_sequences_and_compiled_kernels(owqs):
     """owqs_describe_groups lists the same groups as owqs_describe_launches,
     with valid register-slot sequences (k <= 12 passes, slots below m, the
     first pass on slot 0, a new slot only after every lower one); all but at
-    most two of the brickwork's groups that read an array run on kernels
-    compiled for their sequence, complex128 and virtual-input groups never
-    do."""
+    most two of the brickwork's groups run on kernels compiled for their
+    sequence, the first one from the virtual |+> input included (a 2-qubit
+    register); complex128 groups never do."""
     wl = workloads.brickwork(28, 40)
     h = owqs.load(wl.pattern)
     h.reorder()
@@ -144,9 +144,9 @@ def test_group_slot_sequences_and_compiled_kernels(owqs):
             assert all(s < g["m"] for s in sl) and max(sl) == g["m"] - 1
             for j, s in enumerate(sl):
                 assert s <= max(sl[:j], default=-1) + 1
-            if not real and i == 0:
-                assert not g["specialised"]   # the virtual input: the run-time-slot kernel
-        spec = [g["specialised"] for i, g in enumerate(gs) if real or i > 0]
+            if not real and i == 0:   # the virtual input, on the sequence kernel of a 2-qubit register
+                assert g["m"] == 2 and g["specialised"], g
+        spec = [g["specialised"] for g in gs]
         assert sum(spec) >= len(spec) - 2, spec
         assert not any(g["specialised"] for g in h.describe_groups(wl.outcomes, dtype="c128", real_input=real))
 
