@@ -22,7 +22,7 @@ namespace owqs {
 // dispatches on them per pass.  Bit 30: every probability of the group is
 // exactly 1/2 and only the last pass's norm is summed.
 template <int M, bool VIRT, uint32_t SEQ = 0>
-__global__ void __launch_bounds__(kBlock, M == 4 ? 1 : 2) k_group(const GroupParams G);
+__global__ void __launch_bounds__(kBlock, M == 4 ? 1 : 2) k_group(const __grid_constant__ GroupParams G);
 
 template <int M, bool VIRT, bool NORM>
 __global__ void __launch_bounds__(kBlock, 2) k_group64(const GroupParams G);
@@ -199,7 +199,7 @@ __device__ __forceinline__ void group_pass2(float2 (&x)[2][1 << M], const GroupP
 }
 
 template <int M, bool VIRT, uint32_t SEQ>
-__global__ void __launch_bounds__(kBlock, M == 4 ? 1 : 2) k_group(const GroupParams G) {
+__global__ void __launch_bounds__(kBlock, M == 4 ? 1 : 2) k_group(const __grid_constant__ GroupParams G) {
   if (G.stall_limit > 0) {
     stall_and_give_up(G.stall_limit, G.errflag);
     return;
@@ -400,27 +400,54 @@ __global__ void __launch_bounds__(kBlock, M == 4 ? 1 : 2) k_group(const GroupPar
         }
       }
       const uint32_t b0 = sw ^ lowbits[2 * it], b1 = sw ^ lowbits[2 * it + 1];
-#pragma unroll
-      for (int j = 0; j < kGroupMax; ++j) {
-        if (j >= k) break;
-        const GroupPass& P = G.pass[j];
-        const uint32_t r0 = (b0 << (31 - j)) & 0x80000000u, r1 = (b1 << (31 - j)) & 0x80000000u;
-        // a compile-time slot leaves one code variant per pass
-        const int slot = STATIC ? (int)((SEQ >> (2 * j)) & 3u) : P.slot;
-        float2 acc = make_float2(0.f, 0.f);
-        if (NORM || j == k - 1) {
-          if (M == 1 || slot == 0) group_pass2<M, 0, true>(x, P, r0, r1, acc);
-          else if (M == 2 || slot == 1) group_pass2<M, (M > 1 ? 1 : 0), true>(x, P, r0, r1, acc);
-          else if (M == 3 || slot == 2) group_pass2<M, (M > 2 ? 2 : 0), true>(x, P, r0, r1, acc);
-          else group_pass2<M, (M > 3 ? 3 : 0), true>(x, P, r0, r1, acc);
-        } else {
-          if (M == 1 || slot == 0) group_pass2<M, 0, false>(x, P, r0, r1, acc);
-          else if (M == 2 || slot == 1) group_pass2<M, (M > 1 ? 1 : 0), false>(x, P, r0, r1, acc);
-          else if (M == 3 || slot == 2) group_pass2<M, (M > 2 ? 2 : 0), false>(x, P, r0, r1, acc);
-          else group_pass2<M, (M > 3 ? 3 : 0), false>(x, P, r0, r1, acc);
+      if constexpr (!STATIC && !NORM) {
+        // run-time slots: one rolled loop over the passes, with eight code
+        // variants (four slots, with and without the last pass's norm)
+        // instead of twelve unrolled copies of them, which overflowed the
+        // instruction cache; the pass constants are read from the
+        // grid-constant parameter at the pass index
+#pragma unroll 1
+        for (int j = 0; j < k; ++j) {
+          const GroupPass& P = G.pass[j];
+          const uint32_t r0 = (b0 << (31 - j)) & 0x80000000u, r1 = (b1 << (31 - j)) & 0x80000000u;
+          const int slot = P.slot;
+          float2 acc = make_float2(0.f, 0.f);
+          if (j == k - 1) {
+            if (M == 1 || slot == 0) group_pass2<M, 0, true>(x, P, r0, r1, acc);
+            else if (M == 2 || slot == 1) group_pass2<M, (M > 1 ? 1 : 0), true>(x, P, r0, r1, acc);
+            else if (M == 3 || slot == 2) group_pass2<M, (M > 2 ? 2 : 0), true>(x, P, r0, r1, acc);
+            else group_pass2<M, (M > 3 ? 3 : 0), true>(x, P, r0, r1, acc);
+            hs += acc.x + acc.y;
+          } else {
+            if (M == 1 || slot == 0) group_pass2<M, 0, false>(x, P, r0, r1, acc);
+            else if (M == 2 || slot == 1) group_pass2<M, (M > 1 ? 1 : 0), false>(x, P, r0, r1, acc);
+            else if (M == 3 || slot == 2) group_pass2<M, (M > 2 ? 2 : 0), false>(x, P, r0, r1, acc);
+            else group_pass2<M, (M > 3 ? 3 : 0), false>(x, P, r0, r1, acc);
+          }
         }
-        if (NORM) s[j] += acc.x + acc.y;
-        else if (j == k - 1) hs += acc.x + acc.y;
+      } else {
+#pragma unroll
+        for (int j = 0; j < kGroupMax; ++j) {
+          if (j >= k) break;
+          const GroupPass& P = G.pass[j];
+          const uint32_t r0 = (b0 << (31 - j)) & 0x80000000u, r1 = (b1 << (31 - j)) & 0x80000000u;
+          // a compile-time slot leaves one code variant per pass
+          const int slot = STATIC ? (int)((SEQ >> (2 * j)) & 3u) : P.slot;
+          float2 acc = make_float2(0.f, 0.f);
+          if (NORM || j == k - 1) {
+            if (M == 1 || slot == 0) group_pass2<M, 0, true>(x, P, r0, r1, acc);
+            else if (M == 2 || slot == 1) group_pass2<M, (M > 1 ? 1 : 0), true>(x, P, r0, r1, acc);
+            else if (M == 3 || slot == 2) group_pass2<M, (M > 2 ? 2 : 0), true>(x, P, r0, r1, acc);
+            else group_pass2<M, (M > 3 ? 3 : 0), true>(x, P, r0, r1, acc);
+          } else {
+            if (M == 1 || slot == 0) group_pass2<M, 0, false>(x, P, r0, r1, acc);
+            else if (M == 2 || slot == 1) group_pass2<M, (M > 1 ? 1 : 0), false>(x, P, r0, r1, acc);
+            else if (M == 3 || slot == 2) group_pass2<M, (M > 2 ? 2 : 0), false>(x, P, r0, r1, acc);
+            else group_pass2<M, (M > 3 ? 3 : 0), false>(x, P, r0, r1, acc);
+          }
+          if (NORM) s[j] += acc.x + acc.y;
+          else if (j == k - 1) hs += acc.x + acc.y;
+        }
       }
       const float f0 = __uint_as_float(__float_as_uint(fprev) ^ (b0 & 0x80000000u));
       const float f1 = __uint_as_float(__float_as_uint(fprev) ^ (b1 & 0x80000000u));

@@ -218,6 +218,179 @@ __global__ void __launch_bounds__(kBlock) k_final(const PassParams P) {
   }
 }
 
+// Final pass whose output order moves the low array bits away from the low
+// output bits (perm maps {0..4} elsewhere), so that consecutive outputs are
+// far apart in the array and the loads of k_final would not coalesce.  A
+// tile is every setting of the output bits T (2^10 outputs): {0..4}, the
+// preimage of the array bits {0..4}, and the next output bits up to ten;
+// the other ("free") output bits are fixed: the block reads the tile in array order (the array's low five
+// bits innermost: 256-byte runs), applies the X mask and the sign, and
+// writes it, scaled, in output order (the output's low five bits innermost)
+// through shared memory.  The shared-memory slot of a tile element is its
+// output-order index with the bits above the fifth XORed into the low five
+// (swizzle), so that the 32 lanes of either phase hit 32 different slots
+// modulo 32.  The sign of an index k = k0 | kt (k0: the free bits, fixed per
+// tile; kt: the tile's bits) splits, since c0 + z.k + sum_e k_u(e) (a_e.k)
+// is a quadratic form over GF(2), into a per-tile part, a per-element table
+// bit and the parity of kt against a per-tile mask.  Requires n_in == n_out
+// and perm a permutation of 0..n_out-1 (checked by the launcher).
+constexpr int kFinalTileMax = 10;
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_final_tiled(const PassParams P) {
+  using V = typename Cplx<T>::V;
+  constexpr int TM = 1 << kFinalTileMax;
+  __shared__ V tile[TM];
+  __shared__ uint64_t kt[TM];      // read element e: its array bits within T
+  __shared__ uint64_t jw[TM];      // write element f: its output bits within T
+  __shared__ uint16_t fidx[TM];    // read element e: its shared-memory slot; bit 15: its sign within T
+  __shared__ uint16_t waddr[TM];   // write element f: its shared-memory slot
+  __shared__ uint8_t fbit[64], fperm[64];  // the free output bits and their array bits
+  __shared__ int rbit[kFinalTileMax], wbit[kFinalTileMax], swz[32];
+  __shared__ int tsh, nfsh;
+  const V* __restrict__ in = reinterpret_cast<const V*>(P.in);
+  V* __restrict__ out = reinterpret_cast<V*>(P.out);
+  const int n = P.n_out;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    int pinv[64];
+    for (int i = 0; i < n; ++i) pinv[P.perm[i]] = i;
+    uint64_t o2 = 0;  // the output bits of the array's low five bits
+    for (int a = 0; a < 5; ++a) o2 |= 1ull << pinv[a];
+    // T: the output's low five bits, o2, and the next output bits up to
+    // kFinalTileMax bits (longer output runs, fewer tiles)
+    uint64_t tm = 0x1full | o2;
+    for (int i = 5; i < n && __popcll(tm) < kFinalTileMax; ++i) tm |= 1ull << i;
+    int t = 0;
+    for (int a = 0; a < 5; ++a) rbit[t++] = pinv[a];  // read order: the array's low bits first
+    for (int i = 0; i < n; ++i)
+      if (((tm >> i) & 1ull) && !((o2 >> i) & 1ull)) rbit[t++] = i;
+    int u = 0, used = 0;
+    for (int i = 0; i < n; ++i)  // write order: the output's low bits first
+      if ((tm >> i) & 1ull) wbit[u++] = i;
+    for (int a = 0; a < 5; ++a)
+      if (pinv[a] < 5) used |= 1 << pinv[a];
+    // the write positions 5 + q that hold an array-low bit are XORed into
+    // the low positions that no array-low bit takes, one each
+    int map[kFinalTileMax - 5], nxt = 0;
+    for (int q = 0; q < t - 5; ++q) {
+      map[q] = -1;
+      if ((o2 >> wbit[5 + q]) & 1ull) {
+        while ((used >> nxt) & 1) ++nxt;
+        map[q] = nxt++;
+      }
+    }
+    for (int h = 0; h < 32; ++h) {
+      int x = 0;
+      for (int q = 0; q < t - 5; ++q)
+        if (((h >> q) & 1) && map[q] >= 0) x |= 1 << map[q];
+      swz[h] = x;
+    }
+    int nf = 0;
+    for (int i = 0; i < n; ++i)
+      if (!((tm >> i) & 1ull)) {
+        fbit[nf] = (uint8_t)i;
+        fperm[nf] = (uint8_t)P.perm[i];
+        ++nf;
+      }
+    tsh = t;
+    nfsh = nf;
+  }
+  __syncthreads();
+  const int t = tsh, nf = nfsh;
+  for (int e = threadIdx.x; e < (1 << t); e += blockDim.x) {
+    uint64_t jr = 0, k = 0, jf = 0;
+    for (int r = 0; r < t; ++r)
+      if ((e >> r) & 1) {
+        jr |= 1ull << rbit[r];
+        k |= 1ull << P.perm[rbit[r]];
+        jf |= 1ull << wbit[r];
+      }
+    uint32_t f = 0;
+    for (int r = 0; r < t; ++r) f |= (uint32_t)((jr >> wbit[r]) & 1ull) << r;
+    kt[e] = k;
+    fidx[e] = (uint16_t)((f ^ (uint32_t)swz[f >> 5]) | ((qsign(P, k) ^ (P.c0 & 1u)) << 15));
+    jw[e] = jf;
+    waddr[e] = (uint16_t)(e ^ swz[e >> 5]);
+  }
+  const T sc = (T)(P.scale * prev_scale(P));
+  const uint64_t inmask = (1ull << P.n_in) - 1ull;
+  const uint64_t ntiles = 1ull << (n - t);
+  double acc = 0.0;
+  for (uint64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
+    // the tile's free bits: lane q deposits bits q and q + 32 of tau
+    uint32_t jl = 0, jh = 0, kl = 0, kh = 0;
+    for (int q = lane; q < nf; q += 32)
+      if ((tau >> q) & 1ull) {
+        if (fbit[q] < 32) jl |= 1u << fbit[q];
+        else jh |= 1u << (fbit[q] - 32);
+        if (fperm[q] < 32) kl |= 1u << fperm[q];
+        else kh |= 1u << (fperm[q] - 32);
+      }
+    const uint64_t j0 = (uint64_t)__reduce_or_sync(0xffffffffu, jl) |
+                        ((uint64_t)__reduce_or_sync(0xffffffffu, jh) << 32);
+    const uint64_t k0 = (uint64_t)__reduce_or_sync(0xffffffffu, kl) |
+                        ((uint64_t)__reduce_or_sync(0xffffffffu, kh) << 32);
+    // the fixed part of the sign and the mask that couples it to the tile's bits
+    uint32_t qb = 0;
+    uint64_t mm = 0;
+    for (int e = lane; e < P.nq; e += 32) {
+      const uint32_t ub = (uint32_t)((k0 >> P.qu[e]) & 1ull), pa = par64(k0 & P.qa[e]);
+      qb ^= ub & pa;
+      if (ub) mm ^= P.qa[e];
+      if (pa) mm ^= 1ull << P.qu[e];
+    }
+    const uint32_t s0 = (P.c0 ^ par64(k0 & P.zmask) ^ (uint32_t)__reduce_add_sync(0xffffffffu, qb)) & 1u;
+    uint32_t ml = (uint32_t)mm, mh = (uint32_t)(mm >> 32);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ml ^= __shfl_xor_sync(0xffffffffu, ml, o);
+      mh ^= __shfl_xor_sync(0xffffffffu, mh, o);
+    }
+    mm = ((uint64_t)mh << 32) | ml;
+    __syncthreads();  // the tables are written, and the previous tile is read out
+    for (int e = threadIdx.x; e < (1 << t); e += blockDim.x) {
+      const uint64_t kx = kt[e];
+      const uint64_t i = ((k0 | kx) ^ P.xmask) & inmask;
+      V x;
+      x.x = x.y = (T)0;
+      if (in_extent(i, 1, P.in_cap, P.errflag)) x = in[i];
+      const uint32_t fi = fidx[e];
+      if ((s0 ^ (fi >> 15) ^ par64(kx & mm)) & 1u) x.x = -x.x, x.y = -x.y;
+      tile[fi & 0x7fffu] = x;
+    }
+    __syncthreads();
+    T part = (T)0;
+    for (int f = threadIdx.x; f < (1 << t); f += blockDim.x) {
+      const uint64_t j = j0 | jw[f];
+      V y = tile[waddr[f]];
+      y.x = sc * y.x;
+      y.y = sc * y.y;
+      if (in_extent(j, 1, P.out_cap, P.errflag)) out[j] = y;
+      part += y.x * y.x + y.y * y.y;
+    }
+    acc += (double)part;
+  }
+  if (P.norm_out >= 0) {
+    const double a1[1] = {acc};
+    reduce_to_slots<1>(a1, P.partials, P.counter, P.norms, P.norm_out);
+  }
+}
+
+// whether the final pass takes k_final_tiled: an output order that moves the
+// low five array bits away from the low five output bits, on an array of at
+// least 2^11 amplitudes whose width the pass keeps
+static bool final_needs_tiles(const PassParams& P) {
+  if (P.identity_perm || P.n_out < kFinalTileMax + 1 || P.n_in != P.n_out || P.n_out > 62) return false;
+  uint64_t seen = 0;
+  for (int i = 0; i < P.n_out; ++i) {
+    if (P.perm[i] < 0 || P.perm[i] >= P.n_out || ((seen >> P.perm[i]) & 1ull)) return false;
+    seen |= 1ull << P.perm[i];
+  }
+  for (int i = 0; i < 5; ++i)
+    if (P.perm[i] >= 5) return true;
+  return false;
+}
+
 // ---------------------------------------------------------------------------
 // A whole run of a small pattern in one warp (every array of the run at most
 // 2^kSmallLog amplitudes and at most kSmallMaxPasses passes, where one launch
@@ -762,7 +935,10 @@ static cudaError_t launch_t(const PassParams& P, const LaunchPlan& L, cudaStream
       else go(k_generic<T, 1, 0>, P, L.grid, s);
       break;
     case KK_FINAL:
-      if (!virt) go(k_final<T>, P, L.grid, s);
+      if (!virt) {
+        if (final_needs_tiles(P)) go(k_final_tiled<T>, P, L.grid, s);
+        else go(k_final<T>, P, L.grid, s);
+      }
       else if (P.vdiag) go(k_generic<T, 2, 2>, P, L.grid, s);
       else go(k_generic<T, 2, 1>, P, L.grid, s);
       break;
