@@ -50,10 +50,10 @@ FALLBACK_HBM_GBS = 6800.0
 # c64, the mean over all 105 group launches of one run (k_group on 2-, 3- and
 # 4-qubit registers, 2^28 complex64 amplitudes in and out, the first one
 # reading the virtual input; 2127.2 MB read + 2094.4 MB written), and c128,
-# the mean of three k_group64<3, 0, 0> launches (2^28 complex128; 4297.9 MB
-# read + 4247.1 MB written).  profiles/k_group_c64_brickwork28x40_dram.md.
-NCU_TRAFFIC = {("c12cc41d73f4be1e", "c64"): (223356318720 + 219913363968) / 105.0,
-               ("c12cc41d73f4be1e", "c128"): (12893628416 + 12741225728) / 3.0}
+# the mean of three k_group64<3, 0, 0> launches (2^28 complex128; 4298.3 MB
+# read + 4246.9 MB written).  profiles/k_group_c64_brickwork28x40_dram.md.
+NCU_TRAFFIC = {("a714f94049bbd882", "c64"): (223356161792 + 219915724544) / 105.0,
+               ("a714f94049bbd882", "c128"): (12894790144 + 12740737536) / 3.0}
 # nominal GB300 FP64 rate (no measured FP64 peak exists for this machine)
 FP64_PEAK_TFLOPS = 1.25
 # FP64 flops per output amplitude of the complex128 pass: complex multiply-add
