@@ -21,6 +21,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -46,14 +47,14 @@ def workload_name(rows: int, cols: int) -> str:
 FALLBACK_HBM_GBS = 6800.0
 # ncu DRAM bytes (read + write) per launch of the dominant kernel, keyed by the
 # sha256 prefix of the pass-group sources they were measured on (a changed
-# kernel reports null).  Both are pass groups on the full brickwork workload:
+# kernel reports null; comments do not count).  Both are pass groups on the full brickwork workload:
 # c64, the mean over all 105 group launches of one run (k_group on 2-, 3- and
 # 4-qubit registers, 2^28 complex64 amplitudes in and out, the first one
 # reading the virtual input; 2127.2 MB read + 2094.4 MB written), and c128,
 # the mean of three k_group64<3, 0, 0> launches (2^28 complex128; 4298.3 MB
 # read + 4246.9 MB written).  profiles/k_group_c64_brickwork28x40_dram.md.
-NCU_TRAFFIC = {("a714f94049bbd882", "c64"): (223356161792 + 219915724544) / 105.0,
-               ("a714f94049bbd882", "c128"): (12894790144 + 12740737536) / 3.0}
+NCU_TRAFFIC = {("c92668ad8a6f4fb2", "c64"): (223356161792 + 219915724544) / 105.0,
+               ("c92668ad8a6f4fb2", "c128"): (12894790144 + 12740737536) / 3.0}
 # nominal GB300 FP64 rate (no measured FP64 peak exists for this machine)
 FP64_PEAK_TFLOPS = 1.25
 # FP64 flops per output amplitude of the complex128 pass: complex multiply-add
@@ -169,13 +170,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def kernel_code(text: str) -> str:
+    """C++/CUDA source without its comments and with whitespace collapsed:
+    what the compiler sees, so that editing a comment keeps the key."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash():
-    """sha256 prefix of the pass-group sources (the dominant kernels)."""
+    """sha256 prefix of the code of the pass-group sources (the dominant
+    kernels), comments and whitespace left out."""
     h = hashlib.sha256()
     for name in ("owqs_group.cu", "owqs_group_c64.cuh", "owqs_group_seq.cu", "owqs_device.cuh",
                  "owqs_group_sequences.inc"):
-        with open(os.path.join(ROOT, "paper_1604_05659_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1604_05659_gb300", "csrc", name), encoding="utf-8") as f:
+            h.update(kernel_code(f.read()).encode())
     return h.hexdigest()[:16]
 
 

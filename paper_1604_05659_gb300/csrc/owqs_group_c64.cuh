@@ -19,8 +19,9 @@ namespace owqs {
 // 24-27 nonzero: the group's register-slot sequence fixed at compile time
 // (bits 24-27 the number of passes k, bits 2j and 2j+1 the slot pass j
 // measures); zero: the kernel reads the slots from the parameter block and
-// dispatches on them per pass.  Bit 30: every probability of the group is
-// exactly 1/2 and only the last pass's norm is summed.
+// dispatches on them per pass.  Bit 31: every probability of the group is
+// exactly 1/2 and only the last pass's norm is summed (the slot-dispatching
+// kernel of such groups runs its passes in a rolled loop).
 template <int M, bool VIRT, uint32_t SEQ = 0>
 __global__ void __launch_bounds__(kBlock, M == 4 ? 1 : 2) k_group(const __grid_constant__ GroupParams G);
 
@@ -64,17 +65,16 @@ static cudaError_t launch_group_t(void (*kern)(const GroupParams), const GroupPa
   return cudaGetLastError();
 }
 
-// Register-slot sequences with a compile-time kernel (complex64, read from a
-// materialised input).  A pass's slot is the register position of the qubit
-// it measures; the runtime-dispatched kernel chooses one of M code variants
-// per pass, and the register values must then agree at the join of the
-// variants, which costs moves on every pass and, with twelve passes times
-// three variants unrolled, instruction-cache misses.  A kernel whose slots
-// are constants has one variant per pass.  The table holds the sequences
-// that carry the most work (measurements x 2^width) in brickwork and
-// QFT-shaped J/CZ patterns, whose J(alpha) chains measure a qubit and then
-// its flow successor in the same slot (gen_group_sequences.py rebuilds it);
-// any other sequence runs on the dispatching kernel.
+// Register-slot sequences with a compile-time kernel (complex64, from an
+// input array; on 2-qubit registers also from the virtual |+> input).  A
+// pass's slot is the register position of the qubit it measures; the
+// runtime-dispatched kernel chooses one of M code variants per pass, and the
+// register values must then agree at the join of the variants, which costs
+// moves on every pass.  A kernel whose slots are constants has one variant
+// per pass.  The table holds the sequences that carry the most work
+// (measurements x 2^width) in brickwork, QFT-shaped and random J/CZ patterns
+// and the recognition set's wide unitaries (gen_group_sequences.py rebuilds
+// it); any other sequence runs on the dispatching kernel.
 // Code: bit 31 exact-half, bits 28-30 M, bits 24-27 k, bits 2j and 2j+1 the slot of pass j.
 constexpr uint32_t kGroupSequences[] = {
 #include "owqs_group_sequences.inc"
@@ -92,10 +92,10 @@ cudaError_t launch_group_seq_slice(const GroupParams& G, uint32_t code, cudaStre
 // free index the group is arithmetic on an M-qubit register (the contract,
 // including how the signs and scales are carried, is in owqs_internal.h).
 // Pipelines are warp-private: a warp's tile is 2^(9-M) consecutive free
-// indices, whose 2^M input runs (one per configuration of the register's
-// input qubits) arrive by bulk copies into the warp's own 3-stage ring of
-// 4 KB stages.  The warp refills a stage as soon as its own lanes have read
-// it, so no warp ever waits for another.
+// indices (2^6 with M = 4), whose 2^M input configurations arrive as nruns
+// contiguous runs by bulk copies into the warp's own 3-stage ring of 4 KB
+// stages (8 KB with M = 4).  The warp refills a stage as soon as its own
+// lanes have read it, so no warp ever waits for another.
 // Each lane takes two consecutive elements at a time and holds their 2^M
 // amplitudes in registers.  Per pass and element: one sign bit XORed into w;
 // per butterfly: one complex product and, per output, two FP32 multiply-adds
