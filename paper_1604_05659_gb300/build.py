@@ -3,7 +3,7 @@
 Host C++ goes through g++, the kernels through nvcc with
 -gencode arch=compute_103a,code=sm_103a; the objects are linked into one
 shared library with the CUDA runtime linked statically, so the library has
-no dependency beyond the driver.  Objects go to _build/ next to this file.
+no dependency beyond the CUDA driver (libcuda).  Objects go to _build/ next to this file.
 
 build(bounds_check=True) makes the debug library libowqs_checked.so
 (objects in _build_checked/): the kernels compiled with OWQS_BOUNDS_CHECK,
