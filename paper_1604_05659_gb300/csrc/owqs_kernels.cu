@@ -235,13 +235,17 @@ __global__ void __launch_bounds__(kBlock) k_final(const PassParams P) {
 // bit and the parity of kt against a per-tile mask.  Requires n_in == n_out
 // and perm a permutation of 0..n_out-1 (checked by the launcher).
 constexpr int kFinalTileMax = 10;
-template <typename T>
+__device__ __forceinline__ uint32_t par_idx(uint32_t v) { return (uint32_t)__popc(v) & 1u; }
+__device__ __forceinline__ uint32_t par_idx(uint64_t v) { return par64(v); }
+// I: the index type, uint32_t when the array has at most 2^31 amplitudes
+// (half the integer work of 64-bit indices), else uint64_t
+template <typename T, typename I>
 __global__ void __launch_bounds__(kBlock) k_final_tiled(const PassParams P) {
   using V = typename Cplx<T>::V;
   constexpr int TM = 1 << kFinalTileMax;
   __shared__ V tile[TM];
-  __shared__ uint64_t kt[TM];      // read element e: its array bits within T
-  __shared__ uint64_t jw[TM];      // write element f: its output bits within T
+  __shared__ I kt[TM];             // read element e: its array bits within T
+  __shared__ I jw[TM];             // write element f: its output bits within T
   __shared__ uint16_t fidx[TM];    // read element e: its shared-memory slot; bit 15: its sign within T
   __shared__ uint16_t waddr[TM];   // write element f: its shared-memory slot
   __shared__ uint8_t fbit[64], fperm[64];  // the free output bits and their array bits
@@ -307,17 +311,24 @@ __global__ void __launch_bounds__(kBlock) k_final_tiled(const PassParams P) {
       }
     uint32_t f = 0;
     for (int r = 0; r < t; ++r) f |= (uint32_t)((jr >> wbit[r]) & 1ull) << r;
-    kt[e] = k;
+    kt[e] = (I)k;
     fidx[e] = (uint16_t)((f ^ (uint32_t)swz[f >> 5]) | ((qsign(P, k) ^ (P.c0 & 1u)) << 15));
-    jw[e] = jf;
+    jw[e] = (I)jf;
     waddr[e] = (uint16_t)(e ^ swz[e >> 5]);
   }
   const T sc = (T)(P.scale * prev_scale(P));
-  const uint64_t inmask = (1ull << P.n_in) - 1ull;
+  const I inmask = (I)((1ull << P.n_in) - 1ull), xmask = (I)P.xmask;
   const uint64_t ntiles = 1ull << (n - t);
-  double acc = 0.0;
-  for (uint64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
-    // the tile's free bits: lane q deposits bits q and q + 32 of tau
+  constexpr int EPT = TM / kBlock;  // elements of a tile per thread and phase (t == kFinalTileMax)
+  static_assert(EPT * kBlock == TM, "whole tiles per block");
+  // per tile: the free output bits j0 and their array bits k0 (lane q
+  // deposits bits q and q + 32 of tau), the fixed part s0 of the sign and
+  // the mask mm that couples the tile's bits to it
+  struct Fix {
+    I j0, k0, mm;
+    uint32_t s0;
+  };
+  auto fix = [&](uint64_t tau) {
     uint32_t jl = 0, jh = 0, kl = 0, kh = 0;
     for (int q = lane; q < nf; q += 32)
       if ((tau >> q) & 1ull) {
@@ -330,7 +341,6 @@ __global__ void __launch_bounds__(kBlock) k_final_tiled(const PassParams P) {
                         ((uint64_t)__reduce_or_sync(0xffffffffu, jh) << 32);
     const uint64_t k0 = (uint64_t)__reduce_or_sync(0xffffffffu, kl) |
                         ((uint64_t)__reduce_or_sync(0xffffffffu, kh) << 32);
-    // the fixed part of the sign and the mask that couples it to the tile's bits
     uint32_t qb = 0;
     uint64_t mm = 0;
     for (int e = lane; e < P.nq; e += 32) {
@@ -339,36 +349,70 @@ __global__ void __launch_bounds__(kBlock) k_final_tiled(const PassParams P) {
       if (ub) mm ^= P.qa[e];
       if (pa) mm ^= 1ull << P.qu[e];
     }
-    const uint32_t s0 = (P.c0 ^ par64(k0 & P.zmask) ^ (uint32_t)__reduce_add_sync(0xffffffffu, qb)) & 1u;
     uint32_t ml = (uint32_t)mm, mh = (uint32_t)(mm >> 32);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       ml ^= __shfl_xor_sync(0xffffffffu, ml, o);
       mh ^= __shfl_xor_sync(0xffffffffu, mh, o);
     }
-    mm = ((uint64_t)mh << 32) | ml;
-    __syncthreads();  // the tables are written, and the previous tile is read out
-    for (int e = threadIdx.x; e < (1 << t); e += blockDim.x) {
-      const uint64_t kx = kt[e];
-      const uint64_t i = ((k0 | kx) ^ P.xmask) & inmask;
-      V x;
-      x.x = x.y = (T)0;
-      if (in_extent(i, 1, P.in_cap, P.errflag)) x = in[i];
-      const uint32_t fi = fidx[e];
-      if ((s0 ^ (fi >> 15) ^ par64(kx & mm)) & 1u) x.x = -x.x, x.y = -x.y;
-      tile[fi & 0x7fffu] = x;
+    Fix F;
+    F.j0 = (I)j0;
+    F.k0 = (I)k0;
+    F.mm = (I)(((uint64_t)mh << 32) | ml);
+    F.s0 = (P.c0 ^ par64(k0 & P.zmask) ^ (uint32_t)__reduce_add_sync(0xffffffffu, qb)) & 1u;
+    return F;
+  };
+  // the loads of a tile, into registers
+  auto load = [&](const Fix& F, V (&r)[EPT]) {
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int e = (int)threadIdx.x + u * kBlock;
+      const I i = ((F.k0 | kt[e]) ^ xmask) & inmask;
+      r[u].x = r[u].y = (T)0;
+      if (in_extent((uint64_t)i, 1, P.in_cap, P.errflag)) r[u] = in[i];
     }
-    __syncthreads();
-    T part = (T)0;
-    for (int f = threadIdx.x; f < (1 << t); f += blockDim.x) {
-      const uint64_t j = j0 | jw[f];
-      V y = tile[waddr[f]];
-      y.x = sc * y.x;
-      y.y = sc * y.y;
-      if (in_extent(j, 1, P.out_cap, P.errflag)) out[j] = y;
-      part += y.x * y.x + y.y * y.y;
+  };
+  double acc = 0.0;
+  uint64_t tau = blockIdx.x;
+  __syncthreads();  // the tables are written
+  if (tau < ntiles) {
+    Fix cur = fix(tau);
+    V r[EPT];
+    load(cur, r);
+    for (;;) {
+      const uint64_t nxt = tau + gridDim.x;
+      __syncthreads();  // the previous tile's slots are read out
+#pragma unroll
+      for (int u = 0; u < EPT; ++u) {
+        const int e = (int)threadIdx.x + u * kBlock;
+        const uint32_t fi = fidx[e];
+        V x = r[u];
+        if ((cur.s0 ^ (fi >> 15) ^ par_idx((I)(kt[e] & cur.mm))) & 1u) x.x = -x.x, x.y = -x.y;
+        tile[fi & 0x7fffu] = x;
+      }
+      // the next tile's loads are in flight while this one is written out
+      Fix nx = cur;
+      if (nxt < ntiles) {
+        nx = fix(nxt);
+        load(nx, r);
+      }
+      __syncthreads();
+      T part = (T)0;
+#pragma unroll
+      for (int u = 0; u < EPT; ++u) {
+        const int f = (int)threadIdx.x + u * kBlock;
+        const I j = cur.j0 | jw[f];
+        V y = tile[waddr[f]];
+        y.x = sc * y.x;
+        y.y = sc * y.y;
+        if (in_extent((uint64_t)j, 1, P.out_cap, P.errflag)) out[j] = y;
+        part += y.x * y.x + y.y * y.y;
+      }
+      acc += (double)part;
+      if (nxt >= ntiles) break;
+      tau = nxt;
+      cur = nx;
     }
-    acc += (double)part;
   }
   if (P.norm_out >= 0) {
     const double a1[1] = {acc};
@@ -936,7 +980,10 @@ static cudaError_t launch_t(const PassParams& P, const LaunchPlan& L, cudaStream
       break;
     case KK_FINAL:
       if (!virt) {
-        if (final_needs_tiles(P)) go(k_final_tiled<T>, P, L.grid, s);
+        if (final_needs_tiles(P)) {
+          if (P.n_in <= 31) go(k_final_tiled<T, uint32_t>, P, L.grid, s);
+          else go(k_final_tiled<T, uint64_t>, P, L.grid, s);
+        }
         else go(k_final<T>, P, L.grid, s);
       }
       else if (P.vdiag) go(k_generic<T, 2, 2>, P, L.grid, s);
