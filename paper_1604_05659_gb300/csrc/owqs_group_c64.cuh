@@ -264,9 +264,11 @@ __global__ void __launch_bounds__(kBlock, M == 4 ? 1 : 2) k_group(const __grid_c
 
   // Copies of a tile: its 2^M configurations arrive as nruns contiguous runs.
   // Sequence kernels of 11 or more passes on at most 3 register qubits are
-  // bound by instruction issue: lane r < nruns copies run r, so that the
-  // warp spends one instruction on all of them.  The others (closer to the
-  // memory bound, where this measured slower) issue every run from lane 0.
+  // bound by instruction issue: lane r < nruns computes the addresses of run
+  // r and issues its copy, so that the warp computes every run's addresses
+  // at once instead of lane 0 one run after another.  The others (closer to
+  // the memory bound, where this measured slower) issue every run from
+  // lane 0.
   constexpr bool WARP_ISSUE = M <= 3 && ((SEQ >> 24) & 15u) >= 11;
   int wsorted[M];  // WARP_ISSUE: the register's input bits, ascending
 #pragma unroll
