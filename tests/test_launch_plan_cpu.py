@@ -215,3 +215,30 @@ def test_four_qubit_registers_from_a_width(owqs):
     hb.reorder()
     gs = hb.describe_groups(big.outcomes)
     assert sum(g["m"] == 4 for g in gs) >= 30 and len(gs) <= 106
+
+
+def test_compiled_sequences_cover_the_measured_families(owqs):
+    """The compiled register-slot sequences carry the group work (passes x
+    2^width) of the measured families: every brickwork 28x40 group, and at
+    least 60 % of the recognition set's wide unitaries (13-14 inputs, whose
+    arrays take 4-qubit registers: planned here through the test hook)."""
+    big = workloads.brickwork(28, 40)
+    h = owqs.load(big.pattern)
+    h.reorder()
+    assert all(g["specialised"] for g in h.describe_groups(big.outcomes))
+    wide = [wl for wl in workloads.random_batch(count=256, with_input=False) if len(wl.pattern.inputs) > 12]
+    assert len(wide) >= 50
+    total = covered = 0.0
+    try:
+        owqs.test_group_m4_width(10)
+        for wl in wide:
+            hw = owqs.load(wl.pattern)
+            hw.reorder()
+            for g in hw.describe_groups(wl.outcomes, real_input=True):
+                w = len(g["slots"]) * 2.0 ** g["n_in"]
+                total += w
+                covered += w if g["specialised"] else 0.0
+            hw.close()
+    finally:
+        owqs.test_group_m4_width(0)
+    assert covered >= 0.6 * total, covered / total
