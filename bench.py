@@ -773,7 +773,7 @@ def run_owqs(args):
         run_e2e = lambda: h.run_host(host_in, host_out, dtype="c64", outcomes=wl.outcomes)
         run_e2e()
         e2e_steps = args.e2e_steps or args.steps
-        # the host link of this box on the same pinned buffers: one plain copy
+        # the host link of this machine on the same pinned buffers: one plain copy
         # each way (the end-to-end call moves these bytes before its first
         # launch and after its last), before and after the end-to-end loops,
         # and the copies alone for as many steps as the loops (the host link
